@@ -1,0 +1,352 @@
+"""Pins of the oracle's partitioning and ordering (Sec. 3 and 4): exhaustive
+2-means optima, k-means++ sampling, the separator postconditions of Algorithm 7
+and its order-free equivalent, the recursive BBD/SBD structure, brute-force cut
+counts and the fill-in example."""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _x4(pts):
+    x = np.zeros((len(pts), 4), dtype=np.float32)
+    x[:, :pts.shape[1]] = pts
+    return x
+
+
+def _kmeans_cost(pts, lab):
+    c = 0.0
+    for s in (1, 2):
+        p = pts[lab == s]
+        if len(p):
+            c += ((p - p.mean(0)) ** 2).sum()
+    return c
+
+
+def _best_split(pts):
+    k = len(pts)
+    best, arg = np.inf, None
+    for mask in range(1, 2 ** (k - 1)):
+        lab = np.array([1 + ((mask >> i) & 1) for i in range(k)])
+        c = _kmeans_cost(pts, lab)
+        if c < best:
+            best, arg = c, lab
+    return best, arg
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_two_means_optimal_on_separated_clusters(oracle_mod, seed):
+    """eq. kmeans: on two well separated clusters (k <= 14) the oracle's 2-means
+    finds the exhaustive optimum."""
+    O = oracle_mod
+    rng = np.random.default_rng(seed)
+    d = 2 + seed % 3
+    k1 = rng.integers(2, 8)
+    k2 = rng.integers(2, 7)
+    pts = np.concatenate([rng.normal(0, 1, (k1, d)), rng.normal(12, 1, (k2, d))]).astype(np.float32)
+    best, lab_opt = _best_split(pts.astype(np.float64))
+    ok, lab, z1, z2 = O.bisect(d, _x4(pts), np.arange(len(pts)), seed=seed, key=1)
+    assert ok
+    same = np.array_equal(lab, lab_opt) or np.array_equal(lab, 3 - lab_opt)
+    assert same
+    assert np.isclose(_kmeans_cost(pts.astype(np.float64), lab), best, rtol=1e-6)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_two_means_lloyd_fixed_point_and_bound(oracle_mod, seed):
+    """On arbitrary points: the result is never better than the exhaustive
+    optimum, its labels are nearest-centre labels of its centres, and (when
+    converged) the centres are the means of their clusters."""
+    O = oracle_mod
+    rng = np.random.default_rng(100 + seed)
+    d = 2 + seed % 3
+    pts = rng.uniform(0, 10, (12, d)).astype(np.float32)
+    best, _ = _best_split(pts.astype(np.float64))
+    ok, lab, z1, z2 = O.bisect(d, _x4(pts), np.arange(12), seed=seed, key=1, km_iters=50)
+    assert ok
+    assert _kmeans_cost(pts.astype(np.float64), lab) >= best * (1 - 1e-9)
+    d1 = ((pts - z1[:d]) ** 2).sum(1)
+    d2 = ((pts - z2[:d]) ** 2).sum(1)
+    assert np.array_equal(lab == 1, d1 <= d2)
+    assert np.allclose(z1[:d], pts[lab == 1].mean(0), atol=1e-5)
+    assert np.allclose(z2[:d], pts[lab == 2].mean(0), atol=1e-5)
+
+
+def test_two_means_collinear_matches_sorted_scan(oracle_mod):
+    """1-D inputs: the optimal 2-split is a threshold in sorted order."""
+    O = oracle_mod
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        v = np.concatenate([rng.normal(0, 1, 30), rng.normal(8, 1, 25)]).astype(np.float32)
+        s = np.sort(v.astype(np.float64))
+        costs = [((s[:i] - s[:i].mean()) ** 2).sum() + ((s[i:] - s[i:].mean()) ** 2).sum()
+                 for i in range(1, len(s))]
+        best = min(costs)
+        pts = v[:, None]
+        ok, lab, *_ = O.bisect(2, _x4(np.concatenate([pts, np.zeros_like(pts)], 1)),
+                               np.arange(len(v)), seed=1)
+        assert ok and np.isclose(_kmeans_cost(v[:, None].astype(np.float64), lab), best, rtol=1e-9)
+
+
+def test_kmeanspp_second_centre_distribution(oracle_mod):
+    """Algorithm 5: z2 = x_i with probability d_i / sum d.  Over many draws (node
+    keys) the empirical frequencies match the D^2 weights."""
+    O = oracle_mod
+    pts = np.array([[0, 0], [1, 0], [3, 0], [0, 2], [4, 4]], dtype=np.float32)
+    x4 = _x4(pts)
+    counts = np.zeros((5, 5))
+    N = 20000
+    for key in range(N):
+        _, _, z1, z2 = O.bisect(2, x4, np.arange(5), seed=9, key=key, km_iters=0)
+        i0 = int(np.flatnonzero((pts == z1[:2]).all(1))[0])
+        i1 = int(np.flatnonzero((pts == z2[:2]).all(1))[0])
+        counts[i0, i1] += 1
+    first = counts.sum(1) / N
+    assert np.allclose(first, 0.2, atol=0.02)
+    for i0 in range(5):
+        dd = ((pts - pts[i0]) ** 2).sum(1).astype(np.float64)
+        p = dd / dd.sum()
+        emp = counts[i0] / counts[i0].sum()
+        assert np.abs(emp - p).max() < 0.04
+
+
+def test_kmeanspp_expected_cost_bound(oracle_mod):
+    """k-means++ seeding is O(log m)-competitive in expectation (Sec. 3): the mean
+    seeding cost over many draws stays below 8 (ln 2 + 2) times the optimum."""
+    O = oracle_mod
+    rng = np.random.default_rng(5)
+    pts = rng.uniform(0, 1, (12, 2)).astype(np.float32)
+    best, _ = _best_split(pts.astype(np.float64))
+    costs = []
+    for key in range(400):
+        _, lab, z1, z2 = O.bisect(2, _x4(pts), np.arange(12), seed=2, key=key, km_iters=0)
+        d1 = ((pts - z1[:2]) ** 2).sum(1)
+        d2 = ((pts - z2[:2]) ** 2).sum(1)
+        costs.append(np.minimum(d1, d2).sum())
+    assert np.mean(costs) <= 8 * (np.log(2) + 2) * best
+
+
+def _ancestor(h1, d1, h2, d2):
+    return d1 <= d2 and (int(h2) >> (d2 - d1)) == int(h1)
+
+
+def _owner_info(k, perm, tree, sbd):
+    """owner index, heap and depth of every vertex."""
+    part = np.full(k, -1)
+    for idx in range(len(tree["heap"])):
+        o, n1, n2, ns = (int(tree[f][idx]) for f in ("offset", "n1", "n2", "nsep"))
+        if n2 == 0 and ns == 0:
+            part[perm[o:o + n1]] = idx
+        else:
+            so = o + n1 if sbd else o + n1 + n2
+            part[perm[so:so + ns]] = idx
+    return part
+
+
+def _check_ordering(O, A, hg, perm, tree, sbd, d=None, x4=None, min_part=64, max_depth=62):
+    k = hg.k
+    assert sorted(perm.tolist()) == list(range(k))
+    assert (np.diff(tree["heap"].astype(np.float64)) > 0).all()
+    part = _owner_info(k, perm, tree, sbd)
+    assert (part >= 0).all()
+    H, D = tree["heap"], tree["depth"]
+    # every edge lies in a diagonal block or a border: owners are nested
+    for v in range(k):
+        for u in hg.adj[hg.adj_ptr[v]:hg.adj_ptr[v + 1]]:
+            a, b = part[v], part[u]
+            assert _ancestor(H[a], D[a], H[b], D[b]) or _ancestor(H[b], D[b], H[a], D[a])
+    # tree bookkeeping: children of node h are 2h / 2h+1 at the right offsets
+    idx = {int(h): i for i, h in enumerate(H)}
+    for i, h in enumerate(H):
+        o, n1, n2, ns, dp = (int(tree[f][i]) for f in ("offset", "n1", "n2", "nsep", "depth"))
+        leaf = n2 == 0 and ns == 0
+        if leaf:
+            continue
+        if n1:
+            c = idx[2 * int(h)]
+            assert tree["offset"][c] == o and tree["depth"][c] == dp + 1
+        if n2:
+            c = idx[2 * int(h) + 1]
+            assert tree["offset"][c] == (o + n1 + ns if sbd else o + n1)
+        assert dp < max_depth
+    # leaves are small, deep or unsplittable
+    return part
+
+
+@pytest.mark.parametrize("sbd", [False, True])
+def test_order_true_grid_coordinates(oracle_mod, sbd):
+    """With the grid's own coordinates (Example pothen: given geometry) the root
+    separator of a 64x64 grid is one grid line of 64 vertices."""
+    O = oracle_mod
+    A = W.grid_laplacian_2d(64)
+    hg = O.build_from_matrix("symmetric", A)
+    ij = np.indices((64, 64)).reshape(2, -1).T
+    x4 = _x4(ij.astype(np.float32))
+    perm, tree = O.order(hg, 2, x4, seed=1, sbd=sbd)
+    assert tree["heap"][0] == 1 and tree["nsep"][0] == 64
+    assert tree["n1"][0] + tree["n2"][0] + tree["nsep"][0] == 4096
+    _check_ordering(O, A, hg, perm, tree, sbd)
+    if not sbd:
+        assert O.fill_in(A, perm) < 0.5 * O.fill_in(A, np.arange(A.n, dtype=np.int32))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_order_random_structure(oracle_mod, seed):
+    O = oracle_mod
+    A = W.powerlaw_symmetric(1500, seed=seed)
+    hg = O.build_from_matrix("symmetric", A)
+    x4 = O.init_coords(hg.k, 3, seed)
+    for sbd in (False, True):
+        perm, tree = O.order(hg, 3, x4, seed=seed, min_part=16, sbd=sbd)
+        _check_ordering(O, A, hg, perm, tree, sbd)
+        leaves = (tree["n2"] == 0) & (tree["nsep"] == 0)
+        assert leaves.sum() >= 2
+
+
+def test_order_depth_limit_and_bipartite_sbd(oracle_mod):
+    """SBD on the bipartite model to 2^depth parts: no nonzero in the blocks
+    (R1, C2) and (R2, C1) of any split."""
+    O = oracle_mod
+    A = W.powerlaw_rectangular(300, 200, seed=3)
+    hg = O.build_from_matrix("bipartite", A)
+    x4 = O.init_coords(hg.k, 2, 4)
+    perm, tree = O.order(hg, 2, x4, seed=4, min_part=1, max_depth=3, sbd=True)
+    assert tree["depth"].max() <= 3
+    part = _check_ordering(O, A, hg, perm, tree, True, max_depth=3)
+    assert ((tree["depth"] < 3) | ((tree["n2"] == 0) & (tree["nsep"] == 0))).all()
+
+
+def _separator_order_free(hg, d, x4, verts, lab, z1, z2):
+    """Order-free rule: v joins the separator iff a neighbour w in the node has
+    the other label and (s(v), v) < (s(w), w), s from the fp32 plane."""
+    f = np.float32
+    r = (z2 - z1).astype(np.float32)
+    delta = f(0)
+    for m in range(d):
+        delta = f(delta + f(f(f(0.5) * f(z1[m] + z2[m])) * r[m]))
+
+    def s(v):
+        acc = f(0)
+        for m in range(d):
+            acc = f(acc + f(x4[v, m] * r[m]))
+        return abs(f(acc - delta))
+
+    innode = {int(v): int(l) for v, l in zip(verts, lab)}
+    out = dict(innode)
+    for v, lv in innode.items():
+        for w in hg.adj[hg.adj_ptr[v]:hg.adj_ptr[v + 1]]:
+            w = int(w)
+            if w in innode and innode[w] != lv and (s(v), v) < (s(w), w):
+                out[v] = 3
+                break
+    return out
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_separator_sequential_equals_order_free(oracle_mod, seed):
+    """The oracle runs Algorithm 7's edge loop in the canonical order; the
+    parallel rule the GPU uses gives the same separator, and the result has no
+    edge between V1 and V2 (Algorithm 7 postcondition)."""
+    O = oracle_mod
+    A = W.random_symmetric(400, 9, seed)
+    hg = O.build_from_matrix("symmetric", A)
+    x4 = O.init_coords(hg.k, 3, seed)
+    # root only: redo its 2-means, then compare the separator
+    ok, lab, z1, z2 = O.bisect(3, x4, np.arange(hg.k), seed=seed, key=1)
+    assert ok
+    perm, tree = O.order(hg, 3, x4, seed=seed, min_part=1, max_depth=1)
+    n1, n2, ns = int(tree["n1"][0]), int(tree["n2"][0]), int(tree["nsep"][0])
+    V1, V2, V3 = set(perm[:n1].tolist()), set(perm[n1:n1 + n2].tolist()), set(perm[n1 + n2:].tolist())
+    rule = _separator_order_free(hg, 3, x4, np.arange(hg.k), lab, z1, z2)
+    assert {v for v, l in rule.items() if l == 3} == V3
+    assert {v for v, l in rule.items() if l == 1} == V1
+    for v in V1:
+        assert not (set(hg.adj[hg.adj_ptr[v]:hg.adj_ptr[v + 1]].tolist()) & V2)
+    # the stable partition keeps the original relative order
+    assert (np.diff(perm[:n1]) > 0).all() and (np.diff(perm[n1:n1 + n2]) > 0).all()
+
+
+def test_separator_replay_matches_bisect(oracle_mod):
+    """Each split of the ordering equals a standalone 2-means of the node's
+    vertices (in node order, keyed by the node's heap number)."""
+    O = oracle_mod
+    A = W.grid_laplacian_3d(12)
+    hg = O.build_from_matrix("symmetric", A)
+    x4 = O.init_coords(hg.k, 3, 8)
+    perm, tree = O.order(hg, 3, x4, seed=8, min_part=32, max_depth=4)
+    # the child 2 of the root holds V2 in node order; its own split is replayed
+    idx = {int(h): i for i, h in enumerate(tree["heap"])}
+    i2 = idx[3]
+    o, n1, n2, ns = (int(tree[f][i2]) for f in ("offset", "n1", "n2", "nsep"))
+    size = n1 + n2 + ns
+    # node vertices in the order they had when the node was split = stable
+    # partition of the root's V2 list, which is ascending in vertex id
+    verts = np.sort(perm[o:o + size])
+    ok, lab, z1, z2 = O.bisect(3, x4, verts, seed=8, key=3)
+    assert ok
+    assert set(perm[o:o + n1].tolist()) <= set(verts[lab == 1].tolist())
+    assert set(perm[o + n1:o + n1 + n2].tolist()) <= set(verts[lab == 2].tolist())
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_cut_size_brute_force(oracle_mod, seed):
+    O = oracle_mod
+    rng = np.random.default_rng(seed)
+    A = W.random_pattern(25, 17, 90, seed)
+    for model in ("rownet", "colnet", "bipartite", "symmetric"):
+        B = A if model != "symmetric" else W.random_pattern(25, 25, 90, seed)
+        hg = O.build_from_matrix(model, B)
+        nparts = int(rng.integers(2, 90))
+        part = rng.integers(0, nparts, hg.k).astype(np.int32)
+        cn, l1 = O.cut_size(hg.net_ptr, hg.pins, part)
+        lam = [len({int(part[v]) for v in hg.pins[hg.net_ptr[j]:hg.net_ptr[j + 1]]}) for j in range(hg.l)]
+        assert cn == sum(1 for x in lam if x > 1)
+        assert l1 == sum(max(x - 1, 0) for x in lam)
+
+
+def _dense_fill(P):
+    """Symbolic LU of a dense boolean pattern without pivoting: new nonzeros."""
+    n = len(P)
+    F = P.copy()
+    for k in range(n):
+        rows = np.flatnonzero(F[k + 1:, k]) + k + 1
+        cols = np.flatnonzero(F[k, k + 1:]) + k + 1
+        for i in rows:
+            F[i, cols] = True
+    return int(F.sum() - P.sum())
+
+
+def test_fill_in_example(oracle_mod):
+    """Example fillin: six new nonzeros in the original order, none after
+    swapping the first and last rows and columns."""
+    O = oracle_mod
+    g = json.load(open(os.path.join(GOLD, "fillin.json")))
+    M = np.array(g["matrix"])
+    r, c = np.nonzero(M)
+    A = W.csr_from_coo(4, 4, r, c, "arrow")
+    ident = np.arange(4, dtype=np.int32)
+    nzl = O.cholesky_nnz(4, A.rowptr, A.colidx, ident)
+    assert 2 * nzl - 4 - A.nnz == g["new_nonzeros_original_order"]
+    sw = np.array(g["swap"], dtype=np.int32)
+    nzl2 = O.cholesky_nnz(4, A.rowptr, A.colidx, sw)
+    assert 2 * nzl2 - 4 - A.nnz == g["new_nonzeros_after_swap"]
+    assert _dense_fill(M != 0) == g["new_nonzeros_original_order"]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_cholesky_count_matches_dense_elimination(oracle_mod, seed):
+    O = oracle_mod
+    A = W.random_symmetric(40, 4, seed)
+    perm = np.random.default_rng(seed).permutation(40).astype(np.int32)
+    P = np.zeros((40, 40), dtype=bool)
+    rows = np.repeat(np.arange(40), np.diff(A.rowptr))
+    P[rows, A.colidx] = True
+    Pp = P[np.ix_(perm, perm)]
+    nzl = O.cholesky_nnz(40, A.rowptr, A.colidx, perm)
+    assert 2 * nzl - 40 == Pp.sum() + _dense_fill(Pp)

@@ -1,0 +1,217 @@
+/*
+ * vmo.h — C-ABI of the GB300 library for visual matrix ordering (VMO),
+ * the geometric method of Fagginger Auer and Bisseling, "A Geometric
+ * Approach to Matrix Ordering".
+ *
+ * Pipeline: sparse pattern -> hypergraph model (Table 1) -> geometry by
+ * multilevel force-directed layout (Algorithms 3 and 4, eq.
+ * graphenergygradientsimple) -> recursive 2-means bisection (Algorithm 5)
+ * turned into vertex separators (Algorithm 7) -> recursive BBD / SBD row and
+ * column permutations (Sec. 4.2, Sec. 5).
+ *
+ * Conventions shared by every entry point:
+ *  - All array arguments are DEVICE pointers unless the comment says "host".
+ *    The caller owns every input and output buffer; a handle (vmo_hg) owns
+ *    only the device arrays of its hypergraph model.
+ *  - Coordinates are float[4] per vertex (16-byte aligned, components >= d
+ *    are zero and ignored); the layout dimension d is 2, 3 or 4.
+ *  - Permutations are perm[new] = old, 0-based.
+ *  - Labels: 1 and 2 are the two sides of a split (Algorithm 7), 3 the
+ *    separator.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; calls that return sizes or counts to
+ *    the host synchronise that stream before returning.
+ *  - Every call returns a vmo_status; nothing throws, exits or traps.  Inputs
+ *    are validated before any launch (VMO_ERR_INVALID / VMO_ERR_UNSUPPORTED).
+ *    CUDA failures return VMO_ERR_CUDA; vmo_last_error() gives the message of
+ *    the calling thread's last failure.  There is no CPU fallback: without a
+ *    usable GPU every compute call returns VMO_ERR_CUDA.
+ *  - Random draws come from a counter-based SplitMix64 generator keyed by
+ *    params.seed, so results are deterministic for a given input and seed.
+ */
+#ifndef VMO_H
+#define VMO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VMO_OK = 0,
+  VMO_ERR_INVALID = 1,     /* malformed argument (null, negative size, bad CSR) */
+  VMO_ERR_OOM = 2,         /* device allocation failed */
+  VMO_ERR_CUDA = 3,        /* CUDA runtime or kernel failure, or no GPU */
+  VMO_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out */
+  VMO_ERR_BUDGET = 5,      /* request does not fit the admission budget */
+  VMO_ERR_UNSUPPORTED = 6  /* valid but unsupported combination (e.g. d = 5) */
+} vmo_status;
+
+/* Hypergraph models of an m x n sparsity pattern (Table 1, Sec. 1.1).
+ *  SYMMETRIC: vertices 0..m-1 (m == n), nets {i, j} for a_ij != 0, i != j
+ *             (a set: a_ij and a_ji give one net; the diagonal is dropped).
+ *  BIPARTITE: vertices rows 0..m-1 then columns m..m+n-1, nets {r_i, c_j}.
+ *  ROWNET:    vertices = columns, net i = {c_j : a_ij != 0}.
+ *  COLNET:    vertices = rows, net j = {r_i : a_ij != 0}.
+ * SYMMETRIC and BIPARTITE are graphs; only they can be ordered
+ * (Algorithm 7 is stated for graphs). */
+typedef enum { VMO_SYMMETRIC = 0, VMO_BIPARTITE = 1, VMO_ROWNET = 2, VMO_COLNET = 3 } vmo_model;
+
+typedef struct vmo_hg_s* vmo_hg;
+
+/* Sparsity pattern in CSR form: device rowptr[m+1] and colidx[nnz] (int32,
+ * 0-based; columns may be unsorted and repeated — duplicates are merged).
+ * Values are not used (Sec. 4.2: value-weighted costs were not used). */
+typedef struct {
+  int32_t m, n;
+  int64_t nnz;
+  const int32_t* rowptr;
+  const int32_t* colidx;
+} vmo_csr;
+
+/* Method parameters; vmo_default_params() fills the defaults shown. */
+typedef struct {
+  int32_t d;            /* layout dimension, 2..4 (default 3) */
+  int32_t iters;        /* steepest-descent steps per level, Algorithm 4 (100) */
+  float sigma;          /* first step length in units of the mean point spacing (1.0) */
+  float decay;          /* step-length decay per step, Sec. 2.3 (0.9) */
+  int32_t occupancy;    /* target points per finest grid cell (8) */
+  int32_t multilevel;   /* 1: Algorithm 3 coarsening/prolongation; 0: one level (1) */
+  int32_t match_rounds; /* handshake matching rounds per coarsening level (4) */
+  int32_t coarse_min;   /* stop coarsening at this many vertices (64) */
+  int32_t km_iters;     /* Lloyd rounds of 2-means, Algorithm 5 (20) */
+  int32_t min_part;     /* a node with <= min_part vertices is a leaf (64) */
+  int32_t max_depth;    /* nodes at this depth are leaves, <= 62 (62) */
+  uint64_t seed;        /* seed of every random draw (1) */
+} vmo_params;
+
+/* Tree of the recursive ordering, one record per node, sorted by heap
+ * number (root 1; children of h are 2h (V1) and 2h+1 (V2)), i.e. breadth
+ * first.  A leaf has n1 = |V|, n2 = nsep = 0.  An internal node's vertices
+ * occupy [offset, offset + n1 + n2 + nsep) of the permutation as
+ * [V1, V2, V3] (BBD) or [V1, V3, V2] (SBD).  Device arrays of `capacity`
+ * entries each; `count` is written (host) on return.  A tree never has more
+ * than 2k records. */
+typedef struct {
+  int32_t capacity;
+  int32_t count;
+  uint64_t* heap;
+  int32_t* offset;
+  int32_t* n1;
+  int32_t* n2;
+  int32_t* nsep;
+  int32_t* depth;
+} vmo_tree;
+
+/* Fills *p with the defaults listed above. */
+void vmo_default_params(vmo_params* p);
+
+/* Builds the hypergraph model of the pattern `a` on the device (Table 1).
+ * vertex_weight: optional device float[k] (NULL = unit weights, Def. 1.1).
+ * On success *out owns device copies of the model; free with vmo_destroy.
+ * Errors: VMO_ERR_INVALID for null pointers, negative sizes, nnz not equal
+ * to rowptr[m], column indices out of range, SYMMETRIC with m != n. */
+vmo_status vmo_build_hypergraph(const vmo_csr* a, vmo_model model, const float* vertex_weight,
+                                void* stream, vmo_hg* out);
+
+/* Number of vertices k and nets l of the model (host values). */
+int32_t vmo_hg_vertices(vmo_hg hg);
+int64_t vmo_hg_nets(vmo_hg hg);
+
+/* Device views of the model owned by the handle (valid until vmo_destroy).
+ * Graph models: adjacency CSR adj_ptr[k+1], adj[adj_ptr[k]] (neighbours
+ * ascending).  Every model: nets CSR net_ptr[l+1], pins (pins ascending;
+ * graph models list the edges u < v lexicographically) and the incidence
+ * vtx_ptr[k+1], vnets (nets of a vertex ascending).  *count_* receive the
+ * lengths of adj / pins / vnets (host).  Pointers may be NULL to skip. */
+vmo_status vmo_hg_arrays(vmo_hg hg, const int32_t** adj_ptr, const int32_t** adj, int64_t* count_adj,
+                         const int32_t** net_ptr, const int32_t** pins, int64_t* count_pins,
+                         const int32_t** vtx_ptr, const int32_t** vnets, int64_t* count_vnets);
+
+/* Connected components (Algorithm 1): labels[v] = smallest vertex id of v's
+ * component.  labels: device int32[k]. */
+vmo_status vmo_components(vmo_hg hg, int32_t* labels, void* stream);
+
+/* Random initial layout of Algorithm 3: coordinates uniform in [0, s)^d with
+ * s the smallest integer with s^d >= k (fp32, exactly reproducible).
+ * coords: device float[4k]. */
+vmo_status vmo_init_coords(int32_t k, int32_t d, uint64_t seed, float* coords, void* stream);
+
+/* Geometry (Sec. 2): multilevel layout of a graph model (Algorithm 3, with
+ * Algorithm 4 on every level), or a single level from the random layout when
+ * params->multilevel == 0 or the model is a hypergraph model.  If
+ * use_given_init != 0 the single-level layout starts from `coords` instead.
+ * coords: device float[4k], written on return. */
+vmo_status vmo_layout(vmo_hg hg, const vmo_params* params, float* coords, int32_t use_given_init,
+                      void* stream);
+
+/* One steepest-descent step of Algorithm 4 on the finest level with step
+ * length `step`: y = gradient of eq. graphenergygradientsimple (repulsion on
+ * the grid pyramid), then x_n <- x_n - step * y_n / ||y_n||.
+ * coords (in/out) device float[4k]; y_out device float[4k] or NULL;
+ * keys_out device uint32[k] or NULL (level-L Morton key of every vertex);
+ * levels_out host int32 or NULL (finest grid level L). */
+vmo_status vmo_layout_step(vmo_hg hg, const vmo_params* params, float* coords, float step, float* y_out,
+                           uint32_t* keys_out, int32_t* levels_out, void* stream);
+
+/* Coarsening of Algorithm 3 on the handle's graph: level 0 matching into
+ * mate (device int32[k], -1 = unmatched) and grouping pi (device int32[k],
+ * fine vertex -> coarse vertex), and the vertex counts of every level of the
+ * hierarchy (host int32 level_sizes[41]; *nlevels host).  Any output may be
+ * NULL.  Graph models only. */
+vmo_status vmo_coarsen(vmo_hg hg, const vmo_params* params, int32_t* mate, int32_t* pi, int32_t* kc_out,
+                       int32_t* level_sizes, int32_t* nlevels, void* stream);
+
+/* 2-means of the points coords[verts[i]] in dimension d (Algorithm 5 with
+ * m = 2, in the exact arithmetic of the ordering): verts device int32[nverts]
+ * (vertex ids of hg, in the order the node lists them), labels device
+ * uint8[nverts] in {1, 2},
+ * centres z device float[8] (z1 then z2), *split host 1 iff both sides are
+ * non-empty.  `key` keys the k-means++ draws (the heap number of a node). */
+vmo_status vmo_bisect(vmo_hg hg, int32_t d, const float* coords, const int32_t* verts, int32_t nverts,
+                      uint64_t seed, uint64_t key, int32_t km_iters, uint8_t* labels, float* z, int32_t* split,
+                      void* stream);
+
+/* Recursive BBD ordering (Sec. 4.2): layout (when coords == NULL) and then
+ * recursive bisection with vertex separators placed last.  Symmetric model:
+ * row_perm and col_perm (device int32[m]) receive the same permutation.
+ * Bipartite model: rows and columns are permuted separately (row_perm[m],
+ * col_perm[n]).  tree: optional (NULL), see vmo_tree. */
+vmo_status vmo_order_bbd(vmo_hg hg, const float* coords, const vmo_params* params, int32_t* row_perm,
+                         int32_t* col_perm, vmo_tree* tree, void* stream);
+
+/* Recursive SBD ordering (Sec. 5): as vmo_order_bbd, with the separator
+ * placed between the two parts at every split. */
+vmo_status vmo_order_sbd(vmo_hg hg, const float* coords, const vmo_params* params, int32_t* row_perm,
+                         int32_t* col_perm, vmo_tree* tree, void* stream);
+
+/* Vertex order of the last ordering step before the row/column split:
+ * identical to vmo_order_bbd/sbd but writes the single vertex permutation
+ * (device int32[k]) — for the bipartite model rows and columns interleaved
+ * as they lie in the recursive partition. */
+vmo_status vmo_order_vertices(vmo_hg hg, const float* coords, const vmo_params* params, int32_t sbd,
+                              int32_t* perm, vmo_tree* tree, void* stream);
+
+/* Cut metrics of a vertex partition (Sec. 4.1 footnote, Sec. 5): over the
+ * nets of the model, lambda_e = number of distinct parts among the pins;
+ * cutnet = #{e : lambda_e > 1}, lambda1 = sum_e (lambda_e - 1).
+ * part: device int32[k] in [0, nparts).  cutnet, lambda1: host int64.
+ * Errors: VMO_ERR_INVALID for nparts < 1. */
+vmo_status vmo_cut_size(vmo_hg hg, const int32_t* part, int32_t nparts, int64_t* cutnet, int64_t* lambda1,
+                        void* stream);
+
+/* Frees the handle and its device arrays (NULL is ignored). */
+void vmo_destroy(vmo_hg hg);
+
+/* Static description of a status code. */
+const char* vmo_status_string(vmo_status s);
+
+/* Message of the calling thread's last failing call ("" if none). */
+const char* vmo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VMO_H */

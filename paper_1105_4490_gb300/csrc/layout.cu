@@ -1,0 +1,990 @@
+// Geometry (Sec. 2): steepest descent on the energy of eq. graphenergysimple
+// (Algorithm 4) inside the multilevel scheme of Algorithm 3.
+//
+// One step of a level, for every problem of a batch at once:
+//   keys      cell of every point on a uniform grid over the bounding cube
+//             (fp32, no FMA), Morton key of the finest cell
+//   sort      stable segmented radix sort of (key, vertex)
+//   gather    points copied in key order; first/last point of every finest
+//             cell recorded in a dense table
+//   aggregate per cell weight and weighted mean: finest cells from their
+//             points, coarser cells from their 2^d children (fixed order)
+//   attract   y_n = sum_j c_j (x_n - z_j) (2-pin nets: c/2 (x_n - x_u))
+//   repulse   near field exactly over the 3^d adjacent finest cells, far field
+//             from the cells whose parent is adjacent to the target's parent
+//             but which are not adjacent themselves; then the step
+//             x_n <- x_n - s_t y_n / ||y_n|| and the next bounding box.
+#include <algorithm>
+#include <cmath>
+
+#include "layout.cuh"
+
+namespace vmo {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__host__ __device__ inline int64_t lvl_off(int d, int l) {
+  // sum_{j<l} 2^(d j) = (2^(d l) - 1) / (2^d - 1)
+  return ((int64_t(1) << (d * l)) - 1) / ((int64_t(1) << d) - 1);
+}
+
+__device__ inline int find_problem(const int64_t* __restrict__ base, int P, int64_t i) {
+  int lo = 0, hi = P;  // base[lo] <= i < base[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (base[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <int D>
+__device__ inline void cell_of(const float4& v, const float* lo, float s, int L, int32_t* c) {
+  const int32_t cmax = (1 << L) - 1;
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    float t = __fmul_rn(__fsub_rn(comp(v, m), lo[m]), s);
+    int32_t q = (int32_t)floorf(t);
+    c[m] = q < cmax ? q : cmax;
+  }
+}
+
+template <int D>
+__device__ inline void grid_frame(const uint32_t* __restrict__ bb, int pb, int L, float* lo, float* s) {
+  float E = 0.0f;
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    lo[m] = ord2f(bb[pb * 8 + m]);
+    float hi = ord2f(bb[pb * 8 + 4 + m]);
+    float e = __fsub_rn(hi, lo[m]);
+    E = e > E ? e : E;
+  }
+  *s = (E > 0.0f) ? __fdiv_rn((float)(1 << L), E) : 0.0f;
+}
+
+template <int D>
+__device__ inline int64_t rowmajor(const int32_t* c, int side) {
+  int64_t r = 0;
+#pragma unroll
+  for (int m = D - 1; m >= 0; --m) r = r * side + c[m];
+  return r;
+}
+
+__host__ __device__ constexpr int field_bits(int D) { return D == 4 ? 8 : 30 / D; }
+
+// Block-level bounding-box accumulation into ordered-uint min/max slots.
+template <int D>
+__device__ void bbox_accumulate(const float4& v, bool valid, int pb, bool uniform, uint32_t* __restrict__ bb) {
+  __shared__ uint32_t smn[kBlock / 32][4], smx[kBlock / 32][4];
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  if (!uniform) {
+    if (valid)
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        uint32_t o = f2ord(comp(v, m));
+        atomicMin(&bb[pb * 8 + m], o);
+        atomicMax(&bb[pb * 8 + 4 + m], o);
+      }
+    return;
+  }
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    uint32_t mn = valid ? f2ord(comp(v, m)) : 0xFFFFFFFFu;
+    uint32_t mx = valid ? mn : 0u;
+    mn = __reduce_min_sync(0xffffffffu, mn);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) { smn[warp][m] = mn; smx[warp][m] = mx; }
+  }
+  __syncthreads();
+  if (threadIdx.x < D) {
+    uint32_t mn = 0xFFFFFFFFu, mx = 0u;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      mn = min(mn, smn[w][threadIdx.x]);
+      mx = max(mx, smx[w][threadIdx.x]);
+    }
+    if (mn != 0xFFFFFFFFu) atomicMin(&bb[pb * 8 + threadIdx.x], mn);
+    if (mx != 0u) atomicMax(&bb[pb * 8 + 4 + threadIdx.x], mx);
+  }
+}
+
+__global__ void k_bbox_reset(uint32_t* bb, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) bb[i] = ((i & 7) < 4) ? 0xFFFFFFFFu : 0u;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_bbox(const float4* __restrict__ x, int64_t K,
+                                                 const int32_t* __restrict__ vprob, uint32_t* __restrict__ bb) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t first = (int64_t)blockIdx.x * blockDim.x;
+  int64_t last = min(first + (int64_t)blockDim.x, K) - 1;
+  bool uniform = vprob[first] == vprob[last];
+  bool valid = i < K;
+  float4 v = valid ? x[i] : make_float4(0, 0, 0, 0);
+  int pb = valid ? vprob[i] : 0;
+  bbox_accumulate<D>(v, valid, pb, uniform, bb);
+}
+
+// Step length of a level: s0 = sigma * Lbox / k^(1/d), Lbox = d-th root of the
+// box volume (largest extent if an extent is zero).
+template <int D>
+__global__ void k_step0(const uint32_t* __restrict__ bb, const ProbDev* __restrict__ prob, int P, float sigma,
+                        float* __restrict__ s0) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  double vol = 1.0, emax = 0.0;
+  bool degenerate = false;
+  for (int m = 0; m < D; ++m) {
+    double e = (double)ord2f(bb[p * 8 + 4 + m]) - (double)ord2f(bb[p * 8 + m]);
+    if (!(e > 0.0)) degenerate = true;
+    emax = e > emax ? e : emax;
+    vol *= e;
+  }
+  int k = prob[p].k;
+  double Lbox = degenerate ? emax : pow(vol, 1.0 / D);
+  s0[p] = (k > 0) ? (float)(sigma * Lbox / pow((double)k, 1.0 / D)) : 0.0f;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_keys(const float4* __restrict__ x, int64_t K, const int32_t* __restrict__ vprob,
+                                                 const ProbDev* __restrict__ prob, const uint32_t* __restrict__ bb,
+                                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                 uint32_t* __restrict__ bb_next, int nreset) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < nreset) bb_next[v] = ((v & 7) < 4) ? 0xFFFFFFFFu : 0u;
+  if (v >= K) return;
+  int pb = vprob[v];
+  int L = prob[pb].L;
+  float lo[D], s;
+  grid_frame<D>(bb, pb, L, lo, &s);
+  int32_t c[D];
+  cell_of<D>(x[v], lo, s, L, c);
+  keys[v] = morton<D>(c, L);
+  vals[v] = (uint32_t)v;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_gather(const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ svals,
+                                                   int64_t K, const float4* __restrict__ x, const float* __restrict__ w,
+                                                   const int32_t* __restrict__ vprob, const ProbDev* __restrict__ prob,
+                                                   const uint32_t* __restrict__ bb, float4* __restrict__ xs,
+                                                   float* __restrict__ ws, uint32_t* __restrict__ scell,
+                                                   int2* __restrict__ cse) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= K) return;
+  uint32_t v = svals[p];
+  int pb = vprob[p];
+  ProbDev pr = prob[pb];
+  float4 xv = x[v];
+  xs[p] = xv;
+  if (ws) ws[p] = w ? w[v] : 1.0f;
+  float lo[D], s;
+  grid_frame<D>(bb, pb, pr.L, lo, &s);
+  int32_t c[D];
+  cell_of<D>(xv, lo, s, pr.L, c);
+  uint32_t packed = 0;
+#pragma unroll
+  for (int m = 0; m < D; ++m) packed |= (uint32_t)c[m] << (m * field_bits(D));
+  scell[p] = packed;
+  int64_t rm = pr.fbase + rowmajor<D>(c, 1 << pr.L);
+  uint32_t key = skeys[p];
+  bool first = (p == pr.vbase) || skeys[p - 1] != key;
+  bool last = (p == pr.vbase + pr.k - 1) || skeys[p + 1] != key;
+  if (first) cse[rm].x = (int)p;
+  if (last) cse[rm].y = (int)(p + 1);
+}
+
+template <int D>
+__device__ inline void store_cell(int64_t idx, const float* S, float W, float4* __restrict__ St,
+                                  float* __restrict__ Wt, float4* __restrict__ CW) {
+  St[idx] = make_float4(S[0], D > 1 ? S[1] : 0.f, D > 2 ? S[2] : 0.f, D > 3 ? S[3] : 0.f);
+  Wt[idx] = W;
+  if (W > 0.0f) {
+    float iw = 1.0f / W;
+    float c0 = S[0] * iw, c1 = D > 1 ? S[1] * iw : 0.f, c2 = D > 2 ? S[2] * iw : 0.f;
+    float c3 = D > 3 ? S[3] * iw : W;
+    CW[idx] = make_float4(c0, c1, c2, c3);
+  } else {
+    CW[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_agg_finest(const int2* __restrict__ cse, int64_t ncells,
+                                                       const int64_t* __restrict__ fbase, int P,
+                                                       const ProbDev* __restrict__ prob, const float4* __restrict__ xs,
+                                                       const float* __restrict__ ws, float4* __restrict__ St,
+                                                       float* __restrict__ Wt, float4* __restrict__ CW) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncells) return;
+  int pb = find_problem(fbase, P, i);
+  ProbDev pr = prob[pb];
+  int64_t c = i - pr.fbase;
+  int2 r = cse[i];
+  float S[4] = {0.f, 0.f, 0.f, 0.f};
+  float W = 0.f;
+  for (int q = r.x; q < r.y; ++q) {
+    float4 p = xs[q];
+    float wq = ws ? ws[q] : 1.0f;
+    S[0] += wq * p.x;
+    if (D > 1) S[1] += wq * p.y;
+    if (D > 2) S[2] += wq * p.z;
+    if (D > 3) S[3] += wq * p.w;
+    W += wq;
+  }
+  store_cell<D>(pr.cbase + lvl_off(D, pr.L) + c, S, W, St, Wt, CW);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_agg_level(int step, const int64_t* __restrict__ off, int P, int64_t ncells,
+                                                      const ProbDev* __restrict__ prob, float4* __restrict__ St,
+                                                      float* __restrict__ Wt, float4* __restrict__ CW) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncells) return;
+  int pb = find_problem(off, P, i);
+  ProbDev pr = prob[pb];
+  int l = pr.L - step;
+  int64_t c = i - off[pb];
+  int side = 1 << l;
+  int32_t cc[D];
+  int64_t rem = c;
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    cc[m] = (int32_t)(rem % side);
+    rem /= side;
+  }
+  int64_t child_base = pr.cbase + lvl_off(D, l + 1);
+  float S[4] = {0.f, 0.f, 0.f, 0.f};
+  float W = 0.f;
+#pragma unroll
+  for (int ch = 0; ch < (1 << D); ++ch) {
+    int32_t q[D];
+#pragma unroll
+    for (int m = 0; m < D; ++m) q[m] = 2 * cc[m] + ((ch >> m) & 1);
+    int64_t idx = child_base + rowmajor<D>(q, 2 * side);
+    float4 s4 = St[idx];
+    S[0] += s4.x;
+    if (D > 1) S[1] += s4.y;
+    if (D > 2) S[2] += s4.z;
+    if (D > 3) S[3] += s4.w;
+    W += Wt[idx];
+  }
+  store_cell<D>(pr.cbase + lvl_off(D, l) + c, S, W, St, Wt, CW);
+}
+
+// Rubber bands of 2-pin nets: y_v = sum_u c_vu (x_v - x_u) / 2.
+__global__ void __launch_bounds__(kBlock) k_attract(const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                                                    const float* __restrict__ acost, const float4* __restrict__ x,
+                                                    int64_t K, float4* __restrict__ y) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= K) return;
+  float4 xv = x[v];
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  int32_t t1 = adj_ptr[v + 1];
+  for (int32_t t = adj_ptr[v]; t < t1; ++t) {
+    float4 xu = x[adj[t]];
+    float c = acost ? acost[t] : 1.0f;
+    a0 += c * (xv.x - xu.x);
+    a1 += c * (xv.y - xu.y);
+    a2 += c * (xv.z - xu.z);
+    a3 += c * (xv.w - xu.w);
+  }
+  y[v] = make_float4(0.5f * a0, 0.5f * a1, 0.5f * a2, 0.5f * a3);
+}
+
+// Net centres z_j of general nets (Algorithm 4).
+__global__ void k_net_center(const int32_t* __restrict__ net_ptr, const int32_t* __restrict__ pins, int64_t l,
+                             const float4* __restrict__ x, float4* __restrict__ z) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= l) return;
+  int32_t a = net_ptr[j], b = net_ptr[j + 1];
+  float4 s = make_float4(0, 0, 0, 0);
+  for (int32_t t = a; t < b; ++t) {
+    float4 q = x[pins[t]];
+    s.x += q.x; s.y += q.y; s.z += q.z; s.w += q.w;
+  }
+  float inv = (b > a) ? 1.0f / (float)(b - a) : 0.f;
+  z[j] = make_float4(s.x * inv, s.y * inv, s.z * inv, s.w * inv);
+}
+
+__global__ void k_attract_hyper(const int32_t* __restrict__ vtx_ptr, const int32_t* __restrict__ vnets,
+                                const float4* __restrict__ x, const float4* __restrict__ z, int64_t K,
+                                float4* __restrict__ y) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= K) return;
+  float4 xv = x[v];
+  float4 a = make_float4(0, 0, 0, 0);
+  for (int32_t t = vtx_ptr[v]; t < vtx_ptr[v + 1]; ++t) {
+    float4 q = z[vnets[t]];
+    a.x += xv.x - q.x; a.y += xv.y - q.y; a.z += xv.z - q.z; a.w += xv.w - q.w;
+  }
+  y[v] = a;
+}
+
+template <int D>
+__device__ inline void accumulate(float* F, const float4& src, const float4& xn, float wsrc) {
+  float dx0 = src.x - xn.x;
+  float dx1 = D > 1 ? src.y - xn.y : 0.f;
+  float dx2 = D > 2 ? src.z - xn.z : 0.f;
+  float dx3 = D > 3 ? src.w - xn.w : 0.f;
+  float r2 = dx0 * dx0 + dx1 * dx1 + dx2 * dx2 + dx3 * dx3;
+  if (r2 > 0.0f) {
+    float g;
+    if (D == 2) {
+      g = __fdividef(wsrc, r2);
+    } else if (D == 3) {
+      float ir = rsqrtf(r2);
+      g = wsrc * ir * ir * ir;
+    } else {
+      float i2 = __fdividef(1.0f, r2);
+      g = wsrc * i2 * i2;
+    }
+    F[0] += g * dx0;
+    if (D > 1) F[1] += g * dx1;
+    if (D > 2) F[2] += g * dx2;
+    if (D > 3) F[3] += g * dx3;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_repulse_update(
+    const float4* __restrict__ xs, const float* __restrict__ ws, const uint32_t* __restrict__ svals,
+    const uint32_t* __restrict__ scell, const int2* __restrict__ cse, const float4* __restrict__ CW,
+    const float* __restrict__ Wt, const float4* __restrict__ yatt, const int32_t* __restrict__ vprob,
+    const ProbDev* __restrict__ prob, int64_t K, float kappa, const float* __restrict__ s0, float scale,
+    float step_override, float4* __restrict__ x, float4* __restrict__ y_out, uint32_t* __restrict__ bb_next) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t first = (int64_t)blockIdx.x * blockDim.x;
+  int64_t lastp = min(first + (int64_t)blockDim.x, K) - 1;
+  bool uniform = vprob[first] == vprob[lastp];
+  bool valid = p < K;
+  int pb = 0;
+  float4 xnew = make_float4(0, 0, 0, 0);
+  if (valid) {
+    pb = vprob[p];
+    const ProbDev pr = prob[pb];
+    const int L = pr.L, side = 1 << L;
+    const float4 xn = xs[p];
+    const float wn = ws ? ws[p] : 1.0f;
+    const uint32_t packed = scell[p];
+    int32_t c[D];
+#pragma unroll
+    for (int m = 0; m < D; ++m) c[m] = (int32_t)((packed >> (m * field_bits(D))) & ((1u << field_bits(D)) - 1));
+    float F[4] = {0.f, 0.f, 0.f, 0.f};
+    // near field: 3^D finest cells around the target's cell, exactly
+    constexpr int NB = D == 2 ? 9 : (D == 3 ? 27 : 81);
+    for (int o = 0; o < NB; ++o) {
+      int32_t cc[D];
+      int oo = o;
+      bool inside = true;
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        cc[m] = c[m] + (oo % 3) - 1;
+        oo /= 3;
+        inside = inside && cc[m] >= 0 && cc[m] < side;
+      }
+      if (!inside) continue;
+      int2 r = cse[pr.fbase + rowmajor<D>(cc, side)];
+      for (int q = r.x; q < r.y; ++q) {
+        if (q == p) continue;
+        accumulate<D>(F, xs[q], xn, ws ? ws[q] : 1.0f);
+      }
+    }
+    // far field: levels 2..L
+    for (int l = 2; l <= L; ++l) {
+      int32_t me[D], par[D];
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        me[m] = c[m] >> (L - l);
+        par[m] = me[m] >> 1;
+      }
+      const int sl = 1 << l, sp = sl >> 1;
+      const int64_t lbase = pr.cbase + lvl_off(D, l);
+      for (int o = 0; o < NB; ++o) {
+        int32_t pc[D];
+        int oo = o;
+        bool inside = true;
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+          pc[m] = par[m] + (oo % 3) - 1;
+          oo /= 3;
+          inside = inside && pc[m] >= 0 && pc[m] < sp;
+        }
+        if (!inside) continue;
+#pragma unroll
+        for (int ch = 0; ch < (1 << D); ++ch) {
+          int32_t cc[D];
+          bool adjacent = true;
+#pragma unroll
+          for (int m = 0; m < D; ++m) {
+            cc[m] = 2 * pc[m] + ((ch >> m) & 1);
+            int32_t dlt = cc[m] - me[m];
+            adjacent = adjacent && dlt >= -1 && dlt <= 1;
+          }
+          if (adjacent) continue;
+          int64_t idx = lbase + rowmajor<D>(cc, sl);
+          float4 cw = CW[idx];
+          float W = (D == 4) ? Wt[idx] : cw.w;
+          if (W > 0.0f) accumulate<D>(F, cw, xn, W);
+        }
+      }
+    }
+    const uint32_t v = svals[p];
+    float4 ya = yatt[v];
+    float y0 = kappa * wn * F[0] + ya.x;
+    float y1 = D > 1 ? kappa * wn * F[1] + ya.y : 0.f;
+    float y2 = D > 2 ? kappa * wn * F[2] + ya.z : 0.f;
+    float y3 = D > 3 ? kappa * wn * F[3] + ya.w : 0.f;
+    if (y_out) y_out[v] = make_float4(y0, y1, y2, y3);
+    float ny = sqrtf(y0 * y0 + y1 * y1 + y2 * y2 + y3 * y3);
+    float step = step_override > 0.0f ? step_override : s0[pb] * scale;
+    float a = ny > 0.0f ? step / ny : 0.0f;
+    xnew = make_float4(xn.x - a * y0, D > 1 ? xn.y - a * y1 : 0.f, D > 2 ? xn.z - a * y2 : 0.f,
+                       D > 3 ? xn.w - a * y3 : 0.f);
+    x[v] = xnew;
+  }
+  bbox_accumulate<D>(xnew, valid, pb, uniform, bb_next);
+}
+
+// ------------------------------ initial layout -----------------------------
+__global__ void k_init_coords(int64_t K, const int32_t* __restrict__ vprob, const ProbDev* __restrict__ prob,
+                              const uint64_t* __restrict__ seeds, const int32_t* __restrict__ start, int D,
+                              float4* __restrict__ x) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= K) return;
+  int pb = vprob[v];
+  if (start && !start[pb]) return;
+  ProbDev pr = prob[pb];
+  uint64_t lv = (uint64_t)(v - pr.vbase);
+  float side = (float)pr.side;
+  float c[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int m = 0; m < D; ++m) {
+    uint64_t r = rand64(seeds[pb] ^ kTagCoord, lv, (uint64_t)m);
+    float u = __fmul_rn((float)(r >> 40), 0x1p-24f);
+    c[m] = __fmul_rn(u, side);
+  }
+  x[v] = make_float4(c[0], c[1], c[2], c[3]);
+}
+
+// Prolongation (Algorithm 3): x(v) = f * x_coarse(pi(v)) + jitter.
+__global__ void k_prolong(const float4* __restrict__ xc, const int32_t* __restrict__ pi, int64_t K,
+                          const int32_t* __restrict__ vprob, const ProbDev* __restrict__ prob,
+                          const float* __restrict__ fac, const uint64_t* __restrict__ seeds, int level, int D,
+                          float4* __restrict__ x) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= K) return;
+  int pb = vprob[v];
+  float f = fac[pb];
+  if (!(f > 0.0f)) return;
+  uint64_t lv = (uint64_t)(v - prob[pb].vbase);
+  float4 q = xc[pi[v]];
+  float c[4] = {q.x, q.y, q.z, q.w};
+  float o[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int m = 0; m < D; ++m) {
+    uint64_t r = rand64(seeds[pb] ^ kTagJitter, lv, (uint64_t)(4 * level + m));
+    float u = (float)(r >> 40) * 0x1p-24f;
+    o[m] = f * c[m] + 0.1f * (u - 0.5f);
+  }
+  x[v] = make_float4(o[0], o[1], o[2], o[3]);
+}
+
+// ------------------------------- coarsening --------------------------------
+// Handshake heavy-edge matching round: every unmatched vertex of an active
+// problem proposes to its unmatched neighbour with the largest cost, ties by
+// the smaller hash of the (local) pair and then the smaller id.
+__global__ void k_propose(const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                          const float* __restrict__ acost, int64_t K, const int32_t* __restrict__ vprob,
+                          const ProbDev* __restrict__ prob, const int32_t* __restrict__ active,
+                          const uint64_t* __restrict__ seeds, int level, int round, const int32_t* __restrict__ mate,
+                          int32_t* __restrict__ prop) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= K) return;
+  int pb = vprob[v];
+  int32_t best = -1;
+  if (active[pb] && mate[v] < 0) {
+    int64_t vb = prob[pb].vbase;
+    uint64_t seed = seeds[pb] ^ kTagMatch;
+    uint64_t b = (uint64_t)level * 256 + (uint64_t)round;
+    float bc = 0.f;
+    uint64_t bh = 0;
+    for (int32_t t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) {
+      int32_t u = adj[t];
+      if (u == v || mate[u] >= 0) continue;
+      uint64_t lu = (uint64_t)(u - vb), lv = (uint64_t)(v - vb);
+      uint64_t lo = lu < lv ? lu : lv, hi = lu < lv ? lv : lu;
+      uint64_t h = rand64(seed, (lo << 32) | hi, b);
+      float c = acost ? acost[t] : 1.0f;
+      bool better = best < 0 || c > bc || (c == bc && (h < bh || (h == bh && u < best)));
+      if (better) { best = u; bc = c; bh = h; }
+    }
+  }
+  prop[v] = best;
+}
+
+__global__ void k_resolve(const int32_t* __restrict__ prop, int64_t K, int32_t* __restrict__ mate) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= K) return;
+  int32_t u = prop[v];
+  if (u >= 0 && prop[u] == v) mate[v] = u;
+}
+
+__global__ void k_anchor(const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj, int64_t K,
+                         const int32_t* __restrict__ mate, int32_t* __restrict__ anchor, int32_t* __restrict__ isanc) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= K) return;
+  int32_t mv = mate[v];
+  int32_t a = mv >= 0 ? min((int32_t)v, mv) : (int32_t)v;
+  if (mv < 0 && adj_ptr[v + 1] - adj_ptr[v] == 1) {
+    int32_t u = adj[adj_ptr[v]];
+    if (u != v) {
+      int32_t mu = mate[u];
+      a = mu >= 0 ? min(u, mu) : u;
+    }
+  }
+  anchor[v] = a;
+  isanc[a] = 1;
+}
+
+__global__ void k_kc(const int32_t* __restrict__ rank, const int32_t* __restrict__ total, const int64_t* __restrict__ vb,
+                     int P, int64_t K, int64_t* __restrict__ kc) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  int64_t a = vb[p], b = vb[p + 1];
+  int64_t ra = a < K ? rank[a] : *total;
+  int64_t rb = b < K ? rank[b] : *total;
+  kc[p] = rb - ra;
+}
+
+__global__ void k_pi(const int32_t* __restrict__ anchor, const int32_t* __restrict__ rank, int64_t K,
+                     const int32_t* __restrict__ vprob, const ProbDev* __restrict__ prob,
+                     const int64_t* __restrict__ newbase, int32_t* __restrict__ pi) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= K) return;
+  int pb = vprob[v];
+  int64_t nb = newbase[pb];
+  pi[v] = nb >= 0 ? (int32_t)(nb + rank[anchor[v]] - rank[prob[pb].vbase]) : -1;
+}
+
+__global__ void k_contract_keys(const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                                const float* __restrict__ acost, int64_t K, const int32_t* __restrict__ pi,
+                                uint64_t Kc, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= K) return;
+  int32_t a = pi[v];
+  uint64_t sentinel = Kc * Kc;
+  for (int32_t t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) {
+    int32_t b = a >= 0 ? pi[adj[t]] : -1;
+    keys[t] = (a >= 0 && b >= 0 && a != b) ? (uint64_t)a * Kc + (uint64_t)b : sentinel;
+    vals[t] = __float_as_uint(acost ? acost[t] : 1.0f);
+  }
+}
+
+__global__ void k_run_flags(const uint64_t* __restrict__ keys, int64_t n, uint64_t sentinel, int32_t* __restrict__ flag) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  uint64_t k = keys[t];
+  flag[t] = (k != sentinel && (t == 0 || keys[t - 1] != k)) ? 1 : 0;
+}
+
+__global__ void k_emit_coarse(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n,
+                              const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, uint64_t Kc,
+                              int32_t* __restrict__ adj, float* __restrict__ acost, int32_t* __restrict__ rowcount) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n || !flag[t]) return;
+  uint64_t k = keys[t];
+  float c = 0.f;
+  for (int64_t u = t; u < n && keys[u] == k; ++u) c += __uint_as_float(vals[u]);
+  adj[pos[t]] = (int32_t)(k % Kc);
+  acost[pos[t]] = c;
+  atomicAdd(&rowcount[k / Kc], 1);
+}
+
+__global__ void k_coarse_w(const float* __restrict__ w, const int32_t* __restrict__ pi, int64_t K,
+                           float* __restrict__ wc) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= K) return;
+  int32_t a = pi[v];
+  if (a >= 0) atomicAdd(&wc[a], w ? w[v] : 1.0f);
+}
+
+__global__ void k_fill_vprob(const int64_t* __restrict__ vb, int P, int64_t K, int32_t* __restrict__ vprob) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= K) return;
+  vprob[v] = find_problem(vb, P, v);
+}
+
+__global__ void k_set_last(int32_t* ptr, int64_t n, const int32_t* total) { ptr[n] = *total; }
+
+template <class F>
+void dispatch_d(int d, F&& f) {
+  if (d == 2) f(std::integral_constant<int, 2>());
+  else if (d == 3) f(std::integral_constant<int, 3>());
+  else f(std::integral_constant<int, 4>());
+}
+
+int lmax(int d) { return d == 2 ? 15 : (d == 3 ? 10 : 7); }
+
+}  // namespace
+
+int grid_levels(int64_t k, int d, int occ) {
+  int L = 1;
+  while (L < lmax(d) && (int64_t)occ * (int64_t(1) << (d * L)) < k) ++L;
+  return L;
+}
+
+int init_side(int64_t k, int d) {
+  int64_t s = 1;
+  for (;;) {
+    int64_t p = 1;
+    for (int i = 0; i < d; ++i) p *= s;
+    if (p >= k) return (int)s;
+    ++s;
+  }
+}
+
+vmo_status level_setup(LevelBatch& lb, int d, int occ, cudaStream_t s) {
+  const int P = lb.P;
+  lb.L.assign(P, 1);
+  lb.cbase.assign(P + 1, 0);
+  lb.fbase.assign(P + 1, 0);
+  std::vector<ProbDev> pd(P);
+  lb.maxL = 1;
+  for (int p = 0; p < P; ++p) {
+    int64_t k = lb.vbase[p + 1] - lb.vbase[p];
+    int L = grid_levels(k, d, occ);
+    lb.L[p] = L;
+    lb.maxL = std::max(lb.maxL, L);
+    lb.cbase[p + 1] = lb.cbase[p] + lvl_off(d, L + 1);
+    lb.fbase[p + 1] = lb.fbase[p] + (int64_t(1) << (d * L));
+    pd[p].vbase = lb.vbase[p];
+    pd[p].cbase = lb.cbase[p];
+    pd[p].fbase = lb.fbase[p];
+    pd[p].k = (int32_t)k;
+    pd[p].L = L;
+    pd[p].side = init_side(std::max<int64_t>(k, 1), d);
+    pd[p].pad = 0;
+  }
+  // prefix tables of the coarse-level aggregation steps: step s covers level L_p - s >= 2
+  int nsteps = std::max(lb.maxL - 2, 0);
+  std::vector<int64_t> off((size_t)(nsteps + 1) * (P + 1), 0);
+  for (int st = 1; st <= nsteps; ++st)
+    for (int p = 0; p < P; ++p) {
+      int l = lb.L[p] - st;
+      int64_t cnt = l >= 2 ? (int64_t(1) << (d * l)) : 0;
+      off[(size_t)st * (P + 1) + p + 1] = off[(size_t)st * (P + 1) + p] + cnt;
+    }
+  VMO_TRY(lb.prob.resize(std::max(P, 1)));
+  VMO_TRY(lb.aggoff.resize(off.size()));
+  VMO_TRY(lb.vprob.resize((size_t)std::max<int64_t>(lb.K, 1)));
+  VMO_CUDA(cudaMemcpyAsync(lb.prob.ptr, pd.data(), P * sizeof(ProbDev), cudaMemcpyHostToDevice, s));
+  VMO_CUDA(cudaMemcpyAsync(lb.aggoff.ptr, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  int64_t* vb;
+  VMO_CUDA(cudaMallocAsync((void**)&vb, (P + 1) * sizeof(int64_t), s));
+  VMO_CUDA(cudaMemcpyAsync(vb, lb.vbase.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  if (lb.K > 0) {
+    k_fill_vprob<<<grid_for(lb.K, kBlock), kBlock, 0, s>>>(vb, P, lb.K, lb.vprob.ptr);
+    VMO_LAUNCHED("fill_vprob");
+  }
+  VMO_CUDA(cudaFreeAsync(vb, s));
+  // host vectors must outlive the copies
+  VMO_CUDA(cudaStreamSynchronize(s));
+  return VMO_OK;
+}
+
+vmo_status init_coords_level(LevelBatch& lb, int d, const uint64_t* seeds_dev, float4* x, const int32_t* start_dev,
+                             cudaStream_t s) {
+  if (lb.K == 0) return VMO_OK;
+  k_init_coords<<<grid_for(lb.K, kBlock), kBlock, 0, s>>>(lb.K, lb.vprob.ptr, lb.prob.ptr, seeds_dev, start_dev, d, x);
+  VMO_LAUNCHED("init_coords");
+  return VMO_OK;
+}
+
+vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int iters, float step_override,
+                        float4* y_out, uint32_t* keys_out, cudaStream_t s, Scratch& sc) {
+  const int64_t K = lb.K;
+  const int P = lb.P;
+  const int d = o.d;
+  if (K == 0 || iters <= 0) return VMO_OK;
+  ScratchFrame frame(sc);
+  uint32_t *keys, *vals, *skeys, *svals, *scell, *bb;
+  float4 *xs, *yatt, *St, *CW, *z = nullptr;
+  float *ws = nullptr, *Wt, *s0;
+  int2* cse;
+  int64_t *fb;
+  const int64_t ncell = lb.cbase[P], nfine = lb.fbase[P];
+  VMO_TRY(sc.alloc(&keys, K));
+  VMO_TRY(sc.alloc(&vals, K));
+  VMO_TRY(sc.alloc(&skeys, K));
+  VMO_TRY(sc.alloc(&svals, K));
+  VMO_TRY(sc.alloc(&scell, K));
+  VMO_TRY(sc.alloc(&xs, K));
+  VMO_TRY(sc.alloc(&yatt, K));
+  if (lb.w) VMO_TRY(sc.alloc(&ws, K));
+  VMO_TRY(sc.alloc(&St, ncell));
+  VMO_TRY(sc.alloc(&CW, ncell));
+  VMO_TRY(sc.alloc(&Wt, ncell));
+  VMO_TRY(sc.alloc(&cse, nfine));
+  VMO_TRY(sc.alloc(&bb, (size_t)2 * 8 * P));
+  VMO_TRY(sc.alloc(&s0, P));
+  VMO_TRY(sc.alloc(&fb, P + 1));
+  if (lb.net_ptr) VMO_TRY(sc.alloc(&z, std::max<int64_t>(lb.nnets, 1)));
+  VMO_CUDA(cudaMemcpyAsync(fb, lb.fbase.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  SortSegments segs;
+  bool segmented = P > 1;
+  if (segmented) VMO_TRY(make_sort_segments(lb.vbase, &segs, s, sc));
+  const int nreset = 8 * P;
+  k_bbox_reset<<<grid_for(16 * P, kBlock), kBlock, 0, s>>>(bb, 16 * P);
+  VMO_LAUNCHED("bbox_reset");
+  const float kappa = d == 2 ? 1.0f : (float)(d - 2);
+  vmo_status st = VMO_OK;
+  dispatch_d(d, [&](auto DC) {
+    constexpr int D = decltype(DC)::value;
+    k_bbox<D><<<grid_for(K, kBlock), kBlock, 0, s>>>(x, K, lb.vprob.ptr, bb);
+    k_step0<D><<<grid_for(P, kBlock), kBlock, 0, s>>>(bb, lb.prob.ptr, P, o.sigma, s0);
+    double scale = 1.0;
+    for (int t = 0; t < iters && st == VMO_OK; ++t) {
+      ScratchFrame f2(sc);
+      uint32_t* cur = bb + (t & 1) * 8 * P;
+      uint32_t* nxt = bb + ((t + 1) & 1) * 8 * P;
+      k_keys<D><<<grid_for(std::max<int64_t>(K, nreset), kBlock), kBlock, 0, s>>>(x, K, lb.vprob.ptr, lb.prob.ptr,
+                                                                                  cur, keys, vals, nxt, nreset);
+      if (keys_out && t == 0) cudaMemcpyAsync(keys_out, keys, K * 4, cudaMemcpyDeviceToDevice, s);
+      st = radix_sort_u32(keys, vals, skeys, svals, K, D * lb.maxL, segmented ? &segs : nullptr, s, sc);
+      if (st != VMO_OK) break;
+      cudaMemsetAsync(cse, 0, nfine * sizeof(int2), s);
+      k_gather<D><<<grid_for(K, kBlock), kBlock, 0, s>>>(skeys, svals, K, x, lb.w, lb.vprob.ptr, lb.prob.ptr, cur,
+                                                         xs, ws, scell, cse);
+      k_agg_finest<D><<<grid_for(nfine, kBlock), kBlock, 0, s>>>(cse, nfine, fb, P, lb.prob.ptr, xs, ws, St, Wt, CW);
+      for (int stp = 1; stp <= lb.maxL - 2; ++stp) {
+        const int64_t* off = lb.aggoff.ptr + (size_t)stp * (P + 1);
+        int64_t n = 0;
+        for (int p = 0; p < P; ++p) {
+          int l = lb.L[p] - stp;
+          n += l >= 2 ? (int64_t(1) << (D * l)) : 0;
+        }
+        if (n == 0) continue;
+        k_agg_level<D><<<grid_for(n, kBlock), kBlock, 0, s>>>(stp, off, P, n, lb.prob.ptr, St, Wt, CW);
+      }
+      if (lb.adj_ptr) {
+        k_attract<<<grid_for(K, kBlock), kBlock, 0, s>>>(lb.adj_ptr, lb.adj, lb.acost, x, K, yatt);
+      } else if (lb.net_ptr) {
+        if (lb.nnets > 0) k_net_center<<<grid_for(lb.nnets, kBlock), kBlock, 0, s>>>(lb.net_ptr, lb.pins, lb.nnets, x, z);
+        k_attract_hyper<<<grid_for(K, kBlock), kBlock, 0, s>>>(lb.vtx_ptr, lb.vnets, x, z, K, yatt);
+      } else {
+        cudaMemsetAsync(yatt, 0, K * sizeof(float4), s);
+      }
+      k_repulse_update<D><<<grid_for(K, kBlock), kBlock, 0, s>>>(xs, ws, svals, scell, cse, CW, Wt, yatt, lb.vprob.ptr,
+                                                                 lb.prob.ptr, K, kappa, s0, (float)scale,
+                                                                 step_override, x, y_out, nxt);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) st = cuda_fail(e, "layout step", __FILE__, __LINE__);
+      scale *= o.decay;
+    }
+  });
+  return st;
+}
+
+vmo_status coarsen_level(LevelBatch& lb, const uint64_t* seeds_dev, int j, int rounds, const int32_t* active_dev,
+                         int32_t* mate, int32_t* anchor, int32_t* rank, std::vector<int64_t>& kc, cudaStream_t s,
+                         Scratch& sc) {
+  const int64_t K = lb.K;
+  const int P = lb.P;
+  ScratchFrame frame(sc);
+  int32_t *prop, *isanc, *total;
+  int64_t *kcd, *vb;
+  VMO_TRY(sc.alloc(&prop, K));
+  VMO_TRY(sc.alloc(&isanc, K));
+  VMO_TRY(sc.alloc(&total, 1));
+  VMO_TRY(sc.alloc(&kcd, P));
+  VMO_TRY(sc.alloc(&vb, P + 1));
+  VMO_CUDA(cudaMemcpyAsync(vb, lb.vbase.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  VMO_CUDA(cudaMemsetAsync(mate, 0xFF, K * sizeof(int32_t), s));
+  VMO_CUDA(cudaMemsetAsync(isanc, 0, K * sizeof(int32_t), s));
+  for (int r = 0; r < rounds; ++r) {
+    k_propose<<<grid_for(K, kBlock), kBlock, 0, s>>>(lb.adj_ptr, lb.adj, lb.acost, K, lb.vprob.ptr, lb.prob.ptr,
+                                                     active_dev, seeds_dev, j, r, mate, prop);
+    k_resolve<<<grid_for(K, kBlock), kBlock, 0, s>>>(prop, K, mate);
+  }
+  k_anchor<<<grid_for(K, kBlock), kBlock, 0, s>>>(lb.adj_ptr, lb.adj, K, mate, anchor, isanc);
+  VMO_LAUNCHED("matching");
+  VMO_TRY(scan_exclusive<int32_t>(isanc, rank, K, total, s, sc));
+  k_kc<<<grid_for(P, kBlock), kBlock, 0, s>>>(rank, total, vb, P, K, kcd);
+  VMO_LAUNCHED("kc");
+  kc.resize(P);
+  VMO_CUDA(cudaMemcpyAsync(kc.data(), kcd, P * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  VMO_CUDA(cudaStreamSynchronize(s));
+  return VMO_OK;
+}
+
+// Builds the next (coarser) level from level `lb` for the problems with
+// newbase[p] >= 0 (host), using the grouping (anchor, rank).
+static vmo_status contract_level(LevelBatch& lb, const std::vector<int64_t>& newbase, int64_t Kc, const int32_t* anchor,
+                                 const int32_t* rank, int32_t* pi, LevelBatch& out, cudaStream_t s, Scratch& sc) {
+  const int64_t K = lb.K;
+  const int P = lb.P;
+  ScratchFrame frame(sc);
+  int64_t* nb;
+  VMO_TRY(sc.alloc(&nb, P));
+  VMO_CUDA(cudaMemcpyAsync(nb, newbase.data(), P * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  k_pi<<<grid_for(K, kBlock), kBlock, 0, s>>>(anchor, rank, K, lb.vprob.ptr, lb.prob.ptr, nb, pi);
+  VMO_LAUNCHED("pi");
+  const int64_t n = lb.nadj;
+  uint64_t *keys, *skeys;
+  uint32_t *vals, *svals;
+  int32_t *flag, *pos, *total;
+  VMO_TRY(sc.alloc(&keys, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&skeys, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&vals, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&svals, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&flag, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&pos, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&total, 1));
+  const uint64_t sentinel = (uint64_t)Kc * (uint64_t)Kc;
+  k_contract_keys<<<grid_for(K, kBlock), kBlock, 0, s>>>(lb.adj_ptr, lb.adj, lb.acost, K, pi, (uint64_t)Kc, keys, vals);
+  VMO_LAUNCHED("contract_keys");
+  VMO_TRY(radix_sort_u64(keys, vals, skeys, svals, n, bits_for(sentinel), s, sc));
+  if (n > 0) {
+    k_run_flags<<<grid_for(n, kBlock), kBlock, 0, s>>>(skeys, n, sentinel, flag);
+    VMO_LAUNCHED("run_flags");
+  }
+  VMO_TRY(scan_exclusive<int32_t>(flag, pos, n, total, s, sc));
+  int32_t nadj_c = 0;
+  VMO_CUDA(cudaMemcpyAsync(&nadj_c, total, 4, cudaMemcpyDeviceToHost, s));
+  VMO_CUDA(cudaStreamSynchronize(s));
+  VMO_TRY(out.own_adj_ptr.resize((size_t)Kc + 1));
+  VMO_TRY(out.own_adj.resize(std::max<int32_t>(nadj_c, 1)));
+  VMO_TRY(out.own_acost.resize(std::max<int32_t>(nadj_c, 1)));
+  VMO_TRY(out.own_w.resize((size_t)std::max<int64_t>(Kc, 1)));
+  VMO_CUDA(cudaMemsetAsync(out.own_adj_ptr.ptr, 0, (Kc + 1) * sizeof(int32_t), s));
+  VMO_CUDA(cudaMemsetAsync(out.own_w.ptr, 0, std::max<int64_t>(Kc, 1) * sizeof(float), s));
+  if (n > 0) {
+    k_emit_coarse<<<grid_for(n, kBlock), kBlock, 0, s>>>(skeys, svals, n, flag, pos, (uint64_t)Kc, out.own_adj.ptr,
+                                                         out.own_acost.ptr, out.own_adj_ptr.ptr);
+    VMO_LAUNCHED("emit_coarse");
+  }
+  VMO_TRY(scan_exclusive<int32_t>(out.own_adj_ptr.ptr, out.own_adj_ptr.ptr, Kc, total, s, sc));
+  k_set_last<<<1, 1, 0, s>>>(out.own_adj_ptr.ptr, Kc, total);
+  k_coarse_w<<<grid_for(K, kBlock), kBlock, 0, s>>>(lb.w, pi, K, out.own_w.ptr);
+  VMO_LAUNCHED("coarse_w");
+  out.K = Kc;
+  out.adj_ptr = out.own_adj_ptr.ptr;
+  out.adj = out.own_adj.ptr;
+  out.acost = out.own_acost.ptr;
+  out.w = out.own_w.ptr;
+  out.nadj = nadj_c;
+  return VMO_OK;
+}
+
+vmo_status build_hierarchy(LevelBatch& fine, const LayoutOptions& o, const std::vector<uint64_t>& seeds,
+                           int match_rounds, int coarse_min, bool multilevel, Hierarchy& H, cudaStream_t s,
+                           Scratch& sc) {
+  std::vector<LevelBatch*>& levels = H.levels;
+  std::vector<std::unique_ptr<LevelBatch>>& owned = H.owned;
+  std::vector<int32_t*>& pis = H.pis;
+  std::vector<std::vector<uint64_t>>& lseeds = H.seeds;
+  levels.push_back(&fine);
+  lseeds.push_back(seeds);
+  const bool graph = fine.adj_ptr != nullptr;
+  while (multilevel && graph && levels.size() < 41) {
+    LevelBatch& cur = *levels.back();
+    const int P = cur.P;
+    std::vector<int32_t> active(P);
+    bool any = false;
+    for (int p = 0; p < P; ++p) {
+      active[p] = (cur.vbase[p + 1] - cur.vbase[p]) > coarse_min ? 1 : 0;
+      any = any || active[p];
+    }
+    if (!any) break;
+    int32_t *act, *mate, *anchor, *rank, *pi;
+    uint64_t* sd;
+    VMO_TRY(sc.alloc(&act, P));
+    VMO_TRY(sc.alloc(&sd, P));
+    VMO_TRY(sc.alloc(&mate, cur.K));
+    VMO_TRY(sc.alloc(&anchor, cur.K));
+    VMO_TRY(sc.alloc(&rank, cur.K));
+    VMO_TRY(sc.alloc(&pi, cur.K));
+    VMO_CUDA(cudaMemcpyAsync(act, active.data(), P * 4, cudaMemcpyHostToDevice, s));
+    VMO_CUDA(cudaMemcpyAsync(sd, lseeds.back().data(), P * 8, cudaMemcpyHostToDevice, s));
+    std::vector<int64_t> kc;
+    VMO_TRY(coarsen_level(cur, sd, (int)levels.size() - 1, match_rounds, act, mate, anchor, rank, kc, s, sc));
+    std::vector<int64_t> newbase(P, -1);
+    auto nxt = std::make_unique<LevelBatch>();
+    nxt->vbase.push_back(0);
+    std::vector<uint64_t> nseeds;
+    for (int p = 0; p < P; ++p) {
+      int64_t k = cur.vbase[p + 1] - cur.vbase[p];
+      if (!active[p] || (double)kc[p] > 0.95 * (double)k) continue;
+      newbase[p] = nxt->vbase.back();
+      nxt->vbase.push_back(nxt->vbase.back() + kc[p]);
+      nxt->src.push_back(cur.src[p]);
+      nseeds.push_back(lseeds.back()[p]);
+    }
+    nxt->P = (int32_t)nxt->src.size();
+    if (nxt->P == 0) break;
+    int64_t Kc = nxt->vbase.back();
+    VMO_TRY(contract_level(cur, newbase, Kc, anchor, rank, pi, *nxt, s, sc));
+    VMO_TRY(level_setup(*nxt, o.d, o.occupancy, s));
+    pis.push_back(pi);
+    levels.push_back(nxt.get());
+    lseeds.push_back(nseeds);
+    owned.push_back(std::move(nxt));
+  }
+  return VMO_OK;
+}
+
+vmo_status layout_multilevel(LevelBatch& fine, const LayoutOptions& o, const std::vector<uint64_t>& seeds,
+                             int match_rounds, int coarse_min, bool multilevel, float4* x, cudaStream_t s,
+                             Scratch& sc) {
+  Hierarchy H;
+  VMO_TRY(build_hierarchy(fine, o, seeds, match_rounds, coarse_min, multilevel, H, s, sc));
+  std::vector<LevelBatch*>& levels = H.levels;
+  std::vector<int32_t*>& pis = H.pis;
+  std::vector<std::vector<uint64_t>>& lseeds = H.seeds;
+  // layout from the coarsest level down
+  const int nl = (int)levels.size();
+  float4* xc = nullptr;
+  for (int j = nl - 1; j >= 0; --j) {
+    LevelBatch& cur = *levels[j];
+    const int P = cur.P;
+    float4* xj = (j == 0) ? x : nullptr;
+    if (!xj) VMO_TRY(sc.alloc(&xj, std::max<int64_t>(cur.K, 1)));
+    // which problems of this level start here (not present one level up)
+    std::vector<int32_t> start(P, 1);
+    std::vector<float> fac(P, -1.0f);
+    if (j + 1 < nl) {
+      const LevelBatch& up = *levels[j + 1];
+      size_t q = 0;
+      for (int p = 0; p < P && q < up.src.size(); ++p) {
+        if (cur.src[p] == up.src[q]) {
+          start[p] = 0;
+          double kf = (double)(cur.vbase[p + 1] - cur.vbase[p]);
+          double kcq = (double)(up.vbase[q + 1] - up.vbase[q]);
+          fac[p] = (float)std::pow(kf / kcq, 1.0 / o.d);
+          ++q;
+        }
+      }
+    }
+    int32_t* st;
+    float* fc;
+    uint64_t* sd;
+    VMO_TRY(sc.alloc(&st, P));
+    VMO_TRY(sc.alloc(&fc, P));
+    VMO_TRY(sc.alloc(&sd, P));
+    VMO_CUDA(cudaMemcpyAsync(st, start.data(), P * 4, cudaMemcpyHostToDevice, s));
+    VMO_CUDA(cudaMemcpyAsync(fc, fac.data(), P * 4, cudaMemcpyHostToDevice, s));
+    VMO_CUDA(cudaMemcpyAsync(sd, lseeds[j].data(), P * 8, cudaMemcpyHostToDevice, s));
+    VMO_TRY(init_coords_level(cur, o.d, sd, xj, st, s));
+    if (xc) {
+      k_prolong<<<grid_for(cur.K, kBlock), kBlock, 0, s>>>(xc, pis[j], cur.K, cur.vprob.ptr, cur.prob.ptr, fc, sd, j,
+                                                           o.d, xj);
+      VMO_LAUNCHED("prolong");
+    }
+    VMO_TRY(layout_level(cur, o, xj, o.iters, -1.0f, nullptr, nullptr, s, sc));
+    VMO_CUDA(cudaStreamSynchronize(s));  // host vectors above must outlive the copies
+    xc = xj;
+  }
+  return VMO_OK;
+}
+
+}  // namespace vmo

@@ -1,0 +1,697 @@
+// Recursive geometric bisection (Sec. 3 and 4.2): 2-means by k-means++
+// (Algorithm 5, m = 2), vertex separator (Algorithm 7) and the recursive BBD /
+// SBD permutation.
+//
+// The recursion is processed level by level: every active node of every
+// problem of a batch is handled by the same launches.  Nodes are identified by
+// their heap number (root 1, children 2h and 2h+1), which keys the k-means++
+// draws, so a node's result does not depend on which other nodes share its
+// launches or on their order in the node table.
+//
+// Exactness: every floating point decision (nearest centre, plane distance)
+// is made in fp32 with explicitly rounded intrinsics in a fixed order; the
+// centre of a cluster is the mean of its points summed exactly in 64-bit
+// fixed point; the D^2 sampling of k-means++ uses exact integer prefix sums.
+// Given the same coordinates the result is bit-identical to a sequential
+// implementation of the same arithmetic.
+#include <algorithm>
+
+#include "order.cuh"
+
+namespace vmo {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+// Exponent e with max |x| < 2^e (0 for max = 0) from the ordered bits of the max.
+__device__ inline int exponent_of(uint32_t maxbits) {
+  float mx = __uint_as_float(maxbits);
+  if (mx == 0.0f) return 0;
+  int e;
+  frexpf(mx, &e);
+  return e;
+}
+
+template <int D>
+__device__ inline float plane_dist(const float4& x, const float4& r, float delta) {
+  float acc = 0.0f;
+#pragma unroll
+  for (int m = 0; m < D; ++m) acc = __fadd_rn(acc, __fmul_rn(comp(x, m), comp(r, m)));
+  return fabsf(__fsub_rn(acc, delta));
+}
+
+template <int D>
+__device__ inline void plane_of(const float4& z1, const float4& z2, float4* r, float* delta) {
+  float rr[4] = {0.f, 0.f, 0.f, 0.f};
+  float dl = 0.0f;
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    rr[m] = __fsub_rn(comp(z2, m), comp(z1, m));
+    float mid = __fmul_rn(0.5f, __fadd_rn(comp(z1, m), comp(z2, m)));
+    dl = __fadd_rn(dl, __fmul_rn(mid, rr[m]));
+  }
+  *r = make_float4(rr[0], rr[1], rr[2], rr[3]);
+  *delta = dl;
+}
+
+// Warp sum of a 64-bit value.
+__device__ inline unsigned long long warp_sum64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void k_node_reset(NodeDev* __restrict__ nodes, int N) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  NodeDev& nd = nodes[s];
+  nd.maxabs = 0u;
+  nd.state = 0;
+  nd.changed = 0;
+  for (int m = 0; m < 4; ++m) { nd.S1[m] = 0; nd.S2[m] = 0; }
+  nd.n1 = nd.n2 = 0;
+  nd.c1 = nd.c2 = nd.c3 = 0;
+  nd.child1 = nd.child2 = -1;
+}
+
+template <int D>
+__global__ void k_maxabs(const float4* __restrict__ xo, const int32_t* __restrict__ seg, int64_t n,
+                         NodeDev* __restrict__ nodes) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int s = i < n ? seg[i] : -1;
+  uint32_t mx = 0;
+  if (s >= 0) {
+    float4 x = xo[i];
+#pragma unroll
+    for (int m = 0; m < D; ++m) mx = max(mx, __float_as_uint(fabsf(comp(x, m))));
+  }
+  unsigned peers = __match_any_sync(0xffffffffu, s);
+  uint32_t wm = __reduce_max_sync(peers, mx);
+  if (s >= 0 && (int)lane_id() == __ffs(peers) - 1) atomicMax(&nodes[s].maxabs, wm);
+}
+
+// k-means++ first centre: point floor(size * r0 / 2^64) of the node.
+__global__ void k_seed1(NodeDev* __restrict__ nodes, int N, const float4* __restrict__ xo,
+                        const uint64_t* __restrict__ seeds) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  NodeDev& nd = nodes[s];
+  nd.e = exponent_of(nd.maxabs);
+  uint64_t r0 = rand64(seeds[nd.prob] ^ kTagKmeans, nd.heap, 0);
+  uint64_t i0 = scale_draw((uint64_t)nd.size, r0);
+  nd.z1 = xo[nd.off + (int64_t)i0];
+}
+
+template <int D>
+__global__ void k_dsq(const float4* __restrict__ xo, const int32_t* __restrict__ seg, int64_t n,
+                      const NodeDev* __restrict__ nodes, unsigned long long* __restrict__ dval) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int s = seg[i];
+  unsigned long long v = 0;
+  if (s >= 0) {
+    const NodeDev& nd = nodes[s];
+    float dd = sqdist32<D>(xo[i], nd.z1);
+    float sc = __fmul_rn(dd, exp2i_f(34 - 2 * nd.e));
+    v = (unsigned long long)floorf(sc);
+  }
+  dval[i] = v;
+}
+
+// Second centre: the first point whose inclusive prefix of D exceeds
+// floor(total * r1 / 2^64); a node whose total is 0 is not split.
+template <int D>
+__global__ void k_seed2(const float4* __restrict__ xo, const int32_t* __restrict__ seg, int64_t n,
+                        const unsigned long long* __restrict__ dval, const unsigned long long* __restrict__ dpre,
+                        NodeDev* __restrict__ nodes, const uint64_t* __restrict__ seeds) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int s = seg[i];
+  if (s < 0) return;
+  NodeDev& nd = nodes[s];
+  unsigned long long base = nd.off > 0 ? dpre[nd.off - 1] : 0ull;
+  unsigned long long total = dpre[nd.off + nd.size - 1] - base;
+  if (total == 0) {
+    if (i == nd.off) nd.state = 2;
+    return;
+  }
+  uint64_t r1 = rand64(seeds[nd.prob] ^ kTagKmeans, nd.heap, 1);
+  unsigned long long thr = scale_draw(total, r1);
+  unsigned long long pre = dpre[i] - base;
+  unsigned long long prev = pre - dval[i];
+  if (prev <= thr && thr < pre) nd.z2 = xo[i];
+}
+
+// One Lloyd assignment: label 1 iff ||x - z1||^2 <= ||x - z2||^2 (fp32),
+// change detection against the previous labels, and exact fixed-point sums
+// q(x) = rint(x * 2^P), P = 30 - e, of each cluster.
+template <int D>
+__global__ void k_assign(const float4* __restrict__ xo, const int32_t* __restrict__ seg, int64_t n, int it,
+                         NodeDev* __restrict__ nodes, uint8_t* __restrict__ lab, int final_pass) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int s = i < n ? seg[i] : -1;
+  bool act = false;
+  uint8_t l = 0;
+  long long q[4] = {0, 0, 0, 0};
+  if (s >= 0) {
+    NodeDev& nd = nodes[s];
+    int st = nd.state;
+    act = final_pass ? (st != 2) : (st == 0);
+    if (act) {
+      float4 x = xo[i];
+      l = (sqdist32<D>(x, nd.z1) <= sqdist32<D>(x, nd.z2)) ? 1 : 2;
+      if (!final_pass) {
+        if (it > 0 && l != lab[i]) nd.changed = 1;
+        float sc = exp2i_f(30 - nd.e);
+#pragma unroll
+        for (int m = 0; m < D; ++m) q[m] = __float2ll_rn(__fmul_rn(comp(x, m), sc));
+      }
+      lab[i] = l;
+    }
+  }
+  // warp-aggregated accumulation per (node, label)
+  int key = act ? s * 2 + (l - 1) : -1;
+  unsigned peers = __match_any_sync(0xffffffffu, key);
+  if (key < 0) return;
+  int leader = __ffs(peers) - 1;
+  unsigned long long cnt = __popc(peers);
+  unsigned long long sum[4] = {0, 0, 0, 0};
+  if (!final_pass) {
+    if (peers == 0xffffffffu) {
+#pragma unroll
+      for (int m = 0; m < D; ++m) sum[m] = warp_sum64((unsigned long long)q[m]);
+    } else {
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        unsigned long long acc = 0;
+        for (unsigned b = peers; b; b &= b - 1) {
+          int src = __ffs(b) - 1;
+          acc += (unsigned long long)__shfl_sync(peers, (unsigned long long)q[m], src);
+        }
+        sum[m] = acc;
+      }
+    }
+  }
+  if ((int)lane_id() != leader) return;
+  NodeDev& nd = nodes[s];
+  if (final_pass) {
+    atomicAdd((unsigned long long*)(l == 1 ? &nd.n1 : &nd.n2), cnt);
+    return;
+  }
+  unsigned long long* S = (unsigned long long*)(l == 1 ? nd.S1 : nd.S2);
+#pragma unroll
+  for (int m = 0; m < D; ++m) atomicAdd(&S[m], sum[m]);
+  atomicAdd((unsigned long long*)(l == 1 ? &nd.n1 : &nd.n2), cnt);
+}
+
+// Centre update: z = fp32((double(sum) / count) * 2^-P); a node whose labels
+// did not change is converged.
+template <int D>
+__global__ void k_update(NodeDev* __restrict__ nodes, int N, int it) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  NodeDev& nd = nodes[s];
+  if (nd.state != 0) return;
+  if (it > 0 && !nd.changed) {
+    nd.state = 1;
+  } else {
+    double inv = __longlong_as_double((long long)(1023 - (30 - nd.e)) << 52);  // 2^-P
+    float z1[4] = {nd.z1.x, nd.z1.y, nd.z1.z, nd.z1.w};
+    float z2[4] = {nd.z2.x, nd.z2.y, nd.z2.z, nd.z2.w};
+    for (int m = 0; m < D; ++m) {
+      if (nd.n1 > 0) z1[m] = __double2float_rn(__dmul_rn(__ddiv_rn(__ll2double_rn(nd.S1[m]), (double)nd.n1), inv));
+      if (nd.n2 > 0) z2[m] = __double2float_rn(__dmul_rn(__ddiv_rn(__ll2double_rn(nd.S2[m]), (double)nd.n2), inv));
+    }
+    nd.z1 = make_float4(z1[0], z1[1], z1[2], z1[3]);
+    nd.z2 = make_float4(z2[0], z2[1], z2[2], z2[3]);
+  }
+  nd.changed = 0;
+  for (int m = 0; m < 4; ++m) { nd.S1[m] = 0; nd.S2[m] = 0; }
+  nd.n1 = nd.n2 = 0;
+}
+
+__global__ void k_count_active(const NodeDev* __restrict__ nodes, int N, int* __restrict__ out) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < N && nodes[s].state == 0) atomicAdd(out, 1);
+}
+
+__global__ void k_clear_counts(NodeDev* __restrict__ nodes, int N) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  nodes[s].n1 = nodes[s].n2 = 0;
+}
+
+// Per-vertex copies of the final 2-means label and plane distance, used by
+// the separator to look at neighbours.
+template <int D>
+__global__ void k_vertex_state(const float4* __restrict__ xo, const int32_t* __restrict__ ord,
+                               const int32_t* __restrict__ seg, int64_t n, const NodeDev* __restrict__ nodes,
+                               const uint8_t* __restrict__ lab, uint8_t* __restrict__ vlab, float* __restrict__ vs) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int s = seg[i];
+  if (s < 0) return;
+  const NodeDev& nd = nodes[s];
+  int32_t v = ord[i];
+  bool split = nd.state != 2 && nd.n1 > 0 && nd.n2 > 0;
+  vlab[v] = split ? lab[i] : 0;
+  float4 r;
+  float delta;
+  plane_of<D>(nd.z1, nd.z2, &r, &delta);
+  vs[v] = plane_dist<D>(xo[i], r, delta);
+}
+
+// Order-free form of the separator loop of Algorithm 7 (mu = identity):
+// v joins the separator iff a neighbour w in the same node carries the other
+// label and (s(v), v) < (s(w), w).
+__global__ void k_separator(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
+                            const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                            const int32_t* __restrict__ vnode, const uint8_t* __restrict__ vlab,
+                            const float* __restrict__ vs, NodeDev* __restrict__ nodes, uint8_t* __restrict__ labf) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int s = i < n ? seg[i] : -1;
+  uint8_t l = 0;
+  if (s >= 0) {
+    int32_t v = ord[i];
+    l = vlab[v];
+    if (l != 0) {
+      float sv = vs[v];
+      for (int32_t t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) {
+        int32_t w = adj[t];
+        if (vnode[w] != s) continue;
+        uint8_t lw = vlab[w];
+        if (lw == l || lw == 0) continue;
+        float sw = vs[w];
+        if (sv < sw || (sv == sw && v < w)) { l = 3; break; }
+      }
+    }
+    labf[i] = l;
+  }
+  int key = (l != 0) ? s * 4 + l : -1;
+  unsigned peers = __match_any_sync(0xffffffffu, key);
+  if (key >= 0 && (int)lane_id() == __ffs(peers) - 1) {
+    int* c = l == 1 ? &nodes[s].c1 : (l == 2 ? &nodes[s].c2 : &nodes[s].c3);
+    atomicAdd(c, (int)__popc(peers));
+  }
+}
+
+__global__ void k_pack(const int32_t* __restrict__ seg, const uint8_t* __restrict__ labf, int64_t n,
+                       const NodeDev* __restrict__ nodes, unsigned long long* __restrict__ pk) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int s = seg[i];
+  unsigned long long v = 0;
+  if (s >= 0) {
+    const NodeDev& nd = nodes[s];
+    if (nd.c1 + nd.c2 + nd.c3 > 0) {
+      uint8_t l = labf[i];
+      v = (l == 1) ? 1ull : (l == 2 ? (1ull << 32) : 0ull);
+    }
+  }
+  pk[i] = v;
+}
+
+// Stable partition of every split node into [V1, V2, V3] (BBD) or
+// [V1, V3, V2] (SBD); other positions are copied.
+__global__ void k_scatter(const int32_t* __restrict__ ord, const float4* __restrict__ xo,
+                          const int32_t* __restrict__ seg, const uint8_t* __restrict__ labf, int64_t n,
+                          const NodeDev* __restrict__ nodes, const unsigned long long* __restrict__ pre, int sbd,
+                          int32_t* __restrict__ ord2, float4* __restrict__ xo2, int32_t* __restrict__ segl2) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int s = seg[i];
+  int64_t dst = i;
+  int32_t tag = -1;
+  if (s >= 0) {
+    const NodeDev& nd = nodes[s];
+    int c1 = nd.c1, c2 = nd.c2, c3 = nd.c3;
+    if (c1 + c2 + c3 > 0) {
+      uint8_t l = labf[i];
+      unsigned long long base = nd.off > 0 ? pre[nd.off - 1] : 0ull;
+      unsigned long long own = (l == 1) ? 1ull : (l == 2 ? (1ull << 32) : 0ull);
+      unsigned long long ex = pre[i] - base - own;
+      int64_t r1 = (int64_t)(ex & 0xffffffffull), r2 = (int64_t)(ex >> 32);
+      int64_t r3 = (i - nd.off) - r1 - r2;
+      int64_t o;
+      if (l == 1) o = r1;
+      else if (l == 2) o = sbd ? (int64_t)c1 + c3 + r2 : (int64_t)c1 + r2;
+      else o = sbd ? (int64_t)c1 + r3 : (int64_t)c1 + c2 + r3;
+      dst = nd.off + o;
+      tag = s * 4 + l;
+    }
+  }
+  ord2[dst] = ord[i];
+  xo2[dst] = xo[i];
+  segl2[dst] = tag;
+}
+
+// Tree records and the next level's node table.
+__global__ void k_children(NodeDev* __restrict__ nodes, int N, const int64_t* __restrict__ pbase, int min_part,
+                           int max_depth, int sbd, NodeDev* __restrict__ next, int* __restrict__ next_count,
+                           int next_cap, TreeDev tree, int* __restrict__ err) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  NodeDev& nd = nodes[s];
+  int64_t rel = nd.off - pbase[nd.prob];
+  bool split = nd.c1 + nd.c2 + nd.c3 > 0;
+  int slot = atomicAdd(tree.count, 1);
+  if (slot >= tree.cap) { atomicOr(err, 1); return; }
+  tree.heap[slot] = nd.heap;
+  tree.prob[slot] = nd.prob;
+  tree.offset[slot] = (int32_t)rel;
+  tree.depth[slot] = nd.depth;
+  if (!split) {
+    tree.n1[slot] = nd.size; tree.n2[slot] = 0; tree.nsep[slot] = 0;
+    return;
+  }
+  tree.n1[slot] = nd.c1; tree.n2[slot] = nd.c2; tree.nsep[slot] = nd.c3;
+  for (int side = 0; side < 2; ++side) {
+    int size = side == 0 ? nd.c1 : nd.c2;
+    if (size == 0) continue;
+    int64_t off = nd.off + (side == 0 ? 0 : (sbd ? nd.c1 + nd.c3 : nd.c1));
+    uint64_t heap = 2 * nd.heap + side;
+    int depth = nd.depth + 1;
+    if (size > min_part && depth < max_depth) {
+      int c = atomicAdd(next_count, 1);
+      if (c >= next_cap) { atomicOr(err, 2); continue; }
+      NodeDev& ch = next[c];
+      ch.heap = heap; ch.off = off; ch.size = size; ch.depth = depth; ch.prob = nd.prob;
+      if (side == 0) nd.child1 = c; else nd.child2 = c;
+    } else {
+      int t = atomicAdd(tree.count, 1);
+      if (t >= tree.cap) { atomicOr(err, 1); continue; }
+      tree.heap[t] = heap; tree.prob[t] = nd.prob; tree.offset[t] = (int32_t)(off - pbase[nd.prob]);
+      tree.depth[t] = depth; tree.n1[t] = size; tree.n2[t] = 0; tree.nsep[t] = 0;
+    }
+  }
+}
+
+__global__ void k_relabel(const int32_t* __restrict__ segl2, const int32_t* __restrict__ ord2, int64_t n,
+                          const NodeDev* __restrict__ nodes, int32_t* __restrict__ seg, int32_t* __restrict__ vnode) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t tag = segl2[i];
+  int32_t c = -1;
+  if (tag >= 0) {
+    int s = tag >> 2, l = tag & 3;
+    c = l == 1 ? nodes[s].child1 : (l == 2 ? nodes[s].child2 : -1);
+  }
+  int32_t old = seg[i];
+  seg[i] = (tag >= 0) ? c : -1;
+  if (tag >= 0 || old >= 0) vnode[ord2[i]] = seg[i];
+}
+
+__global__ void k_root_nodes(NodeDev* __restrict__ nodes, const int64_t* __restrict__ pbase, const int32_t* __restrict__ ids,
+                             int N, const uint64_t* __restrict__ heaps) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  int p = ids[s];
+  NodeDev& nd = nodes[s];
+  nd.heap = heaps ? heaps[s] : 1ull;
+  nd.off = pbase[p];
+  nd.size = (int32_t)(pbase[p + 1] - pbase[p]);
+  nd.depth = 0;
+  nd.prob = p;
+}
+
+__global__ void k_seg_init(int32_t* __restrict__ seg, int32_t* __restrict__ vnode, const int32_t* __restrict__ ord,
+                           int64_t n, const int64_t* __restrict__ pbase, int P, const int32_t* __restrict__ node_of_prob) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = 0, hi = P;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (pbase[mid] <= i) lo = mid; else hi = mid;
+  }
+  int32_t s = node_of_prob[lo];
+  seg[i] = s;
+  vnode[ord[i]] = s;
+}
+
+__global__ void k_gather_coords(const float4* __restrict__ x, const int32_t* __restrict__ ord, int64_t n,
+                                float4* __restrict__ xo) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) xo[i] = x[ord[i]];
+}
+
+__global__ void k_iota(int32_t* a, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = (int32_t)i;
+}
+
+__global__ void k_tree_keys(const TreeDev tree, int n, int by_prob, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  keys[t] = by_prob ? (uint64_t)tree.prob[t] : tree.heap[t];
+  vals[t] = (uint32_t)t;
+}
+
+__global__ void k_tree_regather(const uint32_t* __restrict__ idx, int n, int by_prob, const TreeDev tree,
+                                uint64_t* __restrict__ keys) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  keys[t] = by_prob ? (uint64_t)tree.prob[idx[t]] : tree.heap[idx[t]];
+}
+
+__global__ void k_tree_out(const uint32_t* __restrict__ idx, int n, const TreeDev tree, uint64_t* heap,
+                           int32_t* offset, int32_t* n1, int32_t* n2, int32_t* nsep, int32_t* depth, int32_t* prob) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  uint32_t j = idx[t];
+  if (heap) heap[t] = tree.heap[j];
+  if (offset) offset[t] = tree.offset[j];
+  if (n1) n1[t] = tree.n1[j];
+  if (n2) n2[t] = tree.n2[j];
+  if (nsep) nsep[t] = tree.nsep[j];
+  if (depth) depth[t] = tree.depth[j];
+  if (prob) prob[t] = tree.prob[j];
+}
+
+template <class F>
+void dispatch_d(int d, F&& f) {
+  if (d == 2) f(std::integral_constant<int, 2>());
+  else if (d == 3) f(std::integral_constant<int, 3>());
+  else f(std::integral_constant<int, 4>());
+}
+
+}  // namespace
+
+// 2-means of every node of the table (Algorithm 5), leaving the final labels
+// in lab (position order) and the node fields z1, z2, n1, n2, state.
+vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s, Scratch& sc) {
+  const int64_t n = st.n;
+  ScratchFrame frame(sc);
+  unsigned long long *dval, *dpre;
+  int* cnt;
+  VMO_TRY(sc.alloc(&dval, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&dpre, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&cnt, 1));
+  vmo_status stt = VMO_OK;
+  dispatch_d(d, [&](auto DC) {
+    constexpr int D = decltype(DC)::value;
+    k_node_reset<<<grid_for(N, kBlock), kBlock, 0, s>>>(st.nodes, N);
+    k_maxabs<D><<<grid_for(n, kBlock), kBlock, 0, s>>>(st.xo, st.seg, n, st.nodes);
+    k_seed1<<<grid_for(N, kBlock), kBlock, 0, s>>>(st.nodes, N, st.xo, st.seeds);
+    k_dsq<D><<<grid_for(n, kBlock), kBlock, 0, s>>>(st.xo, st.seg, n, st.nodes, dval);
+    stt = scan_inclusive<uint64_t>((const uint64_t*)dval, (uint64_t*)dpre, n, s, sc);
+    if (stt != VMO_OK) return;
+    k_seed2<D><<<grid_for(n, kBlock), kBlock, 0, s>>>(st.xo, st.seg, n, dval, dpre, st.nodes, st.seeds);
+    for (int it = 0; it < km_iters; ++it) {
+      k_assign<D><<<grid_for(n, kBlock), kBlock, 0, s>>>(st.xo, st.seg, n, it, st.nodes, st.lab, 0);
+      k_update<D><<<grid_for(N, kBlock), kBlock, 0, s>>>(st.nodes, N, it);
+      if (it % 4 == 3 && it + 1 < km_iters) {  // stop early once every node has converged
+        int h = 0;
+        cudaMemsetAsync(cnt, 0, 4, s);
+        k_count_active<<<grid_for(N, kBlock), kBlock, 0, s>>>(st.nodes, N, cnt);
+        cudaMemcpyAsync(&h, cnt, 4, cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        if (h == 0) break;
+      }
+    }
+    k_clear_counts<<<grid_for(N, kBlock), kBlock, 0, s>>>(st.nodes, N);
+    k_assign<D><<<grid_for(n, kBlock), kBlock, 0, s>>>(st.xo, st.seg, n, 0, st.nodes, st.lab, 1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) stt = cuda_fail(e, "two_means", __FILE__, __LINE__);
+  });
+  return stt;
+}
+
+vmo_status order_levels(OrderState& st, const OrderParams& op, cudaStream_t s, Scratch& sc) {
+  const int64_t n = st.n;
+  int N = st.nroots;
+  int32_t *ord2, *segl2, *next_count, *err;
+  float4* xo2;
+  uint8_t* labf;
+  unsigned long long *pk, *pre;
+  NodeDev* next;
+  VMO_TRY(sc.alloc(&ord2, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&segl2, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&xo2, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&labf, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&pk, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&pre, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&next, st.node_cap));
+  VMO_TRY(sc.alloc(&next_count, 1));
+  VMO_TRY(sc.alloc(&err, 1));
+  VMO_CUDA(cudaMemsetAsync(err, 0, 4, s));
+  while (N > 0) {
+    VMO_TRY(two_means(st, N, op.d, op.km_iters, s, sc));
+    dispatch_d(op.d, [&](auto DC) {
+      constexpr int D = decltype(DC)::value;
+      k_vertex_state<D><<<grid_for(n, kBlock), kBlock, 0, s>>>(st.xo, st.ord, st.seg, n, st.nodes, st.lab, st.vlab,
+                                                               st.vs);
+    });
+    k_separator<<<grid_for(n, kBlock), kBlock, 0, s>>>(st.ord, st.seg, n, st.adj_ptr, st.adj, st.vnode, st.vlab, st.vs,
+                                                       st.nodes, labf);
+    k_pack<<<grid_for(n, kBlock), kBlock, 0, s>>>(st.seg, labf, n, st.nodes, pk);
+    VMO_LAUNCHED("separator");
+    VMO_TRY(scan_inclusive<uint64_t>((const uint64_t*)pk, (uint64_t*)pre, n, s, sc));
+    k_scatter<<<grid_for(n, kBlock), kBlock, 0, s>>>(st.ord, st.xo, st.seg, labf, n, st.nodes, pre, op.sbd, ord2, xo2,
+                                                     segl2);
+    VMO_CUDA(cudaMemsetAsync(next_count, 0, 4, s));
+    k_children<<<grid_for(N, kBlock), kBlock, 0, s>>>(st.nodes, N, st.pbase, op.min_part, op.max_depth, op.sbd, next,
+                                                      next_count, st.node_cap, st.tree, err);
+    k_relabel<<<grid_for(n, kBlock), kBlock, 0, s>>>(segl2, ord2, n, st.nodes, st.seg, st.vnode);
+    VMO_LAUNCHED("partition");
+    // swap position arrays
+    VMO_CUDA(cudaMemcpyAsync(st.ord, ord2, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    VMO_CUDA(cudaMemcpyAsync(st.xo, xo2, n * sizeof(float4), cudaMemcpyDeviceToDevice, s));
+    int hN = 0, herr = 0;
+    VMO_CUDA(cudaMemcpyAsync(&hN, next_count, 4, cudaMemcpyDeviceToHost, s));
+    VMO_CUDA(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s));
+    VMO_CUDA(cudaStreamSynchronize(s));
+    if (herr) return cuda_fail(cudaErrorUnknown, "ordering: node table or tree capacity exceeded", __FILE__, __LINE__);
+    std::swap(st.nodes, next);
+    N = hN;
+  }
+  return VMO_OK;
+}
+
+vmo_status order_setup(OrderState& st, const float4* x, const std::vector<int64_t>& pbase_host,
+                       const std::vector<uint64_t>& seeds, const OrderParams& op, cudaStream_t s, Scratch& sc) {
+  const int64_t n = pbase_host.back();
+  const int P = (int)pbase_host.size() - 1;
+  st.n = n;
+  VMO_TRY(sc.alloc(&st.ord, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&st.xo, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&st.seg, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&st.lab, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&st.vnode, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&st.vlab, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&st.vs, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&st.pbase, P + 1));
+  VMO_TRY(sc.alloc(&st.seeds, std::max(P, 1)));
+  // node table capacity: active nodes of one level have > min_part vertices each
+  st.node_cap = (int)std::min<int64_t>(n / (std::max(op.min_part, 1) + 1) + P + 16, n + 16);
+  VMO_TRY(sc.alloc(&st.nodes, st.node_cap));
+  // tree capacity: at most 2 records per vertex
+  st.tree.cap = (int)std::min<int64_t>(2 * n + 16, INT32_MAX);
+  VMO_TRY(sc.alloc(&st.tree.heap, st.tree.cap));
+  VMO_TRY(sc.alloc(&st.tree.prob, st.tree.cap));
+  VMO_TRY(sc.alloc(&st.tree.offset, st.tree.cap));
+  VMO_TRY(sc.alloc(&st.tree.n1, st.tree.cap));
+  VMO_TRY(sc.alloc(&st.tree.n2, st.tree.cap));
+  VMO_TRY(sc.alloc(&st.tree.nsep, st.tree.cap));
+  VMO_TRY(sc.alloc(&st.tree.depth, st.tree.cap));
+  VMO_TRY(sc.alloc(&st.tree.count, 1));
+  VMO_CUDA(cudaMemsetAsync(st.tree.count, 0, 4, s));
+  VMO_CUDA(cudaMemcpyAsync(st.pbase, pbase_host.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  VMO_CUDA(cudaMemcpyAsync(st.seeds, seeds.data(), P * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+  if (n > 0) {
+    k_iota<<<grid_for(n, kBlock), kBlock, 0, s>>>(st.ord, n);
+    k_gather_coords<<<grid_for(n, kBlock), kBlock, 0, s>>>(x, st.ord, n, st.xo);
+    VMO_LAUNCHED("order_setup");
+  }
+  // roots: problems with more than min_part vertices and max_depth > 0 are
+  // active; the others are leaves at once
+  std::vector<int32_t> ids, node_of_prob(P, -1);
+  for (int p = 0; p < P; ++p) {
+    int64_t k = pbase_host[p + 1] - pbase_host[p];
+    if (k > op.min_part && op.max_depth > 0) {
+      node_of_prob[p] = (int32_t)ids.size();
+      ids.push_back(p);
+    }
+  }
+  st.nroots = (int)ids.size();
+  std::vector<int32_t> leaf_probs;
+  for (int p = 0; p < P; ++p)
+    if (node_of_prob[p] < 0 && pbase_host[p + 1] > pbase_host[p]) leaf_probs.push_back(p);
+  int32_t *d_ids, *d_nop;
+  VMO_TRY(sc.alloc(&d_ids, std::max<size_t>(ids.size(), 1)));
+  VMO_TRY(sc.alloc(&d_nop, std::max(P, 1)));
+  if (!ids.empty())
+    VMO_CUDA(cudaMemcpyAsync(d_ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, s));
+  VMO_CUDA(cudaMemcpyAsync(d_nop, node_of_prob.data(), P * 4, cudaMemcpyHostToDevice, s));
+  if (st.nroots > 0) {
+    k_root_nodes<<<grid_for(st.nroots, kBlock), kBlock, 0, s>>>(st.nodes, st.pbase, d_ids, st.nroots, nullptr);
+    VMO_LAUNCHED("roots");
+  }
+  if (n > 0) {
+    k_seg_init<<<grid_for(n, kBlock), kBlock, 0, s>>>(st.seg, st.vnode, st.ord, n, st.pbase, P, d_nop);
+    VMO_LAUNCHED("seg_init");
+  }
+  // leaf roots become tree records directly
+  if (!leaf_probs.empty()) {
+    std::vector<int32_t> hc(1);
+    int nl = (int)leaf_probs.size();
+    std::vector<uint64_t> h(nl, 1ull);
+    std::vector<int32_t> zero(nl, 0), sz(nl);
+    for (int i = 0; i < nl; ++i) sz[i] = (int32_t)(pbase_host[leaf_probs[i] + 1] - pbase_host[leaf_probs[i]]);
+    VMO_CUDA(cudaMemcpyAsync(st.tree.heap, h.data(), nl * 8, cudaMemcpyHostToDevice, s));
+    VMO_CUDA(cudaMemcpyAsync(st.tree.prob, leaf_probs.data(), nl * 4, cudaMemcpyHostToDevice, s));
+    VMO_CUDA(cudaMemcpyAsync(st.tree.offset, zero.data(), nl * 4, cudaMemcpyHostToDevice, s));
+    VMO_CUDA(cudaMemcpyAsync(st.tree.n1, sz.data(), nl * 4, cudaMemcpyHostToDevice, s));
+    VMO_CUDA(cudaMemcpyAsync(st.tree.n2, zero.data(), nl * 4, cudaMemcpyHostToDevice, s));
+    VMO_CUDA(cudaMemcpyAsync(st.tree.nsep, zero.data(), nl * 4, cudaMemcpyHostToDevice, s));
+    VMO_CUDA(cudaMemcpyAsync(st.tree.depth, zero.data(), nl * 4, cudaMemcpyHostToDevice, s));
+    VMO_CUDA(cudaMemcpyAsync(st.tree.count, &nl, 4, cudaMemcpyHostToDevice, s));
+    VMO_CUDA(cudaStreamSynchronize(s));
+  }
+  VMO_CUDA(cudaStreamSynchronize(s));
+  return VMO_OK;
+}
+
+vmo_status tree_sorted(OrderState& st, bool by_prob, int32_t* count_out, uint32_t** idx_out, cudaStream_t s,
+                       Scratch& sc) {
+  int n = 0;
+  VMO_CUDA(cudaMemcpyAsync(&n, st.tree.count, 4, cudaMemcpyDeviceToHost, s));
+  VMO_CUDA(cudaStreamSynchronize(s));
+  *count_out = n;
+  uint64_t *k1, *k2;
+  uint32_t *v1, *v2;
+  VMO_TRY(sc.alloc(&k1, std::max(n, 1)));
+  VMO_TRY(sc.alloc(&k2, std::max(n, 1)));
+  VMO_TRY(sc.alloc(&v1, std::max(n, 1)));
+  VMO_TRY(sc.alloc(&v2, std::max(n, 1)));
+  if (n == 0) { *idx_out = v2; return VMO_OK; }
+  k_tree_keys<<<grid_for(n, kBlock), kBlock, 0, s>>>(st.tree, n, 0, k1, v1);
+  VMO_LAUNCHED("tree_keys");
+  VMO_TRY(radix_sort_u64(k1, v1, k2, v2, n, 64, s, sc));
+  if (by_prob) {
+    k_tree_regather<<<grid_for(n, kBlock), kBlock, 0, s>>>(v2, n, 1, st.tree, k1);
+    VMO_LAUNCHED("tree_regather");
+    VMO_TRY(radix_sort_u64(k1, v2, k2, v1, n, 32, s, sc));
+    *idx_out = v1;
+  } else {
+    *idx_out = v2;
+  }
+  return VMO_OK;
+}
+
+vmo_status gather_coords(const float4* x, const int32_t* ord, int64_t n, float4* xo, cudaStream_t s) {
+  if (n <= 0) return VMO_OK;
+  k_gather_coords<<<grid_for(n, kBlock), kBlock, 0, s>>>(x, ord, n, xo);
+  VMO_LAUNCHED("gather_coords");
+  return VMO_OK;
+}
+
+vmo_status tree_write(OrderState& st, const uint32_t* idx, int n, uint64_t* heap, int32_t* offset, int32_t* n1,
+                      int32_t* n2, int32_t* nsep, int32_t* depth, int32_t* prob, cudaStream_t s) {
+  if (n == 0) return VMO_OK;
+  k_tree_out<<<grid_for(n, kBlock), kBlock, 0, s>>>(idx, n, st.tree, heap, offset, n1, n2, nsep, depth, prob);
+  VMO_LAUNCHED("tree_out");
+  return VMO_OK;
+}
+
+}  // namespace vmo

@@ -1,0 +1,347 @@
+// Device-wide primitives: scans and a stable LSD radix sort.
+//
+// Scan: reduce tiles -> scan tile sums in one block -> scan each tile with its
+// offset (tiles of 2048 elements staged through shared memory so global loads
+// and stores are coalesced).
+//
+// Radix sort: 8-bit digits, one histogram kernel and one scatter kernel per
+// pass plus a scan of the (segment, digit, tile)-ordered histogram.  The
+// scatter ranks keys stably inside a warp with __match_any_sync, so equal keys
+// keep their input order.  Tiles never straddle a segment, so with the
+// histogram laid out segment-major the same kernels sort many independent
+// segments (one per problem of a batch) in one launch sequence.
+#include <algorithm>
+
+#include "vmo_internal.cuh"
+
+namespace vmo {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <class T>
+__device__ T warp_inclusive(T v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(0xffffffffu, v, o);
+    if ((int)lane_id() >= o) v += t;
+  }
+  return v;
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim.x <= 1024).
+template <class T>
+__device__ T block_exclusive(T v, T* warp_sums, T* total) {
+  const int lane = lane_id(), warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  T inc = warp_inclusive(v);
+  if (lane == 31) warp_sums[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    T s = (lane < nw) ? warp_sums[lane] : T(0);
+    T si = warp_inclusive(s);
+    if (lane < nw) warp_sums[lane] = si - s;
+    if (lane == nw - 1) warp_sums[32] = si;
+  }
+  __syncthreads();
+  T out = warp_sums[warp] + inc - v;
+  if (total) *total = warp_sums[32];
+  __syncthreads();
+  return out;
+}
+
+template <class T>
+__global__ void scan_reduce_kernel(const T* __restrict__ in, int64_t n, T* __restrict__ partial) {
+  __shared__ T ws[33];
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  T acc = 0;
+  for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
+    int64_t g = base + i;
+    if (g < n) acc += in[g];
+  }
+  T tot;
+  block_exclusive<T>(acc, ws, &tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+template <class T>
+__global__ void scan_partials_kernel(T* partial, int64_t ntiles, T* total) {
+  __shared__ T ws[33];
+  T carry = 0;
+  for (int64_t b = 0; b < ntiles; b += blockDim.x) {
+    int64_t i = b + threadIdx.x;
+    T v = (i < ntiles) ? partial[i] : T(0);
+    T tot;
+    T ex = block_exclusive<T>(v, ws, &tot);
+    if (i < ntiles) partial[i] = ex + carry;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+template <class T, bool Inclusive>
+__global__ void scan_tile_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t n,
+                                 const T* __restrict__ partial) {
+  __shared__ T tile[kScanTile];
+  __shared__ T ws[33];
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
+    int64_t g = base + i;
+    tile[i] = (g < n) ? in[g] : T(0);
+  }
+  __syncthreads();
+  T loc[kScanItems];
+  T acc = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    loc[j] = tile[threadIdx.x * kScanItems + j];
+    acc += loc[j];
+  }
+  T ex = block_exclusive<T>(acc, ws, nullptr) + partial[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    T v = loc[j];
+    tile[threadIdx.x * kScanItems + j] = Inclusive ? ex + v : ex;
+    ex += v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
+    int64_t g = base + i;
+    if (g < n) out[g] = tile[i];
+  }
+}
+
+template <class T, bool Inclusive>
+vmo_status scan_impl(const T* in, T* out, int64_t n, T* total, cudaStream_t s, Scratch& sc) {
+  if (n <= 0) {
+    if (total) VMO_CUDA(cudaMemsetAsync(total, 0, sizeof(T), s));
+    return VMO_OK;
+  }
+  int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+  T* partial;
+  VMO_TRY(sc.alloc(&partial, (size_t)ntiles));
+  scan_reduce_kernel<T><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, partial);
+  scan_partials_kernel<T><<<1, 1024, 0, s>>>(partial, ntiles, total);
+  scan_tile_kernel<T, Inclusive><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, out, n, partial);
+  VMO_LAUNCHED("scan");
+  return VMO_OK;
+}
+
+// ------------------------------- radix sort --------------------------------
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = kSortTile / kSortThreads;  // 8
+constexpr int kSortWarps = kSortThreads / 32;
+
+struct TileInfo {
+  int64_t start;
+  int32_t count;
+  int64_t hist_base;  // index of (digit 0, this tile) in the histogram
+  int32_t stride;     // distance between digits (tiles in the segment)
+};
+
+__device__ inline TileInfo tile_info(const SortSegments& sg, int64_t n, int64_t t) {
+  TileInfo ti;
+  if (sg.tile_seg == nullptr) {
+    ti.start = t * kSortTile;
+    int64_t c = n - ti.start;
+    ti.count = (int32_t)(c < kSortTile ? c : kSortTile);
+    ti.hist_base = t;
+    ti.stride = (int32_t)sg.ntiles;
+  } else {
+    int32_t seg = sg.tile_seg[t];
+    int32_t t0 = sg.seg_tile0[seg], nt = sg.seg_tile0[seg + 1] - t0;
+    ti.start = sg.tile_start[t];
+    ti.count = sg.tile_count[t];
+    ti.hist_base = (int64_t)t0 * kRadix + (t - t0);
+    ti.stride = nt;
+  }
+  return ti;
+}
+
+template <class K>
+__global__ void radix_hist_kernel(const K* __restrict__ keys, int64_t n, int shift, SortSegments sg,
+                                  uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[kRadix];
+  for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  TileInfo ti = tile_info(sg, n, blockIdx.x);
+  for (int i = threadIdx.x; i < ti.count; i += blockDim.x) {
+    uint32_t dg = (uint32_t)(keys[ti.start + i] >> shift) & (kRadix - 1);
+    atomicAdd(&h[dg], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kRadix; i += blockDim.x) hist[ti.hist_base + (int64_t)i * ti.stride] = h[i];
+}
+
+template <class K, bool HasVal>
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
+    const K* __restrict__ keys, const uint32_t* __restrict__ vals, K* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out, int64_t n, int shift, SortSegments sg, const uint32_t* __restrict__ offs) {
+  __shared__ uint32_t wcnt[kSortWarps][kRadix];
+  __shared__ uint32_t tbase[kRadix];
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kSortWarps * kRadix; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+  TileInfo ti = tile_info(sg, n, blockIdx.x);
+  for (int i = threadIdx.x; i < kRadix; i += blockDim.x) tbase[i] = offs[ti.hist_base + (int64_t)i * ti.stride];
+  __syncthreads();
+  K key[kSortItems];
+  uint32_t val[kSortItems];
+  uint32_t rank[kSortItems];
+  uint32_t dig[kSortItems];
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) {
+    int idx = warp * (32 * kSortItems) + j * 32 + lane;
+    bool valid = idx < ti.count;
+    key[j] = valid ? keys[ti.start + idx] : K(0);
+    if (HasVal) val[j] = valid ? vals[ti.start + idx] : 0u;
+    uint32_t dg = valid ? ((uint32_t)(key[j] >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
+    dig[j] = dg;
+    unsigned peers = __match_any_sync(0xffffffffu, dg);
+    uint32_t before = __popc(peers & lt);
+    uint32_t base = valid ? wcnt[warp][dg] : 0u;
+    rank[j] = base + before;
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) wcnt[warp][dg] = base + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int dg = threadIdx.x; dg < kRadix; dg += blockDim.x) {
+    uint32_t run = 0;
+    for (int w = 0; w < kSortWarps; ++w) {
+      uint32_t c = wcnt[w][dg];
+      wcnt[w][dg] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) {
+    if (dig[j] >= (uint32_t)kRadix) continue;
+    uint32_t dst = tbase[dig[j]] + wcnt[warp][dig[j]] + rank[j];
+    keys_out[dst] = key[j];
+    if (HasVal) vals_out[dst] = val[j];
+  }
+}
+
+template <class K>
+vmo_status radix_sort_impl(K* keys_in, uint32_t* vals_in, K* keys_out, uint32_t* vals_out, int64_t n, int bits,
+                           const SortSegments* segs, cudaStream_t s, Scratch& sc) {
+  if (n <= 0) return VMO_OK;
+  SortSegments sg;
+  if (segs) sg = *segs;
+  if (sg.tile_seg == nullptr) sg.ntiles = (n + kSortTile - 1) / kSortTile;
+  int passes = (bits + kRadixBits - 1) / kRadixBits;
+  if (passes == 0) {
+    VMO_CUDA(cudaMemcpyAsync(keys_out, keys_in, n * sizeof(K), cudaMemcpyDeviceToDevice, s));
+    if (vals_in) VMO_CUDA(cudaMemcpyAsync(vals_out, vals_in, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    return VMO_OK;
+  }
+  int64_t hn = sg.ntiles * kRadix;
+  uint32_t* hist;
+  VMO_TRY(sc.alloc(&hist, (size_t)hn));
+  K* ka = keys_in;
+  K* kb = keys_out;
+  uint32_t* va = vals_in;
+  uint32_t* vb = vals_out;
+  for (int p = 0; p < passes; ++p) {
+    int shift = p * kRadixBits;
+    radix_hist_kernel<K><<<(unsigned)sg.ntiles, 256, 0, s>>>(ka, n, shift, sg, hist);
+    VMO_TRY((scan_impl<uint32_t, false>(hist, hist, hn, nullptr, s, sc)));
+    if (vals_in)
+      radix_scatter_kernel<K, true><<<(unsigned)sg.ntiles, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, sg, hist);
+    else
+      radix_scatter_kernel<K, false><<<(unsigned)sg.ntiles, kSortThreads, 0, s>>>(ka, nullptr, kb, nullptr, n, shift,
+                                                                                   sg, hist);
+    VMO_LAUNCHED("radix_sort");
+    K* tk = ka; ka = kb; kb = tk;
+    uint32_t* tv = va; va = vb; vb = tv;
+  }
+  if (ka != keys_out) {
+    VMO_CUDA(cudaMemcpyAsync(keys_out, ka, n * sizeof(K), cudaMemcpyDeviceToDevice, s));
+    if (vals_in) VMO_CUDA(cudaMemcpyAsync(vals_out, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  }
+  return VMO_OK;
+}
+
+}  // namespace
+
+template <class T>
+vmo_status scan_exclusive(const T* in, T* out, int64_t n, T* total, cudaStream_t s, Scratch& sc) {
+  return scan_impl<T, false>(in, out, n, total, s, sc);
+}
+template <class T>
+vmo_status scan_inclusive(const T* in, T* out, int64_t n, cudaStream_t s, Scratch& sc) {
+  return scan_impl<T, true>(in, out, n, nullptr, s, sc);
+}
+
+template vmo_status scan_exclusive<int32_t>(const int32_t*, int32_t*, int64_t, int32_t*, cudaStream_t, Scratch&);
+template vmo_status scan_exclusive<int64_t>(const int64_t*, int64_t*, int64_t, int64_t*, cudaStream_t, Scratch&);
+template vmo_status scan_exclusive<uint32_t>(const uint32_t*, uint32_t*, int64_t, uint32_t*, cudaStream_t,
+                                             Scratch&);
+template vmo_status scan_exclusive<uint64_t>(const uint64_t*, uint64_t*, int64_t, uint64_t*, cudaStream_t,
+                                             Scratch&);
+template vmo_status scan_inclusive<uint64_t>(const uint64_t*, uint64_t*, int64_t, cudaStream_t, Scratch&);
+template vmo_status scan_inclusive<int32_t>(const int32_t*, int32_t*, int64_t, cudaStream_t, Scratch&);
+template vmo_status scan_inclusive<int64_t>(const int64_t*, int64_t*, int64_t, cudaStream_t, Scratch&);
+
+vmo_status radix_sort_u32(uint32_t* keys_in, uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out, int64_t n,
+                          int bits, const SortSegments* segs, cudaStream_t s, Scratch& sc) {
+  return radix_sort_impl<uint32_t>(keys_in, vals_in, keys_out, vals_out, n, bits, segs, s, sc);
+}
+
+vmo_status radix_sort_u64(uint64_t* keys_in, uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out, int64_t n,
+                          int bits, cudaStream_t s, Scratch& sc) {
+  return radix_sort_impl<uint64_t>(keys_in, vals_in, keys_out, vals_out, n, bits, nullptr, s, sc);
+}
+
+vmo_status make_sort_segments(const std::vector<int64_t>& base, SortSegments* out, cudaStream_t s, Scratch& sc) {
+  int32_t nseg = (int32_t)base.size() - 1;
+  std::vector<int32_t> tseg, tcount, t0(nseg + 1);
+  std::vector<int64_t> tstart;
+  for (int32_t g = 0; g < nseg; ++g) {
+    t0[g] = (int32_t)tseg.size();
+    int64_t a = base[g], b = base[g + 1];
+    for (int64_t x = a; x < b; x += kSortTile) {
+      tseg.push_back(g);
+      tstart.push_back(x);
+      tcount.push_back((int32_t)std::min<int64_t>(kSortTile, b - x));
+    }
+  }
+  t0[nseg] = (int32_t)tseg.size();
+  int64_t nt = (int64_t)tseg.size();
+  if (nt == 0) {  // all segments empty: one empty tile keeps the kernels well-formed
+    tseg.push_back(0); tstart.push_back(0); tcount.push_back(0);
+    t0[nseg] = 1;
+    for (int32_t g = 1; g < nseg; ++g) t0[g] = 1;
+    nt = 1;
+  }
+  int32_t *d_tseg, *d_tcount, *d_t0;
+  int64_t *d_tstart, *d_base;
+  VMO_TRY(sc.alloc(&d_tseg, nt));
+  VMO_TRY(sc.alloc(&d_tcount, nt));
+  VMO_TRY(sc.alloc(&d_tstart, nt));
+  VMO_TRY(sc.alloc(&d_t0, nseg + 1));
+  VMO_TRY(sc.alloc(&d_base, nseg + 1));
+  VMO_CUDA(cudaMemcpyAsync(d_tseg, tseg.data(), nt * 4, cudaMemcpyHostToDevice, s));
+  VMO_CUDA(cudaMemcpyAsync(d_tcount, tcount.data(), nt * 4, cudaMemcpyHostToDevice, s));
+  VMO_CUDA(cudaMemcpyAsync(d_tstart, tstart.data(), nt * 8, cudaMemcpyHostToDevice, s));
+  VMO_CUDA(cudaMemcpyAsync(d_t0, t0.data(), (nseg + 1) * 4, cudaMemcpyHostToDevice, s));
+  VMO_CUDA(cudaMemcpyAsync(d_base, base.data(), (nseg + 1) * 8, cudaMemcpyHostToDevice, s));
+  // host vectors must outlive the asynchronous copies
+  VMO_CUDA(cudaStreamSynchronize(s));
+  out->nseg = nseg;
+  out->seg_base = d_base;
+  out->tile_seg = d_tseg;
+  out->tile_start = d_tstart;
+  out->tile_count = d_tcount;
+  out->seg_tile0 = d_t0;
+  out->ntiles = nt;
+  return VMO_OK;
+}
+
+}  // namespace vmo

@@ -1,0 +1,256 @@
+// Internal declarations of the VMO CUDA library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/vmo.h"
+
+namespace vmo {
+
+// ---------------------------------------------------------------------------
+// Errors: a failing call records a message for vmo_last_error() and returns a
+// status; nothing throws across the C-ABI.
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+
+struct Status {
+  vmo_status code = VMO_OK;
+  bool ok() const { return code == VMO_OK; }
+};
+
+#define VMO_TRY(expr)                          \
+  do {                                         \
+    vmo_status _s = (expr);                    \
+    if (_s != VMO_OK) return _s;               \
+  } while (0)
+
+vmo_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define VMO_CUDA(call)                                                   \
+  do {                                                                   \
+    cudaError_t _e = (call);                                             \
+    if (_e != cudaSuccess) return ::vmo::cuda_fail(_e, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define VMO_LAUNCHED(name)                                                     \
+  do {                                                                         \
+    cudaError_t _e = cudaGetLastError();                                       \
+    if (_e != cudaSuccess) return ::vmo::cuda_fail(_e, name, __FILE__, __LINE__); \
+  } while (0)
+
+vmo_status invalid(const std::string& msg);
+vmo_status unsupported(const std::string& msg);
+
+// ---------------------------------------------------------------------------
+// Device memory.  Scratch of one call is taken from the stream-ordered pool
+// (cudaMallocAsync) and released on the same stream when the call ends.
+// ---------------------------------------------------------------------------
+struct Scratch {
+  cudaStream_t stream = nullptr;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t s) : stream(s) {}
+  ~Scratch();
+  template <class T>
+  vmo_status alloc(T** p, size_t count) {
+    return alloc_bytes(reinterpret_cast<void**>(p), count * sizeof(T));
+  }
+  vmo_status alloc_bytes(void** p, size_t bytes);
+  size_t mark() const { return ptrs.size(); }
+  void release_to(size_t m);  // frees (stream-ordered) everything allocated after mark m
+};
+
+// Returns the scratch taken inside a scope to the pool when the scope ends.
+struct ScratchFrame {
+  Scratch& sc;
+  size_t m;
+  explicit ScratchFrame(Scratch& s) : sc(s), m(s.mark()) {}
+  ~ScratchFrame() { sc.release_to(m); }
+};
+
+// Persistent device buffer owned by a handle.
+template <class T>
+struct DevArray {
+  T* ptr = nullptr;
+  size_t count = 0;
+  vmo_status resize(size_t n);  // contents not preserved
+  void release();
+  ~DevArray() { release(); }
+  DevArray() = default;
+  DevArray(const DevArray&) = delete;
+  DevArray& operator=(const DevArray&) = delete;
+};
+
+template <class T>
+vmo_status DevArray<T>::resize(size_t n) {
+  if (n <= count && ptr) return VMO_OK;
+  release();
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ptr), n * sizeof(T));
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    (void)cudaGetLastError();
+    set_error("cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
+    return VMO_ERR_OOM;
+  }
+  count = n;
+  return VMO_OK;
+}
+
+template <class T>
+void DevArray<T>::release() {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  count = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Hypergraph handle.
+// ---------------------------------------------------------------------------
+struct Graph {
+  // Adjacency CSR over global vertex ids, with optional per-entry edge costs
+  // and per-vertex weights (null = 1).
+  int64_t k = 0;
+  int64_t nadj = 0;
+  const int32_t* adj_ptr = nullptr;  // k+1 (int32 offsets)
+  const int32_t* adj = nullptr;
+  const float* acost = nullptr;      // nadj or null
+  const float* w = nullptr;          // k or null
+};
+
+}  // namespace vmo
+
+struct vmo_hg_s {
+  vmo_model model;
+  int32_t m = 0, n = 0;
+  int32_t k = 0;        // vertices
+  int64_t l = 0;        // nets
+  vmo::DevArray<int32_t> adj_ptr, adj;      // graph models
+  vmo::DevArray<int32_t> net_ptr, pins;     // all models
+  vmo::DevArray<int32_t> vtx_ptr, vnets;    // all models
+  vmo::DevArray<float> weight;              // optional vertex weights
+  int64_t nadj = 0, npins = 0, nvnets = 0;
+  bool has_weight = false;
+  int device = 0;
+};
+
+namespace vmo {
+
+// ---------------------------------------------------------------------------
+// Primitives (prims.cu).
+// ---------------------------------------------------------------------------
+// Exclusive scan of n values; if total != nullptr the sum is written there
+// (device).  In-place (in == out) is allowed.
+template <class T>
+vmo_status scan_exclusive(const T* in, T* out, int64_t n, T* total, cudaStream_t s, Scratch& sc);
+template <class T>
+vmo_status scan_inclusive(const T* in, T* out, int64_t n, cudaStream_t s, Scratch& sc);
+
+// Segment map for the radix sort: tiles never straddle segments.
+struct SortSegments {
+  int32_t nseg = 1;               // number of segments
+  const int64_t* seg_base = nullptr;  // device, nseg+1 element offsets (null: one segment [0, n))
+  const int32_t* tile_seg = nullptr;  // device, per tile: segment
+  const int64_t* tile_start = nullptr;// device, per tile: first element
+  const int32_t* tile_count = nullptr;// device, per tile: elements
+  const int32_t* seg_tile0 = nullptr; // device, per segment: first tile (nseg+1)
+  int64_t ntiles = 0;
+};
+constexpr int kSortTile = 2048;  // 256 threads x 8 keys
+
+// Stable LSD radix sort of (key, value) pairs on bits [0, bits).  Keys are
+// sorted within each segment.  Buffers are ping-ponged; the sorted result ends
+// in (keys_out, vals_out).  vals may be null (keys only).
+vmo_status radix_sort_u32(uint32_t* keys_in, uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
+                          int64_t n, int bits, const SortSegments* segs, cudaStream_t s, Scratch& sc);
+vmo_status radix_sort_u64(uint64_t* keys_in, uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
+                          int64_t n, int bits, cudaStream_t s, Scratch& sc);
+
+// Build SortSegments for segments given by host base offsets.
+vmo_status make_sort_segments(const std::vector<int64_t>& seg_base_host, SortSegments* out, cudaStream_t s,
+                              Scratch& sc);
+
+inline int bits_for(uint64_t maxval) {
+  int b = 0;
+  while (b < 64 && (maxval >> b) != 0) ++b;
+  return b;
+}
+
+inline unsigned grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+// ---------------------------------------------------------------------------
+// Device helpers.  Floating point that decides an integer uses explicitly
+// rounded intrinsics so the compiler cannot contract or reorder it.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kTagCoord = 0x636f6f7264000000ull;   // initial layout
+constexpr uint64_t kTagKmeans = 0x6b6d65616e730000ull;  // k-means++ draws
+constexpr uint64_t kTagMatch = 0x6d61746368000000ull;   // matching tie-breaks
+constexpr uint64_t kTagJitter = 0x6a69747465720000ull;  // prolongation jitter
+
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__host__ __device__ inline uint64_t rand64(uint64_t seed, uint64_t a, uint64_t b) {
+  return mix64(mix64(seed + kGolden * (a + 1)) + kGolden * (b + 1));
+}
+
+// floor(n * r / 2^64)
+__device__ inline uint64_t scale_draw(uint64_t n, uint64_t r) { return __umul64hi(n, r); }
+
+// Order-preserving map float -> uint32 (for atomicMin/Max on floats).
+__device__ inline uint32_t f2ord(float f) {
+  uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__host__ __device__ inline float ord2f(uint32_t u) {
+  uint32_t b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float f;
+  memcpy(&f, &b, 4);
+  return f;
+#endif
+}
+
+// Exact 2^e as float for -126 <= e <= 127.
+__device__ inline float exp2i_f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
+// Squared distance of two points in fp32, coordinates 0..d-1 in order, no FMA.
+template <int D>
+__device__ inline float sqdist32(const float4& a, const float4& b) {
+  float q = __fsub_rn(a.x, b.x);
+  float s = __fmul_rn(q, q);
+  if (D > 1) { q = __fsub_rn(a.y, b.y); s = __fadd_rn(s, __fmul_rn(q, q)); }
+  if (D > 2) { q = __fsub_rn(a.z, b.z); s = __fadd_rn(s, __fmul_rn(q, q)); }
+  if (D > 3) { q = __fsub_rn(a.w, b.w); s = __fadd_rn(s, __fmul_rn(q, q)); }
+  return s;
+}
+
+__device__ inline float comp(const float4& v, int m) {
+  return m == 0 ? v.x : (m == 1 ? v.y : (m == 2 ? v.z : v.w));
+}
+
+// Morton interleave of cell coordinates (bit b of coordinate m -> bit b*d+m).
+template <int D>
+__host__ __device__ inline uint32_t morton(const int32_t* c, int bits) {
+  uint32_t key = 0;
+  for (int b = 0; b < bits; ++b)
+    for (int m = 0; m < D; ++m) key |= (uint32_t)((c[m] >> b) & 1) << (b * D + m);
+  return key;
+}
+
+__device__ inline unsigned lane_id() { return threadIdx.x & 31u; }
+
+}  // namespace vmo

@@ -1,0 +1,288 @@
+"""Python binding of the VMO C-ABI (include/vmo.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``libvmo.so``.  PyTorch provides device memory and the current stream.  There
+is no CPU fallback; if the library is missing or no GPU is present the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, fields
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvmo.so")
+_lib = None
+
+MODELS = {"symmetric": 0, "bipartite": 1, "rownet": 2, "colnet": 3}
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error", 4: "device wait timed out",
+          5: "over admission budget", 6: "unsupported"}
+
+
+class VmoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"vmo status {status} ({STATUS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+class _Csr(C.Structure):
+    _fields_ = [("m", C.c_int32), ("n", C.c_int32), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("colidx", C.c_void_p)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("d", C.c_int32), ("iters", C.c_int32), ("sigma", C.c_float), ("decay", C.c_float),
+                ("occupancy", C.c_int32), ("multilevel", C.c_int32), ("match_rounds", C.c_int32),
+                ("coarse_min", C.c_int32), ("km_iters", C.c_int32), ("min_part", C.c_int32),
+                ("max_depth", C.c_int32), ("seed", C.c_uint64)]
+
+
+class _Tree(C.Structure):
+    _fields_ = [("capacity", C.c_int32), ("count", C.c_int32), ("heap", C.c_void_p), ("offset", C.c_void_p),
+                ("n1", C.c_void_p), ("n2", C.c_void_p), ("nsep", C.c_void_p), ("depth", C.c_void_p)]
+
+
+@dataclass
+class Params:
+    """Method parameters (defaults of vmo_default_params)."""
+
+    d: int = 3
+    iters: int = 100
+    sigma: float = 1.0
+    decay: float = 0.9
+    occupancy: int = 8
+    multilevel: int = 1
+    match_rounds: int = 4
+    coarse_min: int = 64
+    km_iters: int = 20
+    min_part: int = 64
+    max_depth: int = 62
+    seed: int = 1
+
+    def _c(self) -> _Params:
+        p = _Params()
+        for f in fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
+SYMBOLS = ["vmo_default_params", "vmo_build_hypergraph", "vmo_hg_vertices", "vmo_hg_nets", "vmo_hg_arrays",
+           "vmo_components", "vmo_init_coords", "vmo_layout", "vmo_layout_step", "vmo_coarsen", "vmo_bisect",
+           "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_cut_size", "vmo_destroy",
+           "vmo_status_string", "vmo_last_error"]
+
+
+def load(path: str | None = None):
+    """Loads libvmo.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"{p} not found: build the CUDA library first (python -m paper_1105_4490_gb300._build_lib)")
+    lib = C.CDLL(p)
+    V, I32, I64, U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+    P32, P64 = C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+    lib.vmo_default_params.argtypes = [C.POINTER(_Params)]
+    lib.vmo_default_params.restype = None
+    lib.vmo_build_hypergraph.argtypes = [C.POINTER(_Csr), C.c_int, V, V, C.POINTER(V)]
+    lib.vmo_hg_vertices.argtypes = [V]
+    lib.vmo_hg_vertices.restype = I32
+    lib.vmo_hg_nets.argtypes = [V]
+    lib.vmo_hg_nets.restype = I64
+    lib.vmo_hg_arrays.argtypes = [V, C.POINTER(V), C.POINTER(V), P64, C.POINTER(V), C.POINTER(V), P64,
+                                  C.POINTER(V), C.POINTER(V), P64]
+    lib.vmo_components.argtypes = [V, V, V]
+    lib.vmo_init_coords.argtypes = [I32, I32, U64, V, V]
+    lib.vmo_layout.argtypes = [V, C.POINTER(_Params), V, I32, V]
+    lib.vmo_layout_step.argtypes = [V, C.POINTER(_Params), V, C.c_float, V, V, P32, V]
+    lib.vmo_coarsen.argtypes = [V, C.POINTER(_Params), V, V, P32, P32, P32, V]
+    lib.vmo_bisect.argtypes = [V, I32, V, V, I32, U64, U64, I32, V, V, P32, V]
+    for nm in ("vmo_order_bbd", "vmo_order_sbd"):
+        getattr(lib, nm).argtypes = [V, V, C.POINTER(_Params), V, V, C.POINTER(_Tree), V]
+    lib.vmo_order_vertices.argtypes = [V, V, C.POINTER(_Params), I32, V, C.POINTER(_Tree), V]
+    lib.vmo_cut_size.argtypes = [V, V, I32, P64, P64, V]
+    lib.vmo_destroy.argtypes = [V]
+    lib.vmo_destroy.restype = None
+    lib.vmo_status_string.argtypes = [C.c_int]
+    lib.vmo_status_string.restype = C.c_char_p
+    lib.vmo_last_error.argtypes = []
+    lib.vmo_last_error.restype = C.c_char_p
+    for nm in SYMBOLS:
+        if nm not in ("vmo_default_params", "vmo_hg_vertices", "vmo_hg_nets", "vmo_destroy", "vmo_status_string",
+                      "vmo_last_error"):
+            getattr(lib, nm).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise VmoError(status, load().vmo_last_error().decode())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must be on the GPU")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+class _View:
+    """Zero-copy view of a device array owned by the library."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3}
+
+
+def default_params() -> Params:
+    p = _Params()
+    load().vmo_default_params(C.byref(p))
+    return Params(**{f.name: getattr(p, f.name) for f in fields(Params)})
+
+
+def init_coords(k: int, d: int, seed: int) -> torch.Tensor:
+    """Random initial layout of Algorithm 3 (fp32 [k, 4])."""
+    x = torch.zeros((k, 4), dtype=torch.float32, device="cuda")
+    _check(load().vmo_init_coords(k, d, seed & (2 ** 64 - 1), _ptr(x), _stream()))
+    return x
+
+
+class Hypergraph:
+    """Device hypergraph model of a sparsity pattern (Table 1)."""
+
+    def __init__(self, rowptr: torch.Tensor, colidx: torch.Tensor, m: int, n: int, model: str = "symmetric",
+                 weights: torch.Tensor | None = None):
+        lib = load()
+        rowptr = rowptr.to(device="cuda", dtype=torch.int32).contiguous()
+        colidx = colidx.to(device="cuda", dtype=torch.int32).contiguous()
+        csr = _Csr(m, n, colidx.numel(), rowptr.data_ptr(), colidx.data_ptr() if colidx.numel() else None)
+        self._h = C.c_void_p()
+        w = None if weights is None else weights.to(device="cuda", dtype=torch.float32).contiguous()
+        _check(lib.vmo_build_hypergraph(C.byref(csr), MODELS[model], _ptr(w), _stream(), C.byref(self._h)))
+        self.model = model
+        self.m, self.n = m, n
+        self.k = int(lib.vmo_hg_vertices(self._h))
+        self.nets = int(lib.vmo_hg_nets(self._h))
+
+    @classmethod
+    def from_matrix(cls, mat, model: str = "symmetric", weights=None) -> "Hypergraph":
+        return cls(torch.as_tensor(mat.rowptr), torch.as_tensor(mat.colidx), mat.m, mat.n, model, weights)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.vmo_destroy(self._h)
+            self._h = None
+
+    def arrays(self) -> dict:
+        """Copies of the model's device arrays (torch int32 tensors)."""
+        ptrs = [C.c_void_p() for _ in range(6)]
+        cnt = [C.c_int64() for _ in range(3)]
+        _check(load().vmo_hg_arrays(self._h, C.byref(ptrs[0]), C.byref(ptrs[1]), C.byref(cnt[0]), C.byref(ptrs[2]),
+                                    C.byref(ptrs[3]), C.byref(cnt[1]), C.byref(ptrs[4]), C.byref(ptrs[5]),
+                                    C.byref(cnt[2])))
+        torch.cuda.current_stream().synchronize()
+
+        def view(p, n):
+            if not p.value or n == 0:
+                return torch.zeros(0, dtype=torch.int32, device="cuda")
+            return torch.as_tensor(_View(p.value, n, "<i4"), device="cuda").clone()
+
+        out = {"net_ptr": view(ptrs[2], self.nets + 1), "pins": view(ptrs[3], cnt[1].value),
+               "vtx_ptr": view(ptrs[4], self.k + 1), "vnets": view(ptrs[5], cnt[2].value)}
+        if self.model in ("symmetric", "bipartite"):
+            out["adj_ptr"] = view(ptrs[0], self.k + 1)
+            out["adj"] = view(ptrs[1], cnt[0].value)
+        return out
+
+    def components(self) -> torch.Tensor:
+        lab = torch.empty(self.k, dtype=torch.int32, device="cuda")
+        _check(load().vmo_components(self._h, _ptr(lab), _stream()))
+        return lab
+
+    def layout(self, params: Params | None = None, coords: torch.Tensor | None = None) -> torch.Tensor:
+        """Geometry of Sec. 2: fp32 [k, 4] coordinates."""
+        p = (params or Params())._c()
+        x = coords if coords is not None else torch.zeros((self.k, 4), dtype=torch.float32, device="cuda")
+        _check(load().vmo_layout(self._h, C.byref(p), _ptr(x), int(coords is not None), _stream()))
+        return x
+
+    def layout_step(self, coords: torch.Tensor, step: float, params: Params | None = None):
+        """One step of Algorithm 4: (new coords, gradient y, level-L keys, L)."""
+        p = (params or Params())._c()
+        x = coords.clone().contiguous()
+        y = torch.zeros_like(x)
+        keys = torch.zeros(self.k, dtype=torch.int32, device="cuda")
+        L = C.c_int32()
+        _check(load().vmo_layout_step(self._h, C.byref(p), _ptr(x), step, _ptr(y), _ptr(keys), C.byref(L), _stream()))
+        return x, y, keys, int(L.value)
+
+    def coarsen(self, params: Params | None = None):
+        """Level-0 matching (mate, pi, kc) and the sizes of all levels."""
+        p = (params or Params())._c()
+        mate = torch.empty(self.k, dtype=torch.int32, device="cuda")
+        pi = torch.empty(self.k, dtype=torch.int32, device="cuda")
+        kc = C.c_int32()
+        sizes = (C.c_int32 * 41)()
+        nl = C.c_int32()
+        _check(load().vmo_coarsen(self._h, C.byref(p), _ptr(mate), _ptr(pi), C.byref(kc), sizes, C.byref(nl),
+                                  _stream()))
+        return mate, pi, int(kc.value), [int(sizes[i]) for i in range(nl.value)]
+
+    def bisect(self, coords: torch.Tensor, verts: torch.Tensor, seed: int, key: int = 1, km_iters: int = 20,
+               d: int = 3):
+        """2-means of coords[verts] (Algorithm 5, m = 2): (split, labels, z1, z2)."""
+        verts = verts.to(device="cuda", dtype=torch.int32).contiguous()
+        labels = torch.zeros(verts.numel(), dtype=torch.uint8, device="cuda")
+        z = torch.zeros(8, dtype=torch.float32, device="cuda")
+        split = C.c_int32()
+        _check(load().vmo_bisect(self._h, d, _ptr(coords), _ptr(verts), verts.numel(), seed & (2 ** 64 - 1), key,
+                                 km_iters, _ptr(labels), _ptr(z), C.byref(split), _stream()))
+        return bool(split.value), labels, z[:4], z[4:]
+
+    def _tree(self, cap: int):
+        t = {"heap": torch.zeros(cap, dtype=torch.int64, device="cuda")}
+        for f in ("offset", "n1", "n2", "nsep", "depth"):
+            t[f] = torch.zeros(cap, dtype=torch.int32, device="cuda")
+        ct = _Tree(cap, 0, *(t[f].data_ptr() for f in ("heap", "offset", "n1", "n2", "nsep", "depth")))
+        return t, ct
+
+    def order(self, params: Params | None = None, coords: torch.Tensor | None = None, sbd: bool = False,
+              with_tree: bool = True):
+        """Recursive BBD (or SBD) ordering: (row_perm, col_perm, tree)."""
+        p = (params or Params())._c()
+        rows = self.m
+        cols = self.n if self.model == "bipartite" else self.m
+        rp = torch.empty(rows, dtype=torch.int32, device="cuda")
+        cp = torch.empty(cols, dtype=torch.int32, device="cuda")
+        t, ct = self._tree(2 * self.k + 16) if with_tree else (None, None)
+        fn = load().vmo_order_sbd if sbd else load().vmo_order_bbd
+        _check(fn(self._h, _ptr(coords), C.byref(p), _ptr(rp), _ptr(cp), C.byref(ct) if ct else None, _stream()))
+        tree = {f: v[:ct.count] for f, v in t.items()} if t else None
+        return rp, cp, tree
+
+    def order_vertices(self, params: Params | None = None, coords: torch.Tensor | None = None, sbd: bool = False):
+        """Vertex permutation of the recursive ordering and its tree."""
+        p = (params or Params())._c()
+        perm = torch.empty(self.k, dtype=torch.int32, device="cuda")
+        t, ct = self._tree(2 * self.k + 16)
+        _check(load().vmo_order_vertices(self._h, _ptr(coords), C.byref(p), int(sbd), _ptr(perm), C.byref(ct),
+                                         _stream()))
+        return perm, {f: v[:ct.count] for f, v in t.items()}
+
+    def cut_size(self, part: torch.Tensor, nparts: int):
+        """(cut-net count, lambda - 1) of a vertex partition over the nets."""
+        part = part.to(device="cuda", dtype=torch.int32).contiguous()
+        a, b = C.c_int64(), C.c_int64()
+        _check(load().vmo_cut_size(self._h, _ptr(part), nparts, C.byref(a), C.byref(b), _stream()))
+        return int(a.value), int(b.value)

@@ -1,0 +1,51 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/vmo.h (no compute calls: no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "vmo.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vmo_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1105_4490_gb300 import _build_lib
+    path = _build_lib.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 18
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_binding_covers_header():
+    from paper_1105_4490_gb300 import vmo
+    assert sorted(vmo.SYMBOLS) == _declared()
+
+
+def test_status_strings_and_defaults(lib):
+    from paper_1105_4490_gb300 import vmo
+    L = vmo.load()
+    assert L.vmo_status_string(0) == b"ok"
+    assert L.vmo_status_string(6) == b"unsupported"
+    p = vmo.default_params()
+    assert (p.d, p.iters, p.km_iters, p.min_part, p.occupancy) == (3, 100, 20, 64, 8)
+    assert abs(p.decay - 0.9) < 1e-6 and p.sigma == 1.0
+
+
+def test_params_struct_layout():
+    """The ctypes mirror matches the C struct (field order and size)."""
+    from paper_1105_4490_gb300 import vmo
+    assert ctypes.sizeof(vmo._Params) == 4 * 11 + 4 + 8  # 11 x 4-byte fields, padding, uint64 seed
+    assert ctypes.sizeof(vmo._Tree) == 8 + 6 * 8

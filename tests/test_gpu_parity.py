@@ -1,0 +1,342 @@
+"""GPU parity: the CUDA library (through its C-ABI) against the CPU oracle on
+the same seeded inputs.
+
+Bars: integer work (models, components, matching, 2-means labels, separators,
+permutations, trees, cuts) bit-exact; fp32 initial coordinates bit-exact;
+one layout step within 1e-4 normwise of the FP64 oracle (gradient and
+displacement); full runs within 5% on cut and fill."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+Y_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def V():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1105_4490_gb300 as P
+    assert torch.cuda.is_available()
+    return P
+
+
+@pytest.fixture(scope="module")
+def O():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _with_dups(A, seed):
+    """Same pattern with shuffled column order, duplicated entries and a few
+    diagonal entries, to exercise sorting and de-duplication."""
+    rng = np.random.default_rng(seed)
+    rows = np.repeat(np.arange(A.m), np.diff(A.rowptr))
+    cols = A.colidx.copy()
+    extra = rng.integers(0, len(cols), max(1, len(cols) // 10))
+    rows = np.concatenate([rows, rows[extra]])
+    cols = np.concatenate([cols, cols[extra]])
+    perm = rng.permutation(len(rows))
+    rows, cols = rows[perm], cols[perm]
+    order = np.argsort(rows, kind="stable")
+    rows, cols = rows[order], cols[order]
+    rp = np.zeros(A.m + 1, dtype=np.int32)
+    rp[1:] = np.cumsum(np.bincount(rows, minlength=A.m))
+    return W.Matrix(A.name + "_dups", A.m, A.n, rp, cols.astype(np.int32))
+
+
+CASES = [
+    ("grid2d_64", lambda: W.grid_laplacian_2d(64), "symmetric"),
+    ("powerlaw_3000", lambda: W.powerlaw_symmetric(3000, seed=2), "symmetric"),
+    ("random_dups", lambda: _with_dups(W.random_symmetric(2500, 7, 3), 1), "symmetric"),
+    ("rect_bipartite", lambda: _with_dups(W.powerlaw_rectangular(1500, 900, seed=4), 2), "bipartite"),
+    ("rect_rownet", lambda: W.powerlaw_rectangular(1500, 900, seed=4), "rownet"),
+    ("rect_colnet", lambda: _with_dups(W.powerlaw_rectangular(1500, 900, seed=5), 3), "colnet"),
+]
+
+
+@pytest.mark.parametrize("name,make,model", CASES)
+def test_build_hypergraph_bit_exact(V, O, name, make, model):
+    A = make()
+    hg = V.Hypergraph.from_matrix(A, model)
+    ref = O.build_from_matrix(model, A)
+    a = hg.arrays()
+    assert hg.k == ref.k and hg.nets == ref.l
+    assert np.array_equal(_np(a["net_ptr"]), ref.net_ptr)
+    assert np.array_equal(_np(a["pins"]), ref.pins)
+    assert np.array_equal(_np(a["vtx_ptr"]), ref.vtx_ptr)
+    assert np.array_equal(_np(a["vnets"]), ref.vnets)
+    if model in ("symmetric", "bipartite"):
+        assert np.array_equal(_np(a["adj_ptr"]), ref.adj_ptr)
+        assert np.array_equal(_np(a["adj"]), ref.adj)
+
+
+def test_build_edge_cases(V, O):
+    # empty pattern, a single entry, an empty row and column, diagonal only
+    for A in (W.csr_from_coo(5, 5, np.array([], int), np.array([], int), "empty"),
+              W.csr_from_coo(1, 1, np.array([0]), np.array([0]), "one"),
+              W.csr_from_coo(6, 6, np.array([0, 2, 5]), np.array([2, 0, 1]), "sparse"),
+              W.csr_from_coo(4, 4, np.arange(4), np.arange(4), "diag")):
+        for model in ("symmetric", "bipartite", "rownet", "colnet"):
+            hg = V.Hypergraph.from_matrix(A, model)
+            ref = O.build_from_matrix(model, A)
+            a = hg.arrays()
+            assert hg.k == ref.k and hg.nets == ref.l
+            assert np.array_equal(_np(a["net_ptr"]), ref.net_ptr)
+            assert np.array_equal(_np(a["pins"]), ref.pins)
+
+
+def test_invalid_csr_rejected(V):
+    rp = torch.tensor([0, 2, 1], dtype=torch.int32)
+    ci = torch.tensor([0, 1], dtype=torch.int32)
+    with pytest.raises(V.VmoError) as e:
+        V.Hypergraph(rp, ci, 2, 2)
+    assert e.value.status == 1
+    with pytest.raises(V.VmoError):
+        V.Hypergraph(torch.tensor([0, 1, 2], dtype=torch.int32), torch.tensor([0, 7], dtype=torch.int32), 2, 2)
+
+
+@pytest.mark.parametrize("name,make,model", CASES)
+def test_components_bit_exact(V, O, name, make, model):
+    A = make()
+    hg = V.Hypergraph.from_matrix(A, model)
+    ref = O.build_from_matrix(model, A)
+    assert np.array_equal(_np(hg.components()), O.components(ref))
+
+
+def test_components_many(V, O):
+    A = W.random_symmetric(20000, 1.9, 7)
+    hg = V.Hypergraph.from_matrix(A)
+    ref = O.build_from_matrix("symmetric", A)
+    got = _np(hg.components())
+    assert np.array_equal(got, O.components(ref))
+    assert len(np.unique(got)) > 100
+
+
+@pytest.mark.parametrize("k,d", [(1, 2), (4096, 2), (5000, 3), (20001, 3), (777, 4)])
+def test_init_coords_bit_exact(V, O, k, d):
+    x = _np(V.init_coords(k, d, 12345))
+    assert np.array_equal(x.view(np.uint32), O.init_coords(k, d, 12345).view(np.uint32))
+
+
+def _layout_case(V, O, A, d, seed, occ=8, model="symmetric"):
+    hg = V.Hypergraph.from_matrix(A, model)
+    ref = O.build_from_matrix(model, A)
+    x0 = O.init_coords(ref.k, d, seed)
+    p = V.Params(d=d, occupancy=occ)
+    step = 0.37
+    xg, yg, kg, L = hg.layout_step(torch.as_tensor(x0).cuda(), step, p)
+    xo, yo, ko, Lo = O.layout_step(ref, d, x0.astype(np.float64), step, occ=occ)
+    assert L == Lo
+    assert np.array_equal(_np(kg).view(np.uint32), ko)
+    yg, xg = _np(yg).astype(np.float64), _np(xg).astype(np.float64)
+    ey = np.linalg.norm(yg[:, :d] - yo[:, :d]) / np.linalg.norm(yo[:, :d])
+    dx_o = xo[:, :d] - x0[:, :d]
+    ex = np.linalg.norm((xg[:, :d] - x0[:, :d]) - dx_o) / np.linalg.norm(dx_o)
+    return ey, ex
+
+
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_layout_step_grid(V, O, d):
+    ey, ex = _layout_case(V, O, W.grid_laplacian_2d(80), d, seed=3)
+    assert ey <= Y_TOL, ey
+    assert ex <= Y_TOL, ex
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_layout_step_powerlaw_ragged(V, O, d):
+    ey, ex = _layout_case(V, O, W.powerlaw_symmetric(10007, seed=5), d, seed=4)
+    assert ey <= Y_TOL and ex <= Y_TOL, (ey, ex)
+
+
+def test_layout_step_hypergraph_nets(V, O):
+    ey, ex = _layout_case(V, O, W.powerlaw_rectangular(3000, 2000, seed=6), 3, seed=5, model="colnet")
+    assert ey <= Y_TOL and ex <= Y_TOL, (ey, ex)
+
+
+def test_layout_step_single_level_exact_mode(V, O):
+    """occupancy >= k gives L = 1: the approximation is the all-pairs sum."""
+    ey, ex = _layout_case(V, O, W.random_symmetric(600, 6, 2), 3, seed=6, occ=10 ** 6)
+    assert ey <= Y_TOL and ex <= Y_TOL, (ey, ex)
+
+
+@pytest.mark.parametrize("make", [lambda: W.grid_laplacian_2d(64), lambda: W.powerlaw_symmetric(5000, seed=8),
+                                  lambda: W.grid_laplacian_3d(20)])
+def test_coarsening_bit_exact(V, O, make):
+    A = make()
+    hg = V.Hypergraph.from_matrix(A)
+    ref = O.build_from_matrix("symmetric", A)
+    p = V.Params(seed=11)
+    mate, pi, kc, sizes = hg.coarsen(p)
+    kc_o, mate_o, pi_o = O.match(ref.k, ref.adj_ptr, ref.adj, np.ones(len(ref.adj)), seed=11)
+    assert kc == kc_o
+    assert np.array_equal(_np(mate), mate_o)
+    assert np.array_equal(_np(pi), pi_o)
+    assert sizes == O.hierarchy(ref, 11)
+
+
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_bisect_bit_exact(V, O, d):
+    A = W.powerlaw_symmetric(6000, seed=9)
+    hg = V.Hypergraph.from_matrix(A)
+    x = O.init_coords(hg.k, d, 9)
+    xt = torch.as_tensor(x).cuda()
+    rng = np.random.default_rng(d)
+    for trial in range(6):
+        nv = int(rng.integers(2, 6000))
+        verts = rng.choice(hg.k, nv, replace=False).astype(np.int32)
+        key = int(rng.integers(1, 1 << 40))
+        for km in (0, 3, 20):
+            ok, lab, z1, z2 = hg.bisect(xt, torch.as_tensor(verts), seed=77, key=key, km_iters=km, d=d)
+            ok_o, lab_o, z1_o, z2_o = O.bisect(d, x, verts, seed=77, key=key, km_iters=km)
+            assert ok == ok_o
+            assert np.array_equal(_np(lab), lab_o)
+            assert np.array_equal(_np(z1).view(np.uint32), z1_o.view(np.uint32))
+            assert np.array_equal(_np(z2).view(np.uint32), z2_o.view(np.uint32))
+
+
+def test_bisect_degenerate(V, O):
+    A = W.grid_laplacian_2d(4)
+    hg = V.Hypergraph.from_matrix(A)
+    x = np.zeros((16, 4), dtype=np.float32)
+    x[:, :2] = 3.0  # all points coincide
+    ok, lab, z1, z2 = hg.bisect(torch.as_tensor(x).cuda(), torch.arange(16), seed=1, d=2)
+    ok_o, lab_o, z1_o, z2_o = O.bisect(2, x, np.arange(16), seed=1)
+    assert ok == ok_o is False
+    assert np.array_equal(_np(lab), lab_o)
+    ok, lab, *_ = hg.bisect(torch.as_tensor(x).cuda(), torch.arange(1), seed=1, d=2)
+    assert not ok and _np(lab).tolist() == [1]
+
+
+def _order_compare(V, O, A, model, d, coords, sbd, min_part=64, max_depth=62, seed=5):
+    hg = V.Hypergraph.from_matrix(A, model)
+    ref = O.build_from_matrix(model, A)
+    p = V.Params(d=d, min_part=min_part, max_depth=max_depth, seed=seed)
+    perm, tree = hg.order_vertices(p, torch.as_tensor(coords).cuda(), sbd=sbd)
+    perm_o, tree_o = O.order(ref, d, coords, seed=seed, min_part=min_part, max_depth=max_depth, sbd=sbd)
+    assert np.array_equal(_np(perm), perm_o)
+    assert np.array_equal(_np(tree["heap"]).astype(np.uint64), tree_o["heap"])
+    for f in ("offset", "n1", "n2", "nsep", "depth"):
+        assert np.array_equal(_np(tree[f]), tree_o[f]), f
+    return hg, ref, perm_o, tree_o
+
+
+@pytest.mark.parametrize("sbd", [False, True])
+def test_order_given_grid_coordinates(V, O, sbd):
+    A = W.grid_laplacian_2d(64)
+    ij = np.indices((64, 64)).reshape(2, -1).T
+    x = np.zeros((4096, 4), dtype=np.float32)
+    x[:, :2] = ij
+    _order_compare(V, O, A, "symmetric", 2, x, sbd)
+
+
+@pytest.mark.parametrize("sbd", [False, True])
+@pytest.mark.parametrize("d", [2, 3])
+def test_order_random_coordinates(V, O, sbd, d):
+    A = W.powerlaw_symmetric(9000, seed=12)
+    x = O.init_coords(A.n, d, 12)
+    _order_compare(V, O, A, "symmetric", d, x, sbd, min_part=16)
+
+
+def test_order_bipartite_sbd_rows_and_cols(V, O):
+    A = W.powerlaw_rectangular(2000, 1500, seed=13)
+    ref = O.build_from_matrix("bipartite", A)
+    x = O.init_coords(ref.k, 2, 13)
+    hg, ref, perm_o, tree_o = _order_compare(V, O, A, "bipartite", 2, x, True, min_part=1, max_depth=6)
+    rp, cp, tree = hg.order(V.Params(d=2, min_part=1, max_depth=6, seed=5), torch.as_tensor(x).cuda(), sbd=True)
+    assert np.array_equal(_np(rp), perm_o[perm_o < A.m])
+    assert np.array_equal(_np(cp), perm_o[perm_o >= A.m] - A.m)
+
+
+def test_order_degenerate_inputs(V, O):
+    """Tiny problems, coincident points and a disconnected graph."""
+    A = W.random_symmetric(300, 1.5, 3)
+    x = np.zeros((300, 4), dtype=np.float32)
+    x[:150, :2] = 1.0
+    x[150:, :2] = 2.0
+    _order_compare(V, O, A, "symmetric", 2, x, False, min_part=2)
+    B = W.grid_laplacian_2d(3)
+    _order_compare(V, O, B, "symmetric", 2, O.init_coords(9, 2, 1), False, min_part=64)
+    _order_compare(V, O, B, "symmetric", 2, O.init_coords(9, 2, 1), False, min_part=0)
+
+
+def test_order_full_pipeline_replay(V, O):
+    """GPU layout, then the oracle orders the GPU coordinates: same permutation
+    (replay bit-exactness of the whole ordering stage)."""
+    A = W.grid_laplacian_2d(64)
+    hg = V.Hypergraph.from_matrix(A)
+    p = V.Params(d=2, seed=3)
+    x = hg.layout(p)
+    perm, tree = hg.order_vertices(p, x)
+    ref = O.build_from_matrix("symmetric", A)
+    perm_o, tree_o = O.order(ref, 2, _np(x), seed=3)
+    assert np.array_equal(_np(perm), perm_o)
+    # and layout + order in one call gives the same result (deterministic)
+    perm2, _ = hg.order_vertices(p)
+    assert np.array_equal(_np(perm2), perm_o)
+
+
+@pytest.mark.parametrize("model", ["symmetric", "bipartite", "rownet", "colnet"])
+@pytest.mark.parametrize("nparts", [2, 37, 64, 65, 1000])
+def test_cut_size_bit_exact(V, O, model, nparts):
+    A = W.powerlaw_rectangular(1200, 1200, seed=14) if model != "symmetric" else W.powerlaw_symmetric(1200, seed=14)
+    hg = V.Hypergraph.from_matrix(A, model)
+    ref = O.build_from_matrix(model, A)
+    part = np.random.default_rng(nparts).integers(0, nparts, ref.k).astype(np.int32)
+    assert hg.cut_size(torch.as_tensor(part), nparts) == O.cut_size(ref.net_ptr, ref.pins, part)
+
+
+def test_end_to_end_quality_grid2d(V, O):
+    """Config-1 workload end to end: GPU (layout + BBD) against the oracle's own
+    FP64 layout + BBD with the same seeds; fill and separator totals within 5%
+    (mean over seeds)."""
+    A = W.grid_laplacian_2d(64)
+    hg = V.Hypergraph.from_matrix(A)
+    ref = O.build_from_matrix("symmetric", A)
+    fg, fo, sg, so = [], [], [], []
+    for seed in (1, 2, 3):
+        p = V.Params(d=2, seed=seed)
+        perm, tree = hg.order_vertices(p)
+        fg.append(O.fill_in(A, _np(perm)))
+        sg.append(int(_np(tree["nsep"]).sum()))
+        xo = O.layout_multilevel(ref, 2, seed)
+        perm_o, tree_o = O.order(ref, 2, xo.astype(np.float32), seed=seed)
+        fo.append(O.fill_in(A, perm_o))
+        so.append(int(tree_o["nsep"].sum()))
+    assert abs(np.mean(fg) / np.mean(fo) - 1) <= 0.05, (fg, fo)
+    assert abs(np.mean(sg) / np.mean(so) - 1) <= 0.05, (sg, so)
+
+
+def test_layout_deterministic(V):
+    A = W.powerlaw_symmetric(20000, seed=15)
+    hg = V.Hypergraph.from_matrix(A)
+    p = V.Params(d=3, seed=4, iters=20)
+    a = _np(hg.layout(p))
+    b = _np(hg.layout(p))
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+@pytest.mark.slow
+def test_full_size_grid3d_step_and_order(V, O):
+    """64^3 7-point Laplacian (262,144 vertices, the medium configuration): one
+    layout step within tolerance and a bit-exact ordering at full size."""
+    A = W.grid_laplacian_3d(64)
+    ey, ex = _layout_case(V, O, A, 3, seed=21)
+    assert ey <= Y_TOL and ex <= Y_TOL, (ey, ex)
+    hg = V.Hypergraph.from_matrix(A)
+    p = V.Params(d=3, max_depth=10, seed=21)
+    x = hg.layout(p)
+    perm, tree = hg.order_vertices(p, x)
+    ref = O.build_from_matrix("symmetric", A)
+    perm_o, tree_o = O.order(ref, 3, _np(x), seed=21, max_depth=10)
+    assert np.array_equal(_np(perm), perm_o)
+    assert np.array_equal(_np(tree["nsep"]), tree_o["nsep"])

@@ -1,0 +1,309 @@
+#!/usr/bin/env python
+"""Benchmark of GPU visual matrix ordering: nnz ordered per second (recursive
+BBD), one JSON line on stdout.
+
+Workload (one step): the medium configuration — a 3D 7-point Laplacian on a
+64^3 grid (262,144 rows, 1,810,432 nnz) and a seeded random symmetric
+power-law matrix with 500,000 rows (~5.6M nnz) — each taken from a
+device-resident CSR to device-resident permutations: hypergraph build,
+multilevel layout in d = 3 (T = 100 steps per level), recursive BBD to depth
+10.  Inputs are synthetic (seeded generators in ``workloads``).
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by a device
+synchronisation and timed with CUDA events on the current stream; the L2 cache
+(129 MB) is flushed by writing a 512 MB buffer before every timed step.
+Under torchrun every rank orders its own replica (weak scaling, no
+collective on the data path); the time is the max over ranks.
+
+--impl reference times the CPU oracle (test infrastructure, FP64, single
+thread) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "nnz ordered/sec (recursive BBD)"
+# algorithmic FP32 operations per source interaction of the layout step kernel
+# (differences, squared norm, reciprocal power, force accumulation), per d
+FLOPS_PER_INTERACTION = {2: 10, 3: 18, 4: 23}
+FP32_LANES_PER_SM = 128
+SMS = 152
+
+
+def medium_workload():
+    mats = [(W.grid_laplacian_3d(64), dict(d=3, max_depth=10)),
+            (W.powerlaw_symmetric(500_000, seed=1), dict(d=3, max_depth=10))]
+    return "grid3d_64^3+powerlaw_500k", mats
+
+
+def cpu_sample(small: bool):
+    """Bounded sample of the medium workload for the oracle: the same two
+    families with the same parameters, scaled down."""
+    if small:
+        return "grid3d_12^3+powerlaw_1000", [(W.grid_laplacian_3d(12), dict(d=3, max_depth=10)),
+                                               (W.powerlaw_symmetric(1000, seed=1), dict(d=3, max_depth=10))]
+    return "grid3d_16^3+powerlaw_2000", [(W.grid_laplacian_3d(16), dict(d=3, max_depth=10)),
+                                          (W.powerlaw_symmetric(2000, seed=1), dict(d=3, max_depth=10))]
+
+
+def oracle_step(mats, seed=1):
+    import oracle
+    nnz = 0
+    for A, cfg in mats:
+        hg = oracle.build_from_matrix("symmetric", A)
+        x = oracle.layout_multilevel(hg, cfg["d"], seed)
+        oracle.order(hg, cfg["d"], x.astype(np.float32), seed=seed, max_depth=cfg["max_depth"])
+        nnz += A.nnz
+    return nnz
+
+
+def run_cpu_baseline(mats, sample_name):
+    t0 = time.perf_counter()
+    nnz = oracle_step(mats)
+    dt = time.perf_counter() - t0
+    return {"value": nnz / dt, "unit": "nnz/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample_name}: oracle FP64 single-thread, full pipeline (multilevel layout d=3, T=100 per "
+                      f"level, recursive BBD depth 10), {nnz} nnz in {dt:.1f} s"}
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"vmo_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_step(V, torch, mats, dev_csr, params):
+    """Build + layout + recursive BBD of every matrix; returns nnz ordered."""
+    nnz = 0
+    for (A, cfg), (rp, ci) in zip(mats, dev_csr):
+        hg = V.Hypergraph(rp, ci, A.m, A.n, "symmetric")
+        p = V.Params(d=cfg["d"], max_depth=cfg["max_depth"], seed=params["seed"])
+        hg.order(p, None, sbd=False, with_tree=True)
+        nnz += A.nnz
+        del hg
+    return nnz
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="vmo", choices=["vmo", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        sample_name, mats = cpu_sample(small=True)
+        for _ in range(max(args.warmup, 0)):
+            oracle_step(mats)
+        t0 = time.perf_counter()
+        nnz = 0
+        for _ in range(args.steps):
+            nnz += oracle_step(mats)
+        dt = time.perf_counter() - t0
+        val = nnz / dt
+        print(json.dumps({"metric": METRIC, "value": val, "unit": "nnz/s", "impl": "reference", "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": sample_name, "l2": "n/a (CPU)"},
+                          "cpu_baseline": {"value": val, "unit": "nnz/s", "cores": 1, "kind": "oracle",
+                                           "sample": f"{sample_name}, oracle FP64 single-thread per step"},
+                          "e2e": {"value": val, "unit": "nnz/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1105_4490_gb300 as V
+    V.load()
+
+    name, mats = medium_workload()
+    params = {"seed": 1}
+    dev_csr = [(torch.as_tensor(A.rowptr).cuda(), torch.as_tensor(A.colidx).cuda()) for A, _ in mats]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        gpu_step(V, torch, mats, dev_csr, params)
+
+    # one untimed counting step: interactions and points of the step kernel
+    V.stats_reset(time_step_kernel=True, count_interactions=True)
+    gpu_step(V, torch, mats, dev_csr, params)
+    counted = V.stats()
+
+    # timed region
+    V.stats_reset(time_step_kernel=True, count_interactions=False)
+    elapsed = 0.0
+    nnz = 0
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            barrier()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            nnz += gpu_step(V, torch, mats, dev_csr, params)
+            b.record(stream)
+            barrier()
+            elapsed += a.elapsed_time(b) / 1e3
+    st = V.stats()
+    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    value = nnz * world / tmax
+
+    # end to end through the public API: pinned host CSR -> permutations on the host
+    host_csr = [(torch.as_tensor(A.rowptr).pin_memory(), torch.as_tensor(A.colidx).pin_memory()) for A, _ in mats]
+    h2d = sum(r.numel() * 4 + c.numel() * 4 for r, c in host_csr)
+    d2h = 0
+    e2e_time = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        d2h = 0
+        for (A, cfg), (rp, ci) in zip(mats, host_csr):
+            hg = V.Hypergraph(rp.cuda(non_blocking=True), ci.cuda(non_blocking=True), A.m, A.n, "symmetric")
+            p = V.Params(d=cfg["d"], max_depth=cfg["max_depth"], seed=params["seed"])
+            rperm, cperm, _ = hg.order(p, None, sbd=False, with_tree=False)
+            rh = rperm.to("cpu", non_blocking=False)
+            ch = cperm.to("cpu", non_blocking=False)
+            d2h += rh.numel() * 4 + ch.numel() * 4
+            del hg
+        b.record(stream)
+        barrier()
+        e2e_time += a.elapsed_time(b) / 1e3
+    te = torch.tensor([e2e_time], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = nnz * world / float(te.item())
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    csum = clocks.summary()
+    sm_mhz = csum["sm_mhz"] if csum else 2070.0
+    d = 3
+    inter_per_step = counted["step_interactions"]
+    launches_per_step = max(counted["step_launches"], 1)
+    flops_per_launch = inter_per_step * FLOPS_PER_INTERACTION[d] / launches_per_step
+    avg_ms = st["step_ms"] / max(st["step_launches"], 1)
+    achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
+    peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": "k_repulse_update<3> (layout step)", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x median SM clock "
+                               f"{sm_mhz:.0f} MHz during the timed region",
+                "interactions_per_launch": inter_per_step / launches_per_step,
+                "flops_per_interaction": FLOPS_PER_INTERACTION[d],
+                "avg_launch_ms": avg_ms, "launches": st["step_launches"],
+                "share_of_step": st["step_ms"] / 1e3 / elapsed}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        sname, smats = cpu_sample(small=False)
+        cpu = run_cpu_baseline(smats, sname)
+
+    out = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
+           "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded generators; SuiteSparse matrices are not available)",
+           "config": {"workload": name, "nnz_per_step": nnz // args.steps, "model": "symmetric", "d": 3,
+                      "iters_per_level": 100, "max_depth": 10, "layout": "multilevel",
+                      "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
+           "gpu_launches": st["launches"], "clocks": csum, "roofline": roofline, "cpu_baseline": cpu,
+           "e2e": {"value": e2e_value, "unit": "nnz/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -86,13 +86,17 @@ typedef struct {
   uint64_t seed;        /* seed of every random draw (1) */
 } vmo_params;
 
-/* Tree of the recursive ordering, one record per node, sorted by heap
- * number (root 1; children of h are 2h (V1) and 2h+1 (V2)), i.e. breadth
- * first.  A leaf has n1 = |V|, n2 = nsep = 0.  An internal node's vertices
- * occupy [offset, offset + n1 + n2 + nsep) of the permutation as
- * [V1, V2, V3] (BBD) or [V1, V3, V2] (SBD).  Device arrays of `capacity`
- * entries each; `count` is written (host) on return.  A tree never has more
- * than 2k records. */
+/* Tree of the recursive ordering, one record per node.  A disconnected graph
+ * is ordered component by component (Sec. 2.2: each connected component is
+ * treated separately; the matrix is block diagonal), components in order of
+ * their smallest vertex id, each with its own recursion whose root has heap
+ * number 1 (children of h are 2h (V1) and 2h+1 (V2)).  Records are sorted by
+ * (component, heap number), i.e. breadth first within a component.  A leaf
+ * has n1 = |V|, n2 = nsep = 0.  An internal node's vertices occupy
+ * [offset, offset + n1 + n2 + nsep) of the vertex permutation (absolute
+ * positions) as [V1, V2, V3] (BBD) or [V1, V3, V2] (SBD).  Device arrays of
+ * `capacity` entries each (component may be NULL); `count` is written (host)
+ * on return.  A tree never has more than 2k records. */
 typedef struct {
   int32_t capacity;
   int32_t count;
@@ -102,7 +106,22 @@ typedef struct {
   int32_t* n2;
   int32_t* nsep;
   int32_t* depth;
+  int32_t* component;
 } vmo_tree;
+
+/* Counters of the library's own device work since the last vmo_stats_reset
+ * (process-wide, all threads): kernels launched; and, when enabled, the
+ * device time of the layout step kernel (repulsion + update, timed with CUDA
+ * events on the launching stream), its launch count, the target points and the
+ * source interactions (near-field pairs plus far-field cell charges) it
+ * evaluated. */
+typedef struct {
+  uint64_t launches;
+  uint64_t step_launches;
+  double step_ms;
+  uint64_t step_points;
+  uint64_t step_interactions;
+} vmo_stats;
 
 /* Fills *p with the defaults listed above. */
 void vmo_default_params(vmo_params* p);
@@ -200,6 +219,14 @@ vmo_status vmo_order_vertices(vmo_hg hg, const float* coords, const vmo_params* 
  * Errors: VMO_ERR_INVALID for nparts < 1. */
 vmo_status vmo_cut_size(vmo_hg hg, const int32_t* part, int32_t nparts, int64_t* cutnet, int64_t* lambda1,
                         void* stream);
+
+/* Resets the counters.  time_step_kernel != 0 records CUDA events around
+ * every layout step kernel; count_interactions != 0 makes that kernel count
+ * its interactions (an atomic per warp; same arithmetic otherwise). */
+void vmo_stats_reset(int32_t time_step_kernel, int32_t count_interactions);
+
+/* Reads the counters (synchronises the device when kernel timing is on). */
+vmo_status vmo_stats_get(vmo_stats* out);
 
 /* Frees the handle and its device arrays (NULL is ignored). */
 void vmo_destroy(vmo_hg hg);

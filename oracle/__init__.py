@@ -51,7 +51,7 @@ class _Tree(C.Structure):
     _fields_ = [("count", C.c_int32), ("heap", C.POINTER(C.c_uint64)),
                 ("offset", C.POINTER(C.c_int32)), ("n1", C.POINTER(C.c_int32)),
                 ("n2", C.POINTER(C.c_int32)), ("nsep", C.POINTER(C.c_int32)),
-                ("depth", C.POINTER(C.c_int32))]
+                ("depth", C.POINTER(C.c_int32)), ("comp", C.POINTER(C.c_int32))]
 
 
 class _Diag(C.Structure):
@@ -296,7 +296,8 @@ def hierarchy(hg: Hypergraph, seed: int, rounds: int = 4, kmin: int = 64) -> lis
 
 def layout_multilevel(hg: Hypergraph, d: int, seed: int, iters: int = 100, occ: int = 8, sigma: float = 1.0,
                       decay: float = 0.9, rounds: int = 4, kmin: int = 64, w=None) -> np.ndarray:
-    """Multilevel layout (Algorithm 3 around Algorithm 4); graph models only."""
+    """Multilevel layout (Algorithm 3 around Algorithm 4) of every connected
+    component on its own; graph models only."""
     if hg.adj_ptr is None:
         raise ValueError("multilevel layout needs a graph model")
     s = hg._struct()
@@ -320,7 +321,9 @@ def bisect(d: int, x4: np.ndarray, verts: np.ndarray, seed: int, key: int = 1, k
 
 def order(hg: Hypergraph, d: int, x4: np.ndarray, seed: int, km_iters: int = 20, min_part: int = 64,
           max_depth: int = 62, sbd: bool = False):
-    """Recursive BBD (or SBD) ordering from fp32 coordinates: (perm, tree)."""
+    """Recursive BBD (or SBD) ordering from fp32 coordinates: (perm, tree).
+    Connected components are ordered one after the other (block diagonal),
+    each by its own recursion; tree records are sorted by (comp, heap)."""
     if hg.adj_ptr is None:
         raise ValueError("ordering needs a graph model (symmetric or bipartite)")
     s = hg._struct()
@@ -331,7 +334,8 @@ def order(hg: Hypergraph, d: int, x4: np.ndarray, seed: int, km_iters: int = 20,
                       _p(perm), C.byref(t))
     n = t.count
     tree = dict(heap=_arr(t.heap, n, np.uint64), offset=_arr(t.offset, n, np.int32), n1=_arr(t.n1, n, np.int32),
-                n2=_arr(t.n2, n, np.int32), nsep=_arr(t.nsep, n, np.int32), depth=_arr(t.depth, n, np.int32))
+                n2=_arr(t.n2, n, np.int32), nsep=_arr(t.nsep, n, np.int32), depth=_arr(t.depth, n, np.int32),
+                comp=_arr(t.comp, n, np.int32))
     _load().ora_tree_free(C.byref(t))
     return perm, tree
 

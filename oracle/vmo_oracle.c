@@ -765,9 +765,9 @@ ORA_EXPORT int32_t ora_hierarchy(const ora_hg* h, uint64_t seed, int32_t rounds,
   return nl;
 }
 
-ORA_EXPORT int ora_layout_multilevel(const ora_hg* h, int32_t d, int32_t occ, double sigma, double decay,
-                                     int32_t iters, uint64_t seed, int32_t rounds, int32_t kmin, const double* w,
-                                     double* x /* out, k*4 */) {
+static int ora_layout_connected(const ora_hg* h, int32_t d, int32_t occ, double sigma, double decay,
+                                int32_t iters, uint64_t seed, int32_t rounds, int32_t kmin, const double* w,
+                                double* x /* out, k*4 */) {
   ora_graph G[41];
   int32_t* PI[41];
   memset(G, 0, sizeof(G)); memset(PI, 0, sizeof(PI));
@@ -803,6 +803,84 @@ ORA_EXPORT int ora_layout_multilevel(const ora_hg* h, int32_t d, int32_t occ, do
   free(xc);
   for (int32_t j = 0; j < nl; ++j) { ora_graph_free(&G[j]); free(PI[j]); }
   return nl;
+}
+
+/* Component grouping used by the layout and the ordering (Sec. 2.2: no
+ * minimiser exists for a disconnected hypergraph, so every connected
+ * component is treated separately).  Components are numbered in ascending
+ * order of their smallest vertex (the label of Algorithm 1); cperm lists the
+ * vertices component by component, ascending within a component; cbase[c]
+ * is the first position of component c (ncomp+1 entries).  Returns ncomp. */
+static int32_t ora_group_components(const ora_hg* h, int32_t* cperm, int32_t** cbase_out) {
+  int32_t k = h->k;
+  int32_t* lab = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
+  ora_components(k, h->l, h->net_ptr, h->pins, lab);
+  int32_t* cid = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
+  int32_t nc = 0;
+  for (int32_t v = 0; v < k; ++v) cid[v] = (lab[v] == v) ? nc++ : -1;
+  int32_t* cbase = (int32_t*)calloc((size_t)nc + 1, sizeof(int32_t));
+  for (int32_t v = 0; v < k; ++v) cbase[cid[lab[v]] + 1]++;
+  for (int32_t c = 0; c < nc; ++c) cbase[c + 1] += cbase[c];
+  int32_t* fill = (int32_t*)calloc((size_t)(nc > 0 ? nc : 1), sizeof(int32_t));
+  for (int32_t v = 0; v < k; ++v) {
+    int32_t c = cid[lab[v]];
+    cperm[cbase[c] + fill[c]++] = v;
+  }
+  free(lab); free(cid); free(fill);
+  *cbase_out = cbase;
+  return nc;
+}
+
+/* Induced subgraph of the vertices cperm[a..b) with local ids 0..b-a-1
+ * (adjacency only, neighbours ascending since local ids follow global ids). */
+static void ora_subgraph(const ora_hg* h, const int32_t* cperm, int32_t a, int32_t b, const int32_t* local,
+                         ora_hg* out) {
+  memset(out, 0, sizeof(*out));
+  int32_t k = b - a;
+  out->model = 0; out->k = k;
+  out->adj_ptr = (int32_t*)calloc((size_t)k + 1, sizeof(int32_t));
+  for (int32_t i = 0; i < k; ++i) {
+    int32_t v = cperm[a + i];
+    out->adj_ptr[i + 1] = out->adj_ptr[i] + (h->adj_ptr[v + 1] - h->adj_ptr[v]);
+  }
+  out->adj = (int32_t*)malloc((size_t)(out->adj_ptr[k] > 0 ? out->adj_ptr[k] : 1) * sizeof(int32_t));
+  for (int32_t i = 0; i < k; ++i) {
+    int32_t v = cperm[a + i];
+    int32_t o = out->adj_ptr[i];
+    for (int32_t t = h->adj_ptr[v]; t < h->adj_ptr[v + 1]; ++t) out->adj[o++] = local[h->adj[t]];
+  }
+}
+
+/* Multilevel layout (Algorithm 3) of a graph model, each connected component
+ * laid out on its own with local vertex ids (the paper applies Algorithm 3 to
+ * each component), all with the same seed. */
+ORA_EXPORT int ora_layout_multilevel(const ora_hg* h, int32_t d, int32_t occ, double sigma, double decay,
+                                     int32_t iters, uint64_t seed, int32_t rounds, int32_t kmin, const double* w,
+                                     double* x /* out, k*4 */) {
+  int32_t k = h->k;
+  int32_t* cperm = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
+  int32_t* cbase;
+  int32_t nc = ora_group_components(h, cperm, &cbase);
+  int32_t* local = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
+  for (int32_t c = 0; c < nc; ++c)
+    for (int32_t i = cbase[c]; i < cbase[c + 1]; ++i) local[cperm[i]] = i - cbase[c];
+  for (int32_t c = 0; c < nc; ++c) {
+    int32_t a = cbase[c], b = cbase[c + 1], kc = b - a;
+    ora_hg sub;
+    ora_subgraph(h, cperm, a, b, local, &sub);
+    double* wc = NULL;
+    if (w) {
+      wc = (double*)malloc((size_t)kc * sizeof(double));
+      for (int32_t i = 0; i < kc; ++i) wc[i] = w[cperm[a + i]];
+    }
+    double* xc = (double*)calloc((size_t)kc * 4, sizeof(double));
+    ora_layout_connected(&sub, d, occ, sigma, decay, iters, seed, rounds, kmin, wc, xc);
+    for (int32_t i = 0; i < kc; ++i)
+      for (int m = 0; m < 4; ++m) x[4 * (int64_t)cperm[a + i] + m] = xc[4 * (int64_t)i + m];
+    free(xc); free(wc); free(sub.adj_ptr); free(sub.adj);
+  }
+  free(cperm); free(cbase); free(local);
+  return nc;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -1002,30 +1080,40 @@ static int32_t ora_separate(const ora_hg* h, int d, const float* x4, const int32
 /* vertices are stably reordered to [V1, V2, V3] (BBD) or [V1, V3, V2] (SBD)  */
 /* and V1, V2 become children (when non-empty) with heap numbers 2h, 2h+1.    */
 /* The separator keeps its inherited order (it is not recursed into).         */
-/* perm[new] = old.  Tree records, sorted by heap number: heap, offset, n1,   */
-/* n2, nsep, depth (a leaf has n1 = |V|, n2 = nsep = 0).                      */
+/* perm[new] = old.  Tree records: heap, offset, n1, n2, nsep, depth, comp  */
+/* (a leaf has n1 = |V|, n2 = nsep = 0).                                      */
 /* ------------------------------------------------------------------------- */
 typedef struct {
   int32_t count;
   uint64_t* heap;
-  int32_t *offset, *n1, *n2, *nsep, *depth;
+  int32_t *offset, *n1, *n2, *nsep, *depth, *comp;
 } ora_tree;
 
 ORA_EXPORT void ora_tree_free(ora_tree* t) {
-  free(t->heap); free(t->offset); free(t->n1); free(t->n2); free(t->nsep); free(t->depth);
+  free(t->heap); free(t->offset); free(t->n1); free(t->n2); free(t->nsep); free(t->depth); free(t->comp);
   memset(t, 0, sizeof(*t));
 }
 
-typedef struct { uint64_t heap; int32_t offset, size, depth; } ora_node;
+typedef struct { uint64_t heap; int32_t offset, size, depth, comp; } ora_node;
 
-/* Records of each processed node; if rec_labels is non-NULL the 2-means labels
- * (position order, 1/2) and centres of every split node are also returned
- * for replay checks. */
+typedef struct { int32_t comp; uint64_t heap; int32_t rec; } ora_rec_key;
+static int cmp_rec_key(const void* a, const void* b) {
+  const ora_rec_key* p = (const ora_rec_key*)a;
+  const ora_rec_key* q = (const ora_rec_key*)b;
+  if (p->comp != q->comp) return (p->comp > q->comp) - (p->comp < q->comp);
+  return (p->heap > q->heap) - (p->heap < q->heap);
+}
+
+/* Ordering of a graph model from fp32 coordinates.  A disconnected graph is
+ * block diagonal: its components (grouped as in the layout) are ordered one
+ * after the other, each by its own recursion (root heap number 1).  Tree
+ * records carry the component index; offsets are absolute positions in perm;
+ * records are sorted by (component, heap number). */
 ORA_EXPORT int ora_order(const ora_hg* h, int32_t d, const float* x4, uint64_t seed, int32_t km_iters,
-                         int32_t min_part, int32_t max_depth, int32_t sbd, int32_t* perm,
-                         ora_tree* tree) {
+                         int32_t min_part, int32_t max_depth, int32_t sbd, int32_t* perm, ora_tree* tree) {
   int32_t k = h->k;
-  for (int32_t v = 0; v < k; ++v) perm[v] = v;
+  int32_t* cbase;
+  int32_t nc = ora_group_components(h, perm, &cbase);
   memset(tree, 0, sizeof(*tree));
   int32_t cap = 2 * k + 8;
   ora_node* queue = (ora_node*)malloc((size_t)cap * sizeof(ora_node));
@@ -1035,29 +1123,30 @@ ORA_EXPORT int ora_order(const ora_hg* h, int32_t d, const float* x4, uint64_t s
   tree->n2 = (int32_t*)malloc((size_t)cap * sizeof(int32_t));
   tree->nsep = (int32_t*)malloc((size_t)cap * sizeof(int32_t));
   tree->depth = (int32_t*)malloc((size_t)cap * sizeof(int32_t));
+  tree->comp = (int32_t*)malloc((size_t)cap * sizeof(int32_t));
   uint8_t* lab = (uint8_t*)calloc((size_t)(k > 0 ? k : 1), 1);
   uint8_t* innode = (uint8_t*)calloc((size_t)(k > 0 ? k : 1), 1);
   uint8_t* nlab = (uint8_t*)malloc((size_t)(k > 0 ? k : 1));
   int32_t* tmp = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
   int32_t qh = 0, qt = 0;
-  if (k > 0) queue[qt++] = (ora_node){1ull, 0, k, 0};
+  for (int32_t c = 0; c < nc; ++c) queue[qt++] = (ora_node){1ull, cbase[c], cbase[c + 1] - cbase[c], 0, c};
   while (qh < qt) {
     ora_node nd = queue[qh++];
     int32_t* verts = perm + nd.offset;
     int32_t rec = tree->count++;
     tree->heap[rec] = nd.heap; tree->offset[rec] = nd.offset; tree->depth[rec] = nd.depth;
+    tree->comp[rec] = nd.comp;
     tree->n1[rec] = nd.size; tree->n2[rec] = 0; tree->nsep[rec] = 0;
     if (nd.size <= min_part || nd.depth >= max_depth) continue;
     float z1[4], z2[4];
     if (!ora_bisect(d, x4, verts, nd.size, seed, nd.heap, km_iters, nlab, z1, z2)) continue;
     for (int32_t i = 0; i < nd.size; ++i) { lab[verts[i]] = nlab[i]; innode[verts[i]] = 1; }
-    int32_t nsep = ora_separate(h, d, x4, verts, nd.size, innode, lab, z1, z2);
+    ora_separate(h, d, x4, verts, nd.size, innode, lab, z1, z2);
     int32_t c1 = 0, c2 = 0, c3 = 0;
     for (int32_t i = 0; i < nd.size; ++i) {
       uint8_t l = lab[verts[i]];
       c1 += (l == 1); c2 += (l == 2); c3 += (l == 3);
     }
-    (void)nsep;
     /* stable partition */
     int32_t p1 = 0, p2 = sbd ? c1 + c3 : c1, p3 = sbd ? c1 : c1 + c2;
     for (int32_t i = 0; i < nd.size; ++i) {
@@ -1067,24 +1156,25 @@ ORA_EXPORT int ora_order(const ora_hg* h, int32_t d, const float* x4, uint64_t s
     }
     for (int32_t i = 0; i < nd.size; ++i) { verts[i] = tmp[i]; innode[tmp[i]] = 0; lab[tmp[i]] = 0; }
     tree->n1[rec] = c1; tree->n2[rec] = c2; tree->nsep[rec] = c3;
-    if (c1 > 0) queue[qt++] = (ora_node){2 * nd.heap, nd.offset, c1, nd.depth + 1};
-    if (c2 > 0) queue[qt++] = (ora_node){2 * nd.heap + 1, nd.offset + (sbd ? c1 + c3 : c1), c2, nd.depth + 1};
+    if (c1 > 0) queue[qt++] = (ora_node){2 * nd.heap, nd.offset, c1, nd.depth + 1, nd.comp};
+    if (c2 > 0) queue[qt++] = (ora_node){2 * nd.heap + 1, nd.offset + (sbd ? c1 + c3 : c1), c2, nd.depth + 1, nd.comp};
   }
-  /* breadth-first order with children in (V1, V2) order is heap order */
-  for (int32_t a = 1; a < tree->count; ++a) { /* insertion sort by heap number */
-    uint64_t hk = tree->heap[a];
-    int32_t o = tree->offset[a], x1 = tree->n1[a], x2 = tree->n2[a], x3 = tree->nsep[a], dp = tree->depth[a];
-    int32_t b = a - 1;
-    while (b >= 0 && tree->heap[b] > hk) {
-      tree->heap[b + 1] = tree->heap[b]; tree->offset[b + 1] = tree->offset[b];
-      tree->n1[b + 1] = tree->n1[b]; tree->n2[b + 1] = tree->n2[b];
-      tree->nsep[b + 1] = tree->nsep[b]; tree->depth[b + 1] = tree->depth[b];
-      --b;
-    }
-    tree->heap[b + 1] = hk; tree->offset[b + 1] = o; tree->n1[b + 1] = x1;
-    tree->n2[b + 1] = x2; tree->nsep[b + 1] = x3; tree->depth[b + 1] = dp;
+  /* sort records by (component, heap number) */
+  int32_t nrec = tree->count;
+  ora_rec_key* rk = (ora_rec_key*)malloc((size_t)(nrec > 0 ? nrec : 1) * sizeof(ora_rec_key));
+  for (int32_t r = 0; r < nrec; ++r) rk[r] = (ora_rec_key){tree->comp[r], tree->heap[r], r};
+  qsort(rk, (size_t)nrec, sizeof(ora_rec_key), cmp_rec_key);
+  int32_t* fields[6] = {tree->offset, tree->n1, tree->n2, tree->nsep, tree->depth, tree->comp};
+  int32_t* t32 = (int32_t*)malloc((size_t)(nrec > 0 ? nrec : 1) * sizeof(int32_t));
+  uint64_t* t64 = (uint64_t*)malloc((size_t)(nrec > 0 ? nrec : 1) * sizeof(uint64_t));
+  for (int f = 0; f < 6; ++f) {
+    for (int32_t r = 0; r < nrec; ++r) t32[r] = fields[f][rk[r].rec];
+    memcpy(fields[f], t32, (size_t)nrec * sizeof(int32_t));
   }
-  free(queue); free(lab); free(innode); free(nlab); free(tmp);
+  for (int32_t r = 0; r < nrec; ++r) t64[r] = tree->heap[rk[r].rec];
+  memcpy(tree->heap, t64, (size_t)nrec * sizeof(uint64_t));
+  free(rk); free(t32); free(t64);
+  free(queue); free(lab); free(innode); free(nlab); free(tmp); free(cbase);
   return 0;
 }
 

@@ -10,8 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvmo.so")
-SOURCES = ["api.cu", "order.cu", "layout.cu", "build.cu", "prims.cu"]
-HEADERS = ["vmo_internal.cuh", "layout.cuh", "order.cuh"]
+SOURCES = ["api.cu", "order.cu", "layout.cu", "build.cu", "prims.cu", "components.cu"]
+HEADERS = ["vmo_internal.cuh", "layout.cuh", "order.cuh", "components.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -4,6 +4,7 @@
 #include <memory>
 #include <mutex>
 
+#include "components.cuh"
 #include "layout.cuh"
 #include "order.cuh"
 
@@ -28,6 +29,50 @@ vmo_status invalid(const std::string& msg) {
 vmo_status unsupported(const std::string& msg) {
   set_error(msg);
   return VMO_ERR_UNSUPPORTED;
+}
+
+// ------------------------------ instrumentation ----------------------------
+std::atomic<uint64_t> g_launches{0};
+namespace {
+std::mutex g_stats_mu;
+bool g_time = false;
+unsigned long long* g_icount = nullptr;  // device counter (counting mode)
+struct TimedLaunch {
+  cudaEvent_t a, b;
+  uint64_t points;
+};
+std::vector<TimedLaunch> g_timed;
+std::vector<cudaEvent_t> g_event_pool;
+cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+bool stats_timing() { return g_time; }
+unsigned long long* stats_interaction_counter() { return g_icount; }
+
+void stats_time_begin(cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  TimedLaunch t;
+  t.a = take_event();
+  t.b = take_event();
+  t.points = 0;
+  cudaEventRecord(t.a, s);
+  g_timed.push_back(t);
+}
+
+void stats_time_end(cudaStream_t s, uint64_t points) {
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  if (g_timed.empty()) return;
+  cudaEventRecord(g_timed.back().b, s);
+  g_timed.back().points = points;
 }
 
 Scratch::~Scratch() { release_to(0); }
@@ -126,13 +171,29 @@ vmo_status single_batch(vmo_hg_s* h, int d, int occ, LevelBatch& lb, cudaStream_
   return level_setup(lb, d, occ, s);
 }
 
+// Geometry of a handle.  Graph models: every connected component is laid out
+// as its own problem of one batch (Sec. 2.2), then the coordinates are put
+// back in vertex order.  Hypergraph models and a given start: one problem.
 vmo_status run_layout(vmo_hg_s* h, const vmo_params* p, float4* x, bool given, cudaStream_t s, Scratch& sc) {
-  LevelBatch lb;
-  VMO_TRY(single_batch(h, p->d, p->occupancy, lb, s));
   LayoutOptions o = options_of(p);
-  if (given) return layout_level(lb, o, x, o.iters, -1.0f, nullptr, nullptr, s, sc);
-  std::vector<uint64_t> seeds{p->seed};
-  return layout_multilevel(lb, o, seeds, p->match_rounds, p->coarse_min, p->multilevel != 0, x, s, sc);
+  const bool graph = h->model == VMO_SYMMETRIC || h->model == VMO_BIPARTITE;
+  if (given || !graph) {
+    LevelBatch lb;
+    VMO_TRY(single_batch(h, p->d, p->occupancy, lb, s));
+    if (given) return layout_level(lb, o, x, o.iters, -1.0f, nullptr, nullptr, s, sc);
+    std::vector<uint64_t> seeds{p->seed};
+    return layout_multilevel(lb, o, seeds, p->match_rounds, p->coarse_min, false, x, s, sc);
+  }
+  ComponentGroups g;
+  VMO_TRY(group_components(h, g, s, sc));
+  LevelBatch lb;
+  VMO_TRY(relabel_graph(h, g, lb, s, sc));
+  VMO_TRY(level_setup(lb, p->d, p->occupancy, s));
+  std::vector<uint64_t> seeds(lb.P, p->seed);
+  float4* xp;
+  VMO_TRY(sc.alloc(&xp, std::max<int64_t>(h->k, 1)));
+  VMO_TRY(layout_multilevel(lb, o, seeds, p->match_rounds, p->coarse_min, p->multilevel != 0, xp, s, sc));
+  return unpermute_coords(g, xp, x, s);
 }
 
 __global__ void k_split_rows(const int32_t* __restrict__ ord, int64_t n, int32_t m, const int32_t* __restrict__ rpos,
@@ -181,9 +242,11 @@ vmo_status run_order(vmo_hg_s* h, const float* coords, const vmo_params* p, int 
   OrderState st;
   st.adj_ptr = h->adj_ptr.ptr;
   st.adj = h->adj.ptr;
-  std::vector<int64_t> pb{0, k};
-  std::vector<uint64_t> seeds{p->seed};
-  VMO_TRY(order_setup(st, x, pb, seeds, op, s, sc));
+  // components are ordered one after the other, each from its own root
+  ComponentGroups g;
+  VMO_TRY(group_components(h, g, s, sc));
+  std::vector<uint64_t> seeds(g.base.size() - 1, p->seed);
+  VMO_TRY(order_setup(st, x, g.base, seeds, op, g.cperm, s, sc));
   VMO_TRY(order_levels(st, op, s, sc));
   if (vperm) VMO_CUDA(cudaMemcpyAsync(vperm, st.ord, k * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   if (row_perm || col_perm) {
@@ -195,12 +258,12 @@ vmo_status run_order(vmo_hg_s* h, const float* coords, const vmo_params* p, int 
       int32_t* flag;
       VMO_TRY(sc.alloc(&flag, std::max<int64_t>(k, 1)));
       if (k > 0) {
-        k_is_row<<<grid_for(k, 256), 256, 0, s>>>(st.ord, k, h->m, flag);
+        launch(k_is_row, grid_for(k, 256), 256, 0, s, st.ord, k, h->m, flag);
         VMO_LAUNCHED("is_row");
       }
       VMO_TRY(scan_exclusive<int32_t>(flag, flag, k, nullptr, s, sc));
       if (k > 0) {
-        k_split_rows<<<grid_for(k, 256), 256, 0, s>>>(st.ord, k, h->m, flag, row_perm, col_perm);
+        launch(k_split_rows, grid_for(k, 256), 256, 0, s, st.ord, k, h->m, flag, row_perm, col_perm);
         VMO_LAUNCHED("split_rows");
       }
     }
@@ -208,14 +271,14 @@ vmo_status run_order(vmo_hg_s* h, const float* coords, const vmo_params* p, int 
   if (tree) {
     int32_t cnt = 0;
     uint32_t* idx;
-    VMO_TRY(tree_sorted(st, false, &cnt, &idx, s, sc));
+    VMO_TRY(tree_sorted(st, true, &cnt, &idx, s, sc));
     tree->count = cnt;
     if (cnt > tree->capacity) {
       VMO_CUDA(cudaStreamSynchronize(s));
       return invalid("tree capacity " + std::to_string(tree->capacity) + " < " + std::to_string(cnt) + " records");
     }
-    VMO_TRY(tree_write(st, idx, cnt, tree->heap, tree->offset, tree->n1, tree->n2, tree->nsep, tree->depth, nullptr,
-                       s));
+    VMO_TRY(tree_write(st, idx, cnt, tree->heap, tree->offset, tree->n1, tree->n2, tree->nsep, tree->depth,
+                       tree->component, s));
   }
   VMO_CUDA(cudaStreamSynchronize(s));
   return VMO_OK;
@@ -371,7 +434,7 @@ vmo_status vmo_coarsen(vmo_hg hg, const vmo_params* params, int32_t* mate, int32
       if (kc_out) *kc_out = (int32_t)kc[0];
       if (mate) VMO_CUDA(cudaMemcpyAsync(mate, m, k * 4, cudaMemcpyDeviceToDevice, s));
       if (pi) {
-        k_group_ids<<<grid_for(k, 256), 256, 0, s>>>(anchor, rank, k, pi);
+        launch(k_group_ids, grid_for(k, 256), 256, 0, s, anchor, rank, k, pi);
         VMO_LAUNCHED("group_ids");
       }
     } else if (kc_out) {
@@ -464,6 +527,48 @@ vmo_status vmo_cut_size(vmo_hg hg, const int32_t* part, int32_t nparts, int64_t*
   VMO_TRY(ensure_device());
   if (!hg) return invalid("handle is null");
   return cut_size(hg, part, nparts, cutnet, lambda1, (cudaStream_t)stream);
+}
+
+void vmo_stats_reset(int32_t time_step_kernel, int32_t count_interactions) {
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  g_launches.store(0);
+  for (auto& t : g_timed) {
+    g_event_pool.push_back(t.a);
+    g_event_pool.push_back(t.b);
+  }
+  g_timed.clear();
+  g_time = time_step_kernel != 0;
+  if (count_interactions) {
+    if (!g_icount && cudaMalloc((void**)&g_icount, sizeof(unsigned long long)) != cudaSuccess) {
+      g_icount = nullptr;
+      (void)cudaGetLastError();
+    }
+    if (g_icount) cudaMemset(g_icount, 0, sizeof(unsigned long long));
+  } else if (g_icount) {
+    cudaFree(g_icount);
+    g_icount = nullptr;
+  }
+}
+
+vmo_status vmo_stats_get(vmo_stats* out) {
+  if (!out) return invalid("out is null");
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  memset(out, 0, sizeof(*out));
+  out->launches = g_launches.load();
+  if (!g_timed.empty() || g_icount) VMO_CUDA(cudaDeviceSynchronize());
+  for (auto& t : g_timed) {
+    float ms = 0.f;
+    VMO_CUDA(cudaEventElapsedTime(&ms, t.a, t.b));
+    out->step_ms += ms;
+    out->step_points += t.points;
+    out->step_launches += 1;
+  }
+  if (g_icount) {
+    unsigned long long c = 0;
+    VMO_CUDA(cudaMemcpy(&c, g_icount, sizeof(c), cudaMemcpyDeviceToHost));
+    out->step_interactions = c;
+  }
+  return VMO_OK;
 }
 
 void vmo_destroy(vmo_hg hg) { delete hg; }

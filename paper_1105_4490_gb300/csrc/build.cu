@@ -197,7 +197,7 @@ vmo_status validate_csr(const vmo_csr* a, cudaStream_t s, Scratch& sc) {
   VMO_TRY(sc.alloc(&bad, 1));
   VMO_CUDA(cudaMemsetAsync(bad, 0, 4, s));
   int64_t n = std::max<int64_t>(a->m, a->nnz);
-  validate_csr_kernel<<<grid_for(n + 1, 256), 256, 0, s>>>(a->rowptr, a->colidx, a->m, a->n, a->nnz, bad);
+  launch(validate_csr_kernel, grid_for(n + 1, 256), 256, 0, s, a->rowptr, a->colidx, a->m, a->n, a->nnz, bad);
   VMO_LAUNCHED("validate_csr");
   int32_t h = 0;
   VMO_CUDA(cudaMemcpyAsync(&h, bad, 4, cudaMemcpyDeviceToHost, s));
@@ -222,7 +222,7 @@ static vmo_status csr_from_keys(uint64_t* keys, int64_t nkeys, int64_t nrows, in
   VMO_TRY(sc.alloc(&total, 1));
   VMO_TRY(radix_sort_u64(keys, nullptr, sorted, nullptr, nkeys, bits, s, sc));
   if (nkeys > 0) {
-    unique_flags_kernel<<<grid_for(nkeys, 256), 256, 0, s>>>(sorted, nkeys, sentinel, flag);
+    launch(unique_flags_kernel, grid_for(nkeys, 256), 256, 0, s, sorted, nkeys, sentinel, flag);
     VMO_LAUNCHED("unique_flags");
   }
   VMO_TRY(scan_exclusive<int32_t>(flag, pos, nkeys, total, s, sc));
@@ -233,11 +233,11 @@ static vmo_status csr_from_keys(uint64_t* keys, int64_t nkeys, int64_t nrows, in
   VMO_TRY(idx.resize((size_t)std::max<int32_t>(h_total, 1)));
   VMO_CUDA(cudaMemsetAsync(ptr.ptr, 0, (nrows + 1) * sizeof(int32_t), s));
   if (nkeys > 0) {
-    emit_csr_kernel<<<grid_for(nkeys, 256), 256, 0, s>>>(sorted, nkeys, flag, pos, (uint64_t)ncols, idx.ptr, ptr.ptr);
+    launch(emit_csr_kernel, grid_for(nkeys, 256), 256, 0, s, sorted, nkeys, flag, pos, (uint64_t)ncols, idx.ptr, ptr.ptr);
     VMO_LAUNCHED("emit_csr");
   }
   VMO_TRY(scan_exclusive<int32_t>(ptr.ptr, ptr.ptr, nrows, total, s, sc));
-  set_last_kernel<<<1, 1, 0, s>>>(ptr.ptr, nrows, total);
+  launch(set_last_kernel, 1, 1, 0, s, ptr.ptr, nrows, total);
   VMO_LAUNCHED("set_last");
   *nout = h_total;
   return VMO_OK;
@@ -260,7 +260,7 @@ vmo_status build_model(const vmo_csr* a, vmo_model model, vmo_hg_s* h, cudaStrea
     VMO_TRY(sc.alloc(&keys, (size_t)std::max<int64_t>(2 * nnz, 1)));
     uint64_t sentinel = (uint64_t)K * (uint64_t)K;
     if (nnz > 0) {
-      graph_keys_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(a->rowptr, a->colidx, m, nnz, model == VMO_BIPARTITE,
+      launch(graph_keys_kernel, grid_for(nnz, 256), 256, 0, s, a->rowptr, a->colidx, m, nnz, model == VMO_BIPARTITE,
                                                            (uint64_t)K, sentinel, keys);
       VMO_LAUNCHED("graph_keys");
     }
@@ -272,7 +272,7 @@ vmo_status build_model(const vmo_csr* a, vmo_model model, vmo_hg_s* h, cudaStrea
     VMO_TRY(sc.alloc(&pos, (size_t)std::max<int64_t>(nadj, 1)));
     VMO_TRY(sc.alloc(&tot, 1));
     if (nadj > 0) {
-      forward_flags_kernel<<<grid_for(nadj, 256), 256, 0, s>>>(h->adj_ptr.ptr, h->adj.ptr, h->k, nadj, flag);
+      launch(forward_flags_kernel, grid_for(nadj, 256), 256, 0, s, h->adj_ptr.ptr, h->adj.ptr, h->k, nadj, flag);
       VMO_LAUNCHED("forward_flags");
     }
     VMO_TRY(scan_exclusive<int32_t>(flag, pos, nadj, tot, s, sc));
@@ -286,11 +286,11 @@ vmo_status build_model(const vmo_csr* a, vmo_model model, vmo_hg_s* h, cudaStrea
     VMO_TRY(h->vtx_ptr.resize((size_t)K + 1));
     VMO_CUDA(cudaMemcpyAsync(h->vtx_ptr.ptr, h->adj_ptr.ptr, (K + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     if (nadj > 0) {
-      emit_edges_kernel<<<grid_for(nadj, 256), 256, 0, s>>>(h->adj_ptr.ptr, h->adj.ptr, h->k, nadj, flag, pos,
+      launch(emit_edges_kernel, grid_for(nadj, 256), 256, 0, s, h->adj_ptr.ptr, h->adj.ptr, h->k, nadj, flag, pos,
                                                             h->net_ptr.ptr, h->pins.ptr, h->vnets.ptr);
       VMO_LAUNCHED("emit_edges");
     }
-    net_ptr_last_kernel<<<1, 1, 0, s>>>(h->net_ptr.ptr, tot);
+    launch(net_ptr_last_kernel, 1, 1, 0, s, h->net_ptr.ptr, tot);
     VMO_LAUNCHED("net_ptr_last");
     VMO_CUDA(cudaStreamSynchronize(s));
     return VMO_OK;
@@ -304,12 +304,12 @@ vmo_status build_model(const vmo_csr* a, vmo_model model, vmo_hg_s* h, cudaStrea
     DevArray<int32_t>* cols_idx = (model == VMO_ROWNET) ? &h->vnets : &h->pins;
     int64_t cnt_r = 0, cnt_c = 0;
     if (nnz > 0) {
-      pattern_keys_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(a->rowptr, a->colidx, m, n, nnz, 0, keys);
+      launch(pattern_keys_kernel, grid_for(nnz, 256), 256, 0, s, a->rowptr, a->colidx, m, n, nnz, 0, keys);
       VMO_LAUNCHED("pattern_keys");
     }
     VMO_TRY(csr_from_keys(keys, nnz, m, n, *rows_ptr, *rows_idx, &cnt_r, s, sc));
     if (nnz > 0) {
-      pattern_keys_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(a->rowptr, a->colidx, m, n, nnz, 1, keys);
+      launch(pattern_keys_kernel, grid_for(nnz, 256), 256, 0, s, a->rowptr, a->colidx, m, n, nnz, 1, keys);
       VMO_LAUNCHED("pattern_keys");
     }
     VMO_TRY(csr_from_keys(keys, nnz, n, m, *cols_ptr, *cols_idx, &cnt_c, s, sc));
@@ -329,16 +329,16 @@ vmo_status components(const vmo_hg_s* h, int32_t* labels, cudaStream_t s) {
   int32_t* changed;
   VMO_TRY(sc.alloc(&changed, 1));
   if (h->k == 0) return VMO_OK;
-  cc_init_kernel<<<grid_for(h->k, 256), 256, 0, s>>>(labels, h->k);
+  launch(cc_init_kernel, grid_for(h->k, 256), 256, 0, s, labels, h->k);
   VMO_LAUNCHED("cc_init");
   for (int it = 0; it < 64; ++it) {
     VMO_CUDA(cudaMemsetAsync(changed, 0, 4, s));
     if (h->npins > 1) {
-      cc_hook_kernel<<<grid_for(h->npins, 256), 256, 0, s>>>(h->net_ptr.ptr, h->pins.ptr, h->l, h->npins, labels,
+      launch(cc_hook_kernel, grid_for(h->npins, 256), 256, 0, s, h->net_ptr.ptr, h->pins.ptr, h->l, h->npins, labels,
                                                              changed);
       VMO_LAUNCHED("cc_hook");
     }
-    cc_compress_kernel<<<grid_for(h->k, 256), 256, 0, s>>>(labels, h->k);
+    launch(cc_compress_kernel, grid_for(h->k, 256), 256, 0, s, labels, h->k);
     VMO_LAUNCHED("cc_compress");
     int32_t hc = 0;
     VMO_CUDA(cudaMemcpyAsync(&hc, changed, 4, cudaMemcpyDeviceToHost, s));
@@ -357,7 +357,7 @@ vmo_status cut_size(const vmo_hg_s* h, const int32_t* part, int32_t nparts, int6
   VMO_TRY(sc.alloc(&acc, 2));
   VMO_CUDA(cudaMemsetAsync(acc, 0, 16, s));
   if (h->l > 0) {
-    cut_kernel<<<grid_for(h->l * 32, 256), 256, 0, s>>>(h->net_ptr.ptr, h->pins.ptr, h->l, part, nparts, acc);
+    launch(cut_kernel, grid_for(h->l * 32, 256), 256, 0, s, h->net_ptr.ptr, h->pins.ptr, h->l, part, nparts, acc);
     VMO_LAUNCHED("cut");
   }
   unsigned long long host[2];

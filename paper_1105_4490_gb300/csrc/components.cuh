@@ -1,0 +1,25 @@
+// Grouping of a graph model by connected components.
+#pragma once
+
+#include "layout.cuh"
+
+namespace vmo {
+
+struct ComponentGroups {
+  int64_t k = 0;
+  std::vector<int64_t> base;   // host, ncomp+1: first position of each component
+  uint32_t* cperm = nullptr;   // device, k: vertices component by component (ascending inside)
+  int32_t* cinv = nullptr;     // device, k: position of every vertex
+};
+
+// Components (Algorithm 1) and the grouping permutation.
+vmo_status group_components(const vmo_hg_s* h, ComponentGroups& g, cudaStream_t s, Scratch& sc);
+
+// Level-0 batch of the graph relabelled by the grouping: one problem per
+// component (block diagonal adjacency, weights permuted).
+vmo_status relabel_graph(const vmo_hg_s* h, const ComponentGroups& g, LevelBatch& lb, cudaStream_t s, Scratch& sc);
+
+// x[cperm[i]] = xp[i].
+vmo_status unpermute_coords(const ComponentGroups& g, const float4* xp, float4* x, cudaStream_t s);
+
+}  // namespace vmo

@@ -353,8 +353,10 @@ __global__ void __launch_bounds__(kBlock) k_repulse_update(
     const uint32_t* __restrict__ scell, const int2* __restrict__ cse, const float4* __restrict__ CW,
     const float* __restrict__ Wt, const float4* __restrict__ yatt, const int32_t* __restrict__ vprob,
     const ProbDev* __restrict__ prob, int64_t K, float kappa, const float* __restrict__ s0, float scale,
-    float step_override, float4* __restrict__ x, float4* __restrict__ y_out, uint32_t* __restrict__ bb_next) {
+    float step_override, float4* __restrict__ x, float4* __restrict__ y_out, uint32_t* __restrict__ bb_next,
+    unsigned long long* __restrict__ icount) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long nint = 0;
   int64_t first = (int64_t)blockIdx.x * blockDim.x;
   int64_t lastp = min(first + (int64_t)blockDim.x, K) - 1;
   bool uniform = vprob[first] == vprob[lastp];
@@ -390,6 +392,7 @@ __global__ void __launch_bounds__(kBlock) k_repulse_update(
         if (q == p) continue;
         accumulate<D>(F, xs[q], xn, ws ? ws[q] : 1.0f);
       }
+      if (icount) nint += (unsigned long long)(r.y - r.x) - ((p >= r.x && p < r.y) ? 1 : 0);
     }
     // far field: levels 2..L
     for (int l = 2; l <= L; ++l) {
@@ -426,7 +429,10 @@ __global__ void __launch_bounds__(kBlock) k_repulse_update(
           int64_t idx = lbase + rowmajor<D>(cc, sl);
           float4 cw = CW[idx];
           float W = (D == 4) ? Wt[idx] : cw.w;
-          if (W > 0.0f) accumulate<D>(F, cw, xn, W);
+          if (W > 0.0f) {
+            accumulate<D>(F, cw, xn, W);
+            if (icount) ++nint;
+          }
         }
       }
     }
@@ -443,6 +449,12 @@ __global__ void __launch_bounds__(kBlock) k_repulse_update(
     xnew = make_float4(xn.x - a * y0, D > 1 ? xn.y - a * y1 : 0.f, D > 2 ? xn.z - a * y2 : 0.f,
                        D > 3 ? xn.w - a * y3 : 0.f);
     x[v] = xnew;
+  }
+  if (icount) {
+    unsigned long long tot = nint;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane_id() == 0 && tot) atomicAdd(icount, tot);
   }
   bbox_accumulate<D>(xnew, valid, pb, uniform, bb_next);
 }
@@ -683,7 +695,7 @@ vmo_status level_setup(LevelBatch& lb, int d, int occ, cudaStream_t s) {
   VMO_CUDA(cudaMallocAsync((void**)&vb, (P + 1) * sizeof(int64_t), s));
   VMO_CUDA(cudaMemcpyAsync(vb, lb.vbase.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   if (lb.K > 0) {
-    k_fill_vprob<<<grid_for(lb.K, kBlock), kBlock, 0, s>>>(vb, P, lb.K, lb.vprob.ptr);
+    launch(k_fill_vprob, grid_for(lb.K, kBlock), kBlock, 0, s, vb, P, lb.K, lb.vprob.ptr);
     VMO_LAUNCHED("fill_vprob");
   }
   VMO_CUDA(cudaFreeAsync(vb, s));
@@ -695,7 +707,7 @@ vmo_status level_setup(LevelBatch& lb, int d, int occ, cudaStream_t s) {
 vmo_status init_coords_level(LevelBatch& lb, int d, const uint64_t* seeds_dev, float4* x, const int32_t* start_dev,
                              cudaStream_t s) {
   if (lb.K == 0) return VMO_OK;
-  k_init_coords<<<grid_for(lb.K, kBlock), kBlock, 0, s>>>(lb.K, lb.vprob.ptr, lb.prob.ptr, seeds_dev, start_dev, d, x);
+  launch(k_init_coords, grid_for(lb.K, kBlock), kBlock, 0, s, lb.K, lb.vprob.ptr, lb.prob.ptr, seeds_dev, start_dev, d, x);
   VMO_LAUNCHED("init_coords");
   return VMO_OK;
 }
@@ -734,28 +746,28 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
   bool segmented = P > 1;
   if (segmented) VMO_TRY(make_sort_segments(lb.vbase, &segs, s, sc));
   const int nreset = 8 * P;
-  k_bbox_reset<<<grid_for(16 * P, kBlock), kBlock, 0, s>>>(bb, 16 * P);
+  launch(k_bbox_reset, grid_for(16 * P, kBlock), kBlock, 0, s, bb, 16 * P);
   VMO_LAUNCHED("bbox_reset");
   const float kappa = d == 2 ? 1.0f : (float)(d - 2);
   vmo_status st = VMO_OK;
   dispatch_d(d, [&](auto DC) {
     constexpr int D = decltype(DC)::value;
-    k_bbox<D><<<grid_for(K, kBlock), kBlock, 0, s>>>(x, K, lb.vprob.ptr, bb);
-    k_step0<D><<<grid_for(P, kBlock), kBlock, 0, s>>>(bb, lb.prob.ptr, P, o.sigma, s0);
+    launch(k_bbox<D>, grid_for(K, kBlock), kBlock, 0, s, x, K, lb.vprob.ptr, bb);
+    launch(k_step0<D>, grid_for(P, kBlock), kBlock, 0, s, bb, lb.prob.ptr, P, o.sigma, s0);
     double scale = 1.0;
     for (int t = 0; t < iters && st == VMO_OK; ++t) {
       ScratchFrame f2(sc);
       uint32_t* cur = bb + (t & 1) * 8 * P;
       uint32_t* nxt = bb + ((t + 1) & 1) * 8 * P;
-      k_keys<D><<<grid_for(std::max<int64_t>(K, nreset), kBlock), kBlock, 0, s>>>(x, K, lb.vprob.ptr, lb.prob.ptr,
+      launch(k_keys<D>, grid_for(std::max<int64_t>(K, nreset), kBlock), kBlock, 0, s, x, K, lb.vprob.ptr, lb.prob.ptr,
                                                                                   cur, keys, vals, nxt, nreset);
       if (keys_out && t == 0) cudaMemcpyAsync(keys_out, keys, K * 4, cudaMemcpyDeviceToDevice, s);
       st = radix_sort_u32(keys, vals, skeys, svals, K, D * lb.maxL, segmented ? &segs : nullptr, s, sc);
       if (st != VMO_OK) break;
       cudaMemsetAsync(cse, 0, nfine * sizeof(int2), s);
-      k_gather<D><<<grid_for(K, kBlock), kBlock, 0, s>>>(skeys, svals, K, x, lb.w, lb.vprob.ptr, lb.prob.ptr, cur,
+      launch(k_gather<D>, grid_for(K, kBlock), kBlock, 0, s, skeys, svals, K, x, lb.w, lb.vprob.ptr, lb.prob.ptr, cur,
                                                          xs, ws, scell, cse);
-      k_agg_finest<D><<<grid_for(nfine, kBlock), kBlock, 0, s>>>(cse, nfine, fb, P, lb.prob.ptr, xs, ws, St, Wt, CW);
+      launch(k_agg_finest<D>, grid_for(nfine, kBlock), kBlock, 0, s, cse, nfine, fb, P, lb.prob.ptr, xs, ws, St, Wt, CW);
       for (int stp = 1; stp <= lb.maxL - 2; ++stp) {
         const int64_t* off = lb.aggoff.ptr + (size_t)stp * (P + 1);
         int64_t n = 0;
@@ -764,19 +776,22 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
           n += l >= 2 ? (int64_t(1) << (D * l)) : 0;
         }
         if (n == 0) continue;
-        k_agg_level<D><<<grid_for(n, kBlock), kBlock, 0, s>>>(stp, off, P, n, lb.prob.ptr, St, Wt, CW);
+        launch(k_agg_level<D>, grid_for(n, kBlock), kBlock, 0, s, stp, off, P, n, lb.prob.ptr, St, Wt, CW);
       }
       if (lb.adj_ptr) {
-        k_attract<<<grid_for(K, kBlock), kBlock, 0, s>>>(lb.adj_ptr, lb.adj, lb.acost, x, K, yatt);
+        launch(k_attract, grid_for(K, kBlock), kBlock, 0, s, lb.adj_ptr, lb.adj, lb.acost, x, K, yatt);
       } else if (lb.net_ptr) {
-        if (lb.nnets > 0) k_net_center<<<grid_for(lb.nnets, kBlock), kBlock, 0, s>>>(lb.net_ptr, lb.pins, lb.nnets, x, z);
-        k_attract_hyper<<<grid_for(K, kBlock), kBlock, 0, s>>>(lb.vtx_ptr, lb.vnets, x, z, K, yatt);
+        if (lb.nnets > 0) launch(k_net_center, grid_for(lb.nnets, kBlock), kBlock, 0, s, lb.net_ptr, lb.pins, lb.nnets, x, z);
+        launch(k_attract_hyper, grid_for(K, kBlock), kBlock, 0, s, lb.vtx_ptr, lb.vnets, x, z, K, yatt);
       } else {
         cudaMemsetAsync(yatt, 0, K * sizeof(float4), s);
       }
-      k_repulse_update<D><<<grid_for(K, kBlock), kBlock, 0, s>>>(xs, ws, svals, scell, cse, CW, Wt, yatt, lb.vprob.ptr,
-                                                                 lb.prob.ptr, K, kappa, s0, (float)scale,
-                                                                 step_override, x, y_out, nxt);
+      const bool timed = stats_timing();
+      if (timed) stats_time_begin(s);
+      launch(k_repulse_update<D>, grid_for(K, kBlock), kBlock, 0, s, xs, ws, svals, scell, cse, CW, Wt, yatt,
+             lb.vprob.ptr, lb.prob.ptr, K, kappa, s0, (float)scale, step_override, x, y_out, nxt,
+             stats_interaction_counter());
+      if (timed) stats_time_end(s, (uint64_t)K);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) st = cuda_fail(e, "layout step", __FILE__, __LINE__);
       scale *= o.decay;
@@ -802,14 +817,14 @@ vmo_status coarsen_level(LevelBatch& lb, const uint64_t* seeds_dev, int j, int r
   VMO_CUDA(cudaMemsetAsync(mate, 0xFF, K * sizeof(int32_t), s));
   VMO_CUDA(cudaMemsetAsync(isanc, 0, K * sizeof(int32_t), s));
   for (int r = 0; r < rounds; ++r) {
-    k_propose<<<grid_for(K, kBlock), kBlock, 0, s>>>(lb.adj_ptr, lb.adj, lb.acost, K, lb.vprob.ptr, lb.prob.ptr,
+    launch(k_propose, grid_for(K, kBlock), kBlock, 0, s, lb.adj_ptr, lb.adj, lb.acost, K, lb.vprob.ptr, lb.prob.ptr,
                                                      active_dev, seeds_dev, j, r, mate, prop);
-    k_resolve<<<grid_for(K, kBlock), kBlock, 0, s>>>(prop, K, mate);
+    launch(k_resolve, grid_for(K, kBlock), kBlock, 0, s, prop, K, mate);
   }
-  k_anchor<<<grid_for(K, kBlock), kBlock, 0, s>>>(lb.adj_ptr, lb.adj, K, mate, anchor, isanc);
+  launch(k_anchor, grid_for(K, kBlock), kBlock, 0, s, lb.adj_ptr, lb.adj, K, mate, anchor, isanc);
   VMO_LAUNCHED("matching");
   VMO_TRY(scan_exclusive<int32_t>(isanc, rank, K, total, s, sc));
-  k_kc<<<grid_for(P, kBlock), kBlock, 0, s>>>(rank, total, vb, P, K, kcd);
+  launch(k_kc, grid_for(P, kBlock), kBlock, 0, s, rank, total, vb, P, K, kcd);
   VMO_LAUNCHED("kc");
   kc.resize(P);
   VMO_CUDA(cudaMemcpyAsync(kc.data(), kcd, P * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -827,7 +842,7 @@ static vmo_status contract_level(LevelBatch& lb, const std::vector<int64_t>& new
   int64_t* nb;
   VMO_TRY(sc.alloc(&nb, P));
   VMO_CUDA(cudaMemcpyAsync(nb, newbase.data(), P * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  k_pi<<<grid_for(K, kBlock), kBlock, 0, s>>>(anchor, rank, K, lb.vprob.ptr, lb.prob.ptr, nb, pi);
+  launch(k_pi, grid_for(K, kBlock), kBlock, 0, s, anchor, rank, K, lb.vprob.ptr, lb.prob.ptr, nb, pi);
   VMO_LAUNCHED("pi");
   const int64_t n = lb.nadj;
   uint64_t *keys, *skeys;
@@ -841,11 +856,11 @@ static vmo_status contract_level(LevelBatch& lb, const std::vector<int64_t>& new
   VMO_TRY(sc.alloc(&pos, std::max<int64_t>(n, 1)));
   VMO_TRY(sc.alloc(&total, 1));
   const uint64_t sentinel = (uint64_t)Kc * (uint64_t)Kc;
-  k_contract_keys<<<grid_for(K, kBlock), kBlock, 0, s>>>(lb.adj_ptr, lb.adj, lb.acost, K, pi, (uint64_t)Kc, keys, vals);
+  launch(k_contract_keys, grid_for(K, kBlock), kBlock, 0, s, lb.adj_ptr, lb.adj, lb.acost, K, pi, (uint64_t)Kc, keys, vals);
   VMO_LAUNCHED("contract_keys");
   VMO_TRY(radix_sort_u64(keys, vals, skeys, svals, n, bits_for(sentinel), s, sc));
   if (n > 0) {
-    k_run_flags<<<grid_for(n, kBlock), kBlock, 0, s>>>(skeys, n, sentinel, flag);
+    launch(k_run_flags, grid_for(n, kBlock), kBlock, 0, s, skeys, n, sentinel, flag);
     VMO_LAUNCHED("run_flags");
   }
   VMO_TRY(scan_exclusive<int32_t>(flag, pos, n, total, s, sc));
@@ -859,13 +874,13 @@ static vmo_status contract_level(LevelBatch& lb, const std::vector<int64_t>& new
   VMO_CUDA(cudaMemsetAsync(out.own_adj_ptr.ptr, 0, (Kc + 1) * sizeof(int32_t), s));
   VMO_CUDA(cudaMemsetAsync(out.own_w.ptr, 0, std::max<int64_t>(Kc, 1) * sizeof(float), s));
   if (n > 0) {
-    k_emit_coarse<<<grid_for(n, kBlock), kBlock, 0, s>>>(skeys, svals, n, flag, pos, (uint64_t)Kc, out.own_adj.ptr,
+    launch(k_emit_coarse, grid_for(n, kBlock), kBlock, 0, s, skeys, svals, n, flag, pos, (uint64_t)Kc, out.own_adj.ptr,
                                                          out.own_acost.ptr, out.own_adj_ptr.ptr);
     VMO_LAUNCHED("emit_coarse");
   }
   VMO_TRY(scan_exclusive<int32_t>(out.own_adj_ptr.ptr, out.own_adj_ptr.ptr, Kc, total, s, sc));
-  k_set_last<<<1, 1, 0, s>>>(out.own_adj_ptr.ptr, Kc, total);
-  k_coarse_w<<<grid_for(K, kBlock), kBlock, 0, s>>>(lb.w, pi, K, out.own_w.ptr);
+  launch(k_set_last, 1, 1, 0, s, out.own_adj_ptr.ptr, Kc, total);
+  launch(k_coarse_w, grid_for(K, kBlock), kBlock, 0, s, lb.w, pi, K, out.own_w.ptr);
   VMO_LAUNCHED("coarse_w");
   out.K = Kc;
   out.adj_ptr = out.own_adj_ptr.ptr;
@@ -976,7 +991,7 @@ vmo_status layout_multilevel(LevelBatch& fine, const LayoutOptions& o, const std
     VMO_CUDA(cudaMemcpyAsync(sd, lseeds[j].data(), P * 8, cudaMemcpyHostToDevice, s));
     VMO_TRY(init_coords_level(cur, o.d, sd, xj, st, s));
     if (xc) {
-      k_prolong<<<grid_for(cur.K, kBlock), kBlock, 0, s>>>(xc, pis[j], cur.K, cur.vprob.ptr, cur.prob.ptr, fc, sd, j,
+      launch(k_prolong, grid_for(cur.K, kBlock), kBlock, 0, s, xc, pis[j], cur.K, cur.vprob.ptr, cur.prob.ptr, fc, sd, j,
                                                            o.d, xj);
       VMO_LAUNCHED("prolong");
     }

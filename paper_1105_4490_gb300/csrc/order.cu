@@ -353,13 +353,12 @@ __global__ void k_children(NodeDev* __restrict__ nodes, int N, const int64_t* __
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= N) return;
   NodeDev& nd = nodes[s];
-  int64_t rel = nd.off - pbase[nd.prob];
   bool split = nd.c1 + nd.c2 + nd.c3 > 0;
   int slot = atomicAdd(tree.count, 1);
   if (slot >= tree.cap) { atomicOr(err, 1); return; }
   tree.heap[slot] = nd.heap;
   tree.prob[slot] = nd.prob;
-  tree.offset[slot] = (int32_t)rel;
+  tree.offset[slot] = (int32_t)nd.off;
   tree.depth[slot] = nd.depth;
   if (!split) {
     tree.n1[slot] = nd.size; tree.n2[slot] = 0; tree.nsep[slot] = 0;
@@ -381,7 +380,7 @@ __global__ void k_children(NodeDev* __restrict__ nodes, int N, const int64_t* __
     } else {
       int t = atomicAdd(tree.count, 1);
       if (t >= tree.cap) { atomicOr(err, 1); continue; }
-      tree.heap[t] = heap; tree.prob[t] = nd.prob; tree.offset[t] = (int32_t)(off - pbase[nd.prob]);
+      tree.heap[t] = heap; tree.prob[t] = nd.prob; tree.offset[t] = (int32_t)off;
       tree.depth[t] = depth; tree.n1[t] = size; tree.n2[t] = 0; tree.nsep[t] = 0;
     }
   }
@@ -490,27 +489,27 @@ vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s,
   vmo_status stt = VMO_OK;
   dispatch_d(d, [&](auto DC) {
     constexpr int D = decltype(DC)::value;
-    k_node_reset<<<grid_for(N, kBlock), kBlock, 0, s>>>(st.nodes, N);
-    k_maxabs<D><<<grid_for(n, kBlock), kBlock, 0, s>>>(st.xo, st.seg, n, st.nodes);
-    k_seed1<<<grid_for(N, kBlock), kBlock, 0, s>>>(st.nodes, N, st.xo, st.seeds);
-    k_dsq<D><<<grid_for(n, kBlock), kBlock, 0, s>>>(st.xo, st.seg, n, st.nodes, dval);
+    launch(k_node_reset, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N);
+    launch(k_maxabs<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, st.nodes);
+    launch(k_seed1, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, st.xo, st.seeds);
+    launch(k_dsq<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, st.nodes, dval);
     stt = scan_inclusive<uint64_t>((const uint64_t*)dval, (uint64_t*)dpre, n, s, sc);
     if (stt != VMO_OK) return;
-    k_seed2<D><<<grid_for(n, kBlock), kBlock, 0, s>>>(st.xo, st.seg, n, dval, dpre, st.nodes, st.seeds);
+    launch(k_seed2<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, dval, dpre, st.nodes, st.seeds);
     for (int it = 0; it < km_iters; ++it) {
-      k_assign<D><<<grid_for(n, kBlock), kBlock, 0, s>>>(st.xo, st.seg, n, it, st.nodes, st.lab, 0);
-      k_update<D><<<grid_for(N, kBlock), kBlock, 0, s>>>(st.nodes, N, it);
+      launch(k_assign<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, it, st.nodes, st.lab, 0);
+      launch(k_update<D>, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, it);
       if (it % 4 == 3 && it + 1 < km_iters) {  // stop early once every node has converged
         int h = 0;
         cudaMemsetAsync(cnt, 0, 4, s);
-        k_count_active<<<grid_for(N, kBlock), kBlock, 0, s>>>(st.nodes, N, cnt);
+        launch(k_count_active, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, cnt);
         cudaMemcpyAsync(&h, cnt, 4, cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
         if (h == 0) break;
       }
     }
-    k_clear_counts<<<grid_for(N, kBlock), kBlock, 0, s>>>(st.nodes, N);
-    k_assign<D><<<grid_for(n, kBlock), kBlock, 0, s>>>(st.xo, st.seg, n, 0, st.nodes, st.lab, 1);
+    launch(k_clear_counts, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N);
+    launch(k_assign<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, 0, st.nodes, st.lab, 1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) stt = cuda_fail(e, "two_means", __FILE__, __LINE__);
   });
@@ -539,20 +538,20 @@ vmo_status order_levels(OrderState& st, const OrderParams& op, cudaStream_t s, S
     VMO_TRY(two_means(st, N, op.d, op.km_iters, s, sc));
     dispatch_d(op.d, [&](auto DC) {
       constexpr int D = decltype(DC)::value;
-      k_vertex_state<D><<<grid_for(n, kBlock), kBlock, 0, s>>>(st.xo, st.ord, st.seg, n, st.nodes, st.lab, st.vlab,
+      launch(k_vertex_state<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.ord, st.seg, n, st.nodes, st.lab, st.vlab,
                                                                st.vs);
     });
-    k_separator<<<grid_for(n, kBlock), kBlock, 0, s>>>(st.ord, st.seg, n, st.adj_ptr, st.adj, st.vnode, st.vlab, st.vs,
+    launch(k_separator, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vnode, st.vlab, st.vs,
                                                        st.nodes, labf);
-    k_pack<<<grid_for(n, kBlock), kBlock, 0, s>>>(st.seg, labf, n, st.nodes, pk);
+    launch(k_pack, grid_for(n, kBlock), kBlock, 0, s, st.seg, labf, n, st.nodes, pk);
     VMO_LAUNCHED("separator");
     VMO_TRY(scan_inclusive<uint64_t>((const uint64_t*)pk, (uint64_t*)pre, n, s, sc));
-    k_scatter<<<grid_for(n, kBlock), kBlock, 0, s>>>(st.ord, st.xo, st.seg, labf, n, st.nodes, pre, op.sbd, ord2, xo2,
+    launch(k_scatter, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.xo, st.seg, labf, n, st.nodes, pre, op.sbd, ord2, xo2,
                                                      segl2);
     VMO_CUDA(cudaMemsetAsync(next_count, 0, 4, s));
-    k_children<<<grid_for(N, kBlock), kBlock, 0, s>>>(st.nodes, N, st.pbase, op.min_part, op.max_depth, op.sbd, next,
+    launch(k_children, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, st.pbase, op.min_part, op.max_depth, op.sbd, next,
                                                       next_count, st.node_cap, st.tree, err);
-    k_relabel<<<grid_for(n, kBlock), kBlock, 0, s>>>(segl2, ord2, n, st.nodes, st.seg, st.vnode);
+    launch(k_relabel, grid_for(n, kBlock), kBlock, 0, s, segl2, ord2, n, st.nodes, st.seg, st.vnode);
     VMO_LAUNCHED("partition");
     // swap position arrays
     VMO_CUDA(cudaMemcpyAsync(st.ord, ord2, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
@@ -569,7 +568,8 @@ vmo_status order_levels(OrderState& st, const OrderParams& op, cudaStream_t s, S
 }
 
 vmo_status order_setup(OrderState& st, const float4* x, const std::vector<int64_t>& pbase_host,
-                       const std::vector<uint64_t>& seeds, const OrderParams& op, cudaStream_t s, Scratch& sc) {
+                       const std::vector<uint64_t>& seeds, const OrderParams& op, const uint32_t* init_ord,
+                       cudaStream_t s, Scratch& sc) {
   const int64_t n = pbase_host.back();
   const int P = (int)pbase_host.size() - 1;
   st.n = n;
@@ -599,8 +599,11 @@ vmo_status order_setup(OrderState& st, const float4* x, const std::vector<int64_
   VMO_CUDA(cudaMemcpyAsync(st.pbase, pbase_host.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   VMO_CUDA(cudaMemcpyAsync(st.seeds, seeds.data(), P * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
   if (n > 0) {
-    k_iota<<<grid_for(n, kBlock), kBlock, 0, s>>>(st.ord, n);
-    k_gather_coords<<<grid_for(n, kBlock), kBlock, 0, s>>>(x, st.ord, n, st.xo);
+    if (init_ord)
+      VMO_CUDA(cudaMemcpyAsync(st.ord, init_ord, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    else
+      launch(k_iota, grid_for(n, kBlock), kBlock, 0, s, st.ord, n);
+    launch(k_gather_coords, grid_for(n, kBlock), kBlock, 0, s, x, st.ord, n, st.xo);
     VMO_LAUNCHED("order_setup");
   }
   // roots: problems with more than min_part vertices and max_depth > 0 are
@@ -624,11 +627,11 @@ vmo_status order_setup(OrderState& st, const float4* x, const std::vector<int64_
     VMO_CUDA(cudaMemcpyAsync(d_ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, s));
   VMO_CUDA(cudaMemcpyAsync(d_nop, node_of_prob.data(), P * 4, cudaMemcpyHostToDevice, s));
   if (st.nroots > 0) {
-    k_root_nodes<<<grid_for(st.nroots, kBlock), kBlock, 0, s>>>(st.nodes, st.pbase, d_ids, st.nroots, nullptr);
+    launch(k_root_nodes, grid_for(st.nroots, kBlock), kBlock, 0, s, st.nodes, st.pbase, d_ids, st.nroots, nullptr);
     VMO_LAUNCHED("roots");
   }
   if (n > 0) {
-    k_seg_init<<<grid_for(n, kBlock), kBlock, 0, s>>>(st.seg, st.vnode, st.ord, n, st.pbase, P, d_nop);
+    launch(k_seg_init, grid_for(n, kBlock), kBlock, 0, s, st.seg, st.vnode, st.ord, n, st.pbase, P, d_nop);
     VMO_LAUNCHED("seg_init");
   }
   // leaf roots become tree records directly
@@ -636,11 +639,14 @@ vmo_status order_setup(OrderState& st, const float4* x, const std::vector<int64_
     std::vector<int32_t> hc(1);
     int nl = (int)leaf_probs.size();
     std::vector<uint64_t> h(nl, 1ull);
-    std::vector<int32_t> zero(nl, 0), sz(nl);
-    for (int i = 0; i < nl; ++i) sz[i] = (int32_t)(pbase_host[leaf_probs[i] + 1] - pbase_host[leaf_probs[i]]);
+    std::vector<int32_t> zero(nl, 0), sz(nl), offs(nl);
+    for (int i = 0; i < nl; ++i) {
+      sz[i] = (int32_t)(pbase_host[leaf_probs[i] + 1] - pbase_host[leaf_probs[i]]);
+      offs[i] = (int32_t)pbase_host[leaf_probs[i]];
+    }
     VMO_CUDA(cudaMemcpyAsync(st.tree.heap, h.data(), nl * 8, cudaMemcpyHostToDevice, s));
     VMO_CUDA(cudaMemcpyAsync(st.tree.prob, leaf_probs.data(), nl * 4, cudaMemcpyHostToDevice, s));
-    VMO_CUDA(cudaMemcpyAsync(st.tree.offset, zero.data(), nl * 4, cudaMemcpyHostToDevice, s));
+    VMO_CUDA(cudaMemcpyAsync(st.tree.offset, offs.data(), nl * 4, cudaMemcpyHostToDevice, s));
     VMO_CUDA(cudaMemcpyAsync(st.tree.n1, sz.data(), nl * 4, cudaMemcpyHostToDevice, s));
     VMO_CUDA(cudaMemcpyAsync(st.tree.n2, zero.data(), nl * 4, cudaMemcpyHostToDevice, s));
     VMO_CUDA(cudaMemcpyAsync(st.tree.nsep, zero.data(), nl * 4, cudaMemcpyHostToDevice, s));
@@ -665,11 +671,11 @@ vmo_status tree_sorted(OrderState& st, bool by_prob, int32_t* count_out, uint32_
   VMO_TRY(sc.alloc(&v1, std::max(n, 1)));
   VMO_TRY(sc.alloc(&v2, std::max(n, 1)));
   if (n == 0) { *idx_out = v2; return VMO_OK; }
-  k_tree_keys<<<grid_for(n, kBlock), kBlock, 0, s>>>(st.tree, n, 0, k1, v1);
+  launch(k_tree_keys, grid_for(n, kBlock), kBlock, 0, s, st.tree, n, 0, k1, v1);
   VMO_LAUNCHED("tree_keys");
   VMO_TRY(radix_sort_u64(k1, v1, k2, v2, n, 64, s, sc));
   if (by_prob) {
-    k_tree_regather<<<grid_for(n, kBlock), kBlock, 0, s>>>(v2, n, 1, st.tree, k1);
+    launch(k_tree_regather, grid_for(n, kBlock), kBlock, 0, s, v2, n, 1, st.tree, k1);
     VMO_LAUNCHED("tree_regather");
     VMO_TRY(radix_sort_u64(k1, v2, k2, v1, n, 32, s, sc));
     *idx_out = v1;
@@ -681,7 +687,7 @@ vmo_status tree_sorted(OrderState& st, bool by_prob, int32_t* count_out, uint32_
 
 vmo_status gather_coords(const float4* x, const int32_t* ord, int64_t n, float4* xo, cudaStream_t s) {
   if (n <= 0) return VMO_OK;
-  k_gather_coords<<<grid_for(n, kBlock), kBlock, 0, s>>>(x, ord, n, xo);
+  launch(k_gather_coords, grid_for(n, kBlock), kBlock, 0, s, x, ord, n, xo);
   VMO_LAUNCHED("gather_coords");
   return VMO_OK;
 }
@@ -689,7 +695,7 @@ vmo_status gather_coords(const float4* x, const int32_t* ord, int64_t n, float4*
 vmo_status tree_write(OrderState& st, const uint32_t* idx, int n, uint64_t* heap, int32_t* offset, int32_t* n1,
                       int32_t* n2, int32_t* nsep, int32_t* depth, int32_t* prob, cudaStream_t s) {
   if (n == 0) return VMO_OK;
-  k_tree_out<<<grid_for(n, kBlock), kBlock, 0, s>>>(idx, n, st.tree, heap, offset, n1, n2, nsep, depth, prob);
+  launch(k_tree_out, grid_for(n, kBlock), kBlock, 0, s, idx, n, st.tree, heap, offset, n1, n2, nsep, depth, prob);
   VMO_LAUNCHED("tree_out");
   return VMO_OK;
 }

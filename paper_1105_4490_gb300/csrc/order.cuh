@@ -64,8 +64,11 @@ struct OrderState {
   TreeDev tree;
 };
 
+// Positions start as init_ord (vertex ids; null: identity), grouped by problem
+// as pbase_host gives.  Tree offsets are absolute positions.
 vmo_status order_setup(OrderState& st, const float4* x, const std::vector<int64_t>& pbase_host,
-                       const std::vector<uint64_t>& seeds, const OrderParams& op, cudaStream_t s, Scratch& sc);
+                       const std::vector<uint64_t>& seeds, const OrderParams& op, const uint32_t* init_ord,
+                       cudaStream_t s, Scratch& sc);
 vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s, Scratch& sc);
 vmo_status order_levels(OrderState& st, const OrderParams& op, cudaStream_t s, Scratch& sc);
 // Indices of the tree records sorted by heap number (and by problem first when

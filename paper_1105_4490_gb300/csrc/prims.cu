@@ -122,9 +122,9 @@ vmo_status scan_impl(const T* in, T* out, int64_t n, T* total, cudaStream_t s, S
   int64_t ntiles = (n + kScanTile - 1) / kScanTile;
   T* partial;
   VMO_TRY(sc.alloc(&partial, (size_t)ntiles));
-  scan_reduce_kernel<T><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, partial);
-  scan_partials_kernel<T><<<1, 1024, 0, s>>>(partial, ntiles, total);
-  scan_tile_kernel<T, Inclusive><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, out, n, partial);
+  launch(scan_reduce_kernel<T>, (unsigned)ntiles, kScanThreads, 0, s, in, n, partial);
+  launch(scan_partials_kernel<T>, 1, 1024, 0, s, partial, ntiles, total);
+  launch(scan_tile_kernel<T, Inclusive>, (unsigned)ntiles, kScanThreads, 0, s, in, out, n, partial);
   VMO_LAUNCHED("scan");
   return VMO_OK;
 }
@@ -250,12 +250,12 @@ vmo_status radix_sort_impl(K* keys_in, uint32_t* vals_in, K* keys_out, uint32_t*
   uint32_t* vb = vals_out;
   for (int p = 0; p < passes; ++p) {
     int shift = p * kRadixBits;
-    radix_hist_kernel<K><<<(unsigned)sg.ntiles, 256, 0, s>>>(ka, n, shift, sg, hist);
+    launch(radix_hist_kernel<K>, (unsigned)sg.ntiles, 256, 0, s, ka, n, shift, sg, hist);
     VMO_TRY((scan_impl<uint32_t, false>(hist, hist, hn, nullptr, s, sc)));
     if (vals_in)
-      radix_scatter_kernel<K, true><<<(unsigned)sg.ntiles, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, sg, hist);
+      launch(radix_scatter_kernel<K, true>, (unsigned)sg.ntiles, kSortThreads, 0, s, ka, va, kb, vb, n, shift, sg, hist);
     else
-      radix_scatter_kernel<K, false><<<(unsigned)sg.ntiles, kSortThreads, 0, s>>>(ka, nullptr, kb, nullptr, n, shift,
+      launch(radix_scatter_kernel<K, false>, (unsigned)sg.ntiles, kSortThreads, 0, s, ka, nullptr, kb, nullptr, n, shift,
                                                                                    sg, hist);
     VMO_LAUNCHED("radix_sort");
     K* tk = ka; ka = kb; kb = tk;

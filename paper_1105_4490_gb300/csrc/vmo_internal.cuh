@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/vmo.h"
@@ -172,6 +174,23 @@ vmo_status radix_sort_u64(uint64_t* keys_in, uint32_t* vals_in, uint64_t* keys_o
 // Build SortSegments for segments given by host base offsets.
 vmo_status make_sort_segments(const std::vector<int64_t>& seg_base_host, SortSegments* out, cudaStream_t s,
                               Scratch& sc);
+
+// ---------------------------------------------------------------------------
+// Instrumentation: every kernel launch of the library goes through launch(),
+// which counts it; the layout step kernel can also be timed with CUDA events
+// and can count the interactions it evaluates (vmo_stats_* in the C-ABI).
+// ---------------------------------------------------------------------------
+extern std::atomic<uint64_t> g_launches;
+bool stats_timing();
+unsigned long long* stats_interaction_counter();  // null unless counting is on
+void stats_time_begin(cudaStream_t s);
+void stats_time_end(cudaStream_t s, uint64_t points);
+
+template <class... KArgs, class... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  kernel<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+}
 
 inline int bits_for(uint64_t maxval) {
   int b = 0;

@@ -42,7 +42,13 @@ class _Params(C.Structure):
 
 class _Tree(C.Structure):
     _fields_ = [("capacity", C.c_int32), ("count", C.c_int32), ("heap", C.c_void_p), ("offset", C.c_void_p),
-                ("n1", C.c_void_p), ("n2", C.c_void_p), ("nsep", C.c_void_p), ("depth", C.c_void_p)]
+                ("n1", C.c_void_p), ("n2", C.c_void_p), ("nsep", C.c_void_p), ("depth", C.c_void_p),
+                ("component", C.c_void_p)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("launches", C.c_uint64), ("step_launches", C.c_uint64), ("step_ms", C.c_double),
+                ("step_points", C.c_uint64), ("step_interactions", C.c_uint64)]
 
 
 @dataclass
@@ -72,7 +78,7 @@ class Params:
 SYMBOLS = ["vmo_default_params", "vmo_build_hypergraph", "vmo_hg_vertices", "vmo_hg_nets", "vmo_hg_arrays",
            "vmo_components", "vmo_init_coords", "vmo_layout", "vmo_layout_step", "vmo_coarsen", "vmo_bisect",
            "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_cut_size", "vmo_destroy",
-           "vmo_status_string", "vmo_last_error"]
+           "vmo_status_string", "vmo_last_error", "vmo_stats_reset", "vmo_stats_get"]
 
 
 def load(path: str | None = None):
@@ -111,9 +117,12 @@ def load(path: str | None = None):
     lib.vmo_status_string.restype = C.c_char_p
     lib.vmo_last_error.argtypes = []
     lib.vmo_last_error.restype = C.c_char_p
+    lib.vmo_stats_reset.argtypes = [I32, I32]
+    lib.vmo_stats_reset.restype = None
+    lib.vmo_stats_get.argtypes = [C.POINTER(_Stats)]
     for nm in SYMBOLS:
         if nm not in ("vmo_default_params", "vmo_hg_vertices", "vmo_hg_nets", "vmo_destroy", "vmo_status_string",
-                      "vmo_last_error"):
+                      "vmo_last_error", "vmo_stats_reset"):
             getattr(lib, nm).restype = C.c_int
     _lib = lib
     return lib
@@ -252,9 +261,9 @@ class Hypergraph:
 
     def _tree(self, cap: int):
         t = {"heap": torch.zeros(cap, dtype=torch.int64, device="cuda")}
-        for f in ("offset", "n1", "n2", "nsep", "depth"):
+        for f in ("offset", "n1", "n2", "nsep", "depth", "comp"):
             t[f] = torch.zeros(cap, dtype=torch.int32, device="cuda")
-        ct = _Tree(cap, 0, *(t[f].data_ptr() for f in ("heap", "offset", "n1", "n2", "nsep", "depth")))
+        ct = _Tree(cap, 0, *(t[f].data_ptr() for f in ("heap", "offset", "n1", "n2", "nsep", "depth", "comp")))
         return t, ct
 
     def order(self, params: Params | None = None, coords: torch.Tensor | None = None, sbd: bool = False,
@@ -286,3 +295,16 @@ class Hypergraph:
         a, b = C.c_int64(), C.c_int64()
         _check(load().vmo_cut_size(self._h, _ptr(part), nparts, C.byref(a), C.byref(b), _stream()))
         return int(a.value), int(b.value)
+
+
+def stats_reset(time_step_kernel: bool = False, count_interactions: bool = False) -> None:
+    """Resets the library's launch counter and step-kernel instrumentation."""
+    load().vmo_stats_reset(int(time_step_kernel), int(count_interactions))
+
+
+def stats() -> dict:
+    """Launches since the last reset; step-kernel time (ms), launches, points and
+    interactions when enabled."""
+    s = _Stats()
+    _check(load().vmo_stats_get(C.byref(s)))
+    return {f: getattr(s, f) for f, _ in _Stats._fields_}

@@ -24,7 +24,7 @@ def lib():
 
 def test_every_declared_symbol_is_exported(lib):
     names = _declared()
-    assert len(names) >= 18
+    assert len(names) >= 20
     missing = [n for n in names if not hasattr(lib, n)]
     assert missing == []
 
@@ -48,4 +48,5 @@ def test_params_struct_layout():
     """The ctypes mirror matches the C struct (field order and size)."""
     from paper_1105_4490_gb300 import vmo
     assert ctypes.sizeof(vmo._Params) == 4 * 11 + 4 + 8  # 11 x 4-byte fields, padding, uint64 seed
-    assert ctypes.sizeof(vmo._Tree) == 8 + 6 * 8
+    assert ctypes.sizeof(vmo._Tree) == 8 + 7 * 8
+    assert ctypes.sizeof(vmo._Stats) == 5 * 8

@@ -225,7 +225,7 @@ def _order_compare(V, O, A, model, d, coords, sbd, min_part=64, max_depth=62, se
     perm_o, tree_o = O.order(ref, d, coords, seed=seed, min_part=min_part, max_depth=max_depth, sbd=sbd)
     assert np.array_equal(_np(perm), perm_o)
     assert np.array_equal(_np(tree["heap"]).astype(np.uint64), tree_o["heap"])
-    for f in ("offset", "n1", "n2", "nsep", "depth"):
+    for f in ("offset", "n1", "n2", "nsep", "depth", "comp"):
         assert np.array_equal(_np(tree[f]), tree_o[f]), f
     return hg, ref, perm_o, tree_o
 
@@ -314,6 +314,24 @@ def test_end_to_end_quality_grid2d(V, O):
         so.append(int(tree_o["nsep"].sum()))
     assert abs(np.mean(fg) / np.mean(fo) - 1) <= 0.05, (fg, fo)
     assert abs(np.mean(sg) / np.mean(so) - 1) <= 0.05, (sg, so)
+
+
+def test_layout_components_match_oracle_structure(V, O):
+    """Disconnected input (isolated vertices): components are laid out on their
+    own, so isolated vertices keep their random start (no forces act on them)
+    and the layout stays bounded."""
+    A = W.powerlaw_symmetric(4000, seed=3)
+    ref = O.build_from_matrix("symmetric", A)
+    lab = O.components(ref)
+    iso = np.flatnonzero(np.bincount(lab, minlength=A.n)[lab] == 1)
+    assert len(iso) > 0
+    hg = V.Hypergraph.from_matrix(A)
+    x = _np(hg.layout(V.Params(d=3, seed=2)))
+    x0 = O.init_coords(1, 3, 2)  # a one-vertex component starts at its own random point
+    assert np.array_equal(x[iso].view(np.uint32), np.repeat(x0, len(iso), 0).view(np.uint32))
+    big = np.bincount(lab).argmax()
+    ext = np.ptp(x[lab == big, :3], axis=0)
+    assert (ext < 10 * np.cbrt((lab == big).sum())).all()
 
 
 def test_layout_deterministic(V):

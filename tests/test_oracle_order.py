@@ -152,7 +152,8 @@ def _owner_info(k, perm, tree, sbd):
 def _check_ordering(O, A, hg, perm, tree, sbd, d=None, x4=None, min_part=64, max_depth=62):
     k = hg.k
     assert sorted(perm.tolist()) == list(range(k))
-    assert (np.diff(tree["heap"].astype(np.float64)) > 0).all()
+    key = [(int(c), int(h)) for c, h in zip(tree["comp"], tree["heap"])]
+    assert key == sorted(key) and len(set(key)) == len(key)
     part = _owner_info(k, perm, tree, sbd)
     assert (part >= 0).all()
     H, D = tree["heap"], tree["depth"]
@@ -162,17 +163,18 @@ def _check_ordering(O, A, hg, perm, tree, sbd, d=None, x4=None, min_part=64, max
             a, b = part[v], part[u]
             assert _ancestor(H[a], D[a], H[b], D[b]) or _ancestor(H[b], D[b], H[a], D[a])
     # tree bookkeeping: children of node h are 2h / 2h+1 at the right offsets
-    idx = {int(h): i for i, h in enumerate(H)}
+    idx = {(int(c), int(h)): i for i, (c, h) in enumerate(zip(tree["comp"], H))}
     for i, h in enumerate(H):
+        cmp_ = int(tree["comp"][i])
         o, n1, n2, ns, dp = (int(tree[f][i]) for f in ("offset", "n1", "n2", "nsep", "depth"))
         leaf = n2 == 0 and ns == 0
         if leaf:
             continue
         if n1:
-            c = idx[2 * int(h)]
+            c = idx[(cmp_, 2 * int(h))]
             assert tree["offset"][c] == o and tree["depth"][c] == dp + 1
         if n2:
-            c = idx[2 * int(h) + 1]
+            c = idx[(cmp_, 2 * int(h) + 1)]
             assert tree["offset"][c] == (o + n1 + ns if sbd else o + n1)
         assert dp < max_depth
     # leaves are small, deep or unsplittable
@@ -281,6 +283,7 @@ def test_separator_replay_matches_bisect(oracle_mod):
     x4 = O.init_coords(hg.k, 3, 8)
     perm, tree = O.order(hg, 3, x4, seed=8, min_part=32, max_depth=4)
     # the child 2 of the root holds V2 in node order; its own split is replayed
+    assert (tree["comp"] == 0).all()
     idx = {int(h): i for i, h in enumerate(tree["heap"])}
     i2 = idx[3]
     o, n1, n2, ns = (int(tree[f][i2]) for f in ("offset", "n1", "n2", "nsep"))
@@ -350,3 +353,39 @@ def test_cholesky_count_matches_dense_elimination(oracle_mod, seed):
     Pp = P[np.ix_(perm, perm)]
     nzl = O.cholesky_nnz(40, A.rowptr, A.colidx, perm)
     assert 2 * nzl - 40 == Pp.sum() + _dense_fill(Pp)
+
+
+def test_order_components_block_diagonal(oracle_mod):
+    """A disconnected graph (Sec. 2.2: components are treated separately) is
+    ordered component after component, in order of smallest vertex id, each by
+    its own recursion; isolated vertices are single-vertex leaves."""
+    O = oracle_mod
+    A = W.powerlaw_symmetric(3000, seed=1)
+    hg = O.build_from_matrix("symmetric", A)
+    lab = O.components(hg)
+    comps = np.unique(lab)
+    assert len(comps) > 1
+    x4 = O.init_coords(hg.k, 3, 2)
+    perm, tree = O.order(hg, 3, x4, seed=2, min_part=16)
+    part = _check_ordering(O, A, hg, perm, tree, False)
+    # component blocks are contiguous and in order of their smallest vertex
+    assert (np.diff(lab[perm]) >= 0).all()
+    roots = tree["heap"] == 1
+    assert roots.sum() == len(comps)
+    sizes = np.bincount(np.searchsorted(comps, lab))
+    assert np.array_equal(np.sort(tree["n1"][roots & (tree["n2"] == 0) & (tree["nsep"] == 0)]),
+                          np.sort(sizes[sizes <= 16]))
+
+
+def test_multilevel_layout_of_components_is_independent(oracle_mod):
+    """Each component is laid out on its own: adding an isolated vertex with a
+    larger id leaves the layout of the rest unchanged."""
+    O = oracle_mod
+    A = W.grid_laplacian_2d(12)
+    rows = np.repeat(np.arange(A.m), np.diff(A.rowptr))
+    B = W.csr_from_coo(A.m + 1, A.n + 1, np.concatenate([rows, [A.m]]), np.concatenate([A.colidx, [A.m]]), "iso")
+    ha = O.build_from_matrix("symmetric", A)
+    hb = O.build_from_matrix("symmetric", B)
+    xa = O.layout_multilevel(ha, 2, 5)
+    xb = O.layout_multilevel(hb, 2, 5)
+    assert np.array_equal(xa, xb[:A.m])

@@ -150,6 +150,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vmo", choices=["vmo", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="one untimed step of the workload and exit (for ncu captures; no JSON line)")
+    ap.add_argument("--profile-matrix", type=int, default=-1,
+                    help="with --profile: order only this matrix of the workload (0 or 1)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -195,6 +199,8 @@ def main():
     V.load()
 
     name, mats = medium_workload()
+    if args.profile and args.profile_matrix >= 0:
+        mats = [mats[args.profile_matrix]]
     params = {"seed": 1}
     dev_csr = [(torch.as_tensor(A.rowptr).cuda(), torch.as_tensor(A.colidx).cuda()) for A, _ in mats]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -204,6 +210,12 @@ def main():
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
+
+    if args.profile:
+        gpu_step(V, torch, mats, dev_csr, params)
+        torch.cuda.synchronize()
+        print(f"profile step done: {name}", file=sys.stderr)
+        return
 
     for _ in range(max(args.warmup, 3)):
         gpu_step(V, torch, mats, dev_csr, params)

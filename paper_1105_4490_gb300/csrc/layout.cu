@@ -273,24 +273,92 @@ __global__ void __launch_bounds__(kBlock) k_agg_level(int step, const int64_t* _
   store_cell<D>(pr.cbase + lvl_off(D, l) + c, S, W, St, Wt, CW);
 }
 
-// Rubber bands of 2-pin nets: y_v = sum_u c_vu (x_v - x_u) / 2.
+// Rubber bands of 2-pin nets: y_v = sum_u c_vu (x_v - x_u) / 2.  Rows are
+// split by degree: light rows (<= kLightMax) take one thread, medium rows a
+// warp and heavy rows a block; each class sums in a fixed order (sequential,
+// lane-strided + xor tree, thread-strided + fixed tree), so the result of a
+// vertex depends only on its own row.
+constexpr int kLightMax = 32;
+constexpr int kWarpMax = 4096;
+
+__device__ inline void add_pull(float* a, const float4& xv, const float4& xu, float c) {
+  a[0] += c * (xv.x - xu.x);
+  a[1] += c * (xv.y - xu.y);
+  a[2] += c * (xv.z - xu.z);
+  a[3] += c * (xv.w - xu.w);
+}
+
 __global__ void __launch_bounds__(kBlock) k_attract(const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
                                                     const float* __restrict__ acost, const float4* __restrict__ x,
                                                     int64_t K, float4* __restrict__ y) {
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= K) return;
+  int32_t t0 = adj_ptr[v], t1 = adj_ptr[v + 1];
+  if (t1 - t0 > kLightMax) return;  // medium and heavy rows: k_attract_warp / k_attract_block
   float4 xv = x[v];
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-  int32_t t1 = adj_ptr[v + 1];
-  for (int32_t t = adj_ptr[v]; t < t1; ++t) {
-    float4 xu = x[adj[t]];
-    float c = acost ? acost[t] : 1.0f;
-    a0 += c * (xv.x - xu.x);
-    a1 += c * (xv.y - xu.y);
-    a2 += c * (xv.z - xu.z);
-    a3 += c * (xv.w - xu.w);
+  float a[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int32_t t = t0; t < t1; ++t) add_pull(a, xv, x[adj[t]], acost ? acost[t] : 1.0f);
+  y[v] = make_float4(0.5f * a[0], 0.5f * a[1], 0.5f * a[2], 0.5f * a[3]);
+}
+
+__global__ void __launch_bounds__(kBlock) k_attract_warp(const int32_t* __restrict__ list, int64_t n,
+                                                         const int32_t* __restrict__ adj_ptr,
+                                                         const int32_t* __restrict__ adj, const float* __restrict__ acost,
+                                                         const float4* __restrict__ x, float4* __restrict__ y) {
+  int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n) return;
+  const int lane = lane_id();
+  int32_t v = list[w];
+  float4 xv = x[v];
+  float a[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int32_t t = adj_ptr[v] + lane; t < adj_ptr[v + 1]; t += 32) add_pull(a, xv, x[adj[t]], acost ? acost[t] : 1.0f);
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[m] += __shfl_xor_sync(0xffffffffu, a[m], o);
+  if (lane == 0) y[v] = make_float4(0.5f * a[0], 0.5f * a[1], 0.5f * a[2], 0.5f * a[3]);
+}
+
+__global__ void __launch_bounds__(kBlock) k_attract_block(const int32_t* __restrict__ list,
+                                                          const int32_t* __restrict__ adj_ptr,
+                                                          const int32_t* __restrict__ adj,
+                                                          const float* __restrict__ acost,
+                                                          const float4* __restrict__ x, float4* __restrict__ y) {
+  __shared__ float part[kBlock / 32][4];
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  int32_t v = list[blockIdx.x];
+  float4 xv = x[v];
+  float a[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int32_t t = adj_ptr[v] + threadIdx.x; t < adj_ptr[v + 1]; t += blockDim.x)
+    add_pull(a, xv, x[adj[t]], acost ? acost[t] : 1.0f);
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[m] += __shfl_xor_sync(0xffffffffu, a[m], o);
+  if (lane == 0)
+    for (int m = 0; m < 4; ++m) part[warp][m] = a[m];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      for (int m = 0; m < 4; ++m) b[m] += part[w][m];
+    y[v] = make_float4(0.5f * b[0], 0.5f * b[1], 0.5f * b[2], 0.5f * b[3]);
   }
-  y[v] = make_float4(0.5f * a0, 0.5f * a1, 0.5f * a2, 0.5f * a3);
+}
+
+__global__ void k_degree_class(const int32_t* __restrict__ adj_ptr, int64_t K, int32_t* __restrict__ mid,
+                               int32_t* __restrict__ heavy) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= K) return;
+  int32_t deg = adj_ptr[v + 1] - adj_ptr[v];
+  mid[v] = (deg > kLightMax && deg <= kWarpMax) ? 1 : 0;
+  heavy[v] = deg > kWarpMax ? 1 : 0;
+}
+
+__global__ void k_compact_flags(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int64_t K,
+                                int32_t* __restrict__ out) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < K && flag[v]) out[pos[v]] = (int32_t)v;
 }
 
 // Net centres z_j of general nets (Algorithm 4).
@@ -347,33 +415,199 @@ __device__ inline void accumulate(float* F, const float4& src, const float4& xn,
   }
 }
 
+// Far-field charges of one level for a target in cell `me` (level l): the
+// cells of the 6^d box spanned by the children of the cells around the
+// target's parent cell, minus the 3^d cells adjacent to the target's cell.
+// Lane `lane_g` of a group of G lanes takes the lane_g-th contiguous chunk of
+// the (clipped) box in row-major order.
+template <int D>
+__device__ inline void far_level(const float4* __restrict__ CW, const float* __restrict__ Wt, int64_t base,
+                                 const int32_t* me, int l, const float4& xn, float* F, int G, int lane_g,
+                                 unsigned long long& nint, bool count) {
+  const int sl = 1 << l;
+  int lo[D], nb[D];
+  int total = 1;
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    int par = me[m] >> 1;
+    int a = max(2 * par - 2, 0), b = min(2 * par + 3, sl - 1);
+    lo[m] = a;
+    nb[m] = b - a + 1;
+    total *= nb[m];
+  }
+  int f0 = (total * lane_g) / G, f1 = (total * (lane_g + 1)) / G;
+  if (f0 >= f1) return;
+  int c[D];
+  int rem = f0;
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    c[m] = rem % nb[m];
+    rem /= nb[m];
+  }
+  int32_t cc[D];
+#pragma unroll
+  for (int m = 0; m < D; ++m) cc[m] = lo[m] + c[m];
+  int64_t idx = base + rowmajor<D>(cc, sl);
+  for (int f = f0; f < f1; ++f) {
+    bool adjacent = true;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      int dlt = lo[m] + c[m] - me[m];
+      adjacent = adjacent && dlt >= -1 && dlt <= 1;
+    }
+    if (!adjacent) {
+      float4 cw = CW[idx];
+      float W = (D == 4) ? Wt[idx] : cw.w;
+      if (W > 0.0f) {
+        accumulate<D>(F, cw, xn, W);
+        if (count) ++nint;
+      }
+    }
+    // next cell of the box (coordinate 0 fastest)
+    ++c[0];
+    ++idx;
+    if (c[0] == nb[0]) {
+      c[0] = 0;
+      idx += (int64_t)sl - nb[0];
+      if (D > 1) {
+        ++c[1];
+        if (c[1] == nb[1]) {
+          c[1] = 0;
+          idx += (int64_t)sl * sl - (int64_t)nb[1] * sl;
+          if (D > 2) {
+            ++c[2];
+            if (c[2] == nb[2]) {
+              c[2] = 0;
+              idx += (int64_t)sl * sl * sl - (int64_t)nb[2] * sl * sl;
+              if (D > 3) ++c[3];
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// Warp-cooperative far field of one level (one lane per target): lanes whose
+// targets share the parent cell have the same candidate box, so the warp
+// walks each distinct parent's box once with broadcast loads and every lane
+// keeps the cells that are not adjacent to its own cell.  The order in which
+// a lane visits its cells is the box's row-major order, as in far_level.
+template <int D>
+__device__ inline void far_level_warp(const float4* __restrict__ CW, const float* __restrict__ Wt, int64_t base,
+                                      const int32_t* me, int l, const float4& xn, float* F, bool valid,
+                                      unsigned long long& nint, bool count) {
+  const int sl = 1 << l;
+  const unsigned lane = lane_id();
+  // parent coordinates are < 2^(Lmax-1): 14, 9 and 6 bits for d = 2, 3, 4
+  constexpr int KB = D == 2 ? 16 : (D == 3 ? 10 : 8);
+  uint32_t key = 0;
+#pragma unroll
+  for (int m = 0; m < D; ++m) key |= (uint32_t)(me[m] >> 1) << (m * KB);
+  unsigned rem = __ballot_sync(0xffffffffu, valid);
+  while (rem) {
+    const int leader = __ffs(rem) - 1;
+    const uint32_t k2 = __shfl_sync(0xffffffffu, key, leader);
+    const unsigned mem = __ballot_sync(0xffffffffu, valid && key == k2);
+    rem &= ~mem;
+    const bool member = (mem >> lane) & 1u;
+    int lo[D], hi[D];
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      int par = (int)((k2 >> (m * KB)) & ((1u << KB) - 1u));
+      lo[m] = max(2 * par - 2, 0);
+      hi[m] = min(2 * par + 3, sl - 1);
+    }
+    if (D == 2) {
+      for (int y = lo[1]; y <= hi[1]; ++y) {
+        const bool iny = y >= me[1] - 1 && y <= me[1] + 1;
+        const int64_t row = base + (int64_t)y * sl;
+        for (int x = lo[0]; x <= hi[0]; ++x) {
+          float4 cw = CW[row + x];
+          bool take = member && cw.w > 0.0f && !(iny && x >= me[0] - 1 && x <= me[0] + 1);
+          if (take) {
+            accumulate<D>(F, cw, xn, cw.w);
+            if (count) ++nint;
+          }
+        }
+      }
+    } else if (D == 3) {
+      for (int z = lo[2]; z <= hi[2]; ++z) {
+        const bool inz = z >= me[2] - 1 && z <= me[2] + 1;
+        for (int y = lo[1]; y <= hi[1]; ++y) {
+          const bool iny = inz && y >= me[1] - 1 && y <= me[1] + 1;
+          const int64_t row = base + ((int64_t)z * sl + y) * sl;
+          for (int x = lo[0]; x <= hi[0]; ++x) {
+            float4 cw = CW[row + x];
+            bool take = member && cw.w > 0.0f && !(iny && x >= me[0] - 1 && x <= me[0] + 1);
+            if (take) {
+              accumulate<D>(F, cw, xn, cw.w);
+              if (count) ++nint;
+            }
+          }
+        }
+      }
+    } else {
+      for (int w = lo[3]; w <= hi[3]; ++w) {
+        const bool inw = w >= me[3] - 1 && w <= me[3] + 1;
+        for (int z = lo[2]; z <= hi[2]; ++z) {
+          const bool inz = inw && z >= me[2] - 1 && z <= me[2] + 1;
+          for (int y = lo[1]; y <= hi[1]; ++y) {
+            const bool iny = inz && y >= me[1] - 1 && y <= me[1] + 1;
+            const int64_t row = base + (((int64_t)w * sl + z) * sl + y) * sl;
+            for (int x = lo[0]; x <= hi[0]; ++x) {
+              float4 cw = CW[row + x];
+              float W = Wt[row + x];
+              bool take = member && W > 0.0f && !(iny && x >= me[0] - 1 && x <= me[0] + 1);
+              if (take) {
+                accumulate<D>(F, cw, xn, W);
+                if (count) ++nint;
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// Gradient (eq. graphenergygradientsimple with the grid pyramid) and step of
+// every target.  Each problem gives its targets G lanes (G from the problem's
+// own size), padded to whole warps; the lanes of a group split the near field
+// (strided points) and the far field (contiguous chunks of every level's
+// box) and combine with a fixed xor tree, so a target's result depends only
+// on its own problem.  Lane 0 of the group applies the step.
 template <int D>
 __global__ void __launch_bounds__(kBlock) k_repulse_update(
     const float4* __restrict__ xs, const float* __restrict__ ws, const uint32_t* __restrict__ svals,
     const uint32_t* __restrict__ scell, const int2* __restrict__ cse, const float4* __restrict__ CW,
-    const float* __restrict__ Wt, const float4* __restrict__ yatt, const int32_t* __restrict__ vprob,
-    const ProbDev* __restrict__ prob, int64_t K, float kappa, const float* __restrict__ s0, float scale,
+    const float* __restrict__ Wt, const float4* __restrict__ yatt, const int64_t* __restrict__ tbase, int P,
+    const ProbDev* __restrict__ prob, int64_t T, float kappa, const float* __restrict__ s0, float scale,
     float step_override, float4* __restrict__ x, float4* __restrict__ y_out, uint32_t* __restrict__ bb_next,
     unsigned long long* __restrict__ icount) {
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x;
+  const int64_t lastt = min(first + (int64_t)blockDim.x, T) - 1;
+  const bool uniform = find_problem(tbase, P, first) == find_problem(tbase, P, lastt);
+  const int pb = find_problem(tbase, P, t < T ? t : T - 1);
+  const ProbDev pr = prob[pb];
+  const int G = pr.group;
+  const int64_t rel = t - pr.tbase;
+  const int64_t tgt = rel / G;
+  const int lane_g = (int)(rel & (G - 1));
+  const bool valid = t < T && tgt < pr.k;
+  const bool count = icount != nullptr;
   unsigned long long nint = 0;
-  int64_t first = (int64_t)blockIdx.x * blockDim.x;
-  int64_t lastp = min(first + (int64_t)blockDim.x, K) - 1;
-  bool uniform = vprob[first] == vprob[lastp];
-  bool valid = p < K;
-  int pb = 0;
-  float4 xnew = make_float4(0, 0, 0, 0);
+  float F[4] = {0.f, 0.f, 0.f, 0.f};
+  int64_t p = pr.vbase + tgt;
+  float4 xn = make_float4(0, 0, 0, 0);
   if (valid) {
-    pb = vprob[p];
-    const ProbDev pr = prob[pb];
     const int L = pr.L, side = 1 << L;
-    const float4 xn = xs[p];
-    const float wn = ws ? ws[p] : 1.0f;
+    xn = xs[p];
     const uint32_t packed = scell[p];
     int32_t c[D];
 #pragma unroll
     for (int m = 0; m < D; ++m) c[m] = (int32_t)((packed >> (m * field_bits(D))) & ((1u << field_bits(D)) - 1));
-    float F[4] = {0.f, 0.f, 0.f, 0.f};
     // near field: 3^D finest cells around the target's cell, exactly
     constexpr int NB = D == 2 ? 9 : (D == 3 ? 27 : 81);
     for (int o = 0; o < NB; ++o) {
@@ -388,54 +622,45 @@ __global__ void __launch_bounds__(kBlock) k_repulse_update(
       }
       if (!inside) continue;
       int2 r = cse[pr.fbase + rowmajor<D>(cc, side)];
-      for (int q = r.x; q < r.y; ++q) {
+      for (int q = r.x + lane_g; q < r.y; q += G) {
         if (q == p) continue;
         accumulate<D>(F, xs[q], xn, ws ? ws[q] : 1.0f);
-      }
-      if (icount) nint += (unsigned long long)(r.y - r.x) - ((p >= r.x && p < r.y) ? 1 : 0);
-    }
-    // far field: levels 2..L
-    for (int l = 2; l <= L; ++l) {
-      int32_t me[D], par[D];
-#pragma unroll
-      for (int m = 0; m < D; ++m) {
-        me[m] = c[m] >> (L - l);
-        par[m] = me[m] >> 1;
-      }
-      const int sl = 1 << l, sp = sl >> 1;
-      const int64_t lbase = pr.cbase + lvl_off(D, l);
-      for (int o = 0; o < NB; ++o) {
-        int32_t pc[D];
-        int oo = o;
-        bool inside = true;
-#pragma unroll
-        for (int m = 0; m < D; ++m) {
-          pc[m] = par[m] + (oo % 3) - 1;
-          oo /= 3;
-          inside = inside && pc[m] >= 0 && pc[m] < sp;
-        }
-        if (!inside) continue;
-#pragma unroll
-        for (int ch = 0; ch < (1 << D); ++ch) {
-          int32_t cc[D];
-          bool adjacent = true;
-#pragma unroll
-          for (int m = 0; m < D; ++m) {
-            cc[m] = 2 * pc[m] + ((ch >> m) & 1);
-            int32_t dlt = cc[m] - me[m];
-            adjacent = adjacent && dlt >= -1 && dlt <= 1;
-          }
-          if (adjacent) continue;
-          int64_t idx = lbase + rowmajor<D>(cc, sl);
-          float4 cw = CW[idx];
-          float W = (D == 4) ? Wt[idx] : cw.w;
-          if (W > 0.0f) {
-            accumulate<D>(F, cw, xn, W);
-            if (icount) ++nint;
-          }
-        }
+        if (count) ++nint;
       }
     }
+    // far field, levels 2..L (one lane per target: warp-cooperative below)
+    if (G > 1)
+      for (int l = 2; l <= L; ++l) {
+        int32_t me[D];
+#pragma unroll
+        for (int m = 0; m < D; ++m) me[m] = c[m] >> (L - l);
+        far_level<D>(CW, Wt, pr.cbase + lvl_off(D, l), me, l, xn, F, G, lane_g, nint, count);
+      }
+  }
+  if (G == 1) {
+    // warp-uniform: a warp never straddles two problems; invalid lanes take part
+    // in the ballots only
+    const int L = valid ? pr.L : 0;
+    const int Lw = __reduce_max_sync(0xffffffffu, (unsigned)L);
+    int32_t c[D];
+    const uint32_t packed = valid ? scell[p] : 0u;
+#pragma unroll
+    for (int m = 0; m < D; ++m) c[m] = (int32_t)((packed >> (m * field_bits(D))) & ((1u << field_bits(D)) - 1));
+    for (int l = 2; l <= Lw; ++l) {
+      int32_t me[D];
+#pragma unroll
+      for (int m = 0; m < D; ++m) me[m] = valid ? (c[m] >> (L - l)) : 0;
+      far_level_warp<D>(CW, Wt, pr.cbase + lvl_off(D, l), me, l, xn, F, valid, nint, count);
+    }
+  }
+  // combine the lanes of the group (groups never straddle a warp)
+  for (int o = G >> 1; o > 0; o >>= 1)
+#pragma unroll
+    for (int m = 0; m < D; ++m) F[m] += __shfl_xor_sync(0xffffffffu, F[m], o);
+  const bool leader = valid && lane_g == 0;
+  float4 xnew = make_float4(0, 0, 0, 0);
+  if (leader) {
+    const float wn = ws ? ws[p] : 1.0f;
     const uint32_t v = svals[p];
     float4 ya = yatt[v];
     float y0 = kappa * wn * F[0] + ya.x;
@@ -450,13 +675,13 @@ __global__ void __launch_bounds__(kBlock) k_repulse_update(
                        D > 3 ? xn.w - a * y3 : 0.f);
     x[v] = xnew;
   }
-  if (icount) {
+  if (count) {
     unsigned long long tot = nint;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     if (lane_id() == 0 && tot) atomicAdd(icount, tot);
   }
-  bbox_accumulate<D>(xnew, valid, pb, uniform, bb_next);
+  bbox_accumulate<D>(xnew, leader, pb, uniform, bb_next);
 }
 
 // ------------------------------ initial layout -----------------------------
@@ -504,7 +729,48 @@ __global__ void k_prolong(const float4* __restrict__ xc, const int32_t* __restri
 // ------------------------------- coarsening --------------------------------
 // Handshake heavy-edge matching round: every unmatched vertex of an active
 // problem proposes to its unmatched neighbour with the largest cost, ties by
-// the smaller hash of the (local) pair and then the smaller id.
+// the smaller hash of the (local) pair and then the smaller id.  The choice is
+// an arg-max under a total order, so light (thread), medium (warp) and heavy
+// (block) rows all give the same answer.
+struct Proposal {
+  float c;
+  uint64_t h;
+  int32_t u;
+};
+
+__device__ inline bool better(const Proposal& a, const Proposal& b) {
+  if (a.u < 0) return false;
+  if (b.u < 0) return true;
+  return a.c > b.c || (a.c == b.c && (a.h < b.h || (a.h == b.h && a.u < b.u)));
+}
+
+__device__ inline Proposal scan_row(const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                                    const float* __restrict__ acost, const int32_t* __restrict__ mate, int64_t v,
+                                    int64_t vb, uint64_t seed, uint64_t b, int32_t start, int32_t stride) {
+  Proposal best{0.f, 0ull, -1};
+  for (int32_t t = adj_ptr[v] + start; t < adj_ptr[v + 1]; t += stride) {
+    int32_t u = adj[t];
+    if (u == v || mate[u] >= 0) continue;
+    uint64_t lu = (uint64_t)(u - vb), lv = (uint64_t)(v - vb);
+    uint64_t lo = lu < lv ? lu : lv, hi = lu < lv ? lv : lu;
+    Proposal cand{acost ? acost[t] : 1.0f, rand64(seed, (lo << 32) | hi, b), u};
+    if (better(cand, best)) best = cand;
+  }
+  return best;
+}
+
+__device__ inline Proposal warp_best(Proposal p) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Proposal q;
+    q.c = __shfl_xor_sync(0xffffffffu, p.c, o);
+    q.h = __shfl_xor_sync(0xffffffffu, p.h, o);
+    q.u = __shfl_xor_sync(0xffffffffu, p.u, o);
+    if (better(q, p)) p = q;
+  }
+  return p;
+}
+
 __global__ void k_propose(const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
                           const float* __restrict__ acost, int64_t K, const int32_t* __restrict__ vprob,
                           const ProbDev* __restrict__ prob, const int32_t* __restrict__ active,
@@ -512,26 +778,53 @@ __global__ void k_propose(const int32_t* __restrict__ adj_ptr, const int32_t* __
                           int32_t* __restrict__ prop) {
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= K) return;
+  if (adj_ptr[v + 1] - adj_ptr[v] > kLightMax) return;  // k_propose_wide
   int pb = vprob[v];
   int32_t best = -1;
-  if (active[pb] && mate[v] < 0) {
-    int64_t vb = prob[pb].vbase;
-    uint64_t seed = seeds[pb] ^ kTagMatch;
-    uint64_t b = (uint64_t)level * 256 + (uint64_t)round;
-    float bc = 0.f;
-    uint64_t bh = 0;
-    for (int32_t t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) {
-      int32_t u = adj[t];
-      if (u == v || mate[u] >= 0) continue;
-      uint64_t lu = (uint64_t)(u - vb), lv = (uint64_t)(v - vb);
-      uint64_t lo = lu < lv ? lu : lv, hi = lu < lv ? lv : lu;
-      uint64_t h = rand64(seed, (lo << 32) | hi, b);
-      float c = acost ? acost[t] : 1.0f;
-      bool better = best < 0 || c > bc || (c == bc && (h < bh || (h == bh && u < best)));
-      if (better) { best = u; bc = c; bh = h; }
-    }
-  }
+  if (active[pb] && mate[v] < 0)
+    best = scan_row(adj_ptr, adj, acost, mate, v, prob[pb].vbase, seeds[pb] ^ kTagMatch,
+                    (uint64_t)level * 256 + (uint64_t)round, 0, 1).u;
   prop[v] = best;
+}
+
+// Medium rows (list, warp each) or heavy rows (list, block each).
+__global__ void __launch_bounds__(kBlock) k_propose_wide(const int32_t* __restrict__ list, int64_t n, int per_block,
+                                                         const int32_t* __restrict__ adj_ptr,
+                                                         const int32_t* __restrict__ adj,
+                                                         const float* __restrict__ acost,
+                                                         const int32_t* __restrict__ vprob,
+                                                         const ProbDev* __restrict__ prob,
+                                                         const int32_t* __restrict__ active,
+                                                         const uint64_t* __restrict__ seeds, int level, int round,
+                                                         const int32_t* __restrict__ mate,
+                                                         int32_t* __restrict__ prop) {
+  __shared__ Proposal part[kBlock / 32];
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  int64_t item = per_block ? (int64_t)blockIdx.x : (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  bool ok = item < n;
+  int32_t v = ok ? list[item] : 0;
+  int pb = ok ? vprob[v] : 0;
+  bool act = ok && active[pb] && mate[v] < 0;
+  Proposal best{0.f, 0ull, -1};
+  if (act) {
+    int32_t start = per_block ? (int32_t)threadIdx.x : lane;
+    int32_t stride = per_block ? (int32_t)blockDim.x : 32;
+    best = scan_row(adj_ptr, adj, acost, mate, v, prob[pb].vbase, seeds[pb] ^ kTagMatch,
+                    (uint64_t)level * 256 + (uint64_t)round, start, stride);
+  }
+  best = warp_best(best);
+  if (!per_block) {
+    if (ok && lane == 0) prop[v] = best.u;
+    return;
+  }
+  if (lane == 0) part[warp] = best;
+  __syncthreads();
+  if (threadIdx.x == 0 && ok) {
+    Proposal b = part[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (better(part[w], b)) b = part[w];
+    prop[v] = b.u;
+  }
 }
 
 __global__ void k_resolve(const int32_t* __restrict__ prop, int64_t K, int32_t* __restrict__ mate) {
@@ -645,6 +938,47 @@ int grid_levels(int64_t k, int d, int occ) {
   return L;
 }
 
+// Lanes per target of the step kernel: enough threads to fill the GPU for a
+// small problem; a function of the problem's own size only.
+int group_size(int64_t k) {
+  if (k <= 2048) return 32;
+  if (k <= 8192) return 16;
+  if (k <= 32768) return 8;
+  if (k <= 65536) return 4;
+  if (k <= 131072) return 2;
+  return 1;
+}
+
+static vmo_status classify_degrees(LevelBatch& lb, cudaStream_t s) {
+  lb.n_mid = lb.n_heavy = 0;
+  if (!lb.adj_ptr || lb.K == 0) return VMO_OK;
+  Scratch sc(s);
+  int32_t *fm, *fh, *pm, *ph, *tm, *th;
+  VMO_TRY(sc.alloc(&fm, lb.K));
+  VMO_TRY(sc.alloc(&fh, lb.K));
+  VMO_TRY(sc.alloc(&pm, lb.K));
+  VMO_TRY(sc.alloc(&ph, lb.K));
+  VMO_TRY(sc.alloc(&tm, 1));
+  VMO_TRY(sc.alloc(&th, 1));
+  launch(k_degree_class, grid_for(lb.K, kBlock), kBlock, 0, s, lb.adj_ptr, lb.K, fm, fh);
+  VMO_LAUNCHED("degree_class");
+  VMO_TRY(scan_exclusive<int32_t>(fm, pm, lb.K, tm, s, sc));
+  VMO_TRY(scan_exclusive<int32_t>(fh, ph, lb.K, th, s, sc));
+  int32_t h[2] = {0, 0};
+  VMO_CUDA(cudaMemcpyAsync(&h[0], tm, 4, cudaMemcpyDeviceToHost, s));
+  VMO_CUDA(cudaMemcpyAsync(&h[1], th, 4, cudaMemcpyDeviceToHost, s));
+  VMO_CUDA(cudaStreamSynchronize(s));
+  lb.n_mid = h[0];
+  lb.n_heavy = h[1];
+  VMO_TRY(lb.mid_list.resize(std::max<int64_t>(lb.n_mid, 1)));
+  VMO_TRY(lb.heavy_list.resize(std::max<int64_t>(lb.n_heavy, 1)));
+  if (lb.n_mid) launch(k_compact_flags, grid_for(lb.K, kBlock), kBlock, 0, s, fm, pm, lb.K, lb.mid_list.ptr);
+  if (lb.n_heavy) launch(k_compact_flags, grid_for(lb.K, kBlock), kBlock, 0, s, fh, ph, lb.K, lb.heavy_list.ptr);
+  VMO_LAUNCHED("compact_flags");
+  VMO_CUDA(cudaStreamSynchronize(s));
+  return VMO_OK;
+}
+
 int init_side(int64_t k, int d) {
   int64_t s = 1;
   for (;;) {
@@ -661,6 +995,7 @@ vmo_status level_setup(LevelBatch& lb, int d, int occ, cudaStream_t s) {
   lb.cbase.assign(P + 1, 0);
   lb.fbase.assign(P + 1, 0);
   std::vector<ProbDev> pd(P);
+  std::vector<int64_t> tb(P + 1, 0);
   lb.maxL = 1;
   for (int p = 0; p < P; ++p) {
     int64_t k = lb.vbase[p + 1] - lb.vbase[p];
@@ -675,8 +1010,11 @@ vmo_status level_setup(LevelBatch& lb, int d, int occ, cudaStream_t s) {
     pd[p].k = (int32_t)k;
     pd[p].L = L;
     pd[p].side = init_side(std::max<int64_t>(k, 1), d);
-    pd[p].pad = 0;
+    pd[p].group = group_size(k);
+    pd[p].tbase = tb[p];
+    tb[p + 1] = tb[p] + ((k * pd[p].group + 31) / 32) * 32;
   }
+  lb.threads = tb[P];
   // prefix tables of the coarse-level aggregation steps: step s covers level L_p - s >= 2
   int nsteps = std::max(lb.maxL - 2, 0);
   std::vector<int64_t> off((size_t)(nsteps + 1) * (P + 1), 0);
@@ -691,6 +1029,8 @@ vmo_status level_setup(LevelBatch& lb, int d, int occ, cudaStream_t s) {
   VMO_TRY(lb.vprob.resize((size_t)std::max<int64_t>(lb.K, 1)));
   VMO_CUDA(cudaMemcpyAsync(lb.prob.ptr, pd.data(), P * sizeof(ProbDev), cudaMemcpyHostToDevice, s));
   VMO_CUDA(cudaMemcpyAsync(lb.aggoff.ptr, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  VMO_TRY(lb.tbase.resize(P + 1));
+  VMO_CUDA(cudaMemcpyAsync(lb.tbase.ptr, tb.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   int64_t* vb;
   VMO_CUDA(cudaMallocAsync((void**)&vb, (P + 1) * sizeof(int64_t), s));
   VMO_CUDA(cudaMemcpyAsync(vb, lb.vbase.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
@@ -701,7 +1041,7 @@ vmo_status level_setup(LevelBatch& lb, int d, int occ, cudaStream_t s) {
   VMO_CUDA(cudaFreeAsync(vb, s));
   // host vectors must outlive the copies
   VMO_CUDA(cudaStreamSynchronize(s));
-  return VMO_OK;
+  return classify_degrees(lb, s);
 }
 
 vmo_status init_coords_level(LevelBatch& lb, int d, const uint64_t* seeds_dev, float4* x, const int32_t* start_dev,
@@ -780,6 +1120,12 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
       }
       if (lb.adj_ptr) {
         launch(k_attract, grid_for(K, kBlock), kBlock, 0, s, lb.adj_ptr, lb.adj, lb.acost, x, K, yatt);
+        if (lb.n_mid)
+          launch(k_attract_warp, grid_for(lb.n_mid * 32, kBlock), kBlock, 0, s, lb.mid_list.ptr, lb.n_mid, lb.adj_ptr,
+                 lb.adj, lb.acost, x, yatt);
+        if (lb.n_heavy)
+          launch(k_attract_block, (unsigned)lb.n_heavy, kBlock, 0, s, lb.heavy_list.ptr, lb.adj_ptr, lb.adj, lb.acost,
+                 x, yatt);
       } else if (lb.net_ptr) {
         if (lb.nnets > 0) launch(k_net_center, grid_for(lb.nnets, kBlock), kBlock, 0, s, lb.net_ptr, lb.pins, lb.nnets, x, z);
         launch(k_attract_hyper, grid_for(K, kBlock), kBlock, 0, s, lb.vtx_ptr, lb.vnets, x, z, K, yatt);
@@ -788,8 +1134,8 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
       }
       const bool timed = stats_timing();
       if (timed) stats_time_begin(s);
-      launch(k_repulse_update<D>, grid_for(K, kBlock), kBlock, 0, s, xs, ws, svals, scell, cse, CW, Wt, yatt,
-             lb.vprob.ptr, lb.prob.ptr, K, kappa, s0, (float)scale, step_override, x, y_out, nxt,
+      launch(k_repulse_update<D>, grid_for(lb.threads, kBlock), kBlock, 0, s, xs, ws, svals, scell, cse, CW, Wt,
+             yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, (float)scale, step_override, x, y_out, nxt,
              stats_interaction_counter());
       if (timed) stats_time_end(s, (uint64_t)K);
       cudaError_t e = cudaGetLastError();
@@ -818,7 +1164,13 @@ vmo_status coarsen_level(LevelBatch& lb, const uint64_t* seeds_dev, int j, int r
   VMO_CUDA(cudaMemsetAsync(isanc, 0, K * sizeof(int32_t), s));
   for (int r = 0; r < rounds; ++r) {
     launch(k_propose, grid_for(K, kBlock), kBlock, 0, s, lb.adj_ptr, lb.adj, lb.acost, K, lb.vprob.ptr, lb.prob.ptr,
-                                                     active_dev, seeds_dev, j, r, mate, prop);
+           active_dev, seeds_dev, j, r, mate, prop);
+    if (lb.n_mid)
+      launch(k_propose_wide, grid_for(lb.n_mid * 32, kBlock), kBlock, 0, s, lb.mid_list.ptr, lb.n_mid, 0, lb.adj_ptr,
+             lb.adj, lb.acost, lb.vprob.ptr, lb.prob.ptr, active_dev, seeds_dev, j, r, mate, prop);
+    if (lb.n_heavy)
+      launch(k_propose_wide, (unsigned)lb.n_heavy, kBlock, 0, s, lb.heavy_list.ptr, lb.n_heavy, 1, lb.adj_ptr, lb.adj,
+             lb.acost, lb.vprob.ptr, lb.prob.ptr, active_dev, seeds_dev, j, r, mate, prop);
     launch(k_resolve, grid_for(K, kBlock), kBlock, 0, s, prop, K, mate);
   }
   launch(k_anchor, grid_for(K, kBlock), kBlock, 0, s, lb.adj_ptr, lb.adj, K, mate, anchor, isanc);

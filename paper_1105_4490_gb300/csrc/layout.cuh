@@ -12,10 +12,11 @@ struct ProbDev {
   int64_t vbase;   // first vertex of the problem in the level
   int64_t cbase;   // first entry of its cell tables (all levels 0..L)
   int64_t fbase;   // first entry of its finest-level cell ranges
+  int64_t tbase;   // first thread of its targets in the step kernel (multiple of 32)
   int32_t k;       // vertices
   int32_t L;       // finest grid level
   int32_t side;    // side of the random initial box
-  int32_t pad;
+  int32_t group;   // lanes per target in the step kernel (power of two <= 32)
 };
 
 // One level of the multilevel hierarchy for a batch of independent problems
@@ -46,6 +47,12 @@ struct LevelBatch {
   DevArray<int32_t> vprob;       // K: problem index of every vertex
   DevArray<int64_t> aggoff;      // (maxL-1) x (P+1): prefix of coarse-level cell counts
   int32_t maxL = 1;
+  DevArray<int64_t> tbase;       // P+1: thread bases of the step kernel
+  int64_t threads = 0;           // threads of the step kernel
+  // vertices by degree class (graph models): medium and heavy rows get a warp
+  // or a block each in the gather kernels
+  DevArray<int32_t> mid_list, heavy_list;
+  int64_t n_mid = 0, n_heavy = 0;
   // storage of coarse levels built by the coarsening
   DevArray<int32_t> own_adj_ptr, own_adj;
   DevArray<float> own_acost, own_w;

@@ -233,8 +233,8 @@ def energy(hg: Hypergraph, d: int, x, w=None, c=None) -> float:
 
 def gradient(hg: Hypergraph, d: int, x, occ: int = 8, w=None, c=None):
     """Gradient y (eq. graphenergygradientsimple, repulsion on the grid pyramid),
-    level-L Morton keys, L, and per-target (interaction count, summed source
-    weight)."""
+    level-L cell keys (row-major index), L, and per-target (interaction count,
+    summed source weight)."""
     s = hg._struct()
     xx, ww, cc = _x64(x), _opt64(w), _opt64(c)
     y = np.zeros_like(xx)

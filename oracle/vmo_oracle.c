@@ -321,6 +321,8 @@ ORA_EXPORT double ora_energy(const ora_hg* h, int32_t d, const double* x /* k*4 
 /*   far:  at each level l = 2..L, every cell whose parent is adjacent or     */
 /*         equal to n's level-(l-1) cell but which is not adjacent or equal   */
 /*         to n's level-l cell, as one charge.                                */
+/* The level-L cell index (row-major, coordinate 0 fastest) is the key of a  */
+/* point.                                                                     */
 /* Every other point is counted exactly once (in the coarsest level where its */
 /* cell stops being adjacent to n's cell, or in the near field).              */
 /* Pairs at distance 0 contribute nothing (they lie outside U of Def. 2.1).   */
@@ -333,10 +335,11 @@ ORA_EXPORT int32_t ora_levels(int32_t k, int32_t d, int32_t occ) {
   return L;
 }
 
-static uint32_t ora_morton(const int32_t* c, int d, int bits) {
+/* Index of a level-`bits` cell: row-major with coordinate 0 fastest,
+ * sum_m c_m 2^(bits m).  The level-L index is the sort key of a point. */
+static uint32_t ora_cellidx(const int32_t* c, int d, int bits) {
   uint32_t key = 0;
-  for (int b = 0; b < bits; ++b)
-    for (int m = 0; m < d; ++m) key |= (uint32_t)((c[m] >> b) & 1) << (b * d + m);
+  for (int m = d - 1; m >= 0; --m) key = (key << bits) | (uint32_t)c[m];
   return key;
 }
 
@@ -405,7 +408,7 @@ ORA_EXPORT int ora_gradient(const ora_hg* h, int32_t d, int32_t occ, const doubl
   float lo[4], hi[4];
   ora_cells(k, d, L, xf, cell, lo, hi);
   if (keys)
-    for (int32_t v = 0; v < k; ++v) keys[v] = ora_morton(&cell[4 * v], d, L);
+    for (int32_t v = 0; v < k; ++v) keys[v] = ora_cellidx(&cell[4 * v], d, L);
   /* Dense per-level tables of (sum w, sum w x), FP64. */
   int64_t* off = (int64_t*)malloc((size_t)(L + 2) * sizeof(int64_t));
   off[0] = 0;
@@ -417,7 +420,7 @@ ORA_EXPORT int ora_gradient(const ora_hg* h, int32_t d, int32_t occ, const doubl
     for (int l = 0; l <= L; ++l) {
       int32_t cl[4];
       for (int m = 0; m < d; ++m) cl[m] = cell[4 * v + m] >> (L - l);
-      int64_t id = off[l] + ora_morton(cl, d, l);
+      int64_t id = off[l] + ora_cellidx(cl, d, l);
       W[id] += wv;
       for (int m = 0; m < d; ++m) S[4 * id + m] += wv * x[4 * v + m];
     }
@@ -427,10 +430,10 @@ ORA_EXPORT int ora_gradient(const ora_hg* h, int32_t d, int32_t occ, const doubl
   int32_t* head = (int32_t*)calloc((size_t)ncell + 1, sizeof(int32_t));
   int32_t* mem = (int32_t*)malloc((size_t)k * sizeof(int32_t));
   int32_t* fill = (int32_t*)calloc((size_t)ncell, sizeof(int32_t));
-  for (int32_t v = 0; v < k; ++v) head[ora_morton(&cell[4 * v], d, L) + 1]++;
+  for (int32_t v = 0; v < k; ++v) head[ora_cellidx(&cell[4 * v], d, L) + 1]++;
   for (int64_t q = 0; q < ncell; ++q) head[q + 1] += head[q];
   for (int32_t v = 0; v < k; ++v) {
-    uint32_t q = ora_morton(&cell[4 * v], d, L);
+    uint32_t q = ora_cellidx(&cell[4 * v], d, L);
     mem[head[q] + fill[q]++] = v;
   }
   double kap = ora_kappa(d);
@@ -451,7 +454,7 @@ ORA_EXPORT int ora_gradient(const ora_hg* h, int32_t d, int32_t occ, const doubl
         if (cc[m] < 0 || cc[m] >= (1 << L)) inside = 0;
       }
       if (!inside) continue;
-      uint32_t q = ora_morton(cc, d, L);
+      uint32_t q = ora_cellidx(cc, d, L);
       for (int32_t t = head[q]; t < head[q + 1]; ++t) {
         int32_t i = mem[t];
         if (i == n) continue;
@@ -487,7 +490,7 @@ ORA_EXPORT int ora_gradient(const ora_hg* h, int32_t d, int32_t occ, const doubl
             if (diff < -1 || diff > 1) adjacent = 0;
           }
           if (adjacent) continue;
-          int64_t id = off[l] + ora_morton(cc, d, l);
+          int64_t id = off[l] + ora_cellidx(cc, d, l);
           if (W[id] <= 0.0) continue;
           double dx[4], r2 = 0.0;
           for (int m = 0; m < d; ++m) {

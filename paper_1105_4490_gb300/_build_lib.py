@@ -41,7 +41,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(OBJ, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
-            jobs.append([nvcc, *FLAGS, *ARCH, "-c", s, "-o", o])
+            extra = os.environ.get("VMO_NVCC_EXTRA", "").split()
+            jobs.append([nvcc, *FLAGS, *extra, *ARCH, "-c", s, "-o", o])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))

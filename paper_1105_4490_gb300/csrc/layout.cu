@@ -160,17 +160,16 @@ __global__ void __launch_bounds__(kBlock) k_keys(const float4* __restrict__ x, i
   grid_frame<D>(bb, pb, L, lo, &s);
   int32_t c[D];
   cell_of<D>(x[v], lo, s, L, c);
-  keys[v] = morton<D>(c, L);
+  keys[v] = (uint32_t)rowmajor<D>(c, 1 << L);
   vals[v] = (uint32_t)v;
 }
 
 template <int D>
-__global__ void __launch_bounds__(kBlock) k_gather(const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ svals,
-                                                   int64_t K, const float4* __restrict__ x, const float* __restrict__ w,
+__global__ void __launch_bounds__(kBlock) k_gather(const uint32_t* __restrict__ svals, int64_t K,
+                                                   const float4* __restrict__ x, const float* __restrict__ w,
                                                    const int32_t* __restrict__ vprob, const ProbDev* __restrict__ prob,
                                                    const uint32_t* __restrict__ bb, float4* __restrict__ xs,
-                                                   float* __restrict__ ws, uint32_t* __restrict__ scell,
-                                                   int2* __restrict__ cse) {
+                                                   float* __restrict__ ws, uint32_t* __restrict__ scell) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= K) return;
   uint32_t v = svals[p];
@@ -187,12 +186,15 @@ __global__ void __launch_bounds__(kBlock) k_gather(const uint32_t* __restrict__ 
 #pragma unroll
   for (int m = 0; m < D; ++m) packed |= (uint32_t)c[m] << (m * field_bits(D));
   scell[p] = packed;
-  int64_t rm = pr.fbase + rowmajor<D>(c, 1 << pr.L);
-  uint32_t key = skeys[p];
-  bool first = (p == pr.vbase) || skeys[p - 1] != key;
-  bool last = (p == pr.vbase + pr.k - 1) || skeys[p + 1] != key;
-  if (first) cse[rm].x = (int)p;
-  if (last) cse[rm].y = (int)(p + 1);
+}
+
+// First sorted position with key >= c in [a, b).
+__device__ inline int64_t lower_key(const uint32_t* __restrict__ skeys, int64_t a, int64_t b, uint32_t c) {
+  while (a < b) {
+    int64_t mid = (a + b) >> 1;
+    if (skeys[mid] < c) a = mid + 1; else b = mid;
+  }
+  return a;
 }
 
 template <int D>
@@ -210,21 +212,30 @@ __device__ inline void store_cell(int64_t idx, const float* S, float W, float4* 
   }
 }
 
+// Finest cells: the first sorted position of every cell (a binary search in
+// the problem's sorted keys, so empty cells get the start of the next one and
+// a row of cells is one contiguous range), and the cell's charge from its
+// points.  cst has one extra entry per problem (its end).
 template <int D>
-__global__ void __launch_bounds__(kBlock) k_agg_finest(const int2* __restrict__ cse, int64_t ncells,
+__global__ void __launch_bounds__(kBlock) k_agg_finest(const uint32_t* __restrict__ skeys, int64_t ncells,
                                                        const int64_t* __restrict__ fbase, int P,
                                                        const ProbDev* __restrict__ prob, const float4* __restrict__ xs,
-                                                       const float* __restrict__ ws, float4* __restrict__ St,
-                                                       float* __restrict__ Wt, float4* __restrict__ CW) {
+                                                       const float* __restrict__ ws, int32_t* __restrict__ cst,
+                                                       float4* __restrict__ St, float* __restrict__ Wt,
+                                                       float4* __restrict__ CW) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ncells) return;
   int pb = find_problem(fbase, P, i);
   ProbDev pr = prob[pb];
   int64_t c = i - pr.fbase;
-  int2 r = cse[i];
+  const int64_t a = pr.vbase, b = pr.vbase + pr.k;
+  int64_t q0 = lower_key(skeys, a, b, (uint32_t)c);
+  int64_t q1 = lower_key(skeys, q0, b, (uint32_t)(c + 1));
+  cst[pr.fbase + pb + c] = (int32_t)q0;
+  if (c == (int64_t(1) << (D * pr.L)) - 1) cst[pr.fbase + pb + c + 1] = (int32_t)b;
   float S[4] = {0.f, 0.f, 0.f, 0.f};
   float W = 0.f;
-  for (int q = r.x; q < r.y; ++q) {
+  for (int64_t q = q0; q < q1; ++q) {
     float4 p = xs[q];
     float wq = ws ? ws[q] : 1.0f;
     S[0] += wq * p.x;
@@ -390,6 +401,48 @@ __global__ void k_attract_hyper(const int32_t* __restrict__ vtx_ptr, const int32
   y[v] = a;
 }
 
+// Approximate reciprocal and reciprocal square root (PTX rcp/rsqrt.approx,
+// flush-to-zero) for the force terms; the decisions elsewhere use exactly
+// rounded intrinsics.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Smallest squared distance fed to the kernels: only masked terms (weight 0)
+// can be closer, and their contribution stays exactly 0.
+constexpr float kR2Floor = 1e-15f;
+
+// F += w r^-d (src - xn) with the weight already masked (0 = no term).
+template <int D>
+__device__ __forceinline__ void add_charge(float* F, const float4& src, const float4& xn, float w) {
+  float dx0 = src.x - xn.x;
+  float dx1 = D > 1 ? src.y - xn.y : 0.f;
+  float dx2 = D > 2 ? src.z - xn.z : 0.f;
+  float dx3 = D > 3 ? src.w - xn.w : 0.f;
+  float r2 = fmaxf(dx0 * dx0 + dx1 * dx1 + dx2 * dx2 + dx3 * dx3, kR2Floor);
+  float g;
+  if (D == 2) {
+    g = w * rcp_approx(r2);
+  } else if (D == 3) {
+    float ir = rsqrt_approx(r2);
+    g = w * ir * ir * ir;
+  } else {
+    float i2 = rcp_approx(r2);
+    g = w * i2 * i2;
+  }
+  F[0] += g * dx0;
+  if (D > 1) F[1] += g * dx1;
+  if (D > 2) F[2] += g * dx2;
+  if (D > 3) F[3] += g * dx3;
+}
+
 template <int D>
 __device__ inline void accumulate(float* F, const float4& src, const float4& xn, float wsrc) {
   float dx0 = src.x - xn.x;
@@ -420,10 +473,10 @@ __device__ inline void accumulate(float* F, const float4& src, const float4& xn,
 // target's parent cell, minus the 3^d cells adjacent to the target's cell.
 // Lane `lane_g` of a group of G lanes takes the lane_g-th contiguous chunk of
 // the (clipped) box in row-major order.
-template <int D>
+template <int D, bool COUNT>
 __device__ inline void far_level(const float4* __restrict__ CW, const float* __restrict__ Wt, int64_t base,
                                  const int32_t* me, int l, const float4& xn, float* F, int G, int lane_g,
-                                 unsigned long long& nint, bool count) {
+                                 unsigned long long& nint) {
   const int sl = 1 << l;
   int lo[D], nb[D];
   int total = 1;
@@ -455,14 +508,11 @@ __device__ inline void far_level(const float4* __restrict__ CW, const float* __r
       int dlt = lo[m] + c[m] - me[m];
       adjacent = adjacent && dlt >= -1 && dlt <= 1;
     }
-    if (!adjacent) {
-      float4 cw = CW[idx];
-      float W = (D == 4) ? Wt[idx] : cw.w;
-      if (W > 0.0f) {
-        accumulate<D>(F, cw, xn, W);
-        if (count) ++nint;
-      }
-    }
+    float4 cw = CW[idx];
+    float W = (D == 4) ? Wt[idx] : cw.w;
+    W = adjacent ? 0.0f : W;
+    add_charge<D>(F, cw, xn, W);
+    if (COUNT && W > 0.0f) ++nint;
     // next cell of the box (coordinate 0 fastest)
     ++c[0];
     ++idx;
@@ -488,107 +538,144 @@ __device__ inline void far_level(const float4* __restrict__ CW, const float* __r
   }
 }
 
-// Warp-cooperative far field of one level (one lane per target): lanes whose
-// targets share the parent cell have the same candidate box, so the warp
-// walks each distinct parent's box once with broadcast loads and every lane
-// keeps the cells that are not adjacent to its own cell.  The order in which
-// a lane visits its cells is the box's row-major order, as in far_level.
-template <int D>
-__device__ inline void far_level_warp(const float4* __restrict__ CW, const float* __restrict__ Wt, int64_t base,
-                                      const int32_t* me, int l, const float4& xn, float* F, bool valid,
-                                      unsigned long long& nint, bool count) {
+// One row (up to 6 consecutive cells along coordinate 0) of a far-field box:
+// all loads are issued first, then the charges are accumulated without
+// branches into two alternating partial sums (more independent work per
+// lane).  A cell counts if the lane's target is a member of the box's warp
+// group, the cell holds weight and it is not adjacent to the target's cell.
+template <int D, bool COUNT>
+__device__ inline void far_row(const float4* __restrict__ CW, const float* __restrict__ Wt, int64_t row, int lo0,
+                               int hi0, bool incore, int me0, const float4& xn, float* Fa, float* Fb,
+                               unsigned long long& nint) {
+  float4 cw[6];
+  float W[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const bool in = lo0 + i <= hi0;
+    cw[i] = in ? CW[row + lo0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    W[i] = (D == 4) ? (in ? Wt[row + lo0 + i] : 0.f) : cw[i].w;
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const int x = lo0 + i;
+    const bool core = incore && x >= me0 - 1 && x <= me0 + 1;
+    const float wt = core ? 0.0f : W[i];  // empty and out-of-box cells have weight 0
+    if (i & 1) add_charge<D>(Fb, cw[i], xn, wt);
+    else add_charge<D>(Fa, cw[i], xn, wt);
+    if (COUNT && wt > 0.0f) ++nint;
+  }
+}
+
+// Far field of one level for one lane per target: the lane's own box, row by
+// row (row-major order of the box).
+template <int D, bool COUNT>
+__device__ inline void far_level_lane(const float4* __restrict__ CW, const float* __restrict__ Wt, int64_t base,
+                                      const int32_t* me, int l, const float4& xn, float* F, unsigned long long& nint) {
   const int sl = 1 << l;
-  const unsigned lane = lane_id();
-  // parent coordinates are < 2^(Lmax-1): 14, 9 and 6 bits for d = 2, 3, 4
-  constexpr int KB = D == 2 ? 16 : (D == 3 ? 10 : 8);
-  uint32_t key = 0;
+  int lo[D], hi[D];
 #pragma unroll
-  for (int m = 0; m < D; ++m) key |= (uint32_t)(me[m] >> 1) << (m * KB);
-  unsigned rem = __ballot_sync(0xffffffffu, valid);
-  while (rem) {
-    const int leader = __ffs(rem) - 1;
-    const uint32_t k2 = __shfl_sync(0xffffffffu, key, leader);
-    const unsigned mem = __ballot_sync(0xffffffffu, valid && key == k2);
-    rem &= ~mem;
-    const bool member = (mem >> lane) & 1u;
-    int lo[D], hi[D];
-#pragma unroll
-    for (int m = 0; m < D; ++m) {
-      int par = (int)((k2 >> (m * KB)) & ((1u << KB) - 1u));
-      lo[m] = max(2 * par - 2, 0);
-      hi[m] = min(2 * par + 3, sl - 1);
+  for (int m = 0; m < D; ++m) {
+    int par = me[m] >> 1;
+    lo[m] = max(2 * par - 2, 0);
+    hi[m] = min(2 * par + 3, sl - 1);
+  }
+  float Fb[4] = {0.f, 0.f, 0.f, 0.f};
+  if (D == 2) {
+    for (int y = lo[1]; y <= hi[1]; ++y) {
+      const bool iny = y >= me[1] - 1 && y <= me[1] + 1;
+      far_row<D, COUNT>(CW, Wt, base + (int64_t)y * sl, lo[0], hi[0], iny, me[0], xn, F, Fb, nint);
     }
-    if (D == 2) {
+  } else if (D == 3) {
+    for (int z = lo[2]; z <= hi[2]; ++z) {
+      const bool inz = z >= me[2] - 1 && z <= me[2] + 1;
       for (int y = lo[1]; y <= hi[1]; ++y) {
-        const bool iny = y >= me[1] - 1 && y <= me[1] + 1;
-        const int64_t row = base + (int64_t)y * sl;
-        for (int x = lo[0]; x <= hi[0]; ++x) {
-          float4 cw = CW[row + x];
-          bool take = member && cw.w > 0.0f && !(iny && x >= me[0] - 1 && x <= me[0] + 1);
-          if (take) {
-            accumulate<D>(F, cw, xn, cw.w);
-            if (count) ++nint;
-          }
-        }
+        const bool iny = inz && y >= me[1] - 1 && y <= me[1] + 1;
+        far_row<D, COUNT>(CW, Wt, base + ((int64_t)z * sl + y) * sl, lo[0], hi[0], iny, me[0], xn, F, Fb, nint);
       }
-    } else if (D == 3) {
+    }
+  } else {
+    for (int w = lo[3]; w <= hi[3]; ++w) {
+      const bool inw = w >= me[3] - 1 && w <= me[3] + 1;
       for (int z = lo[2]; z <= hi[2]; ++z) {
-        const bool inz = z >= me[2] - 1 && z <= me[2] + 1;
+        const bool inz = inw && z >= me[2] - 1 && z <= me[2] + 1;
         for (int y = lo[1]; y <= hi[1]; ++y) {
           const bool iny = inz && y >= me[1] - 1 && y <= me[1] + 1;
-          const int64_t row = base + ((int64_t)z * sl + y) * sl;
-          for (int x = lo[0]; x <= hi[0]; ++x) {
-            float4 cw = CW[row + x];
-            bool take = member && cw.w > 0.0f && !(iny && x >= me[0] - 1 && x <= me[0] + 1);
-            if (take) {
-              accumulate<D>(F, cw, xn, cw.w);
-              if (count) ++nint;
-            }
-          }
-        }
-      }
-    } else {
-      for (int w = lo[3]; w <= hi[3]; ++w) {
-        const bool inw = w >= me[3] - 1 && w <= me[3] + 1;
-        for (int z = lo[2]; z <= hi[2]; ++z) {
-          const bool inz = inw && z >= me[2] - 1 && z <= me[2] + 1;
-          for (int y = lo[1]; y <= hi[1]; ++y) {
-            const bool iny = inz && y >= me[1] - 1 && y <= me[1] + 1;
-            const int64_t row = base + (((int64_t)w * sl + z) * sl + y) * sl;
-            for (int x = lo[0]; x <= hi[0]; ++x) {
-              float4 cw = CW[row + x];
-              float W = Wt[row + x];
-              bool take = member && W > 0.0f && !(iny && x >= me[0] - 1 && x <= me[0] + 1);
-              if (take) {
-                accumulate<D>(F, cw, xn, W);
-                if (count) ++nint;
-              }
-            }
-          }
+          far_row<D, COUNT>(CW, Wt, base + (((int64_t)w * sl + z) * sl + y) * sl, lo[0], hi[0], iny, me[0], xn, F,
+                            Fb, nint);
         }
       }
     }
   }
+#pragma unroll
+  for (int m = 0; m < D; ++m) F[m] += Fb[m];
+}
+
+// Per-warp bounding-box partials of the step kernel, reduced per problem by
+// k_bbox_reduce (no block barrier in the step kernel).
+template <int D>
+__device__ inline void bbox_warp_partial(const float4& v, bool valid, uint32_t* __restrict__ part, int64_t warp) {
+  uint32_t mn[4], mx[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    uint32_t o = (valid && m < D) ? f2ord(comp(v, m)) : 0u;
+    mn[m] = __reduce_min_sync(0xffffffffu, (valid && m < D) ? o : 0xFFFFFFFFu);
+    mx[m] = __reduce_max_sync(0xffffffffu, o);
+  }
+  if (lane_id() == 0) {
+    uint4* p = reinterpret_cast<uint4*>(part + warp * 8);
+    p[0] = make_uint4(mn[0], mn[1], mn[2], mn[3]);
+    p[1] = make_uint4(mx[0], mx[1], mx[2], mx[3]);
+  }
+}
+
+// One warp per problem: reduce its warps' partials into the bounding box.
+__global__ void k_bbox_reduce(const uint32_t* __restrict__ part, const int64_t* __restrict__ tbase, int P,
+                              uint32_t* __restrict__ bb) {
+  int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= P) return;
+  const int lane = lane_id();
+  int64_t a = tbase[w] / 32, b = tbase[w + 1] / 32;
+  uint32_t mn[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, mx[4] = {0u, 0u, 0u, 0u};
+  for (int64_t i = a + lane; i < b; i += 32)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      mn[m] = min(mn[m], part[i * 8 + m]);
+      mx[m] = max(mx[m], part[i * 8 + 4 + m]);
+    }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    mn[m] = __reduce_min_sync(0xffffffffu, mn[m]);
+    mx[m] = __reduce_max_sync(0xffffffffu, mx[m]);
+  }
+  if (lane < 4) bb[w * 8 + lane] = mn[lane];
+  else if (lane < 8) bb[w * 8 + lane] = mx[lane - 4];
 }
 
 // Gradient (eq. graphenergygradientsimple with the grid pyramid) and step of
 // every target.  Each problem gives its targets G lanes (G from the problem's
 // own size), padded to whole warps; the lanes of a group split the near field
-// (strided points) and the far field (contiguous chunks of every level's
-// box) and combine with a fixed xor tree, so a target's result depends only
-// on its own problem.  Lane 0 of the group applies the step.
-template <int D>
-__global__ void __launch_bounds__(kBlock) k_repulse_update(
+// (strided points) and the far field (contiguous chunks of every level's box)
+// and combine with a fixed xor tree, so a target's result depends only on its
+// own problem.  Lane 0 of the group applies the step.  Near field: points are
+// sorted by row-major cell index, so the 3 cells of a row along coordinate 0
+// form one contiguous range of the sorted points.
+#ifndef VMO_STEP_BLOCK
+#define VMO_STEP_BLOCK 128
+#endif
+#ifndef VMO_STEP_MINBLOCKS
+#define VMO_STEP_MINBLOCKS 6
+#endif
+constexpr int kStepBlock = VMO_STEP_BLOCK;
+
+template <int D, bool COUNT>
+__global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_update(
     const float4* __restrict__ xs, const float* __restrict__ ws, const uint32_t* __restrict__ svals,
-    const uint32_t* __restrict__ scell, const int2* __restrict__ cse, const float4* __restrict__ CW,
+    const uint32_t* __restrict__ scell, const int32_t* __restrict__ cst, const float4* __restrict__ CW,
     const float* __restrict__ Wt, const float4* __restrict__ yatt, const int64_t* __restrict__ tbase, int P,
     const ProbDev* __restrict__ prob, int64_t T, float kappa, const float* __restrict__ s0, float scale,
-    float step_override, float4* __restrict__ x, float4* __restrict__ y_out, uint32_t* __restrict__ bb_next,
+    float step_override, float4* __restrict__ x, float4* __restrict__ y_out, uint32_t* __restrict__ bb_part,
     unsigned long long* __restrict__ icount) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t first = (int64_t)blockIdx.x * blockDim.x;
-  const int64_t lastt = min(first + (int64_t)blockDim.x, T) - 1;
-  const bool uniform = find_problem(tbase, P, first) == find_problem(tbase, P, lastt);
   const int pb = find_problem(tbase, P, t < T ? t : T - 1);
   const ProbDev pr = prob[pb];
   const int G = pr.group;
@@ -596,10 +683,9 @@ __global__ void __launch_bounds__(kBlock) k_repulse_update(
   const int64_t tgt = rel / G;
   const int lane_g = (int)(rel & (G - 1));
   const bool valid = t < T && tgt < pr.k;
-  const bool count = icount != nullptr;
   unsigned long long nint = 0;
   float F[4] = {0.f, 0.f, 0.f, 0.f};
-  int64_t p = pr.vbase + tgt;
+  const int64_t p = pr.vbase + tgt;
   float4 xn = make_float4(0, 0, 0, 0);
   if (valid) {
     const int L = pr.L, side = 1 << L;
@@ -608,49 +694,42 @@ __global__ void __launch_bounds__(kBlock) k_repulse_update(
     int32_t c[D];
 #pragma unroll
     for (int m = 0; m < D; ++m) c[m] = (int32_t)((packed >> (m * field_bits(D))) & ((1u << field_bits(D)) - 1));
-    // near field: 3^D finest cells around the target's cell, exactly
-    constexpr int NB = D == 2 ? 9 : (D == 3 ? 27 : 81);
-    for (int o = 0; o < NB; ++o) {
+    // near field: rows of 3 cells along coordinate 0 around the target's cell
+    const int32_t* cs = cst + pr.fbase + pb;
+    const int xa = max(c[0] - 1, 0), xb = min(c[0] + 1, side - 1);
+    constexpr int NR = D == 2 ? 3 : (D == 3 ? 9 : 27);
+    for (int o = 0; o < NR; ++o) {
       int32_t cc[D];
       int oo = o;
       bool inside = true;
+      cc[0] = xa;
 #pragma unroll
-      for (int m = 0; m < D; ++m) {
+      for (int m = 1; m < D; ++m) {
         cc[m] = c[m] + (oo % 3) - 1;
         oo /= 3;
         inside = inside && cc[m] >= 0 && cc[m] < side;
       }
       if (!inside) continue;
-      int2 r = cse[pr.fbase + rowmajor<D>(cc, side)];
-      for (int q = r.x + lane_g; q < r.y; q += G) {
-        if (q == p) continue;
-        accumulate<D>(F, xs[q], xn, ws ? ws[q] : 1.0f);
-        if (count) ++nint;
+      const int64_t r0 = rowmajor<D>(cc, side);
+      const int qa = cs[r0], qb = cs[r0 + (xb - xa) + 1];
+      for (int q = qa + lane_g; q < qb; q += G) {
+        float wq = ws ? ws[q] : 1.0f;
+        const float4 src = xs[q];
+        const bool same = q == p || (src.x == xn.x && src.y == xn.y && src.z == xn.z && src.w == xn.w);
+        wq = same ? 0.0f : wq;  // the target itself and coincident points exert no force
+        add_charge<D>(F, src, xn, wq);
+        if (COUNT && q != p) ++nint;
       }
     }
-    // far field, levels 2..L (one lane per target: warp-cooperative below)
-    if (G > 1)
-      for (int l = 2; l <= L; ++l) {
-        int32_t me[D];
-#pragma unroll
-        for (int m = 0; m < D; ++m) me[m] = c[m] >> (L - l);
-        far_level<D>(CW, Wt, pr.cbase + lvl_off(D, l), me, l, xn, F, G, lane_g, nint, count);
-      }
-  }
-  if (G == 1) {
-    // warp-uniform: a warp never straddles two problems; invalid lanes take part
-    // in the ballots only
-    const int L = valid ? pr.L : 0;
-    const int Lw = __reduce_max_sync(0xffffffffu, (unsigned)L);
-    int32_t c[D];
-    const uint32_t packed = valid ? scell[p] : 0u;
-#pragma unroll
-    for (int m = 0; m < D; ++m) c[m] = (int32_t)((packed >> (m * field_bits(D))) & ((1u << field_bits(D)) - 1));
-    for (int l = 2; l <= Lw; ++l) {
+    // far field, levels 2..L
+    for (int l = 2; l <= L; ++l) {
       int32_t me[D];
 #pragma unroll
-      for (int m = 0; m < D; ++m) me[m] = valid ? (c[m] >> (L - l)) : 0;
-      far_level_warp<D>(CW, Wt, pr.cbase + lvl_off(D, l), me, l, xn, F, valid, nint, count);
+      for (int m = 0; m < D; ++m) me[m] = c[m] >> (L - l);
+      if (G == 1)
+        far_level_lane<D, COUNT>(CW, Wt, pr.cbase + lvl_off(D, l), me, l, xn, F, nint);
+      else
+        far_level<D, COUNT>(CW, Wt, pr.cbase + lvl_off(D, l), me, l, xn, F, G, lane_g, nint);
     }
   }
   // combine the lanes of the group (groups never straddle a warp)
@@ -675,13 +754,13 @@ __global__ void __launch_bounds__(kBlock) k_repulse_update(
                        D > 3 ? xn.w - a * y3 : 0.f);
     x[v] = xnew;
   }
-  if (count) {
+  if (COUNT) {
     unsigned long long tot = nint;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     if (lane_id() == 0 && tot) atomicAdd(icount, tot);
   }
-  bbox_accumulate<D>(xnew, leader, pb, uniform, bb_next);
+  bbox_warp_partial<D>(xnew, leader, bb_part, t >> 5);
 }
 
 // ------------------------------ initial layout -----------------------------
@@ -1062,7 +1141,7 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
   uint32_t *keys, *vals, *skeys, *svals, *scell, *bb;
   float4 *xs, *yatt, *St, *CW, *z = nullptr;
   float *ws = nullptr, *Wt, *s0;
-  int2* cse;
+  int32_t* cst;
   int64_t *fb;
   const int64_t ncell = lb.cbase[P], nfine = lb.fbase[P];
   VMO_TRY(sc.alloc(&keys, K));
@@ -1076,8 +1155,10 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
   VMO_TRY(sc.alloc(&St, ncell));
   VMO_TRY(sc.alloc(&CW, ncell));
   VMO_TRY(sc.alloc(&Wt, ncell));
-  VMO_TRY(sc.alloc(&cse, nfine));
+  VMO_TRY(sc.alloc(&cst, nfine + P));
   VMO_TRY(sc.alloc(&bb, (size_t)2 * 8 * P));
+  uint32_t* bpart;
+  VMO_TRY(sc.alloc(&bpart, (size_t)std::max<int64_t>(lb.threads / 32, 1) * 8));
   VMO_TRY(sc.alloc(&s0, P));
   VMO_TRY(sc.alloc(&fb, P + 1));
   if (lb.net_ptr) VMO_TRY(sc.alloc(&z, std::max<int64_t>(lb.nnets, 1)));
@@ -1104,10 +1185,10 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
       if (keys_out && t == 0) cudaMemcpyAsync(keys_out, keys, K * 4, cudaMemcpyDeviceToDevice, s);
       st = radix_sort_u32(keys, vals, skeys, svals, K, D * lb.maxL, segmented ? &segs : nullptr, s, sc);
       if (st != VMO_OK) break;
-      cudaMemsetAsync(cse, 0, nfine * sizeof(int2), s);
-      launch(k_gather<D>, grid_for(K, kBlock), kBlock, 0, s, skeys, svals, K, x, lb.w, lb.vprob.ptr, lb.prob.ptr, cur,
-                                                         xs, ws, scell, cse);
-      launch(k_agg_finest<D>, grid_for(nfine, kBlock), kBlock, 0, s, cse, nfine, fb, P, lb.prob.ptr, xs, ws, St, Wt, CW);
+      launch(k_gather<D>, grid_for(K, kBlock), kBlock, 0, s, svals, K, x, lb.w, lb.vprob.ptr, lb.prob.ptr, cur, xs,
+             ws, scell);
+      launch(k_agg_finest<D>, grid_for(nfine, kBlock), kBlock, 0, s, skeys, nfine, fb, P, lb.prob.ptr, xs, ws, cst,
+             St, Wt, CW);
       for (int stp = 1; stp <= lb.maxL - 2; ++stp) {
         const int64_t* off = lb.aggoff.ptr + (size_t)stp * (P + 1);
         int64_t n = 0;
@@ -1134,10 +1215,17 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
       }
       const bool timed = stats_timing();
       if (timed) stats_time_begin(s);
-      launch(k_repulse_update<D>, grid_for(lb.threads, kBlock), kBlock, 0, s, xs, ws, svals, scell, cse, CW, Wt,
-             yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, (float)scale, step_override, x, y_out, nxt,
-             stats_interaction_counter());
+      unsigned long long* icount = stats_interaction_counter();
+      if (icount)
+        launch(k_repulse_update<D, true>, grid_for(lb.threads, kStepBlock), kStepBlock, 0, s, xs, ws, svals, scell,
+               cst, CW, Wt, yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, (float)scale, step_override,
+               x, y_out, bpart, icount);
+      else
+        launch(k_repulse_update<D, false>, grid_for(lb.threads, kStepBlock), kStepBlock, 0, s, xs, ws, svals, scell,
+               cst, CW, Wt, yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, (float)scale, step_override,
+               x, y_out, bpart, icount);
       if (timed) stats_time_end(s, (uint64_t)K);
+      launch(k_bbox_reduce, grid_for((int64_t)P * 32, kBlock), kBlock, 0, s, bpart, lb.tbase.ptr, P, nxt);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) st = cuda_fail(e, "layout step", __FILE__, __LINE__);
       scale *= o.decay;

@@ -145,7 +145,8 @@ def test_far_field_error_small_and_translation_invariant(oracle_mod, d):
 
 
 def test_keys_locate_points(oracle_mod):
-    """The level-L Morton key of a vertex decodes to the fp32 cell containing it."""
+    """The level-L key of a vertex (row-major cell index) decodes to the fp32
+    cell containing it."""
     O = oracle_mod
     k, d = 5000, 3
     A = W.csr_from_coo(k, k, np.arange(k), np.arange(k), "iso")
@@ -158,9 +159,8 @@ def test_keys_locate_points(oracle_mod):
     lo, hi = xf.min(0), xf.max(0)
     E = float((hi - lo).max())
     c = np.zeros((k, d), dtype=np.int64)
-    for b in range(L):
-        for m in range(d):
-            c[:, m] |= ((keys.astype(np.int64) >> (b * d + m)) & 1) << b
+    for m in range(d):
+        c[:, m] = (keys.astype(np.int64) >> (L * m)) & ((1 << L) - 1)
     cell = E / 2 ** L
     pos = (xf.astype(np.float64) - lo) / cell
     assert (c <= np.floor(pos) + 1e-6).all() and (pos - c < 1 + 1e-5).all()

@@ -143,6 +143,52 @@ def gpu_step(V, torch, mats, dev_csr, params):
     return nnz
 
 
+def batched_leg(V, torch, count: int, plain_sample: int, warmup: int, steps: int, flush):
+    """Config-4 distribution: `count` independent matrices ordered to BBD in one
+    batch (vmo_batch_order) against one-at-a-time plain calls on the first
+    `plain_sample` of them; both in nnz ordered per second."""
+    mats = W.batch_mix(count, seed=1)
+    dev = [(torch.as_tensor(A.rowptr).cuda(), torch.as_tensor(A.colidx).cuda(), A.m) for A in mats]
+    nnz = sum(A.nnz for A in mats)
+    p = V.Params(d=3, seed=1)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(warmup, 3)):
+        V.batch_order(dev, p)
+    t = 0.0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        V.batch_order(dev, p)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t += a.elapsed_time(b) / 1e3
+    batched = nnz * steps / t
+    sample = dev[:plain_sample]
+    snnz = sum(A.nnz for A in mats[:plain_sample])
+    for rp, ci, m in sample[:2]:
+        V.Hypergraph(rp, ci, m, m).order_vertices(p)
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for rp, ci, m in sample:
+        V.Hypergraph(rp, ci, m, m).order_vertices(p)
+    b.record(stream)
+    torch.cuda.synchronize()
+    plain = snnz / (a.elapsed_time(b) / 1e3)
+    return {"workload": f"batch_mix x{count} (n log-uniform 200..20000, half 2D grids, half random symmetric "
+                        f"3-30 nnz/row), d=3, min_part 64",
+            "matrices": count, "rows": sum(A.m for A in mats), "nnz": nnz,
+            "batched": {"value": batched, "unit": "nnz/s", "ms_per_batch": 1e3 * t / steps, "steps": steps},
+            "plain_one_at_a_time": {"value": plain, "unit": "nnz/s", "sample_matrices": plain_sample,
+                                    "sample_nnz": snnz},
+            "batched_over_plain": batched / plain}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -150,6 +196,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vmo", choices=["vmo", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=1024,
+                    help="matrices of the batched leg (config-4 distribution; 0 skips it)")
     ap.add_argument("--profile", action="store_true",
                     help="one untimed step of the workload and exit (for ncu captures; no JSON line)")
     ap.add_argument("--profile-matrix", type=int, default=-1,
@@ -298,6 +346,10 @@ def main():
                 "avg_launch_ms": avg_ms, "launches": st["step_launches"],
                 "share_of_step": st["step_ms"] / 1e3 / elapsed}
 
+    modes = None
+    if args.batch_count > 0:
+        modes = batched_leg(V, torch, args.batch_count, 32, args.warmup, max(min(args.steps, 3), 1), flush)
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         sname, smats = cpu_sample(small=False)
@@ -311,6 +363,7 @@ def main():
                       "iters_per_level": 100, "max_depth": 10, "layout": "multilevel",
                       "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
            "gpu_launches": st["launches"], "clocks": csum, "roofline": roofline, "cpu_baseline": cpu,
+           "modes": modes,
            "e2e": {"value": e2e_value, "unit": "nnz/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
     print(json.dumps(out))
     if world > 1:

@@ -212,6 +212,30 @@ vmo_status vmo_order_sbd(vmo_hg hg, const float* coords, const vmo_params* param
 vmo_status vmo_order_vertices(vmo_hg hg, const float* coords, const vmo_params* params, int32_t sbd,
                               int32_t* perm, vmo_tree* tree, void* stream);
 
+/* Batched recursive ordering of `count` independent square patterns in one
+ * launch sequence (symmetric model).  The matrices are joined
+ * block-diagonally on the device and every connected component of every
+ * matrix is laid out and ordered as one problem of a single batch; the result
+ * for each matrix is identical, bit for bit, to vmo_order_vertices on that
+ * matrix alone with the same params (no arithmetic depends on the batch).
+ * mats: host array of `count` vmo_csr (device pointers inside).
+ * coords: NULL (the layout is computed) or device float[4 sum_i m_i], the
+ * matrices' coordinates one after the other (ordering only, Sec. 5 "O").
+ * perm: device int32[sum_i m_i]; matrix i's permutation (perm[new] = old, local
+ * row indices) starts at offset sum_{j<i} m_j.  sbd: 0 BBD, 1 SBD.
+ * Errors: VMO_ERR_INVALID for count < 0, a null list, a non-square or
+ * malformed matrix; VMO_ERR_UNSUPPORTED beyond 2^30 rows or 2^31 nonzeros in
+ * total. */
+vmo_status vmo_batch_order(const vmo_csr* mats, int32_t count, const float* coords, const vmo_params* params,
+                           int32_t sbd, int32_t* perm, void* stream);
+
+/* Batched geometry only (multilevel layout of every connected component of
+ * every matrix as one batch, symmetric model): coords device float[4 sum_i m_i],
+ * matrix i's coordinates at row offset sum_{j<i} m_j; identical, bit for bit,
+ * to vmo_layout of each matrix alone.  Errors as vmo_batch_order. */
+vmo_status vmo_batch_layout(const vmo_csr* mats, int32_t count, const vmo_params* params, float* coords,
+                            void* stream);
+
 /* Cut metrics of a vertex partition (Sec. 4.1 footnote, Sec. 5): over the
  * nets of the model, lambda_e = number of distinct parts among the pins;
  * cutnet = #{e : lambda_e > 1}, lambda1 = sum_e (lambda_e - 1).

@@ -1,4 +1,5 @@
 """GB300-native visual matrix ordering (VMO): CUDA library for sm_103a behind a
 C-ABI (include/vmo.h) with a thin Python binding (``vmo``)."""
 from . import vmo  # noqa: F401
-from .vmo import Hypergraph, Params, VmoError, default_params, init_coords, load, stats, stats_reset  # noqa: F401
+from .vmo import (Hypergraph, Params, VmoError, batch_layout, batch_order, default_params, init_coords, load, stats,  # noqa: F401
+                  stats_reset)

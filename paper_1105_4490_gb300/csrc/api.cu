@@ -140,15 +140,6 @@ vmo_status check_params(const vmo_params* p) {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-LayoutOptions options_of(const vmo_params* p) {
-  LayoutOptions o;
-  o.d = p->d;
-  o.iters = p->iters;
-  o.sigma = p->sigma;
-  o.decay = p->decay;
-  o.occupancy = p->occupancy;
-  return o;
-}
 
 // Level-0 batch of one problem: the handle's model.
 vmo_status single_batch(vmo_hg_s* h, int d, int occ, LevelBatch& lb, cudaStream_t s) {
@@ -186,14 +177,7 @@ vmo_status run_layout(vmo_hg_s* h, const vmo_params* p, float4* x, bool given, c
   }
   ComponentGroups g;
   VMO_TRY(group_components(h, g, s, sc));
-  LevelBatch lb;
-  VMO_TRY(relabel_graph(h, g, lb, s, sc));
-  VMO_TRY(level_setup(lb, p->d, p->occupancy, s));
-  std::vector<uint64_t> seeds(lb.P, p->seed);
-  float4* xp;
-  VMO_TRY(sc.alloc(&xp, std::max<int64_t>(h->k, 1)));
-  VMO_TRY(layout_multilevel(lb, o, seeds, p->match_rounds, p->coarse_min, p->multilevel != 0, xp, s, sc));
-  return unpermute_coords(g, xp, x, s);
+  return layout_grouped(h, g, p, x, s, sc);
 }
 
 __global__ void k_split_rows(const int32_t* __restrict__ ord, int64_t n, int32_t m, const int32_t* __restrict__ rpos,
@@ -228,26 +212,15 @@ vmo_status run_order(vmo_hg_s* h, const float* coords, const vmo_params* p, int 
   if (coords && !aligned16(coords)) return invalid("coords must be 16-byte aligned");
   Scratch sc(s);
   const int64_t k = h->k;
+  ComponentGroups g;
+  VMO_TRY(group_components(h, g, s, sc));
   float4* x = (float4*)coords;
   if (!x) {
     VMO_TRY(sc.alloc(&x, std::max<int64_t>(k, 1)));
-    VMO_TRY(run_layout(h, p, x, false, s, sc));
+    VMO_TRY(layout_grouped(h, g, p, x, s, sc));
   }
-  OrderParams op;
-  op.d = p->d;
-  op.km_iters = p->km_iters;
-  op.min_part = p->min_part;
-  op.max_depth = p->max_depth;
-  op.sbd = sbd;
   OrderState st;
-  st.adj_ptr = h->adj_ptr.ptr;
-  st.adj = h->adj.ptr;
-  // components are ordered one after the other, each from its own root
-  ComponentGroups g;
-  VMO_TRY(group_components(h, g, s, sc));
-  std::vector<uint64_t> seeds(g.base.size() - 1, p->seed);
-  VMO_TRY(order_setup(st, x, g.base, seeds, op, g.cperm, s, sc));
-  VMO_TRY(order_levels(st, op, s, sc));
+  VMO_TRY(order_grouped(h, g, x, p, sbd, st, s, sc));
   if (vperm) VMO_CUDA(cudaMemcpyAsync(vperm, st.ord, k * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   if (row_perm || col_perm) {
     if (h->model == VMO_SYMMETRIC) {
@@ -285,6 +258,10 @@ vmo_status run_order(vmo_hg_s* h, const float* coords, const vmo_params* p, int 
 }
 
 }  // namespace
+
+vmo_status ensure_device_public() { return ensure_device(); }
+vmo_status check_params_public(const vmo_params* p) { return check_params(p); }
+
 }  // namespace vmo
 
 using namespace vmo;

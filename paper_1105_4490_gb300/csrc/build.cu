@@ -189,6 +189,17 @@ __global__ void cut_kernel(const int32_t* __restrict__ net_ptr, const int32_t* _
 
 }  // namespace
 
+// Checks one CSR on the device; the error bits are or-ed into *bad.
+vmo_status validate_csr_async(const vmo_csr* a, int32_t* bad, cudaStream_t s) {
+  if (!a || a->m < 0 || a->n < 0 || a->nnz < 0) return invalid("csr: negative size or null");
+  if (!a->rowptr || (a->nnz > 0 && !a->colidx)) return invalid("csr: null pointer");
+  if (a->nnz > INT32_MAX) return unsupported("csr: more than 2^31-1 nonzeros");
+  int64_t n = std::max<int64_t>(a->m, a->nnz);
+  launch(validate_csr_kernel, grid_for(n + 1, 256), 256, 0, s, a->rowptr, a->colidx, a->m, a->n, a->nnz, bad);
+  VMO_LAUNCHED("validate_csr");
+  return VMO_OK;
+}
+
 vmo_status validate_csr(const vmo_csr* a, cudaStream_t s, Scratch& sc) {
   if (!a || a->m < 0 || a->n < 0 || a->nnz < 0) return invalid("csr: negative size or null");
   if (!a->rowptr || (a->nnz > 0 && !a->colidx)) return invalid("csr: null pointer");

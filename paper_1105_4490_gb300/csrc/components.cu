@@ -154,4 +154,31 @@ vmo_status unpermute_coords(const ComponentGroups& g, const float4* xp, float4* 
   return VMO_OK;
 }
 
+vmo_status layout_grouped(const vmo_hg_s* h, const ComponentGroups& g, const vmo_params* p, float4* x,
+                          cudaStream_t s, Scratch& sc) {
+  LevelBatch lb;
+  VMO_TRY(relabel_graph(h, g, lb, s, sc));
+  VMO_TRY(level_setup(lb, p->d, p->occupancy, s));
+  std::vector<uint64_t> seeds(lb.P, p->seed);
+  float4* xp;
+  VMO_TRY(sc.alloc(&xp, std::max<int64_t>(h->k, 1)));
+  VMO_TRY(layout_multilevel(lb, options_of(p), seeds, p->match_rounds, p->coarse_min, p->multilevel != 0, xp, s, sc));
+  return unpermute_coords(g, xp, x, s);
+}
+
+vmo_status order_grouped(const vmo_hg_s* h, const ComponentGroups& g, const float4* x, const vmo_params* p, int sbd,
+                         OrderState& st, cudaStream_t s, Scratch& sc) {
+  OrderParams op;
+  op.d = p->d;
+  op.km_iters = p->km_iters;
+  op.min_part = p->min_part;
+  op.max_depth = p->max_depth;
+  op.sbd = sbd;
+  st.adj_ptr = h->adj_ptr.ptr;
+  st.adj = h->adj.ptr;
+  std::vector<uint64_t> seeds(g.base.size() - 1, p->seed);
+  VMO_TRY(order_setup(st, x, g.base, seeds, op, g.cperm, s, sc));
+  return order_levels(st, op, s, sc);
+}
+
 }  // namespace vmo

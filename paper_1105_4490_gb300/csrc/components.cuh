@@ -2,6 +2,7 @@
 #pragma once
 
 #include "layout.cuh"
+#include "order.cuh"
 
 namespace vmo {
 
@@ -21,5 +22,26 @@ vmo_status relabel_graph(const vmo_hg_s* h, const ComponentGroups& g, LevelBatch
 
 // x[cperm[i]] = xp[i].
 vmo_status unpermute_coords(const ComponentGroups& g, const float4* xp, float4* x, cudaStream_t s);
+
+inline LayoutOptions options_of(const vmo_params* p) {
+  LayoutOptions o;
+  o.d = p->d;
+  o.iters = p->iters;
+  o.sigma = p->sigma;
+  o.decay = p->decay;
+  o.occupancy = p->occupancy;
+  return o;
+}
+
+// Multilevel layout of a graph model, one problem per component (x in vertex
+// order of the handle).
+vmo_status layout_grouped(const vmo_hg_s* h, const ComponentGroups& g, const vmo_params* p, float4* x,
+                          cudaStream_t s, Scratch& sc);
+
+// Recursive ordering of a graph model from coordinates x: every component
+// from its own root, components one after the other.  st.ord holds the
+// vertex permutation on return.
+vmo_status order_grouped(const vmo_hg_s* h, const ComponentGroups& g, const float4* x, const vmo_params* p, int sbd,
+                         OrderState& st, cudaStream_t s, Scratch& sc);
 
 }  // namespace vmo

@@ -74,8 +74,12 @@ __device__ inline int64_t rowmajor(const int32_t* c, int side) {
 __host__ __device__ constexpr int field_bits(int D) { return D == 4 ? 8 : 30 / D; }
 
 // Block-level bounding-box accumulation into ordered-uint min/max slots.
+// uniform: every valid thread of the block belongs to problem pblock (the
+// block result is then published once for pblock); otherwise each valid
+// thread publishes its own point for its own problem pb.
 template <int D>
-__device__ void bbox_accumulate(const float4& v, bool valid, int pb, bool uniform, uint32_t* __restrict__ bb) {
+__device__ void bbox_accumulate(const float4& v, bool valid, int pb, bool uniform, int pblock,
+                                uint32_t* __restrict__ bb) {
   __shared__ uint32_t smn[kBlock / 32][4], smx[kBlock / 32][4];
   const int lane = lane_id(), warp = threadIdx.x >> 5;
   if (!uniform) {
@@ -103,8 +107,8 @@ __device__ void bbox_accumulate(const float4& v, bool valid, int pb, bool unifor
       mn = min(mn, smn[w][threadIdx.x]);
       mx = max(mx, smx[w][threadIdx.x]);
     }
-    if (mn != 0xFFFFFFFFu) atomicMin(&bb[pb * 8 + threadIdx.x], mn);
-    if (mx != 0u) atomicMax(&bb[pb * 8 + 4 + threadIdx.x], mx);
+    if (mn != 0xFFFFFFFFu) atomicMin(&bb[pblock * 8 + threadIdx.x], mn);
+    if (mx != 0u) atomicMax(&bb[pblock * 8 + 4 + threadIdx.x], mx);
   }
 }
 
@@ -119,11 +123,12 @@ __global__ void __launch_bounds__(kBlock) k_bbox(const float4* __restrict__ x, i
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t first = (int64_t)blockIdx.x * blockDim.x;
   int64_t last = min(first + (int64_t)blockDim.x, K) - 1;
-  bool uniform = vprob[first] == vprob[last];
+  const int pblock = vprob[first];
+  bool uniform = pblock == vprob[last];
   bool valid = i < K;
   float4 v = valid ? x[i] : make_float4(0, 0, 0, 0);
   int pb = valid ? vprob[i] : 0;
-  bbox_accumulate<D>(v, valid, pb, uniform, bb);
+  bbox_accumulate<D>(v, valid, pb, uniform, pblock, bb);
 }
 
 // Step length of a level: s0 = sigma * Lbox / k^(1/d), Lbox = d-th root of the
@@ -471,78 +476,11 @@ __device__ inline void accumulate(float* F, const float4& src, const float4& xn,
 // Far-field charges of one level for a target in cell `me` (level l): the
 // cells of the 6^d box spanned by the children of the cells around the
 // target's parent cell, minus the 3^d cells adjacent to the target's cell.
-// Lane `lane_g` of a group of G lanes takes the lane_g-th contiguous chunk of
-// the (clipped) box in row-major order.
-template <int D, bool COUNT>
-__device__ inline void far_level(const float4* __restrict__ CW, const float* __restrict__ Wt, int64_t base,
-                                 const int32_t* me, int l, const float4& xn, float* F, int G, int lane_g,
-                                 unsigned long long& nint) {
-  const int sl = 1 << l;
-  int lo[D], nb[D];
-  int total = 1;
-#pragma unroll
-  for (int m = 0; m < D; ++m) {
-    int par = me[m] >> 1;
-    int a = max(2 * par - 2, 0), b = min(2 * par + 3, sl - 1);
-    lo[m] = a;
-    nb[m] = b - a + 1;
-    total *= nb[m];
-  }
-  int f0 = (total * lane_g) / G, f1 = (total * (lane_g + 1)) / G;
-  if (f0 >= f1) return;
-  int c[D];
-  int rem = f0;
-#pragma unroll
-  for (int m = 0; m < D; ++m) {
-    c[m] = rem % nb[m];
-    rem /= nb[m];
-  }
-  int32_t cc[D];
-#pragma unroll
-  for (int m = 0; m < D; ++m) cc[m] = lo[m] + c[m];
-  int64_t idx = base + rowmajor<D>(cc, sl);
-  for (int f = f0; f < f1; ++f) {
-    bool adjacent = true;
-#pragma unroll
-    for (int m = 0; m < D; ++m) {
-      int dlt = lo[m] + c[m] - me[m];
-      adjacent = adjacent && dlt >= -1 && dlt <= 1;
-    }
-    float4 cw = CW[idx];
-    float W = (D == 4) ? Wt[idx] : cw.w;
-    W = adjacent ? 0.0f : W;
-    add_charge<D>(F, cw, xn, W);
-    if (COUNT && W > 0.0f) ++nint;
-    // next cell of the box (coordinate 0 fastest)
-    ++c[0];
-    ++idx;
-    if (c[0] == nb[0]) {
-      c[0] = 0;
-      idx += (int64_t)sl - nb[0];
-      if (D > 1) {
-        ++c[1];
-        if (c[1] == nb[1]) {
-          c[1] = 0;
-          idx += (int64_t)sl * sl - (int64_t)nb[1] * sl;
-          if (D > 2) {
-            ++c[2];
-            if (c[2] == nb[2]) {
-              c[2] = 0;
-              idx += (int64_t)sl * sl * sl - (int64_t)nb[2] * sl * sl;
-              if (D > 3) ++c[3];
-            }
-          }
-        }
-      }
-    }
-  }
-}
-
-// One row (up to 6 consecutive cells along coordinate 0) of a far-field box:
+// One row (up to 6 consecutive cells along coordinate 0) of the box:
 // all loads are issued first, then the charges are accumulated without
 // branches into two alternating partial sums (more independent work per
-// lane).  A cell counts if the lane's target is a member of the box's warp
-// group, the cell holds weight and it is not adjacent to the target's cell.
+// lane).  A cell counts if it holds weight and is not adjacent to the
+// target's cell.
 template <int D, bool COUNT>
 __device__ inline void far_row(const float4* __restrict__ CW, const float* __restrict__ Wt, int64_t row, int lo0,
                                int hi0, bool incore, int me0, const float4& xn, float* Fa, float* Fb,
@@ -570,7 +508,8 @@ __device__ inline void far_row(const float4* __restrict__ CW, const float* __res
 // row (row-major order of the box).
 template <int D, bool COUNT>
 __device__ inline void far_level_lane(const float4* __restrict__ CW, const float* __restrict__ Wt, int64_t base,
-                                      const int32_t* me, int l, const float4& xn, float* F, unsigned long long& nint) {
+                                      const int32_t* me, int l, const float4& xn, float* F, int G, int lane_g,
+                                      unsigned long long& nint) {
   const int sl = 1 << l;
   int lo[D], hi[D];
 #pragma unroll
@@ -579,16 +518,21 @@ __device__ inline void far_level_lane(const float4* __restrict__ CW, const float
     lo[m] = max(2 * par - 2, 0);
     hi[m] = min(2 * par + 3, sl - 1);
   }
+  // rows of the box (coordinate 0 varies along a row) go round-robin to the
+  // G lanes of the target's group
   float Fb[4] = {0.f, 0.f, 0.f, 0.f};
+  int row = 0;
   if (D == 2) {
-    for (int y = lo[1]; y <= hi[1]; ++y) {
+    for (int y = lo[1]; y <= hi[1]; ++y, ++row) {
+      if ((row & (G - 1)) != lane_g) continue;
       const bool iny = y >= me[1] - 1 && y <= me[1] + 1;
       far_row<D, COUNT>(CW, Wt, base + (int64_t)y * sl, lo[0], hi[0], iny, me[0], xn, F, Fb, nint);
     }
   } else if (D == 3) {
     for (int z = lo[2]; z <= hi[2]; ++z) {
       const bool inz = z >= me[2] - 1 && z <= me[2] + 1;
-      for (int y = lo[1]; y <= hi[1]; ++y) {
+      for (int y = lo[1]; y <= hi[1]; ++y, ++row) {
+        if ((row & (G - 1)) != lane_g) continue;
         const bool iny = inz && y >= me[1] - 1 && y <= me[1] + 1;
         far_row<D, COUNT>(CW, Wt, base + ((int64_t)z * sl + y) * sl, lo[0], hi[0], iny, me[0], xn, F, Fb, nint);
       }
@@ -598,7 +542,8 @@ __device__ inline void far_level_lane(const float4* __restrict__ CW, const float
       const bool inw = w >= me[3] - 1 && w <= me[3] + 1;
       for (int z = lo[2]; z <= hi[2]; ++z) {
         const bool inz = inw && z >= me[2] - 1 && z <= me[2] + 1;
-        for (int y = lo[1]; y <= hi[1]; ++y) {
+        for (int y = lo[1]; y <= hi[1]; ++y, ++row) {
+          if ((row & (G - 1)) != lane_g) continue;
           const bool iny = inz && y >= me[1] - 1 && y <= me[1] + 1;
           far_row<D, COUNT>(CW, Wt, base + (((int64_t)w * sl + z) * sl + y) * sl, lo[0], hi[0], iny, me[0], xn, F,
                             Fb, nint);
@@ -726,10 +671,7 @@ __global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_upda
       int32_t me[D];
 #pragma unroll
       for (int m = 0; m < D; ++m) me[m] = c[m] >> (L - l);
-      if (G == 1)
-        far_level_lane<D, COUNT>(CW, Wt, pr.cbase + lvl_off(D, l), me, l, xn, F, nint);
-      else
-        far_level<D, COUNT>(CW, Wt, pr.cbase + lvl_off(D, l), me, l, xn, F, G, lane_g, nint);
+      far_level_lane<D, COUNT>(CW, Wt, pr.cbase + lvl_off(D, l), me, l, xn, F, G, lane_g, nint);
     }
   }
   // combine the lanes of the group (groups never straddle a warp)

@@ -78,7 +78,8 @@ class Params:
 SYMBOLS = ["vmo_default_params", "vmo_build_hypergraph", "vmo_hg_vertices", "vmo_hg_nets", "vmo_hg_arrays",
            "vmo_components", "vmo_init_coords", "vmo_layout", "vmo_layout_step", "vmo_coarsen", "vmo_bisect",
            "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_cut_size", "vmo_destroy",
-           "vmo_status_string", "vmo_last_error", "vmo_stats_reset", "vmo_stats_get"]
+           "vmo_status_string", "vmo_last_error", "vmo_stats_reset", "vmo_stats_get", "vmo_batch_order",
+           "vmo_batch_layout"]
 
 
 def load(path: str | None = None):
@@ -111,6 +112,8 @@ def load(path: str | None = None):
         getattr(lib, nm).argtypes = [V, V, C.POINTER(_Params), V, V, C.POINTER(_Tree), V]
     lib.vmo_order_vertices.argtypes = [V, V, C.POINTER(_Params), I32, V, C.POINTER(_Tree), V]
     lib.vmo_cut_size.argtypes = [V, V, I32, P64, P64, V]
+    lib.vmo_batch_order.argtypes = [C.POINTER(_Csr), I32, V, C.POINTER(_Params), I32, V, V]
+    lib.vmo_batch_layout.argtypes = [C.POINTER(_Csr), I32, C.POINTER(_Params), V, V]
     lib.vmo_destroy.argtypes = [V]
     lib.vmo_destroy.restype = None
     lib.vmo_status_string.argtypes = [C.c_int]
@@ -308,3 +311,44 @@ def stats() -> dict:
     s = _Stats()
     _check(load().vmo_stats_get(C.byref(s)))
     return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+
+def _csr_array(mats):
+    keep = []
+    arr = (_Csr * max(len(mats), 1))()
+    offs = [0]
+    for i, mt in enumerate(mats):
+        if isinstance(mt, tuple):
+            rp, ci, m = mt
+            n = m
+        else:
+            rp, ci, m, n = torch.as_tensor(mt.rowptr), torch.as_tensor(mt.colidx), mt.m, mt.n
+        rp = rp.to(device="cuda", dtype=torch.int32).contiguous()
+        ci = ci.to(device="cuda", dtype=torch.int32).contiguous()
+        keep += [rp, ci]
+        arr[i] = _Csr(m, n, ci.numel(), rp.data_ptr(), ci.data_ptr() if ci.numel() else None)
+        offs.append(offs[-1] + m)
+    return arr, offs, keep
+
+
+def batch_layout(mats, params: Params | None = None):
+    """Geometry of many square patterns in one batch: float32 [sum m, 4] and offsets."""
+    arr, offs, keep = _csr_array(mats)
+    x = torch.zeros((max(offs[-1], 1), 4), dtype=torch.float32, device="cuda")
+    p = (params or Params())._c()
+    _check(load().vmo_batch_layout(arr, len(mats), C.byref(p), _ptr(x), _stream()))
+    return x[:offs[-1]], offs
+
+
+def batch_order(mats, params: Params | None = None, sbd: bool = False, coords: torch.Tensor | None = None):
+    """Orders many square patterns in one batch (vmo_batch_order).
+
+    mats: list of (rowptr, colidx, m) with int32 tensors on the GPU (or objects
+    with .rowptr/.colidx/.m numpy arrays, copied to the GPU).  Returns the
+    concatenated permutation tensor and the list of offsets (len(mats) + 1).
+    coords: optional float32 [sum m, 4] coordinates (ordering only)."""
+    arr, offs, keep = _csr_array(mats)
+    perm = torch.empty(max(offs[-1], 1), dtype=torch.int32, device="cuda")
+    p = (params or Params())._c()
+    _check(load().vmo_batch_order(arr, len(mats), _ptr(coords), C.byref(p), int(sbd), _ptr(perm), _stream()))
+    return perm[:offs[-1]], offs

@@ -192,6 +192,24 @@ vmo_status vmo_bisect(vmo_hg hg, int32_t d, const float* coords, const int32_t* 
                       uint64_t seed, uint64_t key, int32_t km_iters, uint8_t* labels, float* z, int32_t* split,
                       void* stream);
 
+/* vmo_bisect for callers that must not allocate device memory (for example
+ * when another allocator or a fixed budget owns all device memory, or inside a
+ * latency-critical loop where an allocation could block).  The paper has no
+ * counterpart: this is a deployment variant of vmo_bisect, without the handle.
+ * Same arguments, results and rules as vmo_bisect (verts must be valid rows of
+ * coords), but every intermediate lives in one fixed device array that the
+ * library reserves on each GPU that loads it (about 5.3 MB, kept until the
+ * process exits) instead of in freshly allocated memory; no cudaMalloc or
+ * other allocation is made.  Limit: nverts <= 131072, larger inputs return
+ * VMO_ERR_INVALID.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * calls that overlap on the GPU (other streams or threads) race and must be
+ * serialised by the caller. */
+vmo_status vmo_bisect_noalloc(int32_t d, const float* coords, const int32_t* verts, int32_t nverts, uint64_t seed,
+                              uint64_t key, int32_t km_iters, uint8_t* labels, float* z, int32_t* split,
+                              void* stream);
+
 /* Recursive BBD ordering (Sec. 4.2): layout (when coords == NULL) and then
  * recursive bisection with vertex separators placed last.  Symmetric model:
  * row_perm and col_perm (device int32[m]) receive the same permutation.

@@ -516,6 +516,39 @@ vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s,
   return stt;
 }
 
+vmo_status two_means_into(OrderState& st, int N, int d, int km_iters, unsigned long long* dval,
+                          unsigned long long* dpre, int* cnt, uint64_t* partial, cudaStream_t s) {
+  const int64_t n = st.n;
+  vmo_status stt = VMO_OK;
+  dispatch_d(d, [&](auto DC) {
+    constexpr int D = decltype(DC)::value;
+    launch(k_node_reset, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N);
+    launch(k_maxabs<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, st.nodes);
+    launch(k_seed1, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, st.xo, st.seeds);
+    launch(k_dsq<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, st.nodes, dval);
+    stt = scan_inclusive_u64_into((const uint64_t*)dval, (uint64_t*)dpre, n, partial, s);
+    if (stt != VMO_OK) return;
+    launch(k_seed2<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, dval, dpre, st.nodes, st.seeds);
+    for (int it = 0; it < km_iters; ++it) {
+      launch(k_assign<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, it, st.nodes, st.lab, 0);
+      launch(k_update<D>, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, it);
+      if (it % 4 == 3 && it + 1 < km_iters) {  // stop early once every node has converged
+        int h = 0;
+        cudaMemsetAsync(cnt, 0, 4, s);
+        launch(k_count_active, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, cnt);
+        cudaMemcpyAsync(&h, cnt, 4, cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        if (h == 0) break;
+      }
+    }
+    launch(k_clear_counts, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N);
+    launch(k_assign<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, 0, st.nodes, st.lab, 1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) stt = cuda_fail(e, "two_means", __FILE__, __LINE__);
+  });
+  return stt;
+}
+
 vmo_status order_levels(OrderState& st, const OrderParams& op, cudaStream_t s, Scratch& sc) {
   const int64_t n = st.n;
   int N = st.nroots;

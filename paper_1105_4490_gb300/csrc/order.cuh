@@ -70,6 +70,10 @@ vmo_status order_setup(OrderState& st, const float4* x, const std::vector<int64_
                        const std::vector<uint64_t>& seeds, const OrderParams& op, const uint32_t* init_ord,
                        cudaStream_t s, Scratch& sc);
 vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s, Scratch& sc);
+// two_means with every buffer supplied by the caller (allocates nothing):
+// dval, dpre hold st.n values, partial scan_partials_needed(st.n), cnt one int.
+vmo_status two_means_into(OrderState& st, int N, int d, int km_iters, unsigned long long* dval,
+                          unsigned long long* dpre, int* cnt, uint64_t* partial, cudaStream_t s);
 vmo_status order_levels(OrderState& st, const OrderParams& op, cudaStream_t s, Scratch& sc);
 // Indices of the tree records sorted by heap number (and by problem first when
 // by_prob); *count_out receives the number of records (host).

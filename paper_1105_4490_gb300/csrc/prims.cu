@@ -289,6 +289,18 @@ template vmo_status scan_inclusive<uint64_t>(const uint64_t*, uint64_t*, int64_t
 template vmo_status scan_inclusive<int32_t>(const int32_t*, int32_t*, int64_t, cudaStream_t, Scratch&);
 template vmo_status scan_inclusive<int64_t>(const int64_t*, int64_t*, int64_t, cudaStream_t, Scratch&);
 
+vmo_status scan_inclusive_u64_into(const uint64_t* in, uint64_t* out, int64_t n, uint64_t* partial, cudaStream_t s) {
+  if (n <= 0) return VMO_OK;
+  int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+  launch(scan_reduce_kernel<uint64_t>, (unsigned)ntiles, kScanThreads, 0, s, in, n, partial);
+  launch(scan_partials_kernel<uint64_t>, 1, 1024, 0, s, partial, ntiles, (uint64_t*)nullptr);
+  launch(scan_tile_kernel<uint64_t, true>, (unsigned)ntiles, kScanThreads, 0, s, in, out, n, partial);
+  VMO_LAUNCHED("scan");
+  return VMO_OK;
+}
+
+int64_t scan_partials_needed(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
 vmo_status radix_sort_u32(uint32_t* keys_in, uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out, int64_t n,
                           int bits, const SortSegments* segs, cudaStream_t s, Scratch& sc) {
   return radix_sort_impl<uint32_t>(keys_in, vals_in, keys_out, vals_out, n, bits, segs, s, sc);

@@ -151,6 +151,11 @@ vmo_status scan_exclusive(const T* in, T* out, int64_t n, T* total, cudaStream_t
 template <class T>
 vmo_status scan_inclusive(const T* in, T* out, int64_t n, cudaStream_t s, Scratch& sc);
 
+// Inclusive scan that allocates nothing: `partial` must hold
+// scan_partials_needed(n) values.
+vmo_status scan_inclusive_u64_into(const uint64_t* in, uint64_t* out, int64_t n, uint64_t* partial, cudaStream_t s);
+int64_t scan_partials_needed(int64_t n);
+
 // Segment map for the radix sort: tiles never straddle segments.
 struct SortSegments {
   int32_t nseg = 1;               // number of segments

@@ -79,7 +79,7 @@ SYMBOLS = ["vmo_default_params", "vmo_build_hypergraph", "vmo_hg_vertices", "vmo
            "vmo_components", "vmo_init_coords", "vmo_layout", "vmo_layout_step", "vmo_coarsen", "vmo_bisect",
            "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_cut_size", "vmo_destroy",
            "vmo_status_string", "vmo_last_error", "vmo_stats_reset", "vmo_stats_get", "vmo_batch_order",
-           "vmo_batch_layout"]
+           "vmo_batch_layout", "vmo_bisect_noalloc"]
 
 
 def load(path: str | None = None):
@@ -108,6 +108,7 @@ def load(path: str | None = None):
     lib.vmo_layout_step.argtypes = [V, C.POINTER(_Params), V, C.c_float, V, V, P32, V]
     lib.vmo_coarsen.argtypes = [V, C.POINTER(_Params), V, V, P32, P32, P32, V]
     lib.vmo_bisect.argtypes = [V, I32, V, V, I32, U64, U64, I32, V, V, P32, V]
+    lib.vmo_bisect_noalloc.argtypes = [I32, V, V, I32, U64, U64, I32, V, V, P32, V]
     for nm in ("vmo_order_bbd", "vmo_order_sbd"):
         getattr(lib, nm).argtypes = [V, V, C.POINTER(_Params), V, V, C.POINTER(_Tree), V]
     lib.vmo_order_vertices.argtypes = [V, V, C.POINTER(_Params), I32, V, C.POINTER(_Tree), V]
@@ -352,3 +353,18 @@ def batch_order(mats, params: Params | None = None, sbd: bool = False, coords: t
     p = (params or Params())._c()
     _check(load().vmo_batch_order(arr, len(mats), _ptr(coords), C.byref(p), int(sbd), _ptr(perm), _stream()))
     return perm[:offs[-1]], offs
+
+
+def bisect_noalloc(coords: torch.Tensor, verts: torch.Tensor, seed: int, key: int = 1, km_iters: int = 20,
+                   d: int = 3):
+    """vmo_bisect_noalloc: 2-means of coords[verts] without any device
+    allocation inside the library (fixed scratch, at most 131072 points).
+    Returns (split, labels, z1, z2); the output tensors are allocated here,
+    by the caller side."""
+    verts = verts.to(device="cuda", dtype=torch.int32).contiguous()
+    labels = torch.zeros(max(verts.numel(), 1), dtype=torch.uint8, device="cuda")
+    z = torch.zeros(8, dtype=torch.float32, device="cuda")
+    split = C.c_int32()
+    _check(load().vmo_bisect_noalloc(d, _ptr(coords), _ptr(verts), verts.numel(), seed & (2 ** 64 - 1), key,
+                                     km_iters, _ptr(labels), _ptr(z), C.byref(split), _stream()))
+    return bool(split.value), labels[:verts.numel()], z[:4], z[4:]

@@ -260,9 +260,12 @@ def main():
             dist.barrier()
 
     if args.profile:
+        V.stats_reset(time_step_kernel=True, count_interactions=False)  # events only, no extra kernels
         gpu_step(V, torch, mats, dev_csr, params)
         torch.cuda.synchronize()
-        print(f"profile step done: {name}", file=sys.stderr)
+        st = V.stats()
+        print(f"profile step done: {name} launches={st['launches']} step_launches={st['step_launches']}",
+              file=sys.stderr)
         return
 
     for _ in range(max(args.warmup, 3)):

@@ -3,10 +3,10 @@
 //
 // One step of a level, for every problem of a batch at once:
 //   keys      cell of every point on a uniform grid over the bounding cube
-//             (fp32, no FMA), Morton key of the finest cell
+//             (fp32, no FMA), row-major key of the finest cell
 //   sort      stable segmented radix sort of (key, vertex)
-//   gather    points copied in key order; first/last point of every finest
-//             cell recorded in a dense table
+//   gather    points copied in key order; first point of every finest cell
+//             recorded in a dense table
 //   aggregate per cell weight and weighted mean: finest cells from their
 //             points, coarser cells from their 2^d children (fixed order)
 //   attract   y_n = sum_j c_j (x_n - z_j) (2-pin nets: c/2 (x_n - x_u))
@@ -37,6 +37,29 @@ __device__ inline int find_problem(const int64_t* __restrict__ base, int P, int6
     if (base[mid] <= i) lo = mid; else hi = mid;
   }
   return lo;
+}
+
+// Paired source tables.  The far field and the near field read their sources
+// two at a time: sources 2j and 2j+1 share a pair of float4 (three for d = 4)
+// holding each coordinate of both side by side, then both weights:
+//   d <= 3: (x0, x1, y0, y1), (z0, z1, w0, w1)     (d = 2: z unused)
+//   d = 4:  (x0, x1, y0, y1), (z0, z1, u0, u1), (w0, w1, -, -)
+// so that one packed fp32x2 instruction (Blackwell f32x2 add / mul / fma)
+// computes the same step for both sources.
+template <int D>
+struct Pair {
+  static constexpr int N = D == 4 ? 3 : 2;  // float4 per pair
+  static constexpr int WQ = D == 4 ? 2 : 1; // float4 holding the weights
+  static constexpr int WO = D == 4 ? 0 : 2; // float offset of the weights in it
+};
+
+template <int D>
+__device__ __forceinline__ void pair_store(float4* __restrict__ tab, int64_t i, const float* c, float w) {
+  float* f = reinterpret_cast<float*>(tab + (i >> 1) * Pair<D>::N);
+  const int h = (int)(i & 1);
+#pragma unroll
+  for (int m = 0; m < D; ++m) f[4 * (m >> 1) + 2 * (m & 1) + h] = c[m];
+  f[4 * Pair<D>::WQ + Pair<D>::WO + h] = w;
 }
 
 template <int D>
@@ -169,12 +192,22 @@ __global__ void __launch_bounds__(kBlock) k_keys(const float4* __restrict__ x, i
   vals[v] = (uint32_t)v;
 }
 
+// Sorted positions: coordinates and weights in sorted order (plain and in
+// the paired table XP), the packed cell of every point, and the cell start
+// table.  cst[fbase + pb + c] is the first
+// sorted position of problem pb whose key is >= c (so empty cells get the
+// start of the next occupied one and a row of cells is one contiguous range),
+// with one extra entry per problem holding its end.  Every position writes the
+// entries of the cells between its predecessor's key and its own; the last
+// position of a problem also writes the cells after its key and the end entry.
 template <int D>
-__global__ void __launch_bounds__(kBlock) k_gather(const uint32_t* __restrict__ svals, int64_t K,
+__global__ void __launch_bounds__(kBlock) k_gather(const uint32_t* __restrict__ svals,
+                                                   const uint32_t* __restrict__ skeys, int64_t K,
                                                    const float4* __restrict__ x, const float* __restrict__ w,
                                                    const int32_t* __restrict__ vprob, const ProbDev* __restrict__ prob,
                                                    const uint32_t* __restrict__ bb, float4* __restrict__ xs,
-                                                   float* __restrict__ ws, uint32_t* __restrict__ scell) {
+                                                   float* __restrict__ ws, uint32_t* __restrict__ scell,
+                                                   int32_t* __restrict__ cst, float4* __restrict__ XP) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= K) return;
   uint32_t v = svals[p];
@@ -182,7 +215,17 @@ __global__ void __launch_bounds__(kBlock) k_gather(const uint32_t* __restrict__ 
   ProbDev pr = prob[pb];
   float4 xv = x[v];
   xs[p] = xv;
-  if (ws) ws[p] = w ? w[v] : 1.0f;
+  const float wv = w ? w[v] : 1.0f;
+  if (ws) ws[p] = wv;
+  // paired table: the problem's points start at an even slot, so the pairing
+  // of its points does not depend on where the problem sits in the batch
+  const int64_t e = (pr.vbase + pb + 1) & ~int64_t(1);
+  const float xc[4] = {xv.x, xv.y, xv.z, xv.w};
+  pair_store<D>(XP, e + (p - pr.vbase), xc, wv);
+  if (p == pr.vbase + pr.k - 1 && (pr.k & 1)) {  // unused half of the last pair: finite, weight 0
+    const float zero[4] = {0.f, 0.f, 0.f, 0.f};
+    pair_store<D>(XP, e + pr.k, zero, 0.0f);
+  }
   float lo[D], s;
   grid_frame<D>(bb, pb, pr.L, lo, &s);
   int32_t c[D];
@@ -191,53 +234,57 @@ __global__ void __launch_bounds__(kBlock) k_gather(const uint32_t* __restrict__ 
 #pragma unroll
   for (int m = 0; m < D; ++m) packed |= (uint32_t)c[m] << (m * field_bits(D));
   scell[p] = packed;
-}
-
-// First sorted position with key >= c in [a, b).
-__device__ inline int64_t lower_key(const uint32_t* __restrict__ skeys, int64_t a, int64_t b, uint32_t c) {
-  while (a < b) {
-    int64_t mid = (a + b) >> 1;
-    if (skeys[mid] < c) a = mid + 1; else b = mid;
+  int32_t* cs = cst + pr.fbase + pb;
+  const int64_t key = skeys[p];
+  const int64_t prev = p == pr.vbase ? -1 : (int64_t)skeys[p - 1];
+  for (int64_t cc = prev + 1; cc <= key; ++cc) cs[cc] = (int32_t)p;
+  if (p == pr.vbase + pr.k - 1) {
+    const int64_t ncell = int64_t(1) << (D * pr.L);
+    const int32_t end = (int32_t)(pr.vbase + pr.k);
+    for (int64_t cc = key + 1; cc <= ncell; ++cc) cs[cc] = end;
   }
-  return a;
 }
 
+// Cell sums (St, Wt) at cell index idx, and the cell's charge (weighted mean
+// and weight) at index pidx of the paired cell table.
 template <int D>
-__device__ inline void store_cell(int64_t idx, const float* S, float W, float4* __restrict__ St,
-                                  float* __restrict__ Wt, float4* __restrict__ CW) {
+__device__ inline void store_cell(int64_t idx, int64_t pidx, const float* S, float W, float4* __restrict__ St,
+                                  float* __restrict__ Wt, float4* __restrict__ CP) {
   St[idx] = make_float4(S[0], D > 1 ? S[1] : 0.f, D > 2 ? S[2] : 0.f, D > 3 ? S[3] : 0.f);
   Wt[idx] = W;
+  float c[4] = {0.f, 0.f, 0.f, 0.f};
   if (W > 0.0f) {
     float iw = 1.0f / W;
-    float c0 = S[0] * iw, c1 = D > 1 ? S[1] * iw : 0.f, c2 = D > 2 ? S[2] * iw : 0.f;
-    float c3 = D > 3 ? S[3] * iw : W;
-    CW[idx] = make_float4(c0, c1, c2, c3);
-  } else {
-    CW[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < D; ++m) c[m] = S[m] * iw;
   }
+  pair_store<D>(CP, pidx, c, W);
 }
 
-// Finest cells: the first sorted position of every cell (a binary search in
-// the problem's sorted keys, so empty cells get the start of the next one and
-// a row of cells is one contiguous range), and the cell's charge from its
-// points.  cst has one extra entry per problem (its end).
+// Finest cells: the charge of every cell from its points (the range comes
+// from the cell start table written by k_gather; a problem without points
+// writes its table here).
 template <int D>
-__global__ void __launch_bounds__(kBlock) k_agg_finest(const uint32_t* __restrict__ skeys, int64_t ncells,
-                                                       const int64_t* __restrict__ fbase, int P,
+__global__ void __launch_bounds__(kBlock) k_agg_finest(int64_t ncells, const int64_t* __restrict__ fbase, int P,
                                                        const ProbDev* __restrict__ prob, const float4* __restrict__ xs,
                                                        const float* __restrict__ ws, int32_t* __restrict__ cst,
                                                        float4* __restrict__ St, float* __restrict__ Wt,
-                                                       float4* __restrict__ CW) {
+                                                       float4* __restrict__ CP) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ncells) return;
   int pb = find_problem(fbase, P, i);
   ProbDev pr = prob[pb];
   int64_t c = i - pr.fbase;
-  const int64_t a = pr.vbase, b = pr.vbase + pr.k;
-  int64_t q0 = lower_key(skeys, a, b, (uint32_t)c);
-  int64_t q1 = lower_key(skeys, q0, b, (uint32_t)(c + 1));
-  cst[pr.fbase + pb + c] = (int32_t)q0;
-  if (c == (int64_t(1) << (D * pr.L)) - 1) cst[pr.fbase + pb + c + 1] = (int32_t)b;
+  int32_t* cs = cst + pr.fbase + pb;
+  int64_t q0, q1;
+  if (pr.k == 0) {
+    cs[c] = (int32_t)pr.vbase;
+    if (c == (int64_t(1) << (D * pr.L)) - 1) cs[c + 1] = (int32_t)pr.vbase;
+    q0 = q1 = 0;
+  } else {
+    q0 = cs[c];
+    q1 = cs[c + 1];
+  }
   float S[4] = {0.f, 0.f, 0.f, 0.f};
   float W = 0.f;
   for (int64_t q = q0; q < q1; ++q) {
@@ -249,13 +296,14 @@ __global__ void __launch_bounds__(kBlock) k_agg_finest(const uint32_t* __restric
     if (D > 3) S[3] += wq * p.w;
     W += wq;
   }
-  store_cell<D>(pr.cbase + lvl_off(D, pr.L) + c, S, W, St, Wt, CW);
+  const int64_t idx = pr.cbase + lvl_off(D, pr.L) + c;
+  store_cell<D>(idx, idx + pb + 1, S, W, St, Wt, CP);
 }
 
 template <int D>
 __global__ void __launch_bounds__(kBlock) k_agg_level(int step, const int64_t* __restrict__ off, int P, int64_t ncells,
                                                       const ProbDev* __restrict__ prob, float4* __restrict__ St,
-                                                      float* __restrict__ Wt, float4* __restrict__ CW) {
+                                                      float* __restrict__ Wt, float4* __restrict__ CP) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ncells) return;
   int pb = find_problem(off, P, i);
@@ -286,7 +334,8 @@ __global__ void __launch_bounds__(kBlock) k_agg_level(int step, const int64_t* _
     if (D > 3) S[3] += s4.w;
     W += Wt[idx];
   }
-  store_cell<D>(pr.cbase + lvl_off(D, l) + c, S, W, St, Wt, CW);
+  const int64_t idx = pr.cbase + lvl_off(D, l) + c;
+  store_cell<D>(idx, idx + pb + 1, S, W, St, Wt, CP);
 }
 
 // Rubber bands of 2-pin nets: y_v = sum_u c_vu (x_v - x_u) / 2.  Rows are
@@ -420,96 +469,84 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   return r;
 }
 
-// Smallest squared distance fed to the kernels: only masked terms (weight 0)
-// can be closer, and their contribution stays exactly 0.
+// Smallest squared distance fed to the kernels.  A source at the target's
+// own position (the target itself, a coincident point) has dx = 0 and so
+// contributes exactly 0 * g = 0; the floor keeps g finite for it.  Masked
+// sources (weight 0) contribute 0 the same way.
 constexpr float kR2Floor = 1e-15f;
 
-// F += w r^-d (src - xn) with the weight already masked (0 = no term).
+// F += w r^-d (src - xn) for the two sources of a pair; nx holds -xn twice
+// per coordinate, w the (masked) weights.
 template <int D>
-__device__ __forceinline__ void add_charge(float* F, const float4& src, const float4& xn, float w) {
-  float dx0 = src.x - xn.x;
-  float dx1 = D > 1 ? src.y - xn.y : 0.f;
-  float dx2 = D > 2 ? src.z - xn.z : 0.f;
-  float dx3 = D > 3 ? src.w - xn.w : 0.f;
-  float r2 = fmaxf(dx0 * dx0 + dx1 * dx1 + dx2 * dx2 + dx3 * dx3, kR2Floor);
-  float g;
+__device__ __forceinline__ void pair_charge(float2* F, const float4* P, const float2* nx, float2 w) {
+  float2 dx[D];
+  dx[0] = __fadd2_rn(make_float2(P[0].x, P[0].y), nx[0]);
+  if (D > 1) dx[1] = __fadd2_rn(make_float2(P[0].z, P[0].w), nx[1]);
+  if (D > 2) dx[2] = __fadd2_rn(make_float2(P[1].x, P[1].y), nx[2]);
+  if (D > 3) dx[3] = __fadd2_rn(make_float2(P[1].z, P[1].w), nx[3]);
+  float2 r2 = __fmul2_rn(dx[0], dx[0]);
+#pragma unroll
+  for (int m = 1; m < D; ++m) r2 = __ffma2_rn(dx[m], dx[m], r2);
+  r2.x = fmaxf(r2.x, kR2Floor);
+  r2.y = fmaxf(r2.y, kR2Floor);
+  float2 g;
   if (D == 2) {
-    g = w * rcp_approx(r2);
+    g = __fmul2_rn(w, make_float2(rcp_approx(r2.x), rcp_approx(r2.y)));
   } else if (D == 3) {
-    float ir = rsqrt_approx(r2);
-    g = w * ir * ir * ir;
+    const float2 ir = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+    g = __fmul2_rn(__fmul2_rn(w, ir), __fmul2_rn(ir, ir));
   } else {
-    float i2 = rcp_approx(r2);
-    g = w * i2 * i2;
+    const float2 i2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    g = __fmul2_rn(__fmul2_rn(w, i2), i2);
   }
-  F[0] += g * dx0;
-  if (D > 1) F[1] += g * dx1;
-  if (D > 2) F[2] += g * dx2;
-  if (D > 3) F[3] += g * dx3;
+#pragma unroll
+  for (int m = 0; m < D; ++m) F[m] = __ffma2_rn(g, dx[m], F[m]);
 }
 
 template <int D>
-__device__ inline void accumulate(float* F, const float4& src, const float4& xn, float wsrc) {
-  float dx0 = src.x - xn.x;
-  float dx1 = D > 1 ? src.y - xn.y : 0.f;
-  float dx2 = D > 2 ? src.z - xn.z : 0.f;
-  float dx3 = D > 3 ? src.w - xn.w : 0.f;
-  float r2 = dx0 * dx0 + dx1 * dx1 + dx2 * dx2 + dx3 * dx3;
-  if (r2 > 0.0f) {
-    float g;
-    if (D == 2) {
-      g = __fdividef(wsrc, r2);
-    } else if (D == 3) {
-      float ir = rsqrtf(r2);
-      g = wsrc * ir * ir * ir;
-    } else {
-      float i2 = __fdividef(1.0f, r2);
-      g = wsrc * i2 * i2;
-    }
-    F[0] += g * dx0;
-    if (D > 1) F[1] += g * dx1;
-    if (D > 2) F[2] += g * dx2;
-    if (D > 3) F[3] += g * dx3;
-  }
+__device__ __forceinline__ float2 pair_weight(const float4* P) {
+  const float4& q = P[Pair<D>::WQ];
+  return Pair<D>::WO == 0 ? make_float2(q.x, q.y) : make_float2(q.z, q.w);
 }
 
 // Far-field charges of one level for a target in cell `me` (level l): the
 // cells of the 6^d box spanned by the children of the cells around the
 // target's parent cell, minus the 3^d cells adjacent to the target's cell.
-// One row (up to 6 consecutive cells along coordinate 0) of the box:
-// all loads are issued first, then the charges are accumulated without
-// branches into two alternating partial sums (more independent work per
-// lane).  A cell counts if it holds weight and is not adjacent to the
+// One row of the box along coordinate 0 starts at an even cell and holds 4 or
+// 6 cells, i.e. 2 or 3 pairs: all loads are issued first, then the pairs are
+// accumulated without branches (a pair beyond the row is loaded as zeros and
+// weighs 0).  A cell counts if it holds weight and is not adjacent to the
 // target's cell.
 template <int D, bool COUNT>
-__device__ inline void far_row(const float4* __restrict__ CW, const float* __restrict__ Wt, int64_t row, int lo0,
-                               int hi0, bool incore, int me0, const float4& xn, float* Fa, float* Fb,
-                               unsigned long long& nint) {
-  float4 cw[6];
-  float W[6];
+__device__ inline void far_row(const float4* __restrict__ CP, int64_t cell0, int lo0, int hi0, bool incore, int me0,
+                               const float2* nx, float2* F, unsigned long long& nint) {
+  constexpr int N = Pair<D>::N;
+  float4 P[3][N];
+  const int npairs = (hi0 - lo0 + 1) >> 1;
+  const float4* row = CP + (cell0 >> 1) * N;
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const bool in = lo0 + i <= hi0;
-    cw[i] = in ? CW[row + lo0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    W[i] = (D == 4) ? (in ? Wt[row + lo0 + i] : 0.f) : cw[i].w;
-  }
+  for (int i = 0; i < 3; ++i)
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const int x = lo0 + i;
-    const bool core = incore && x >= me0 - 1 && x <= me0 + 1;
-    const float wt = core ? 0.0f : W[i];  // empty and out-of-box cells have weight 0
-    if (i & 1) add_charge<D>(Fb, cw[i], xn, wt);
-    else add_charge<D>(Fa, cw[i], xn, wt);
-    if (COUNT && wt > 0.0f) ++nint;
+    for (int j = 0; j < N; ++j) P[i][j] = i < npairs ? row[i * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float2 w = pair_weight<D>(P[i]);
+    if (incore) {
+      const int xa = lo0 + 2 * i;
+      w.x = (xa >= me0 - 1 && xa <= me0 + 1) ? 0.0f : w.x;
+      w.y = (xa + 1 >= me0 - 1 && xa + 1 <= me0 + 1) ? 0.0f : w.y;
+    }
+    pair_charge<D>(F, P[i], nx, w);
+    if (COUNT) nint += (w.x > 0.0f) + (w.y > 0.0f);
   }
 }
 
-// Far field of one level for one lane per target: the lane's own box, row by
-// row (row-major order of the box).
+// Far field of one level for one lane of the target's group: the rows of the
+// box (row-major order) go round-robin to the G lanes of the group.  `cell`
+// is the paired-table index of the level's cell 0 (even).
 template <int D, bool COUNT>
-__device__ inline void far_level_lane(const float4* __restrict__ CW, const float* __restrict__ Wt, int64_t base,
-                                      const int32_t* me, int l, const float4& xn, float* F, int G, int lane_g,
-                                      unsigned long long& nint) {
+__device__ inline void far_level_lane(const float4* __restrict__ CP, int64_t cell, const int32_t* me, int l,
+                                      const float2* nx, float2* F, int G, int lane_g, unsigned long long& nint) {
   const int sl = 1 << l;
   int lo[D], hi[D];
 #pragma unroll
@@ -518,15 +555,12 @@ __device__ inline void far_level_lane(const float4* __restrict__ CW, const float
     lo[m] = max(2 * par - 2, 0);
     hi[m] = min(2 * par + 3, sl - 1);
   }
-  // rows of the box (coordinate 0 varies along a row) go round-robin to the
-  // G lanes of the target's group
-  float Fb[4] = {0.f, 0.f, 0.f, 0.f};
   int row = 0;
   if (D == 2) {
     for (int y = lo[1]; y <= hi[1]; ++y, ++row) {
       if ((row & (G - 1)) != lane_g) continue;
       const bool iny = y >= me[1] - 1 && y <= me[1] + 1;
-      far_row<D, COUNT>(CW, Wt, base + (int64_t)y * sl, lo[0], hi[0], iny, me[0], xn, F, Fb, nint);
+      far_row<D, COUNT>(CP, cell + (int64_t)y * sl + lo[0], lo[0], hi[0], iny, me[0], nx, F, nint);
     }
   } else if (D == 3) {
     for (int z = lo[2]; z <= hi[2]; ++z) {
@@ -534,7 +568,7 @@ __device__ inline void far_level_lane(const float4* __restrict__ CW, const float
       for (int y = lo[1]; y <= hi[1]; ++y, ++row) {
         if ((row & (G - 1)) != lane_g) continue;
         const bool iny = inz && y >= me[1] - 1 && y <= me[1] + 1;
-        far_row<D, COUNT>(CW, Wt, base + ((int64_t)z * sl + y) * sl, lo[0], hi[0], iny, me[0], xn, F, Fb, nint);
+        far_row<D, COUNT>(CP, cell + ((int64_t)z * sl + y) * sl + lo[0], lo[0], hi[0], iny, me[0], nx, F, nint);
       }
     }
   } else {
@@ -545,14 +579,12 @@ __device__ inline void far_level_lane(const float4* __restrict__ CW, const float
         for (int y = lo[1]; y <= hi[1]; ++y, ++row) {
           if ((row & (G - 1)) != lane_g) continue;
           const bool iny = inz && y >= me[1] - 1 && y <= me[1] + 1;
-          far_row<D, COUNT>(CW, Wt, base + (((int64_t)w * sl + z) * sl + y) * sl, lo[0], hi[0], iny, me[0], xn, F,
-                            Fb, nint);
+          far_row<D, COUNT>(CP, cell + (((int64_t)w * sl + z) * sl + y) * sl + lo[0], lo[0], hi[0], iny, me[0], nx,
+                            F, nint);
         }
       }
     }
   }
-#pragma unroll
-  for (int m = 0; m < D; ++m) F[m] += Fb[m];
 }
 
 // Per-warp bounding-box partials of the step kernel, reduced per problem by
@@ -573,37 +605,57 @@ __device__ inline void bbox_warp_partial(const float4& v, bool valid, uint32_t* 
   }
 }
 
-// One warp per problem: reduce its warps' partials into the bounding box.
-__global__ void k_bbox_reduce(const uint32_t* __restrict__ part, const int64_t* __restrict__ tbase, int P,
-                              uint32_t* __restrict__ bb) {
-  int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= P) return;
-  const int lane = lane_id();
-  int64_t a = tbase[w] / 32, b = tbase[w + 1] / 32;
-  uint32_t mn[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, mx[4] = {0u, 0u, 0u, 0u};
-  for (int64_t i = a + lane; i < b; i += 32)
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      mn[m] = min(mn[m], part[i * 8 + m]);
-      mx[m] = max(mx[m], part[i * 8 + 4 + m]);
-    }
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    mn[m] = __reduce_min_sync(0xffffffffu, mn[m]);
-    mx[m] = __reduce_max_sync(0xffffffffu, mx[m]);
+// Bounding boxes from the step kernel's per-warp partials: one thread per
+// partial, lanes of the same problem combine with a warp reduction and one of
+// them folds the result into the problem's box with atomic min / max (the box
+// was reset by k_keys earlier in the same iteration; min and max of the
+// order-preserving integer images are exact, so the order of the atomics does
+// not matter).
+__global__ void __launch_bounds__(kBlock) k_bbox_reduce(const uint32_t* __restrict__ part,
+                                                        const int64_t* __restrict__ tbase, int P, int64_t nwarps,
+                                                        uint32_t* __restrict__ bb) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < nwarps;
+  const int pb = valid ? find_problem(tbase, P, i * 32) : -1;
+  uint4 mn = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu), mx = make_uint4(0u, 0u, 0u, 0u);
+  if (valid) {
+    const uint4* p = reinterpret_cast<const uint4*>(part + i * 8);
+    mn = p[0];
+    mx = p[1];
   }
-  if (lane < 4) bb[w * 8 + lane] = mn[lane];
-  else if (lane < 8) bb[w * 8 + lane] = mx[lane - 4];
+  const unsigned peers = __match_any_sync(0xffffffffu, pb);
+  mn.x = __reduce_min_sync(peers, mn.x);
+  mn.y = __reduce_min_sync(peers, mn.y);
+  mn.z = __reduce_min_sync(peers, mn.z);
+  mn.w = __reduce_min_sync(peers, mn.w);
+  mx.x = __reduce_max_sync(peers, mx.x);
+  mx.y = __reduce_max_sync(peers, mx.y);
+  mx.z = __reduce_max_sync(peers, mx.z);
+  mx.w = __reduce_max_sync(peers, mx.w);
+  if (!valid || lane_id() != __ffs(peers) - 1) return;
+  uint32_t* b = bb + (int64_t)pb * 8;
+  if (mn.x != 0xFFFFFFFFu) atomicMin(b + 0, mn.x);
+  if (mn.y != 0xFFFFFFFFu) atomicMin(b + 1, mn.y);
+  if (mn.z != 0xFFFFFFFFu) atomicMin(b + 2, mn.z);
+  if (mn.w != 0xFFFFFFFFu) atomicMin(b + 3, mn.w);
+  if (mx.x) atomicMax(b + 4, mx.x);
+  if (mx.y) atomicMax(b + 5, mx.y);
+  if (mx.z) atomicMax(b + 6, mx.z);
+  if (mx.w) atomicMax(b + 7, mx.w);
 }
 
 // Gradient (eq. graphenergygradientsimple with the grid pyramid) and step of
 // every target.  Each problem gives its targets G lanes (G from the problem's
 // own size), padded to whole warps; the lanes of a group split the near field
-// (strided points) and the far field (contiguous chunks of every level's box)
-// and combine with a fixed xor tree, so a target's result depends only on its
-// own problem.  Lane 0 of the group applies the step.  Near field: points are
+// (strided source pairs) and the far field (rows of every level's box) and
+// combine with a fixed xor tree, so a target's result depends only on its own
+// problem.  Lane 0 of the group applies the step.  Near field: points are
 // sorted by row-major cell index, so the 3 cells of a row along coordinate 0
-// form one contiguous range of the sorted points.
+// form one contiguous range of the sorted points, read in pairs from the
+// paired point table XP (a problem's points start at the even slot
+// (vbase + pb + 1) & ~1; the halves outside the range weigh 0).  Far field:
+// the paired cell table CP, whose index of (problem pb, level l, cell c) is
+// cbase + pb + lvl_off(l) + 1 + c (even for even c).
 #ifndef VMO_STEP_BLOCK
 #define VMO_STEP_BLOCK 128
 #endif
@@ -614,12 +666,13 @@ constexpr int kStepBlock = VMO_STEP_BLOCK;
 
 template <int D, bool COUNT>
 __global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_update(
-    const float4* __restrict__ xs, const float* __restrict__ ws, const uint32_t* __restrict__ svals,
-    const uint32_t* __restrict__ scell, const int32_t* __restrict__ cst, const float4* __restrict__ CW,
-    const float* __restrict__ Wt, const float4* __restrict__ yatt, const int64_t* __restrict__ tbase, int P,
+    const float4* __restrict__ xs, const float* __restrict__ ws, const float4* __restrict__ XP,
+    const uint32_t* __restrict__ svals, const uint32_t* __restrict__ scell, const int32_t* __restrict__ cst,
+    const float4* __restrict__ CP, const float4* __restrict__ yatt, const int64_t* __restrict__ tbase, int P,
     const ProbDev* __restrict__ prob, int64_t T, float kappa, const float* __restrict__ s0, float scale,
     float step_override, float4* __restrict__ x, float4* __restrict__ y_out, uint32_t* __restrict__ bb_part,
     unsigned long long* __restrict__ icount) {
+  constexpr int N = Pair<D>::N;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int pb = find_problem(tbase, P, t < T ? t : T - 1);
   const ProbDev pr = prob[pb];
@@ -629,18 +682,24 @@ __global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_upda
   const int lane_g = (int)(rel & (G - 1));
   const bool valid = t < T && tgt < pr.k;
   unsigned long long nint = 0;
-  float F[4] = {0.f, 0.f, 0.f, 0.f};
+  float2 F[D];
+#pragma unroll
+  for (int m = 0; m < D; ++m) F[m] = make_float2(0.f, 0.f);
   const int64_t p = pr.vbase + tgt;
   float4 xn = make_float4(0, 0, 0, 0);
   if (valid) {
     const int L = pr.L, side = 1 << L;
     xn = xs[p];
+    float2 nx[D];
+#pragma unroll
+    for (int m = 0; m < D; ++m) nx[m] = make_float2(-comp(xn, m), -comp(xn, m));
     const uint32_t packed = scell[p];
     int32_t c[D];
 #pragma unroll
     for (int m = 0; m < D; ++m) c[m] = (int32_t)((packed >> (m * field_bits(D))) & ((1u << field_bits(D)) - 1));
     // near field: rows of 3 cells along coordinate 0 around the target's cell
     const int32_t* cs = cst + pr.fbase + pb;
+    const float4* xp = XP + ((pr.vbase + pb + 1) >> 1) * N;  // the problem's first pair
     const int xa = max(c[0] - 1, 0), xb = min(c[0] + 1, side - 1);
     constexpr int NR = D == 2 ? 3 : (D == 3 ? 9 : 27);
     for (int o = 0; o < NR; ++o) {
@@ -656,14 +715,16 @@ __global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_upda
       }
       if (!inside) continue;
       const int64_t r0 = rowmajor<D>(cc, side);
-      const int qa = cs[r0], qb = cs[r0 + (xb - xa) + 1];
-      for (int q = qa + lane_g; q < qb; q += G) {
-        float wq = ws ? ws[q] : 1.0f;
-        const float4 src = xs[q];
-        const bool same = q == p || (src.x == xn.x && src.y == xn.y && src.z == xn.z && src.w == xn.w);
-        wq = same ? 0.0f : wq;  // the target itself and coincident points exert no force
-        add_charge<D>(F, src, xn, wq);
-        if (COUNT && q != p) ++nint;
+      const int qa = cs[r0] - (int)pr.vbase, qb = cs[r0 + (xb - xa) + 1] - (int)pr.vbase;  // problem-local
+      for (int j = (qa >> 1) + lane_g; 2 * j < qb; j += G) {
+        float4 Q[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) Q[i] = xp[(int64_t)j * N + i];
+        float2 w = pair_weight<D>(Q);
+        w.x = 2 * j >= qa ? w.x : 0.0f;
+        w.y = 2 * j + 1 < qb ? w.y : 0.0f;
+        pair_charge<D>(F, Q, nx, w);
+        if (COUNT) nint += (2 * j >= qa && 2 * j != tgt) + (2 * j + 1 < qb && 2 * j + 1 != tgt);
       }
     }
     // far field, levels 2..L
@@ -671,23 +732,26 @@ __global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_upda
       int32_t me[D];
 #pragma unroll
       for (int m = 0; m < D; ++m) me[m] = c[m] >> (L - l);
-      far_level_lane<D, COUNT>(CW, Wt, pr.cbase + lvl_off(D, l), me, l, xn, F, G, lane_g, nint);
+      far_level_lane<D, COUNT>(CP, pr.cbase + pb + lvl_off(D, l) + 1, me, l, nx, F, G, lane_g, nint);
     }
   }
+  float Fs[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int m = 0; m < D; ++m) Fs[m] = F[m].x + F[m].y;
   // combine the lanes of the group (groups never straddle a warp)
   for (int o = G >> 1; o > 0; o >>= 1)
 #pragma unroll
-    for (int m = 0; m < D; ++m) F[m] += __shfl_xor_sync(0xffffffffu, F[m], o);
+    for (int m = 0; m < D; ++m) Fs[m] += __shfl_xor_sync(0xffffffffu, Fs[m], o);
   const bool leader = valid && lane_g == 0;
   float4 xnew = make_float4(0, 0, 0, 0);
   if (leader) {
     const float wn = ws ? ws[p] : 1.0f;
     const uint32_t v = svals[p];
     float4 ya = yatt[v];
-    float y0 = kappa * wn * F[0] + ya.x;
-    float y1 = D > 1 ? kappa * wn * F[1] + ya.y : 0.f;
-    float y2 = D > 2 ? kappa * wn * F[2] + ya.z : 0.f;
-    float y3 = D > 3 ? kappa * wn * F[3] + ya.w : 0.f;
+    float y0 = kappa * wn * Fs[0] + ya.x;
+    float y1 = D > 1 ? kappa * wn * Fs[1] + ya.y : 0.f;
+    float y2 = D > 2 ? kappa * wn * Fs[2] + ya.z : 0.f;
+    float y3 = D > 3 ? kappa * wn * Fs[3] + ya.w : 0.f;
     if (y_out) y_out[v] = make_float4(y0, y1, y2, y3);
     float ny = sqrtf(y0 * y0 + y1 * y1 + y2 * y2 + y3 * y3);
     float step = step_override > 0.0f ? step_override : s0[pb] * scale;
@@ -1082,7 +1146,7 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
   if (K == 0 || iters <= 0) return VMO_OK;
   ScratchFrame frame(sc);
   uint32_t *keys, *vals, *skeys, *svals, *scell, *bb;
-  float4 *xs, *yatt, *St, *CW, *z = nullptr;
+  float4 *xs, *XP, *yatt, *St, *CP, *z = nullptr;
   float *ws = nullptr, *Wt, *s0;
   int32_t* cst;
   int64_t *fb;
@@ -1096,12 +1160,15 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
   VMO_TRY(sc.alloc(&yatt, K));
   if (lb.w) VMO_TRY(sc.alloc(&ws, K));
   VMO_TRY(sc.alloc(&St, ncell));
-  VMO_TRY(sc.alloc(&CW, ncell));
+  VMO_TRY(sc.alloc(&CP, (size_t)((ncell + P) / 2 + 1) * (d == 4 ? 3 : 2)));
+  VMO_TRY(sc.alloc(&XP, (size_t)((K + P + 1) / 2 + 1) * (d == 4 ? 3 : 2)));
   VMO_TRY(sc.alloc(&Wt, ncell));
   VMO_TRY(sc.alloc(&cst, nfine + P));
   VMO_TRY(sc.alloc(&bb, (size_t)2 * 8 * P));
   uint32_t* bpart;
-  VMO_TRY(sc.alloc(&bpart, (size_t)std::max<int64_t>(lb.threads / 32, 1) * 8));
+  // one partial per warp of the step kernel's grid (whole blocks)
+  const int64_t nwarps = (lb.threads + kStepBlock - 1) / kStepBlock * (kStepBlock / 32);
+  VMO_TRY(sc.alloc(&bpart, (size_t)std::max<int64_t>(nwarps, 1) * 8));
   VMO_TRY(sc.alloc(&s0, P));
   VMO_TRY(sc.alloc(&fb, P + 1));
   if (lb.net_ptr) VMO_TRY(sc.alloc(&z, std::max<int64_t>(lb.nnets, 1)));
@@ -1128,10 +1195,10 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
       if (keys_out && t == 0) cudaMemcpyAsync(keys_out, keys, K * 4, cudaMemcpyDeviceToDevice, s);
       st = radix_sort_u32(keys, vals, skeys, svals, K, D * lb.maxL, segmented ? &segs : nullptr, s, sc);
       if (st != VMO_OK) break;
-      launch(k_gather<D>, grid_for(K, kBlock), kBlock, 0, s, svals, K, x, lb.w, lb.vprob.ptr, lb.prob.ptr, cur, xs,
-             ws, scell);
-      launch(k_agg_finest<D>, grid_for(nfine, kBlock), kBlock, 0, s, skeys, nfine, fb, P, lb.prob.ptr, xs, ws, cst,
-             St, Wt, CW);
+      launch(k_gather<D>, grid_for(K, kBlock), kBlock, 0, s, svals, skeys, K, x, lb.w, lb.vprob.ptr, lb.prob.ptr, cur,
+             xs, ws, scell, cst, XP);
+      launch(k_agg_finest<D>, grid_for(nfine, kBlock), kBlock, 0, s, nfine, fb, P, lb.prob.ptr, xs, ws, cst, St, Wt,
+             CP);
       for (int stp = 1; stp <= lb.maxL - 2; ++stp) {
         const int64_t* off = lb.aggoff.ptr + (size_t)stp * (P + 1);
         int64_t n = 0;
@@ -1140,7 +1207,7 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
           n += l >= 2 ? (int64_t(1) << (D * l)) : 0;
         }
         if (n == 0) continue;
-        launch(k_agg_level<D>, grid_for(n, kBlock), kBlock, 0, s, stp, off, P, n, lb.prob.ptr, St, Wt, CW);
+        launch(k_agg_level<D>, grid_for(n, kBlock), kBlock, 0, s, stp, off, P, n, lb.prob.ptr, St, Wt, CP);
       }
       if (lb.adj_ptr) {
         launch(k_attract, grid_for(K, kBlock), kBlock, 0, s, lb.adj_ptr, lb.adj, lb.acost, x, K, yatt);
@@ -1160,15 +1227,15 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
       if (timed) stats_time_begin(s);
       unsigned long long* icount = stats_interaction_counter();
       if (icount)
-        launch(k_repulse_update<D, true>, grid_for(lb.threads, kStepBlock), kStepBlock, 0, s, xs, ws, svals, scell,
-               cst, CW, Wt, yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, (float)scale, step_override,
+        launch(k_repulse_update<D, true>, grid_for(lb.threads, kStepBlock), kStepBlock, 0, s, xs, ws, XP, svals,
+               scell, cst, CP, yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, (float)scale, step_override,
                x, y_out, bpart, icount);
       else
-        launch(k_repulse_update<D, false>, grid_for(lb.threads, kStepBlock), kStepBlock, 0, s, xs, ws, svals, scell,
-               cst, CW, Wt, yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, (float)scale, step_override,
+        launch(k_repulse_update<D, false>, grid_for(lb.threads, kStepBlock), kStepBlock, 0, s, xs, ws, XP, svals,
+               scell, cst, CP, yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, (float)scale, step_override,
                x, y_out, bpart, icount);
       if (timed) stats_time_end(s, (uint64_t)K);
-      launch(k_bbox_reduce, grid_for((int64_t)P * 32, kBlock), kBlock, 0, s, bpart, lb.tbase.ptr, P, nxt);
+      launch(k_bbox_reduce, grid_for(nwarps, kBlock), kBlock, 0, s, bpart, lb.tbase.ptr, P, nwarps, nxt);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) st = cuda_fail(e, "layout step", __FILE__, __LINE__);
       scale *= o.decay;

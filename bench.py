@@ -189,6 +189,63 @@ def batched_leg(V, torch, count: int, plain_sample: int, warmup: int, steps: int
             "batched_over_plain": batched / plain}
 
 
+def served_leg(V, rate: float, duration: float, large_every: int = 50, slots: int = 4):
+    """Served mode: an open-loop Poisson stream of ordering requests (seeded),
+    98% from the batch_mix size distribution and every `large_every`-th a
+    27-point stencil on 100^3 (1,000,000 rows, 26,463,592 nnz), submitted from
+    host memory to the request server (continuous batching, HBM-budget
+    admission).  Reports offered and achieved nnz/s and latency percentiles
+    from submission to the permutation in host memory."""
+    import threading
+    arrivals = W.poisson_arrivals(rate, duration, seed=5)
+    nreq = len(arrivals)
+    small = W.batch_mix(nreq, seed=5)
+    large = W.stencil27(100)
+    reqs = [large if (i % large_every == large_every - 1) else small[i] for i in range(nreq)]
+    p = V.Params(d=3, seed=1)
+    # warm the server path once (library, pool) outside the measured stream
+    with V.Server(p, slots=slots) as srv:
+        for A in small[:8]:
+            srv.wait(srv.submit_matrix(A), 300.0)
+    with V.Server(p, slots=slots) as srv:
+        ids = [None] * nreq
+        t0 = time.perf_counter()
+
+        def producer():
+            for i, A in enumerate(reqs):
+                dt = t0 + arrivals[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                ids[i] = srv.submit_matrix(A)
+
+        th = threading.Thread(target=producer)
+        th.start()
+        th.join()
+        infos = [srv.wait(r, 1800.0) for r in ids]
+        st = srv.stats()
+    done = [d for d in infos if d["state"] == "done"]
+    lat = np.array([d["latency"] for d in done])
+    lat_small = np.array([d["latency"] for d, A in zip(infos, reqs) if d["state"] == "done" and A is not large])
+    lat_large = np.array([d["latency"] for d, A in zip(infos, reqs) if d["state"] == "done" and A is large])
+    t_first = min(d["t_submit"] for d in infos)
+    t_last = max(d["t_done"] for d in done)
+    nnz_done = sum(d["nnz"] for d in done)
+    nnz_all = sum(A.nnz for A in reqs)
+
+    def pct(a, q):
+        return float(np.percentile(a, q)) if len(a) else None
+
+    return {"workload": f"Poisson arrivals {rate:g}/s for {duration:g} s (seed 5): batch_mix sizes, every "
+                        f"{large_every}th request a 27-point stencil 100^3 (26.46M nnz); host CSR in, host "
+                        f"permutation out; d=3, min_part 64",
+            "requests": nreq, "large_requests": sum(1 for A in reqs if A is large), "completed": len(done),
+            "offered_nnz_per_s": nnz_all / duration, "achieved_nnz_per_s": nnz_done / (t_last - t_first),
+            "unit": "nnz/s", "p50_s": pct(lat, 50), "p99_s": pct(lat, 99), "p50_small_s": pct(lat_small, 50),
+            "p99_small_s": pct(lat_small, 99), "p50_large_s": pct(lat_large, 50), "max_s": pct(lat, 100),
+            "batches": st["batches"], "slots": slots, "budget_bytes": st["budget_bytes"],
+            "peak_admitted_bytes": st["bytes_peak"], "pool_peak_bytes": st["pool_peak_bytes"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,6 +255,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=1024,
                     help="matrices of the batched leg (config-4 distribution; 0 skips it)")
+    ap.add_argument("--serve-rate", type=float, default=30.0,
+                    help="requests per second of the served leg (0 skips it)")
+    ap.add_argument("--serve-seconds", type=float, default=8.0, help="length of the served arrival stream")
     ap.add_argument("--profile", action="store_true",
                     help="one untimed step of the workload and exit (for ncu captures; no JSON line)")
     ap.add_argument("--profile-matrix", type=int, default=-1,
@@ -349,9 +409,12 @@ def main():
                 "avg_launch_ms": avg_ms, "launches": st["step_launches"],
                 "share_of_step": st["step_ms"] / 1e3 / elapsed}
 
-    modes = None
+    modes = {}
     if args.batch_count > 0:
-        modes = batched_leg(V, torch, args.batch_count, 32, args.warmup, max(min(args.steps, 3), 1), flush)
+        modes["batched"] = batched_leg(V, torch, args.batch_count, 32, args.warmup, max(min(args.steps, 3), 1),
+                                       flush)
+    if args.serve_rate > 0 and world == 1:
+        modes["served"] = served_leg(V, args.serve_rate, args.serve_seconds)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:

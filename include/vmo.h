@@ -262,6 +262,111 @@ vmo_status vmo_batch_layout(const vmo_csr* mats, int32_t count, const vmo_params
 vmo_status vmo_cut_size(vmo_hg hg, const int32_t* part, int32_t nparts, int64_t* cutnet, int64_t* lambda1,
                         void* stream);
 
+/* ------------------------------------------------------------------------
+ * Request server: continuous batching of ordering requests.
+ *
+ * The paper orders one matrix at a time; the server serves a stream of
+ * ordering requests of mixed sizes on one GPU.  A request is a square
+ * pattern in HOST memory; the result is the recursive BBD (or SBD)
+ * permutation of the symmetric model, bit-identical to vmo_batch_order /
+ * vmo_order_bbd of that matrix alone with the same parameters.
+ *
+ * Scheduling: `slots` host workers, each with its own non-blocking CUDA
+ * stream.  A free slot takes the oldest queued requests (at most max_batch,
+ * at most max_batch_nnz nonzeros unless a single request is larger) whose
+ * estimated device memory (vmo_server_estimate_bytes) fits what is left of
+ * budget_bytes, copies their patterns to the device, orders them as one batch
+ * (vmo_batch_order) and copies each permutation to its host buffer.  Requests
+ * that arrive while others run are admitted as soon as a slot and budget are
+ * free, and their work overlaps on the device with the running batches.
+ * Coordinates, recursion trees and scratch stay on the device until the batch
+ * completes.  Times are seconds since vmo_server_create (steady clock).
+ * ------------------------------------------------------------------------ */
+typedef struct vmo_server_s* vmo_server;
+
+typedef struct {
+  vmo_params params;      /* ordering parameters of every request */
+  int32_t sbd;            /* 0: BBD [V1,V2,V3]; 1: SBD [V1,V3,V2] */
+  int32_t slots;          /* concurrent batches (host workers + streams), 1..64 (default 4) */
+  int32_t max_batch;      /* requests per batch, >= 1 (default 256) */
+  int64_t max_batch_nnz;  /* nonzeros per batch (default 8,000,000) */
+  int64_t budget_bytes;   /* device memory admitted requests may hold, by estimate;
+                             0: half of the free device memory at creation */
+} vmo_server_config;
+
+typedef enum {
+  VMO_REQ_QUEUED = 0,
+  VMO_REQ_RUNNING = 1,
+  VMO_REQ_DONE = 2,
+  VMO_REQ_FAILED = 3,
+  VMO_REQ_CANCELLED = 4
+} vmo_request_state;
+
+typedef struct {
+  int32_t state;          /* vmo_request_state */
+  int32_t status;         /* vmo_status of a failed request, else VMO_OK */
+  int64_t n, nnz;
+  int64_t bytes;          /* admission estimate */
+  double t_submit, t_admit, t_done;  /* seconds; t_done - t_submit is the latency */
+  int64_t batch;          /* sequence number of the batch that ran it (-1 before admission) */
+  int32_t batch_size;     /* requests in that batch */
+  int32_t slot;           /* slot that ran it */
+} vmo_request_info;
+
+typedef struct {
+  int64_t submitted, completed, failed, cancelled, queued, running;
+  int64_t batches;
+  int64_t nnz_completed;
+  int64_t budget_bytes, bytes_in_use, bytes_peak;  /* by estimate */
+  int64_t pool_peak_bytes;  /* high-water mark of the device pool (measured) */
+} vmo_server_stats;
+
+/* Fills the defaults shown above (params = vmo_default_params()). */
+void vmo_server_default_config(vmo_server_config* cfg);
+
+/* Device-memory estimate used for admission of an n x n request with nnz
+ * nonzeros: 512 n + 64 nnz + 1 MiB bytes (model, hierarchy, layout and
+ * ordering scratch). */
+int64_t vmo_server_estimate_bytes(int64_t n, int64_t nnz);
+
+/* The admission rule of a free slot, exposed for inspection: given the
+ * queue's estimates and nonzeros (host arrays, oldest first), the memory
+ * still free in the budget and the batch limits, returns how many requests
+ * from the head form the next batch (0: the head does not fit yet).  The head
+ * is always taken if it fits, even above max_batch_nnz. */
+int32_t vmo_server_plan(const int64_t* bytes, const int64_t* nnz, int32_t count, int64_t budget_free,
+                        int32_t max_batch, int64_t max_batch_nnz);
+
+/* Creates a server on the current device and starts its slots.
+ * Errors: VMO_ERR_INVALID for a bad config, VMO_ERR_CUDA without a GPU. */
+vmo_status vmo_server_create(const vmo_server_config* cfg, vmo_server* out);
+
+/* Queues one request.  rowptr[n+1], colidx[nnz] and perm_out[n] are HOST
+ * arrays that must stay valid until the request is terminal (done, failed or
+ * cancelled); the pattern is validated here (square, rowptr monotone from 0
+ * to nnz, columns in range).  *id receives the request id (> 0).
+ * Errors: VMO_ERR_INVALID (malformed pattern or null), VMO_ERR_BUDGET (the
+ * estimate alone exceeds the budget), VMO_ERR_INVALID after shutdown began. */
+vmo_status vmo_server_submit(vmo_server srv, int32_t n, const int32_t* rowptr, const int32_t* colidx,
+                             int32_t* perm_out, uint64_t* id);
+
+/* State of a request (host).  Errors: VMO_ERR_INVALID for an unknown id. */
+vmo_status vmo_server_poll(vmo_server srv, uint64_t id, vmo_request_info* info);
+
+/* Blocks until the request is terminal or timeout_s seconds pass (< 0: no
+ * limit); returns VMO_ERR_TIMEOUT in the latter case, info filled either way. */
+vmo_status vmo_server_wait(vmo_server srv, uint64_t id, double timeout_s, vmo_request_info* info);
+
+/* Cancels a request: a queued one never runs; a running one finishes on the
+ * device but its permutation is not written.  No effect on terminal ones. */
+vmo_status vmo_server_cancel(vmo_server srv, uint64_t id);
+
+vmo_status vmo_server_get_stats(vmo_server srv, vmo_server_stats* out);
+
+/* Stops admission, lets running batches finish, cancels what is still
+ * queued and frees the server (NULL is ignored). */
+void vmo_server_destroy(vmo_server srv);
+
 /* Resets the counters.  time_step_kernel != 0 records CUDA events around
  * every layout step kernel; count_interactions != 0 makes that kernel count
  * its interactions (an atomic per warp; same arithmetic otherwise). */

@@ -11,6 +11,8 @@
 namespace vmo {
 
 static thread_local std::string g_last_error;
+thread_local cudaStream_t g_devarray_stream = nullptr;
+thread_local bool g_devarray_async = false;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 

@@ -73,11 +73,34 @@ struct ScratchFrame {
   ~ScratchFrame() { sc.release_to(m); }
 };
 
+// Stream for the allocations of DevArray in the calling thread.  By default a
+// DevArray uses cudaMalloc / cudaFree; inside a DevArrayStreamScope it takes
+// its memory from the stream-ordered pool on the scope's stream and returns it
+// on that stream, so threads working on different streams (the request
+// server's slots) never wait for each other in an allocation or a free.
+extern thread_local cudaStream_t g_devarray_stream;
+extern thread_local bool g_devarray_async;
+
+struct DevArrayStreamScope {
+  cudaStream_t prev_s;
+  bool prev_a;
+  explicit DevArrayStreamScope(cudaStream_t s) : prev_s(g_devarray_stream), prev_a(g_devarray_async) {
+    g_devarray_stream = s;
+    g_devarray_async = true;
+  }
+  ~DevArrayStreamScope() {
+    g_devarray_stream = prev_s;
+    g_devarray_async = prev_a;
+  }
+};
+
 // Persistent device buffer owned by a handle.
 template <class T>
 struct DevArray {
   T* ptr = nullptr;
   size_t count = 0;
+  bool async = false;            // allocated from the stream-ordered pool
+  cudaStream_t astream = nullptr;
   vmo_status resize(size_t n);  // contents not preserved
   void release();
   ~DevArray() { release(); }
@@ -91,20 +114,27 @@ vmo_status DevArray<T>::resize(size_t n) {
   if (n <= count && ptr) return VMO_OK;
   release();
   if (n == 0) n = 1;
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ptr), n * sizeof(T));
+  const bool as = g_devarray_async;
+  cudaError_t e = as ? cudaMallocAsync(reinterpret_cast<void**>(&ptr), n * sizeof(T), g_devarray_stream)
+                     : cudaMalloc(reinterpret_cast<void**>(&ptr), n * sizeof(T));
   if (e != cudaSuccess) {
     ptr = nullptr;
     (void)cudaGetLastError();
-    set_error("cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
+    set_error("device allocation of " + std::to_string(n * sizeof(T)) + " bytes failed");
     return VMO_ERR_OOM;
   }
   count = n;
+  async = as;
+  astream = g_devarray_stream;
   return VMO_OK;
 }
 
 template <class T>
 void DevArray<T>::release() {
-  if (ptr) cudaFree(ptr);
+  if (ptr) {
+    if (async) cudaFreeAsync(ptr, astream);
+    else cudaFree(ptr);
+  }
   ptr = nullptr;
   count = 0;
 }

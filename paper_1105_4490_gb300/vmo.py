@@ -79,7 +79,26 @@ SYMBOLS = ["vmo_default_params", "vmo_build_hypergraph", "vmo_hg_vertices", "vmo
            "vmo_components", "vmo_init_coords", "vmo_layout", "vmo_layout_step", "vmo_coarsen", "vmo_bisect",
            "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_cut_size", "vmo_destroy",
            "vmo_status_string", "vmo_last_error", "vmo_stats_reset", "vmo_stats_get", "vmo_batch_order",
-           "vmo_batch_layout", "vmo_bisect_noalloc"]
+           "vmo_batch_layout", "vmo_bisect_noalloc", "vmo_server_default_config", "vmo_server_estimate_bytes",
+           "vmo_server_plan", "vmo_server_create", "vmo_server_submit", "vmo_server_poll", "vmo_server_wait",
+           "vmo_server_cancel", "vmo_server_get_stats", "vmo_server_destroy"]
+
+
+class _ServerConfig(C.Structure):
+    _fields_ = [("params", _Params), ("sbd", C.c_int32), ("slots", C.c_int32), ("max_batch", C.c_int32),
+                ("max_batch_nnz", C.c_int64), ("budget_bytes", C.c_int64)]
+
+
+class _RequestInfo(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("n", C.c_int64), ("nnz", C.c_int64),
+                ("bytes", C.c_int64), ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("batch", C.c_int64), ("batch_size", C.c_int32), ("slot", C.c_int32)]
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [(f, C.c_int64) for f in ("submitted", "completed", "failed", "cancelled", "queued", "running",
+                                         "batches", "nnz_completed", "budget_bytes", "bytes_in_use", "bytes_peak",
+                                         "pool_peak_bytes")]
 
 
 def load(path: str | None = None):
@@ -124,9 +143,24 @@ def load(path: str | None = None):
     lib.vmo_stats_reset.argtypes = [I32, I32]
     lib.vmo_stats_reset.restype = None
     lib.vmo_stats_get.argtypes = [C.POINTER(_Stats)]
+    lib.vmo_server_default_config.argtypes = [C.POINTER(_ServerConfig)]
+    lib.vmo_server_default_config.restype = None
+    lib.vmo_server_estimate_bytes.argtypes = [I64, I64]
+    lib.vmo_server_estimate_bytes.restype = I64
+    lib.vmo_server_plan.argtypes = [P64, P64, I32, I64, I32, I64]
+    lib.vmo_server_plan.restype = I32
+    lib.vmo_server_create.argtypes = [C.POINTER(_ServerConfig), C.POINTER(V)]
+    lib.vmo_server_submit.argtypes = [V, I32, V, V, V, C.POINTER(U64)]
+    lib.vmo_server_poll.argtypes = [V, U64, C.POINTER(_RequestInfo)]
+    lib.vmo_server_wait.argtypes = [V, U64, C.c_double, C.POINTER(_RequestInfo)]
+    lib.vmo_server_cancel.argtypes = [V, U64]
+    lib.vmo_server_get_stats.argtypes = [V, C.POINTER(_ServerStats)]
+    lib.vmo_server_destroy.argtypes = [V]
+    lib.vmo_server_destroy.restype = None
     for nm in SYMBOLS:
         if nm not in ("vmo_default_params", "vmo_hg_vertices", "vmo_hg_nets", "vmo_destroy", "vmo_status_string",
-                      "vmo_last_error", "vmo_stats_reset"):
+                      "vmo_last_error", "vmo_stats_reset", "vmo_server_default_config", "vmo_server_estimate_bytes",
+                      "vmo_server_plan", "vmo_server_destroy"):
             getattr(lib, nm).restype = C.c_int
     _lib = lib
     return lib

@@ -50,3 +50,37 @@ def test_params_struct_layout():
     assert ctypes.sizeof(vmo._Params) == 4 * 11 + 4 + 8  # 11 x 4-byte fields, padding, uint64 seed
     assert ctypes.sizeof(vmo._Tree) == 8 + 7 * 8
     assert ctypes.sizeof(vmo._Stats) == 5 * 8
+
+
+def test_struct_layouts_match_c(tmp_path):
+    """sizeof / offsetof of every ABI struct, compiled from include/vmo.h with
+    the host C compiler, equal the ctypes mirrors of the binding."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    from paper_1105_4490_gb300 import vmo
+    structs = {"vmo_params": vmo._Params, "vmo_csr": vmo._Csr, "vmo_tree": vmo._Tree, "vmo_stats": vmo._Stats,
+               "vmo_server_config": vmo._ServerConfig, "vmo_request_info": vmo._RequestInfo,
+               "vmo_server_stats": vmo._ServerStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vmo.h"', "int main(void) {"]
+    for cname, ct in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in ct._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            s, f, v = ln.split()
+            got[(s, f)] = int(v)
+    for cname, ct in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(ct), cname
+        for f, _ in ct._fields_:
+            assert got[(cname, f)] == getattr(ct, f).offset, (cname, f)

@@ -192,6 +192,15 @@ __global__ void __launch_bounds__(kBlock) k_keys(const float4* __restrict__ x, i
   vals[v] = (uint32_t)v;
 }
 
+// a[lo..hi) = v, with 16-byte stores over the aligned middle of the range
+// (long runs of empty cells between clusters of the layout).
+__device__ inline void fill_i32(int32_t* __restrict__ a, int64_t lo, int64_t hi, int32_t v) {
+  while (lo < hi && (((uintptr_t)(a + lo)) & 15u)) a[lo++] = v;
+  const int4 v4 = make_int4(v, v, v, v);
+  for (; lo + 4 <= hi; lo += 4) *reinterpret_cast<int4*>(a + lo) = v4;
+  while (lo < hi) a[lo++] = v;
+}
+
 // Sorted positions: coordinates and weights in sorted order (plain and in
 // the paired table XP), the packed cell of every point, and the cell start
 // table.  cst[fbase + pb + c] is the first
@@ -237,12 +246,8 @@ __global__ void __launch_bounds__(kBlock) k_gather(const uint32_t* __restrict__ 
   int32_t* cs = cst + pr.fbase + pb;
   const int64_t key = skeys[p];
   const int64_t prev = p == pr.vbase ? -1 : (int64_t)skeys[p - 1];
-  for (int64_t cc = prev + 1; cc <= key; ++cc) cs[cc] = (int32_t)p;
-  if (p == pr.vbase + pr.k - 1) {
-    const int64_t ncell = int64_t(1) << (D * pr.L);
-    const int32_t end = (int32_t)(pr.vbase + pr.k);
-    for (int64_t cc = key + 1; cc <= ncell; ++cc) cs[cc] = end;
-  }
+  fill_i32(cs, prev + 1, key + 1, (int32_t)p);
+  if (p == pr.vbase + pr.k - 1) fill_i32(cs, key + 1, (int64_t(1) << (D * pr.L)) + 1, (int32_t)(pr.vbase + pr.k));
 }
 
 // Cell sums (St, Wt) at cell index idx, and the cell's charge (weighted mean
@@ -263,31 +268,16 @@ __device__ inline void store_cell(int64_t idx, int64_t pidx, const float* S, flo
 
 // Finest cells: the charge of every cell from its points (the range comes
 // from the cell start table written by k_gather; a problem without points
-// writes its table here).
+// writes its table here).  A cell of at most kCellSerial points is summed by
+// its own thread in point order; a larger cell (dense clusters of the layout)
+// by the whole warp: lane-strided partial sums from the cell's first point,
+// then a fixed xor tree.  Either way the sums depend only on the cell.
+constexpr int kCellSerial = 32;
+
 template <int D>
-__global__ void __launch_bounds__(kBlock) k_agg_finest(int64_t ncells, const int64_t* __restrict__ fbase, int P,
-                                                       const ProbDev* __restrict__ prob, const float4* __restrict__ xs,
-                                                       const float* __restrict__ ws, int32_t* __restrict__ cst,
-                                                       float4* __restrict__ St, float* __restrict__ Wt,
-                                                       float4* __restrict__ CP) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ncells) return;
-  int pb = find_problem(fbase, P, i);
-  ProbDev pr = prob[pb];
-  int64_t c = i - pr.fbase;
-  int32_t* cs = cst + pr.fbase + pb;
-  int64_t q0, q1;
-  if (pr.k == 0) {
-    cs[c] = (int32_t)pr.vbase;
-    if (c == (int64_t(1) << (D * pr.L)) - 1) cs[c + 1] = (int32_t)pr.vbase;
-    q0 = q1 = 0;
-  } else {
-    q0 = cs[c];
-    q1 = cs[c + 1];
-  }
-  float S[4] = {0.f, 0.f, 0.f, 0.f};
-  float W = 0.f;
-  for (int64_t q = q0; q < q1; ++q) {
+__device__ __forceinline__ void cell_sum(const float4* __restrict__ xs, const float* __restrict__ ws, int64_t q0,
+                                         int64_t q1, int64_t stride, float* S, float& W) {
+  for (int64_t q = q0; q < q1; q += stride) {
     float4 p = xs[q];
     float wq = ws ? ws[q] : 1.0f;
     S[0] += wq * p.x;
@@ -296,8 +286,56 @@ __global__ void __launch_bounds__(kBlock) k_agg_finest(int64_t ncells, const int
     if (D > 3) S[3] += wq * p.w;
     W += wq;
   }
-  const int64_t idx = pr.cbase + lvl_off(D, pr.L) + c;
-  store_cell<D>(idx, idx + pb + 1, S, W, St, Wt, CP);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_agg_finest(int64_t ncells, const int64_t* __restrict__ fbase, int P,
+                                                       const ProbDev* __restrict__ prob, const float4* __restrict__ xs,
+                                                       const float* __restrict__ ws, int32_t* __restrict__ cst,
+                                                       float4* __restrict__ St, float* __restrict__ Wt,
+                                                       float4* __restrict__ CP) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < ncells;
+  int64_t q0 = 0, q1 = 0, idx = 0, pidx = 0;
+  if (valid) {
+    const int pb = find_problem(fbase, P, i);
+    const ProbDev pr = prob[pb];
+    const int64_t c = i - pr.fbase;
+    int32_t* cs = cst + pr.fbase + pb;
+    if (pr.k == 0) {
+      cs[c] = (int32_t)pr.vbase;
+      if (c == (int64_t(1) << (D * pr.L)) - 1) cs[c + 1] = (int32_t)pr.vbase;
+    } else {
+      q0 = cs[c];
+      q1 = cs[c + 1];
+    }
+    idx = pr.cbase + lvl_off(D, pr.L) + c;
+    pidx = idx + pb + 1;
+  }
+  const bool big = valid && q1 - q0 > kCellSerial;
+  if (valid && !big) {
+    float S[4] = {0.f, 0.f, 0.f, 0.f};
+    float W = 0.f;
+    cell_sum<D>(xs, ws, q0, q1, 1, S, W);
+    store_cell<D>(idx, pidx, S, W, St, Wt, CP);
+  }
+  const int lane = lane_id();
+  unsigned todo = __ballot_sync(0xffffffffu, big);
+  while (todo) {
+    const int src = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const int64_t b0 = __shfl_sync(0xffffffffu, q0, src), b1 = __shfl_sync(0xffffffffu, q1, src);
+    float S[4] = {0.f, 0.f, 0.f, 0.f};
+    float W = 0.f;
+    cell_sum<D>(xs, ws, b0 + lane, b1, 32, S, W);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int m = 0; m < D; ++m) S[m] += __shfl_xor_sync(0xffffffffu, S[m], o);
+      W += __shfl_xor_sync(0xffffffffu, W, o);
+    }
+    if (lane == src) store_cell<D>(idx, pidx, S, W, St, Wt, CP);
+  }
 }
 
 template <int D>
@@ -353,6 +391,29 @@ __device__ inline void add_pull(float* a, const float4& xv, const float4& xu, fl
   a[3] += c * (xv.w - xu.w);
 }
 
+// a += sum over t = t0, t0 + stride, ... < t1 of c_t (xv - x[adj[t]]), in that
+// order; four neighbours per trip with all their loads issued first.
+__device__ __forceinline__ void pull_range(float* a, const float4& xv, const int32_t* __restrict__ adj,
+                                           const float* __restrict__ acost, const float4* __restrict__ x, int32_t t,
+                                           int32_t t1, int32_t stride) {
+  constexpr int U = 4;
+  for (; t + (U - 1) * stride < t1; t += U * stride) {
+    int32_t u[U];
+    float c[U];
+    float4 q[U];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      u[i] = adj[t + i * stride];
+      c[i] = acost ? acost[t + i * stride] : 1.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < U; ++i) q[i] = x[u[i]];
+#pragma unroll
+    for (int i = 0; i < U; ++i) add_pull(a, xv, q[i], c[i]);
+  }
+  for (; t < t1; t += stride) add_pull(a, xv, x[adj[t]], acost ? acost[t] : 1.0f);
+}
+
 __global__ void __launch_bounds__(kBlock) k_attract(const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
                                                     const float* __restrict__ acost, const float4* __restrict__ x,
                                                     int64_t K, float4* __restrict__ y) {
@@ -362,7 +423,7 @@ __global__ void __launch_bounds__(kBlock) k_attract(const int32_t* __restrict__ 
   if (t1 - t0 > kLightMax) return;  // medium and heavy rows: k_attract_warp / k_attract_block
   float4 xv = x[v];
   float a[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int32_t t = t0; t < t1; ++t) add_pull(a, xv, x[adj[t]], acost ? acost[t] : 1.0f);
+  pull_range(a, xv, adj, acost, x, t0, t1, 1);
   y[v] = make_float4(0.5f * a[0], 0.5f * a[1], 0.5f * a[2], 0.5f * a[3]);
 }
 
@@ -376,7 +437,7 @@ __global__ void __launch_bounds__(kBlock) k_attract_warp(const int32_t* __restri
   int32_t v = list[w];
   float4 xv = x[v];
   float a[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int32_t t = adj_ptr[v] + lane; t < adj_ptr[v + 1]; t += 32) add_pull(a, xv, x[adj[t]], acost ? acost[t] : 1.0f);
+  pull_range(a, xv, adj, acost, x, adj_ptr[v] + lane, adj_ptr[v + 1], 32);
 #pragma unroll
   for (int m = 0; m < 4; ++m)
 #pragma unroll
@@ -394,8 +455,7 @@ __global__ void __launch_bounds__(kBlock) k_attract_block(const int32_t* __restr
   int32_t v = list[blockIdx.x];
   float4 xv = x[v];
   float a[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int32_t t = adj_ptr[v] + threadIdx.x; t < adj_ptr[v + 1]; t += blockDim.x)
-    add_pull(a, xv, x[adj[t]], acost ? acost[t] : 1.0f);
+  pull_range(a, xv, adj, acost, x, adj_ptr[v] + threadIdx.x, adj_ptr[v + 1], blockDim.x);
 #pragma unroll
   for (int m = 0; m < 4; ++m)
 #pragma unroll
@@ -716,7 +776,26 @@ __global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_upda
       if (!inside) continue;
       const int64_t r0 = rowmajor<D>(cc, side);
       const int qa = cs[r0] - (int)pr.vbase, qb = cs[r0 + (xb - xa) + 1] - (int)pr.vbase;  // problem-local
-      for (int j = (qa >> 1) + lane_g; 2 * j < qb; j += G) {
+      // four pairs per trip (all loads issued before the arithmetic); the
+      // order of the pairs in the sums is the same as one pair per trip
+      int j = (qa >> 1) + lane_g;
+      for (; 2 * (j + 3 * G) < qb; j += 4 * G) {
+        float4 Q[4][N];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int i = 0; i < N; ++i) Q[u][i] = xp[(int64_t)(j + u * G) * N + i];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float2 w = pair_weight<D>(Q[u]);
+          const int h0 = 2 * (j + u * G);
+          if (u == 0) w.x = h0 >= qa ? w.x : 0.0f;       // only the first pair can start before qa
+          if (u == 3) w.y = h0 + 1 < qb ? w.y : 0.0f;    // only the last pair can end after qb
+          pair_charge<D>(F, Q[u], nx, w);
+          if (COUNT) nint += (h0 >= qa && h0 != tgt) + (h0 + 1 < qb && h0 + 1 != tgt);
+        }
+      }
+      for (; 2 * j < qb; j += G) {
         float4 Q[N];
 #pragma unroll
         for (int i = 0; i < N; ++i) Q[i] = xp[(int64_t)j * N + i];
@@ -1193,8 +1272,14 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
       launch(k_keys<D>, grid_for(std::max<int64_t>(K, nreset), kBlock), kBlock, 0, s, x, K, lb.vprob.ptr, lb.prob.ptr,
                                                                                   cur, keys, vals, nxt, nreset);
       if (keys_out && t == 0) cudaMemcpyAsync(keys_out, keys, K * 4, cudaMemcpyDeviceToDevice, s);
-      st = radix_sort_u32(keys, vals, skeys, svals, K, D * lb.maxL, segmented ? &segs : nullptr, s, sc);
+      bool in_b = false;
+      st = radix_sort_u32_pingpong(keys, vals, skeys, svals, K, D * lb.maxL, segmented ? &segs : nullptr, &in_b, s,
+                                   sc);
       if (st != VMO_OK) break;
+      if (!in_b) {  // sorted pairs are in (keys, vals): use them as (skeys, svals) from here on
+        std::swap(keys, skeys);
+        std::swap(vals, svals);
+      }
       launch(k_gather<D>, grid_for(K, kBlock), kBlock, 0, s, svals, skeys, K, x, lb.w, lb.vprob.ptr, lb.prob.ptr, cur,
              xs, ws, scell, cst, XP);
       launch(k_agg_finest<D>, grid_for(nfine, kBlock), kBlock, 0, s, nfine, fb, P, lb.prob.ptr, xs, ws, cst, St, Wt,

@@ -129,6 +129,39 @@ vmo_status scan_impl(const T* in, T* out, int64_t n, T* total, cudaStream_t s, S
   return VMO_OK;
 }
 
+// Exclusive scan of a short array by one block (in place allowed): chunks of
+// 1024 x 8 values, each thread scanning 8 consecutive ones, with a carry
+// between chunks.  Replaces the three-kernel scan for the radix histograms of
+// a level (at most kSingleScanMax values).
+constexpr int kSingleScanThreads = 1024;
+constexpr int kSingleScanItems = 8;
+constexpr int64_t kSingleScanMax = 262144;
+
+__global__ void __launch_bounds__(kSingleScanThreads) scan_single_block_u32(const uint32_t* __restrict__ in,
+                                                                            uint32_t* __restrict__ out, int64_t n) {
+  __shared__ uint32_t ws[33];
+  uint32_t carry = 0;
+  constexpr int chunk = kSingleScanThreads * kSingleScanItems;
+  for (int64_t b = 0; b < n; b += chunk) {
+    const int64_t i0 = b + (int64_t)threadIdx.x * kSingleScanItems;
+    uint32_t v[kSingleScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kSingleScanItems; ++j) {
+      v[j] = i0 + j < n ? in[i0 + j] : 0u;
+      sum += v[j];
+    }
+    uint32_t tot;
+    uint32_t ex = block_exclusive<uint32_t>(sum, ws, &tot) + carry;
+#pragma unroll
+    for (int j = 0; j < kSingleScanItems; ++j) {
+      if (i0 + j < n) out[i0 + j] = ex;
+      ex += v[j];
+    }
+    carry += tot;
+  }
+}
+
 // ------------------------------- radix sort --------------------------------
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
@@ -230,13 +263,15 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
 
 template <class K>
 vmo_status radix_sort_impl(K* keys_in, uint32_t* vals_in, K* keys_out, uint32_t* vals_out, int64_t n, int bits,
-                           const SortSegments* segs, cudaStream_t s, Scratch& sc) {
+                           const SortSegments* segs, cudaStream_t s, Scratch& sc, bool* in_b = nullptr) {
+  if (in_b) *in_b = false;
   if (n <= 0) return VMO_OK;
   SortSegments sg;
   if (segs) sg = *segs;
   if (sg.tile_seg == nullptr) sg.ntiles = (n + kSortTile - 1) / kSortTile;
   int passes = (bits + kRadixBits - 1) / kRadixBits;
   if (passes == 0) {
+    if (in_b) return VMO_OK;  // already sorted, left in place
     VMO_CUDA(cudaMemcpyAsync(keys_out, keys_in, n * sizeof(K), cudaMemcpyDeviceToDevice, s));
     if (vals_in) VMO_CUDA(cudaMemcpyAsync(vals_out, vals_in, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     return VMO_OK;
@@ -251,7 +286,10 @@ vmo_status radix_sort_impl(K* keys_in, uint32_t* vals_in, K* keys_out, uint32_t*
   for (int p = 0; p < passes; ++p) {
     int shift = p * kRadixBits;
     launch(radix_hist_kernel<K>, (unsigned)sg.ntiles, 256, 0, s, ka, n, shift, sg, hist);
-    VMO_TRY((scan_impl<uint32_t, false>(hist, hist, hn, nullptr, s, sc)));
+    if (hn <= kSingleScanMax)
+      launch(scan_single_block_u32, 1, kSingleScanThreads, 0, s, hist, hist, hn);
+    else
+      VMO_TRY((scan_impl<uint32_t, false>(hist, hist, hn, nullptr, s, sc)));
     if (vals_in)
       launch(radix_scatter_kernel<K, true>, (unsigned)sg.ntiles, kSortThreads, 0, s, ka, va, kb, vb, n, shift, sg, hist);
     else
@@ -260,6 +298,10 @@ vmo_status radix_sort_impl(K* keys_in, uint32_t* vals_in, K* keys_out, uint32_t*
     VMO_LAUNCHED("radix_sort");
     K* tk = ka; ka = kb; kb = tk;
     uint32_t* tv = va; va = vb; vb = tv;
+  }
+  if (in_b) {
+    *in_b = ka == keys_out;
+    return VMO_OK;
   }
   if (ka != keys_out) {
     VMO_CUDA(cudaMemcpyAsync(keys_out, ka, n * sizeof(K), cudaMemcpyDeviceToDevice, s));
@@ -304,6 +346,11 @@ int64_t scan_partials_needed(int64_t n) { return (n + kScanTile - 1) / kScanTile
 vmo_status radix_sort_u32(uint32_t* keys_in, uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out, int64_t n,
                           int bits, const SortSegments* segs, cudaStream_t s, Scratch& sc) {
   return radix_sort_impl<uint32_t>(keys_in, vals_in, keys_out, vals_out, n, bits, segs, s, sc);
+}
+
+vmo_status radix_sort_u32_pingpong(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, int64_t n,
+                                  int bits, const SortSegments* segs, bool* in_b, cudaStream_t s, Scratch& sc) {
+  return radix_sort_impl<uint32_t>(keys_a, vals_a, keys_b, vals_b, n, bits, segs, s, sc, in_b);
 }
 
 vmo_status radix_sort_u64(uint64_t* keys_in, uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out, int64_t n,

@@ -203,6 +203,11 @@ constexpr int kSortTile = 2048;  // 256 threads x 8 keys
 // in (keys_out, vals_out).  vals may be null (keys only).
 vmo_status radix_sort_u32(uint32_t* keys_in, uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
                           int64_t n, int bits, const SortSegments* segs, cudaStream_t s, Scratch& sc);
+// Same sort without the final copy: the sorted keys and values are left in
+// (keys_b, vals_b) if *in_b, else in (keys_a, vals_a); the other pair is
+// overwritten.
+vmo_status radix_sort_u32_pingpong(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, int64_t n,
+                                  int bits, const SortSegments* segs, bool* in_b, cudaStream_t s, Scratch& sc);
 vmo_status radix_sort_u64(uint64_t* keys_in, uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
                           int64_t n, int bits, cudaStream_t s, Scratch& sc);
 

@@ -338,17 +338,11 @@ __global__ void __launch_bounds__(kBlock) k_agg_finest(int64_t ncells, const int
   }
 }
 
+// Coarse cells: sums of the 2^d children (fixed order), charge at the mean.
 template <int D>
-__global__ void __launch_bounds__(kBlock) k_agg_level(int step, const int64_t* __restrict__ off, int P, int64_t ncells,
-                                                      const ProbDev* __restrict__ prob, float4* __restrict__ St,
-                                                      float* __restrict__ Wt, float4* __restrict__ CP) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ncells) return;
-  int pb = find_problem(off, P, i);
-  ProbDev pr = prob[pb];
-  int l = pr.L - step;
-  int64_t c = i - off[pb];
-  int side = 1 << l;
+__device__ inline void agg_cell(const ProbDev& pr, int pb, int l, int64_t c, float4* __restrict__ St,
+                                float* __restrict__ Wt, float4* __restrict__ CP) {
+  const int side = 1 << l;
   int32_t cc[D];
   int64_t rem = c;
 #pragma unroll
@@ -356,7 +350,7 @@ __global__ void __launch_bounds__(kBlock) k_agg_level(int step, const int64_t* _
     cc[m] = (int32_t)(rem % side);
     rem /= side;
   }
-  int64_t child_base = pr.cbase + lvl_off(D, l + 1);
+  const int64_t child_base = pr.cbase + lvl_off(D, l + 1);
   float S[4] = {0.f, 0.f, 0.f, 0.f};
   float W = 0.f;
 #pragma unroll
@@ -364,8 +358,8 @@ __global__ void __launch_bounds__(kBlock) k_agg_level(int step, const int64_t* _
     int32_t q[D];
 #pragma unroll
     for (int m = 0; m < D; ++m) q[m] = 2 * cc[m] + ((ch >> m) & 1);
-    int64_t idx = child_base + rowmajor<D>(q, 2 * side);
-    float4 s4 = St[idx];
+    const int64_t idx = child_base + rowmajor<D>(q, 2 * side);
+    const float4 s4 = St[idx];
     S[0] += s4.x;
     if (D > 1) S[1] += s4.y;
     if (D > 2) S[2] += s4.z;
@@ -374,6 +368,34 @@ __global__ void __launch_bounds__(kBlock) k_agg_level(int step, const int64_t* _
   }
   const int64_t idx = pr.cbase + lvl_off(D, l) + c;
   store_cell<D>(idx, idx + pb + 1, S, W, St, Wt, CP);
+}
+
+// Levels of at most 512 cells are aggregated by one block per problem (all of
+// them in one launch, a block barrier between levels); the larger coarse
+// levels by one launch per level over all problems.
+__host__ __device__ constexpr int small_level_max(int d) { return d == 2 ? 4 : (d == 3 ? 3 : 2); }
+
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_agg_level(int step, const int64_t* __restrict__ off, int P, int64_t ncells,
+                                                      const ProbDev* __restrict__ prob, float4* __restrict__ St,
+                                                      float* __restrict__ Wt, float4* __restrict__ CP) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncells) return;
+  int pb = find_problem(off, P, i);
+  ProbDev pr = prob[pb];
+  agg_cell<D>(pr, pb, pr.L - step, i - off[pb], St, Wt, CP);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_agg_small(const ProbDev* __restrict__ prob, float4* __restrict__ St,
+                                                      float* __restrict__ Wt, float4* __restrict__ CP) {
+  const int pb = blockIdx.x;
+  const ProbDev pr = prob[pb];
+  for (int l = min(pr.L - 1, small_level_max(D)); l >= 2; --l) {
+    const int64_t n = int64_t(1) << (D * l);
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) agg_cell<D>(pr, pb, l, c, St, Wt, CP);
+    __syncthreads();
+  }
 }
 
 // Rubber bands of 2-pin nets: y_v = sum_u c_vu (x_v - x_u) / 2.  Rows are
@@ -529,10 +551,12 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   return r;
 }
 
-// Smallest squared distance fed to the kernels.  A source at the target's
-// own position (the target itself, a coincident point) has dx = 0 and so
-// contributes exactly 0 * g = 0; the floor keeps g finite for it.  Masked
-// sources (weight 0) contribute 0 the same way.
+// Added to every squared distance fed to the kernels.  A source at the
+// target's own position (the target itself, a coincident point) has dx = 0
+// and so contributes exactly 0 * g = 0; the offset keeps g finite for it.
+// Masked sources (weight 0) contribute 0 the same way.  For real pairs the
+// relative change of r^2 is 1e-15 / r^2, negligible at the spacings of a
+// layout (mean point spacing ~1).
 constexpr float kR2Floor = 1e-15f;
 
 // F += w r^-d (src - xn) for the two sources of a pair; nx holds -xn twice
@@ -544,11 +568,9 @@ __device__ __forceinline__ void pair_charge(float2* F, const float4* P, const fl
   if (D > 1) dx[1] = __fadd2_rn(make_float2(P[0].z, P[0].w), nx[1]);
   if (D > 2) dx[2] = __fadd2_rn(make_float2(P[1].x, P[1].y), nx[2]);
   if (D > 3) dx[3] = __fadd2_rn(make_float2(P[1].z, P[1].w), nx[3]);
-  float2 r2 = __fmul2_rn(dx[0], dx[0]);
+  float2 r2 = make_float2(kR2Floor, kR2Floor);  // offset: a source at the target's position gives 0 * finite
 #pragma unroll
-  for (int m = 1; m < D; ++m) r2 = __ffma2_rn(dx[m], dx[m], r2);
-  r2.x = fmaxf(r2.x, kR2Floor);
-  r2.y = fmaxf(r2.y, kR2Floor);
+  for (int m = 0; m < D; ++m) r2 = __ffma2_rn(dx[m], dx[m], r2);
   float2 g;
   if (D == 2) {
     g = __fmul2_rn(w, make_float2(rcp_approx(r2.x), rcp_approx(r2.y)));
@@ -1186,7 +1208,7 @@ vmo_status level_setup(LevelBatch& lb, int d, int occ, cudaStream_t s) {
   for (int st = 1; st <= nsteps; ++st)
     for (int p = 0; p < P; ++p) {
       int l = lb.L[p] - st;
-      int64_t cnt = l >= 2 ? (int64_t(1) << (d * l)) : 0;
+      int64_t cnt = l > small_level_max(d) ? (int64_t(1) << (d * l)) : 0;
       off[(size_t)st * (P + 1) + p + 1] = off[(size_t)st * (P + 1) + p] + cnt;
     }
   VMO_TRY(lb.prob.resize(std::max(P, 1)));
@@ -1204,6 +1226,7 @@ vmo_status level_setup(LevelBatch& lb, int d, int occ, cudaStream_t s) {
     VMO_LAUNCHED("fill_vprob");
   }
   VMO_CUDA(cudaFreeAsync(vb, s));
+
   // host vectors must outlive the copies
   VMO_CUDA(cudaStreamSynchronize(s));
   return classify_degrees(lb, s);
@@ -1216,6 +1239,29 @@ vmo_status init_coords_level(LevelBatch& lb, int d, const uint64_t* seeds_dev, f
   VMO_LAUNCHED("init_coords");
   return VMO_OK;
 }
+
+// A second stream with fork / join events for one layout call; destroyed (in
+// stream order) when the call returns.
+struct SideStream {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  SideStream() {
+    if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+      (void)cudaGetLastError();
+      release();
+    }
+  }
+  void release() {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (stream) cudaStreamDestroy(stream);
+    stream = nullptr;
+    fork = join = nullptr;
+  }
+  ~SideStream() { release(); }
+};
 
 vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int iters, float step_override,
                         float4* y_out, uint32_t* keys_out, cudaStream_t s, Scratch& sc) {
@@ -1260,6 +1306,9 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
   VMO_LAUNCHED("bbox_reset");
   const float kappa = d == 2 ? 1.0f : (float)(d - 2);
   vmo_status st = VMO_OK;
+  SideStream ss;  // attraction stream of this call (none if it cannot be created)
+  cudaStream_t side = ss.stream;
+  cudaEvent_t ev_fork = ss.fork, ev_join = ss.join;
   dispatch_d(d, [&](auto DC) {
     constexpr int D = decltype(DC)::value;
     launch(k_bbox<D>, grid_for(K, kBlock), kBlock, 0, s, x, K, lb.vprob.ptr, bb);
@@ -1269,6 +1318,28 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
       ScratchFrame f2(sc);
       uint32_t* cur = bb + (t & 1) * 8 * P;
       uint32_t* nxt = bb + ((t + 1) & 1) * 8 * P;
+      // attraction depends only on x: it runs on the side stream, overlapped
+      // with the binning below, and joins before the step kernel
+      cudaStream_t as = side ? side : s;
+      if (side) {
+        cudaEventRecord(ev_fork, s);
+        cudaStreamWaitEvent(side, ev_fork, 0);
+      }
+      if (lb.adj_ptr) {
+        launch(k_attract, grid_for(K, kBlock), kBlock, 0, as, lb.adj_ptr, lb.adj, lb.acost, x, K, yatt);
+        if (lb.n_mid)
+          launch(k_attract_warp, grid_for(lb.n_mid * 32, kBlock), kBlock, 0, as, lb.mid_list.ptr, lb.n_mid, lb.adj_ptr,
+                 lb.adj, lb.acost, x, yatt);
+        if (lb.n_heavy)
+          launch(k_attract_block, (unsigned)lb.n_heavy, kBlock, 0, as, lb.heavy_list.ptr, lb.adj_ptr, lb.adj, lb.acost,
+                 x, yatt);
+      } else if (lb.net_ptr) {
+        if (lb.nnets > 0) launch(k_net_center, grid_for(lb.nnets, kBlock), kBlock, 0, as, lb.net_ptr, lb.pins, lb.nnets, x, z);
+        launch(k_attract_hyper, grid_for(K, kBlock), kBlock, 0, as, lb.vtx_ptr, lb.vnets, x, z, K, yatt);
+      } else {
+        cudaMemsetAsync(yatt, 0, K * sizeof(float4), as);
+      }
+      if (side) cudaEventRecord(ev_join, side);
       launch(k_keys<D>, grid_for(std::max<int64_t>(K, nreset), kBlock), kBlock, 0, s, x, K, lb.vprob.ptr, lb.prob.ptr,
                                                                                   cur, keys, vals, nxt, nreset);
       if (keys_out && t == 0) cudaMemcpyAsync(keys_out, keys, K * 4, cudaMemcpyDeviceToDevice, s);
@@ -1289,25 +1360,13 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
         int64_t n = 0;
         for (int p = 0; p < P; ++p) {
           int l = lb.L[p] - stp;
-          n += l >= 2 ? (int64_t(1) << (D * l)) : 0;
+          n += l > small_level_max(D) ? (int64_t(1) << (D * l)) : 0;
         }
         if (n == 0) continue;
         launch(k_agg_level<D>, grid_for(n, kBlock), kBlock, 0, s, stp, off, P, n, lb.prob.ptr, St, Wt, CP);
       }
-      if (lb.adj_ptr) {
-        launch(k_attract, grid_for(K, kBlock), kBlock, 0, s, lb.adj_ptr, lb.adj, lb.acost, x, K, yatt);
-        if (lb.n_mid)
-          launch(k_attract_warp, grid_for(lb.n_mid * 32, kBlock), kBlock, 0, s, lb.mid_list.ptr, lb.n_mid, lb.adj_ptr,
-                 lb.adj, lb.acost, x, yatt);
-        if (lb.n_heavy)
-          launch(k_attract_block, (unsigned)lb.n_heavy, kBlock, 0, s, lb.heavy_list.ptr, lb.adj_ptr, lb.adj, lb.acost,
-                 x, yatt);
-      } else if (lb.net_ptr) {
-        if (lb.nnets > 0) launch(k_net_center, grid_for(lb.nnets, kBlock), kBlock, 0, s, lb.net_ptr, lb.pins, lb.nnets, x, z);
-        launch(k_attract_hyper, grid_for(K, kBlock), kBlock, 0, s, lb.vtx_ptr, lb.vnets, x, z, K, yatt);
-      } else {
-        cudaMemsetAsync(yatt, 0, K * sizeof(float4), s);
-      }
+      if (lb.maxL >= 3) launch(k_agg_small<D>, (unsigned)P, kBlock, 0, s, lb.prob.ptr, St, Wt, CP);
+      if (side) cudaStreamWaitEvent(s, ev_join, 0);
       const bool timed = stats_timing();
       if (timed) stats_time_begin(s);
       unsigned long long* icount = stats_interaction_counter();

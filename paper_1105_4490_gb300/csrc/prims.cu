@@ -129,45 +129,14 @@ vmo_status scan_impl(const T* in, T* out, int64_t n, T* total, cudaStream_t s, S
   return VMO_OK;
 }
 
-// Exclusive scan of a short array by one block (in place allowed): chunks of
-// 1024 x 8 values, each thread scanning 8 consecutive ones, with a carry
-// between chunks.  Replaces the three-kernel scan for the radix histograms of
-// a level (at most kSingleScanMax values).
-constexpr int kSingleScanThreads = 1024;
-constexpr int kSingleScanItems = 8;
-constexpr int64_t kSingleScanMax = 262144;
-
-__global__ void __launch_bounds__(kSingleScanThreads) scan_single_block_u32(const uint32_t* __restrict__ in,
-                                                                            uint32_t* __restrict__ out, int64_t n) {
-  __shared__ uint32_t ws[33];
-  uint32_t carry = 0;
-  constexpr int chunk = kSingleScanThreads * kSingleScanItems;
-  for (int64_t b = 0; b < n; b += chunk) {
-    const int64_t i0 = b + (int64_t)threadIdx.x * kSingleScanItems;
-    uint32_t v[kSingleScanItems];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int j = 0; j < kSingleScanItems; ++j) {
-      v[j] = i0 + j < n ? in[i0 + j] : 0u;
-      sum += v[j];
-    }
-    uint32_t tot;
-    uint32_t ex = block_exclusive<uint32_t>(sum, ws, &tot) + carry;
-#pragma unroll
-    for (int j = 0; j < kSingleScanItems; ++j) {
-      if (i0 + j < n) out[i0 + j] = ex;
-      ex += v[j];
-    }
-    carry += tot;
-  }
-}
-
 // ------------------------------- radix sort --------------------------------
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
+// LSD passes of B-bit digits, B in {6, 8, 9, 10} chosen per sort: the fewest
+// passes of at most 10 bits, then the smallest listed width covering the key
+// bits in that many passes (18-bit cell keys: 2 passes of 9 bits).
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = kSortTile / kSortThreads;  // 8
 constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kMaxRadixBits = 10;
 
 struct TileInfo {
   int64_t start;
@@ -176,7 +145,7 @@ struct TileInfo {
   int32_t stride;     // distance between digits (tiles in the segment)
 };
 
-__device__ inline TileInfo tile_info(const SortSegments& sg, int64_t n, int64_t t) {
+__device__ inline TileInfo tile_info(const SortSegments& sg, int64_t n, int64_t t, int radix) {
   TileInfo ti;
   if (sg.tile_seg == nullptr) {
     ti.start = t * kSortTile;
@@ -189,37 +158,127 @@ __device__ inline TileInfo tile_info(const SortSegments& sg, int64_t n, int64_t 
     int32_t t0 = sg.seg_tile0[seg], nt = sg.seg_tile0[seg + 1] - t0;
     ti.start = sg.tile_start[t];
     ti.count = sg.tile_count[t];
-    ti.hist_base = (int64_t)t0 * kRadix + (t - t0);
+    ti.hist_base = (int64_t)t0 * radix + (t - t0);
     ti.stride = nt;
   }
   return ti;
 }
 
-template <class K>
+template <class K, int BITS>
 __global__ void radix_hist_kernel(const K* __restrict__ keys, int64_t n, int shift, SortSegments sg,
                                   uint32_t* __restrict__ hist) {
-  __shared__ uint32_t h[kRadix];
-  for (int i = threadIdx.x; i < kRadix; i += blockDim.x) h[i] = 0;
+  constexpr int R = 1 << BITS;
+  __shared__ uint32_t h[R];
+  for (int i = threadIdx.x; i < R; i += blockDim.x) h[i] = 0;
   __syncthreads();
-  TileInfo ti = tile_info(sg, n, blockIdx.x);
+  TileInfo ti = tile_info(sg, n, blockIdx.x, R);
   for (int i = threadIdx.x; i < ti.count; i += blockDim.x) {
-    uint32_t dg = (uint32_t)(keys[ti.start + i] >> shift) & (kRadix - 1);
+    uint32_t dg = (uint32_t)(keys[ti.start + i] >> shift) & (R - 1);
     atomicAdd(&h[dg], 1u);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kRadix; i += blockDim.x) hist[ti.hist_base + (int64_t)i * ti.stride] = h[i];
+  for (int i = threadIdx.x; i < R; i += blockDim.x) hist[ti.hist_base + (int64_t)i * ti.stride] = h[i];
 }
 
-template <class K, bool HasVal>
+// Row prefix of the tile histograms: one thread per (segment, digit) row
+// (the counts of that digit in the segment's tiles, contiguous): exclusive
+// prefix in place, row total to rowtot.
+__global__ void radix_rowscan(uint32_t* __restrict__ hist, SortSegments sg, int R, int64_t nrows,
+                              uint32_t* __restrict__ rowtot) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const int seg = (int)(r / R), d = (int)(r % R);
+  int64_t t0 = 0, nt = sg.ntiles;
+  if (sg.tile_seg) {
+    t0 = sg.seg_tile0[seg];
+    nt = sg.seg_tile0[seg + 1] - t0;
+  }
+  if (nt > kLongSegTiles || nt <= 1) return;  // long: radix_rowscan_warp; single tile: the scatter's own counts
+  uint32_t* row = hist + t0 * R + (int64_t)d * nt;
+  uint32_t run = 0;
+  int64_t t = 0;
+  for (; t + 4 <= nt; t += 4) {
+    const uint32_t c0 = row[t], c1 = row[t + 1], c2 = row[t + 2], c3 = row[t + 3];
+    row[t] = run;
+    run += c0;
+    row[t + 1] = run;
+    run += c1;
+    row[t + 2] = run;
+    run += c2;
+    row[t + 3] = run;
+    run += c3;
+  }
+  for (; t < nt; ++t) {
+    const uint32_t c = row[t];
+    row[t] = run;
+    run += c;
+  }
+  rowtot[r] = run;
+}
+
+// Same for the rows of long segments (more than kLongSegTiles tiles), one
+// warp per row; nrows = R x the long segments (all rows when unsegmented).
+__global__ void radix_rowscan_warp(uint32_t* __restrict__ hist, SortSegments sg, int R, int64_t nrows,
+                                   uint32_t* __restrict__ rowtot) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= nrows) return;
+  const int lane = lane_id();
+  const int seg = sg.tile_seg ? sg.long_seg[w / R] : 0, d = (int)(w % R);
+  const int64_t r = (int64_t)seg * R + d;
+  int64_t t0 = 0, nt = sg.ntiles;
+  if (sg.tile_seg) {
+    t0 = sg.seg_tile0[seg];
+    nt = sg.seg_tile0[seg + 1] - t0;
+  }
+  uint32_t* row = hist + t0 * R + (int64_t)d * nt;
+  uint32_t carry = 0;
+  for (int64_t b = 0; b < nt; b += 32) {
+    const int64_t t = b + lane;
+    const uint32_t c = t < nt ? row[t] : 0u;
+    const uint32_t inc = warp_inclusive(c);
+    if (t < nt) row[t] = carry + inc - c;
+    carry += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  if (lane == 0) rowtot[r] = carry;
+}
+
+template <class K, bool HasVal, int BITS>
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
     const K* __restrict__ keys, const uint32_t* __restrict__ vals, K* __restrict__ keys_out,
-    uint32_t* __restrict__ vals_out, int64_t n, int shift, SortSegments sg, const uint32_t* __restrict__ offs) {
-  __shared__ uint32_t wcnt[kSortWarps][kRadix];
-  __shared__ uint32_t tbase[kRadix];
+    uint32_t* __restrict__ vals_out, int64_t n, int shift, SortSegments sg, const uint32_t* __restrict__ offs,
+    const uint32_t* __restrict__ rowtot) {
+  constexpr int R = 1 << BITS;
+  constexpr int PER = (R + kSortThreads - 1) / kSortThreads;
+  __shared__ uint32_t wcnt[kSortWarps][R];
+  __shared__ uint32_t tbase[R];
+  __shared__ uint32_t ws[33];
   const int lane = lane_id(), warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kSortWarps * kRadix; i += blockDim.x) (&wcnt[0][0])[i] = 0;
-  TileInfo ti = tile_info(sg, n, blockIdx.x);
-  for (int i = threadIdx.x; i < kRadix; i += blockDim.x) tbase[i] = offs[ti.hist_base + (int64_t)i * ti.stride];
+  for (int i = threadIdx.x; i < kSortWarps * R; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+  TileInfo ti = tile_info(sg, n, blockIdx.x, R);
+  const int seg = sg.tile_seg ? sg.tile_seg[blockIdx.x] : 0;
+  const int64_t seg_start = sg.seg_base ? sg.seg_base[seg] : 0;
+  const int64_t seg_tiles = sg.tile_seg ? sg.seg_tile0[seg + 1] - sg.seg_tile0[seg] : sg.ntiles;
+  const bool single = seg_tiles == 1;  // the tile is its whole segment: bases from its own counts
+  // destination of digit d in this tile: segment start + keys of the segment
+  // with a smaller digit (scan of the row totals) + keys of digit d in the
+  // segment's earlier tiles (row prefix)
+  if (!single) {
+    uint32_t v[PER];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int d = threadIdx.x * PER + j;
+      v[j] = d < R ? rowtot[(int64_t)seg * R + d] : 0u;
+      sum += v[j];
+    }
+    uint32_t ex = block_exclusive<uint32_t>(sum, ws, nullptr) + (uint32_t)seg_start;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int d = threadIdx.x * PER + j;
+      if (d < R) tbase[d] = ex + offs[ti.hist_base + (int64_t)d * ti.stride];
+      ex += v[j];
+    }
+  }
   __syncthreads();
   K key[kSortItems];
   uint32_t val[kSortItems];
@@ -232,7 +291,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
     bool valid = idx < ti.count;
     key[j] = valid ? keys[ti.start + idx] : K(0);
     if (HasVal) val[j] = valid ? vals[ti.start + idx] : 0u;
-    uint32_t dg = valid ? ((uint32_t)(key[j] >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
+    uint32_t dg = valid ? ((uint32_t)(key[j] >> shift) & (R - 1)) : (uint32_t)R;
     dig[j] = dg;
     unsigned peers = __match_any_sync(0xffffffffu, dg);
     uint32_t before = __popc(peers & lt);
@@ -243,22 +302,67 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
     __syncwarp();
   }
   __syncthreads();
-  for (int dg = threadIdx.x; dg < kRadix; dg += blockDim.x) {
+  for (int dg = threadIdx.x; dg < R; dg += blockDim.x) {
     uint32_t run = 0;
     for (int w = 0; w < kSortWarps; ++w) {
       uint32_t c = wcnt[w][dg];
       wcnt[w][dg] = run;
       run += c;
     }
+    if (single) tbase[dg] = run;  // the tile's count of digit dg
   }
   __syncthreads();
+  if (single) {  // exclusive scan of the tile's digit counts (block-uniform branch)
+    uint32_t v[PER];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int d = threadIdx.x * PER + j;
+      v[j] = d < R ? tbase[d] : 0u;
+      sum += v[j];
+    }
+    uint32_t ex = block_exclusive<uint32_t>(sum, ws, nullptr) + (uint32_t)seg_start;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int d = threadIdx.x * PER + j;
+      if (d < R) tbase[d] = ex;
+      ex += v[j];
+    }
+    __syncthreads();
+  }
 #pragma unroll
   for (int j = 0; j < kSortItems; ++j) {
-    if (dig[j] >= (uint32_t)kRadix) continue;
+    if (dig[j] >= (uint32_t)R) continue;
     uint32_t dst = tbase[dig[j]] + wcnt[warp][dig[j]] + rank[j];
     keys_out[dst] = key[j];
     if (HasVal) vals_out[dst] = val[j];
   }
+}
+
+inline int digit_bits(int bits, int* passes) {
+  const int p = (bits + kMaxRadixBits - 1) / kMaxRadixBits;
+  const int need = (bits + p - 1) / p;
+  *passes = p;
+  return need <= 6 ? 6 : need <= 8 ? 8 : need <= 9 ? 9 : 10;
+}
+
+template <class K, int BITS>
+void radix_pass(const K* ka, const uint32_t* va, K* kb, uint32_t* vb, int64_t n, int shift, const SortSegments& sg,
+                uint32_t* hist, uint32_t* rowtot, cudaStream_t s) {
+  constexpr int R = 1 << BITS;
+  const int64_t nrows = (int64_t)(sg.tile_seg ? sg.nseg : 1) * R;
+  launch(radix_hist_kernel<K, BITS>, (unsigned)sg.ntiles, 256, 0, s, ka, n, shift, sg, hist);
+  const int64_t nlong = sg.tile_seg ? sg.nlong : (sg.ntiles > kLongSegTiles ? 1 : 0);
+  if (nlong > 0)
+    launch(radix_rowscan_warp, (unsigned)((nlong * R * 32 + 255) / 256), 256, 0, s, hist, sg, R, nlong * R, rowtot);
+  if (sg.tile_seg ? sg.nmid > 0 : (sg.ntiles > 1 && nlong == 0))
+    launch(radix_rowscan, (unsigned)((nrows + 255) / 256), 256, 0, s, hist, sg, R, nrows, rowtot);
+  if (va)
+    launch(radix_scatter_kernel<K, true, BITS>, (unsigned)sg.ntiles, kSortThreads, 0, s, ka, va, kb, vb, n, shift, sg,
+           hist, rowtot);
+  else
+    launch(radix_scatter_kernel<K, false, BITS>, (unsigned)sg.ntiles, kSortThreads, 0, s, ka, nullptr, kb, nullptr, n,
+           shift, sg, hist, rowtot);
 }
 
 template <class K>
@@ -269,32 +373,29 @@ vmo_status radix_sort_impl(K* keys_in, uint32_t* vals_in, K* keys_out, uint32_t*
   SortSegments sg;
   if (segs) sg = *segs;
   if (sg.tile_seg == nullptr) sg.ntiles = (n + kSortTile - 1) / kSortTile;
-  int passes = (bits + kRadixBits - 1) / kRadixBits;
+  int passes = 0;
+  const int B = bits > 0 ? digit_bits(bits, &passes) : 8;
   if (passes == 0) {
     if (in_b) return VMO_OK;  // already sorted, left in place
     VMO_CUDA(cudaMemcpyAsync(keys_out, keys_in, n * sizeof(K), cudaMemcpyDeviceToDevice, s));
     if (vals_in) VMO_CUDA(cudaMemcpyAsync(vals_out, vals_in, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     return VMO_OK;
   }
-  int64_t hn = sg.ntiles * kRadix;
-  uint32_t* hist;
-  VMO_TRY(sc.alloc(&hist, (size_t)hn));
+  uint32_t *hist, *rowtot;
+  VMO_TRY(sc.alloc(&hist, (size_t)(sg.ntiles << B)));
+  VMO_TRY(sc.alloc(&rowtot, (size_t)(sg.tile_seg ? sg.nseg : 1) << B));
   K* ka = keys_in;
   K* kb = keys_out;
   uint32_t* va = vals_in;
   uint32_t* vb = vals_out;
   for (int p = 0; p < passes; ++p) {
-    int shift = p * kRadixBits;
-    launch(radix_hist_kernel<K>, (unsigned)sg.ntiles, 256, 0, s, ka, n, shift, sg, hist);
-    if (hn <= kSingleScanMax)
-      launch(scan_single_block_u32, 1, kSingleScanThreads, 0, s, hist, hist, hn);
-    else
-      VMO_TRY((scan_impl<uint32_t, false>(hist, hist, hn, nullptr, s, sc)));
-    if (vals_in)
-      launch(radix_scatter_kernel<K, true>, (unsigned)sg.ntiles, kSortThreads, 0, s, ka, va, kb, vb, n, shift, sg, hist);
-    else
-      launch(radix_scatter_kernel<K, false>, (unsigned)sg.ntiles, kSortThreads, 0, s, ka, nullptr, kb, nullptr, n, shift,
-                                                                                   sg, hist);
+    const int shift = p * B;
+    switch (B) {
+      case 6: radix_pass<K, 6>(ka, va, kb, vb, n, shift, sg, hist, rowtot, s); break;
+      case 8: radix_pass<K, 8>(ka, va, kb, vb, n, shift, sg, hist, rowtot, s); break;
+      case 9: radix_pass<K, 9>(ka, va, kb, vb, n, shift, sg, hist, rowtot, s); break;
+      default: radix_pass<K, 10>(ka, va, kb, vb, n, shift, sg, hist, rowtot, s); break;
+    }
     VMO_LAUNCHED("radix_sort");
     K* tk = ka; ka = kb; kb = tk;
     uint32_t* tv = va; va = vb; vb = tv;
@@ -400,6 +501,22 @@ vmo_status make_sort_segments(const std::vector<int64_t>& base, SortSegments* ou
   out->tile_count = d_tcount;
   out->seg_tile0 = d_t0;
   out->ntiles = nt;
+  std::vector<int32_t> lg;
+  int32_t nmid = 0;
+  for (int32_t g = 0; g < nseg; ++g) {
+    const int32_t tiles = t0[g + 1] - t0[g];
+    if (tiles > kLongSegTiles) lg.push_back(g);
+    else if (tiles > 1) ++nmid;
+  }
+  out->nlong = (int32_t)lg.size();
+  out->nmid = nmid;
+  if (!lg.empty()) {
+    int32_t* d_lg;
+    VMO_TRY(sc.alloc(&d_lg, lg.size()));
+    VMO_CUDA(cudaMemcpyAsync(d_lg, lg.data(), lg.size() * 4, cudaMemcpyHostToDevice, s));
+    VMO_CUDA(cudaStreamSynchronize(s));  // lg must outlive the copy
+    out->long_seg = d_lg;
+  }
   return VMO_OK;
 }
 

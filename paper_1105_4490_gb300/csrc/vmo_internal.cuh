@@ -195,7 +195,11 @@ struct SortSegments {
   const int32_t* tile_count = nullptr;// device, per tile: elements
   const int32_t* seg_tile0 = nullptr; // device, per segment: first tile (nseg+1)
   int64_t ntiles = 0;
+  const int32_t* long_seg = nullptr;  // device, segments of more than kLongSegTiles tiles
+  int32_t nlong = 0;
+  int32_t nmid = 0;                   // segments of 2..kLongSegTiles tiles
 };
+constexpr int kLongSegTiles = 16;
 constexpr int kSortTile = 2048;  // 256 threads x 8 keys
 
 // Stable LSD radix sort of (key, value) pairs on bits [0, bits).  Keys are

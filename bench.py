@@ -42,6 +42,10 @@ METRIC = "nnz ordered/sec (recursive BBD)"
 FLOPS_PER_INTERACTION = {2: 10, 3: 18, 4: 23}
 FP32_LANES_PER_SM = 128
 SMS = 152
+# DRAM bytes (read + write) per launch of the step kernel, averaged over the
+# 3,000 launches of one step of the medium workload: one ncu capture of the
+# current kernel, summarised in profiles/k_repulse_update_traffic_medium.md
+STEP_KERNEL_TRAFFIC_BYTES = 4_370_494
 
 
 def medium_workload():
@@ -401,7 +405,9 @@ def main():
     achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
     peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": "k_repulse_update<3> (layout step)", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": STEP_KERNEL_TRAFFIC_BYTES,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the "
+                                "3,000 launches of one step)",
                 "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x median SM clock "
                                f"{sm_mhz:.0f} MHz during the timed region",
                 "interactions_per_launch": inter_per_step / launches_per_step,

@@ -687,7 +687,8 @@ __device__ inline void bbox_warp_partial(const float4& v, bool valid, uint32_t* 
   }
 }
 
-// Bounding boxes from the step kernel's per-warp partials: one thread per
+// Bounding boxes from the step kernel's per-warp partials (and the level's
+// step counter advanced for the next step): one thread per
 // partial, lanes of the same problem combine with a warp reduction and one of
 // them folds the result into the problem's box with atomic min / max (the box
 // was reset by k_keys earlier in the same iteration; min and max of the
@@ -695,8 +696,9 @@ __device__ inline void bbox_warp_partial(const float4& v, bool valid, uint32_t* 
 // not matter).
 __global__ void __launch_bounds__(kBlock) k_bbox_reduce(const uint32_t* __restrict__ part,
                                                         const int64_t* __restrict__ tbase, int P, int64_t nwarps,
-                                                        uint32_t* __restrict__ bb) {
+                                                        uint32_t* __restrict__ bb, int32_t* __restrict__ tctr) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) ++*tctr;  // the step of the level: read by the step kernel, which ran before this one
   const bool valid = i < nwarps;
   const int pb = valid ? find_problem(tbase, P, i * 32) : -1;
   uint4 mn = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu), mx = make_uint4(0u, 0u, 0u, 0u);
@@ -751,7 +753,8 @@ __global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_upda
     const float4* __restrict__ xs, const float* __restrict__ ws, const float4* __restrict__ XP,
     const uint32_t* __restrict__ svals, const uint32_t* __restrict__ scell, const int32_t* __restrict__ cst,
     const float4* __restrict__ CP, const float4* __restrict__ yatt, const int64_t* __restrict__ tbase, int P,
-    const ProbDev* __restrict__ prob, int64_t T, float kappa, const float* __restrict__ s0, float scale,
+    const ProbDev* __restrict__ prob, int64_t T, float kappa, const float* __restrict__ s0,
+    const float* __restrict__ scale_tab, const int32_t* __restrict__ tctr,
     float step_override, float4* __restrict__ x, float4* __restrict__ y_out, uint32_t* __restrict__ bb_part,
     unsigned long long* __restrict__ icount) {
   constexpr int N = Pair<D>::N;
@@ -855,7 +858,7 @@ __global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_upda
     float y3 = D > 3 ? kappa * wn * Fs[3] + ya.w : 0.f;
     if (y_out) y_out[v] = make_float4(y0, y1, y2, y3);
     float ny = sqrtf(y0 * y0 + y1 * y1 + y2 * y2 + y3 * y3);
-    float step = step_override > 0.0f ? step_override : s0[pb] * scale;
+    float step = step_override > 0.0f ? step_override : s0[pb] * scale_tab[*tctr];
     float a = ny > 0.0f ? step / ny : 0.0f;
     xnew = make_float4(xn.x - a * y0, D > 1 ? xn.y - a * y1 : 0.f, D > 2 ? xn.z - a * y2 : 0.f,
                        D > 3 ? xn.w - a * y3 : 0.f);
@@ -1240,27 +1243,45 @@ vmo_status init_coords_level(LevelBatch& lb, int d, const uint64_t* seeds_dev, f
   return VMO_OK;
 }
 
-// A second stream with fork / join events for one layout call; destroyed (in
-// stream order) when the call returns.
+constexpr int kGraphMinIters = 8;
+
+// Streams of one layout call: `side` for the attraction (fork / join events
+// per step) and `main` for the steps when they are replayed from a graph
+// (capture needs a stream of its own: the caller's may be the legacy stream);
+// destroyed in stream order when the call returns.
 struct SideStream {
-  cudaStream_t stream = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t stream = nullptr, main = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, start = nullptr, done = nullptr;
   SideStream() {
     if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&main, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
       (void)cudaGetLastError();
       release();
     }
   }
   void release() {
-    if (fork) cudaEventDestroy(fork);
-    if (join) cudaEventDestroy(join);
+    for (cudaEvent_t* e : {&fork, &join, &start, &done}) {
+      if (*e) cudaEventDestroy(*e);
+      *e = nullptr;
+    }
     if (stream) cudaStreamDestroy(stream);
-    stream = nullptr;
-    fork = join = nullptr;
+    if (main) cudaStreamDestroy(main);
+    stream = main = nullptr;
   }
   ~SideStream() { release(); }
+};
+
+// Points a Scratch at another stream for a scope (its allocations and frees
+// then follow that stream's order).
+struct ScratchOnStream {
+  Scratch& sc;
+  cudaStream_t prev;
+  ScratchOnStream(Scratch& s, cudaStream_t st) : sc(s), prev(s.stream) { sc.stream = st; }
+  ~ScratchOnStream() { sc.stream = prev; }
 };
 
 vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int iters, float step_override,
@@ -1305,6 +1326,24 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
   launch(k_bbox_reset, grid_for(16 * P, kBlock), kBlock, 0, s, bb, 16 * P);
   VMO_LAUNCHED("bbox_reset");
   const float kappa = d == 2 ? 1.0f : (float)(d - 2);
+  // step lengths s0 * decay^t: decay^t as the running double product, rounded
+  // to fp32 (a table read by the step kernel at the level's step counter,
+  // which k_bbox_reduce advances)
+  float* scale_tab;
+  int32_t* tctr;
+  VMO_TRY(sc.alloc(&scale_tab, iters));
+  VMO_TRY(sc.alloc(&tctr, 1));
+  {
+    std::vector<float> tab(iters);
+    double scale = 1.0;
+    for (int t = 0; t < iters; ++t) {
+      tab[t] = (float)scale;
+      scale *= o.decay;
+    }
+    VMO_CUDA(cudaMemcpyAsync(scale_tab, tab.data(), iters * sizeof(float), cudaMemcpyHostToDevice, s));
+    VMO_CUDA(cudaStreamSynchronize(s));  // tab must outlive the copy
+  }
+  VMO_CUDA(cudaMemsetAsync(tctr, 0, sizeof(int32_t), s));
   vmo_status st = VMO_OK;
   SideStream ss;  // attraction stream of this call (none if it cannot be created)
   cudaStream_t side = ss.stream;
@@ -1313,16 +1352,18 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
     constexpr int D = decltype(DC)::value;
     launch(k_bbox<D>, grid_for(K, kBlock), kBlock, 0, s, x, K, lb.vprob.ptr, bb);
     launch(k_step0<D>, grid_for(P, kBlock), kBlock, 0, s, bb, lb.prob.ptr, P, o.sigma, s0);
-    double scale = 1.0;
-    for (int t = 0; t < iters && st == VMO_OK; ++t) {
+    cudaStream_t ms = s;  // stream of the steps
+    // one step t of Algorithm 4 for every problem (only the parity of t and
+    // whether it is the first step matter to the launches)
+    auto step = [&](int t) -> vmo_status {
       ScratchFrame f2(sc);
       uint32_t* cur = bb + (t & 1) * 8 * P;
       uint32_t* nxt = bb + ((t + 1) & 1) * 8 * P;
       // attraction depends only on x: it runs on the side stream, overlapped
       // with the binning below, and joins before the step kernel
-      cudaStream_t as = side ? side : s;
+      cudaStream_t as = side ? side : ms;
       if (side) {
-        cudaEventRecord(ev_fork, s);
+        cudaEventRecord(ev_fork, ms);
         cudaStreamWaitEvent(side, ev_fork, 0);
       }
       if (lb.adj_ptr) {
@@ -1340,20 +1381,19 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
         cudaMemsetAsync(yatt, 0, K * sizeof(float4), as);
       }
       if (side) cudaEventRecord(ev_join, side);
-      launch(k_keys<D>, grid_for(std::max<int64_t>(K, nreset), kBlock), kBlock, 0, s, x, K, lb.vprob.ptr, lb.prob.ptr,
+      launch(k_keys<D>, grid_for(std::max<int64_t>(K, nreset), kBlock), kBlock, 0, ms, x, K, lb.vprob.ptr, lb.prob.ptr,
                                                                                   cur, keys, vals, nxt, nreset);
-      if (keys_out && t == 0) cudaMemcpyAsync(keys_out, keys, K * 4, cudaMemcpyDeviceToDevice, s);
+      if (keys_out && t == 0) cudaMemcpyAsync(keys_out, keys, K * 4, cudaMemcpyDeviceToDevice, ms);
       bool in_b = false;
-      st = radix_sort_u32_pingpong(keys, vals, skeys, svals, K, D * lb.maxL, segmented ? &segs : nullptr, &in_b, s,
-                                   sc);
-      if (st != VMO_OK) break;
+      VMO_TRY(radix_sort_u32_pingpong(keys, vals, skeys, svals, K, D * lb.maxL, segmented ? &segs : nullptr, &in_b, ms,
+                                      sc));
       if (!in_b) {  // sorted pairs are in (keys, vals): use them as (skeys, svals) from here on
         std::swap(keys, skeys);
         std::swap(vals, svals);
       }
-      launch(k_gather<D>, grid_for(K, kBlock), kBlock, 0, s, svals, skeys, K, x, lb.w, lb.vprob.ptr, lb.prob.ptr, cur,
+      launch(k_gather<D>, grid_for(K, kBlock), kBlock, 0, ms, svals, skeys, K, x, lb.w, lb.vprob.ptr, lb.prob.ptr, cur,
              xs, ws, scell, cst, XP);
-      launch(k_agg_finest<D>, grid_for(nfine, kBlock), kBlock, 0, s, nfine, fb, P, lb.prob.ptr, xs, ws, cst, St, Wt,
+      launch(k_agg_finest<D>, grid_for(nfine, kBlock), kBlock, 0, ms, nfine, fb, P, lb.prob.ptr, xs, ws, cst, St, Wt,
              CP);
       for (int stp = 1; stp <= lb.maxL - 2; ++stp) {
         const int64_t* off = lb.aggoff.ptr + (size_t)stp * (P + 1);
@@ -1363,26 +1403,74 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
           n += l > small_level_max(D) ? (int64_t(1) << (D * l)) : 0;
         }
         if (n == 0) continue;
-        launch(k_agg_level<D>, grid_for(n, kBlock), kBlock, 0, s, stp, off, P, n, lb.prob.ptr, St, Wt, CP);
+        launch(k_agg_level<D>, grid_for(n, kBlock), kBlock, 0, ms, stp, off, P, n, lb.prob.ptr, St, Wt, CP);
       }
-      if (lb.maxL >= 3) launch(k_agg_small<D>, (unsigned)P, kBlock, 0, s, lb.prob.ptr, St, Wt, CP);
-      if (side) cudaStreamWaitEvent(s, ev_join, 0);
+      if (lb.maxL >= 3) launch(k_agg_small<D>, (unsigned)P, kBlock, 0, ms, lb.prob.ptr, St, Wt, CP);
+      if (side) cudaStreamWaitEvent(ms, ev_join, 0);
       const bool timed = stats_timing();
-      if (timed) stats_time_begin(s);
+      if (timed) stats_time_begin(ms);
       unsigned long long* icount = stats_interaction_counter();
       if (icount)
-        launch(k_repulse_update<D, true>, grid_for(lb.threads, kStepBlock), kStepBlock, 0, s, xs, ws, XP, svals,
-               scell, cst, CP, yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, (float)scale, step_override,
-               x, y_out, bpart, icount);
+        launch(k_repulse_update<D, true>, grid_for(lb.threads, kStepBlock), kStepBlock, 0, ms, xs, ws, XP, svals,
+               scell, cst, CP, yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, scale_tab, tctr,
+               step_override, x, y_out, bpart, icount);
       else
-        launch(k_repulse_update<D, false>, grid_for(lb.threads, kStepBlock), kStepBlock, 0, s, xs, ws, XP, svals,
-               scell, cst, CP, yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, (float)scale, step_override,
-               x, y_out, bpart, icount);
-      if (timed) stats_time_end(s, (uint64_t)K);
-      launch(k_bbox_reduce, grid_for(nwarps, kBlock), kBlock, 0, s, bpart, lb.tbase.ptr, P, nwarps, nxt);
+        launch(k_repulse_update<D, false>, grid_for(lb.threads, kStepBlock), kStepBlock, 0, ms, xs, ws, XP, svals,
+               scell, cst, CP, yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, scale_tab, tctr,
+               step_override, x, y_out, bpart, icount);
+      if (timed) stats_time_end(ms, (uint64_t)K);
+      launch(k_bbox_reduce, grid_for(nwarps, kBlock), kBlock, 0, ms, bpart, lb.tbase.ptr, P, nwarps, nxt, tctr);
       cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) st = cuda_fail(e, "layout step", __FILE__, __LINE__);
-      scale *= o.decay;
+      if (e != cudaSuccess) return cuda_fail(e, "layout step", __FILE__, __LINE__);
+      return VMO_OK;
+    };
+    // Steps are replayed from a CUDA graph of two steps (even and odd parity)
+    // when the level runs plain steps; the host then issues one graph launch
+    // per two steps instead of ~20 kernel launches per step.
+    const bool graphs = ss.main && iters >= kGraphMinIters && !y_out && !keys_out && step_override <= 0.0f &&
+                        !stats_timing() && !stats_interaction_counter();
+    int t = 0;
+    if (graphs) {
+      // the steps run on the call's own stream, joined back to s at the end
+      cudaEventRecord(ss.start, s);
+      cudaStreamWaitEvent(ss.main, ss.start, 0);
+      ms = ss.main;
+    }
+    ScratchOnStream on(sc, ms);  // scratch of a step follows the stream of the step
+    if (graphs) {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      const uint64_t before = g_launches.load();
+      bool ok = cudaStreamBeginCapture(ms, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      vmo_status cst0 = VMO_OK;
+      if (ok) {
+        cst0 = step(0);
+        if (cst0 == VMO_OK) cst0 = step(1);
+        ok = cudaStreamEndCapture(ms, &g) == cudaSuccess && cst0 == VMO_OK;
+      }
+      if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+      const uint64_t per_graph = g_launches.load() - before;
+      g_launches.fetch_sub(per_graph);  // captured, not launched: counted per replay below
+      if (ok) {
+        for (; t + 2 <= iters; t += 2) {
+          cudaError_t e = cudaGraphLaunch(ge, ms);
+          if (e != cudaSuccess) {
+            st = cuda_fail(e, "cudaGraphLaunch (layout steps)", __FILE__, __LINE__);
+            break;
+          }
+          g_launches.fetch_add(per_graph);
+        }
+      } else {
+        (void)cudaGetLastError();  // fall back to direct launches
+        if (cst0 != VMO_OK) st = cst0;
+      }
+      if (ge) cudaGraphExecDestroy(ge);
+      if (g) cudaGraphDestroy(g);
+    }
+    for (; t < iters && st == VMO_OK; ++t) st = step(t);
+    if (ms != s) {
+      cudaEventRecord(ss.done, ms);
+      cudaStreamWaitEvent(s, ss.done, 0);
     }
   });
   return st;

@@ -379,10 +379,26 @@ def main():
     tmax = float(t.item())
     value = nnz * world / tmax
 
-    # end to end through the public API: pinned host CSR -> permutations on the host
+    # end to end through the public API: pinned host CSR -> permutations in
+    # pinned host memory (one untimed warm-up pass, then K timed passes)
     host_csr = [(torch.as_tensor(A.rowptr).pin_memory(), torch.as_tensor(A.colidx).pin_memory()) for A, _ in mats]
+    host_out = [(torch.empty(A.m, dtype=torch.int32).pin_memory(), torch.empty(A.n, dtype=torch.int32).pin_memory())
+                for A, _ in mats]
     h2d = sum(r.numel() * 4 + c.numel() * 4 for r, c in host_csr)
-    d2h = 0
+    d2h = sum(r.numel() * 4 + c.numel() * 4 for r, c in host_out)
+
+    def e2e_pass():
+        for (A, cfg), (rp, ci), (ro, co) in zip(mats, host_csr, host_out):
+            hg = V.Hypergraph(rp.cuda(non_blocking=True), ci.cuda(non_blocking=True), A.m, A.n, "symmetric")
+            p = V.Params(d=cfg["d"], max_depth=cfg["max_depth"], seed=params["seed"])
+            rperm, cperm, _ = hg.order(p, None, sbd=False, with_tree=False)
+            ro.copy_(rperm, non_blocking=True)
+            co.copy_(cperm, non_blocking=True)
+            del hg
+
+    V.stats_reset(time_step_kernel=False, count_interactions=False)  # plain library calls, as in the timed region
+    e2e_pass()
+    barrier()
     e2e_time = 0.0
     for _ in range(args.steps):
         flush.fill_(1.0)
@@ -390,15 +406,7 @@ def main():
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        d2h = 0
-        for (A, cfg), (rp, ci) in zip(mats, host_csr):
-            hg = V.Hypergraph(rp.cuda(non_blocking=True), ci.cuda(non_blocking=True), A.m, A.n, "symmetric")
-            p = V.Params(d=cfg["d"], max_depth=cfg["max_depth"], seed=params["seed"])
-            rperm, cperm, _ = hg.order(p, None, sbd=False, with_tree=False)
-            rh = rperm.to("cpu", non_blocking=False)
-            ch = cperm.to("cpu", non_blocking=False)
-            d2h += rh.numel() * 4 + ch.numel() * 4
-            del hg
+        e2e_pass()
         b.record(stream)
         barrier()
         e2e_time += a.elapsed_time(b) / 1e3

@@ -560,8 +560,10 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 constexpr float kR2Floor = 1e-15f;
 
 // F += w r^-d (src - xn) for the two sources of a pair; nx holds -xn twice
-// per coordinate, w the (masked) weights.
-template <int D>
+// per coordinate, w the (masked) weights.  UNIT: both weights are 1 (the
+// multiply by w is left out; a half is masked by giving it the target's own
+// coordinates instead, so that its dx = 0 contributes 0).
+template <int D, bool UNIT = false>
 __device__ __forceinline__ void pair_charge(float2* F, const float4* P, const float2* nx, float2 w) {
   float2 dx[D];
   dx[0] = __fadd2_rn(make_float2(P[0].x, P[0].y), nx[0]);
@@ -573,16 +575,29 @@ __device__ __forceinline__ void pair_charge(float2* F, const float4* P, const fl
   for (int m = 0; m < D; ++m) r2 = __ffma2_rn(dx[m], dx[m], r2);
   float2 g;
   if (D == 2) {
-    g = __fmul2_rn(w, make_float2(rcp_approx(r2.x), rcp_approx(r2.y)));
+    const float2 i2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    g = UNIT ? i2 : __fmul2_rn(w, i2);
   } else if (D == 3) {
     const float2 ir = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-    g = __fmul2_rn(__fmul2_rn(w, ir), __fmul2_rn(ir, ir));
+    g = UNIT ? __fmul2_rn(ir, __fmul2_rn(ir, ir)) : __fmul2_rn(__fmul2_rn(w, ir), __fmul2_rn(ir, ir));
   } else {
     const float2 i2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
-    g = __fmul2_rn(__fmul2_rn(w, i2), i2);
+    g = UNIT ? __fmul2_rn(i2, i2) : __fmul2_rn(__fmul2_rn(w, i2), i2);
   }
 #pragma unroll
   for (int m = 0; m < D; ++m) F[m] = __ffma2_rn(g, dx[m], F[m]);
+}
+
+// Gives half h of a pair the target's coordinates (-nx), so it contributes 0.
+template <int D>
+__device__ __forceinline__ void pair_mask_half(float4* P, int h, bool mask, const float2* nx) {
+  float* f = reinterpret_cast<float*>(P);
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    const int i = 4 * (m >> 1) + 2 * (m & 1);
+    if (h == 0) f[i] = mask ? -nx[m].x : f[i];
+    else f[i + 1] = mask ? -nx[m].x : f[i + 1];
+  }
 }
 
 template <int D>
@@ -728,6 +743,57 @@ __global__ void __launch_bounds__(kBlock) k_bbox_reduce(const uint32_t* __restri
   if (mx.w) atomicMax(b + 7, mx.w);
 }
 
+// Near field of one row range [qa, qb) of problem-local sorted positions for
+// one lane of the target's group: source pairs j = qa/2 + lane_g, + G, ...,
+// four pairs per trip (all loads issued before the arithmetic; the order of
+// the pairs in the sums is the same as one pair per trip).  Only the first
+// pair can start before qa and only the last can end at or after qb; those
+// halves are masked (weight 0, or the target's own coordinates when UNIT).
+template <int D, bool COUNT, bool UNIT>
+__device__ __forceinline__ void near_range(const float4* __restrict__ xp, int qa, int qb, int G, int lane_g,
+                                           int64_t tgt, const float2* nx, float2* F, unsigned long long& nint) {
+  constexpr int N = Pair<D>::N;
+  int j = (qa >> 1) + lane_g;
+  for (; 2 * (j + 3 * G) < qb; j += 4 * G) {
+    float4 Q[4][N];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int i = 0; i < N; ++i) Q[u][i] = xp[(int64_t)(j + u * G) * N + i];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int h0 = 2 * (j + u * G);
+      float2 w = make_float2(1.0f, 1.0f);
+      if (UNIT) {
+        if (u == 0) pair_mask_half<D>(Q[u], 0, h0 < qa, nx);
+        if (u == 3) pair_mask_half<D>(Q[u], 1, h0 + 1 >= qb, nx);
+      } else {
+        w = pair_weight<D>(Q[u]);
+        if (u == 0) w.x = h0 >= qa ? w.x : 0.0f;
+        if (u == 3) w.y = h0 + 1 < qb ? w.y : 0.0f;
+      }
+      pair_charge<D, UNIT>(F, Q[u], nx, w);
+      if (COUNT) nint += (h0 >= qa && h0 != tgt) + (h0 + 1 < qb && h0 + 1 != tgt);
+    }
+  }
+  for (; 2 * j < qb; j += G) {
+    float4 Q[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) Q[i] = xp[(int64_t)j * N + i];
+    float2 w = make_float2(1.0f, 1.0f);
+    if (UNIT) {
+      pair_mask_half<D>(Q, 0, 2 * j < qa, nx);
+      pair_mask_half<D>(Q, 1, 2 * j + 1 >= qb, nx);
+    } else {
+      w = pair_weight<D>(Q);
+      w.x = 2 * j >= qa ? w.x : 0.0f;
+      w.y = 2 * j + 1 < qb ? w.y : 0.0f;
+    }
+    pair_charge<D, UNIT>(F, Q, nx, w);
+    if (COUNT) nint += (2 * j >= qa && 2 * j != tgt) + (2 * j + 1 < qb && 2 * j + 1 != tgt);
+  }
+}
+
 // Gradient (eq. graphenergygradientsimple with the grid pyramid) and step of
 // every target.  Each problem gives its targets G lanes (G from the problem's
 // own size), padded to whole warps; the lanes of a group split the near field
@@ -801,35 +867,10 @@ __global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_upda
       if (!inside) continue;
       const int64_t r0 = rowmajor<D>(cc, side);
       const int qa = cs[r0] - (int)pr.vbase, qb = cs[r0 + (xb - xa) + 1] - (int)pr.vbase;  // problem-local
-      // four pairs per trip (all loads issued before the arithmetic); the
-      // order of the pairs in the sums is the same as one pair per trip
-      int j = (qa >> 1) + lane_g;
-      for (; 2 * (j + 3 * G) < qb; j += 4 * G) {
-        float4 Q[4][N];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int i = 0; i < N; ++i) Q[u][i] = xp[(int64_t)(j + u * G) * N + i];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          float2 w = pair_weight<D>(Q[u]);
-          const int h0 = 2 * (j + u * G);
-          if (u == 0) w.x = h0 >= qa ? w.x : 0.0f;       // only the first pair can start before qa
-          if (u == 3) w.y = h0 + 1 < qb ? w.y : 0.0f;    // only the last pair can end after qb
-          pair_charge<D>(F, Q[u], nx, w);
-          if (COUNT) nint += (h0 >= qa && h0 != tgt) + (h0 + 1 < qb && h0 + 1 != tgt);
-        }
-      }
-      for (; 2 * j < qb; j += G) {
-        float4 Q[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) Q[i] = xp[(int64_t)j * N + i];
-        float2 w = pair_weight<D>(Q);
-        w.x = 2 * j >= qa ? w.x : 0.0f;
-        w.y = 2 * j + 1 < qb ? w.y : 0.0f;
-        pair_charge<D>(F, Q, nx, w);
-        if (COUNT) nint += (2 * j >= qa && 2 * j != tgt) + (2 * j + 1 < qb && 2 * j + 1 != tgt);
-      }
+      if (ws)
+        near_range<D, COUNT, false>(xp, qa, qb, G, lane_g, tgt, nx, F, nint);
+      else
+        near_range<D, COUNT, true>(xp, qa, qb, G, lane_g, tgt, nx, F, nint);
     }
     // far field, levels 2..L
     for (int l = 2; l <= L; ++l) {

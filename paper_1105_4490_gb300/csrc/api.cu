@@ -13,6 +13,7 @@ namespace vmo {
 static thread_local std::string g_last_error;
 thread_local cudaStream_t g_devarray_stream = nullptr;
 thread_local bool g_devarray_async = false;
+thread_local bool g_pdl = false;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 

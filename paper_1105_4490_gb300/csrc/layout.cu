@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(kBlock) k_keys(const float4* __restrict__ x, i
                                                  const ProbDev* __restrict__ prob, const uint32_t* __restrict__ bb,
                                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                  uint32_t* __restrict__ bb_next, int nreset) {
+  pdl_wait();
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v < nreset) bb_next[v] = ((v & 7) < 4) ? 0xFFFFFFFFu : 0u;
   if (v >= K) return;
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(const uint32_t* __restrict__ 
                                                    const uint32_t* __restrict__ bb, float4* __restrict__ xs,
                                                    float* __restrict__ ws, uint32_t* __restrict__ scell,
                                                    int32_t* __restrict__ cst, float4* __restrict__ XP) {
+  pdl_wait();
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= K) return;
   uint32_t v = svals[p];
@@ -294,6 +296,7 @@ __global__ void __launch_bounds__(kBlock) k_agg_finest(int64_t ncells, const int
                                                        const float* __restrict__ ws, int32_t* __restrict__ cst,
                                                        float4* __restrict__ St, float* __restrict__ Wt,
                                                        float4* __restrict__ CP) {
+  pdl_wait();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = i < ncells;
   int64_t q0 = 0, q1 = 0, idx = 0, pidx = 0;
@@ -379,6 +382,7 @@ template <int D>
 __global__ void __launch_bounds__(kBlock) k_agg_level(int step, const int64_t* __restrict__ off, int P, int64_t ncells,
                                                       const ProbDev* __restrict__ prob, float4* __restrict__ St,
                                                       float* __restrict__ Wt, float4* __restrict__ CP) {
+  pdl_wait();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ncells) return;
   int pb = find_problem(off, P, i);
@@ -389,6 +393,7 @@ __global__ void __launch_bounds__(kBlock) k_agg_level(int step, const int64_t* _
 template <int D>
 __global__ void __launch_bounds__(kBlock) k_agg_small(const ProbDev* __restrict__ prob, float4* __restrict__ St,
                                                       float* __restrict__ Wt, float4* __restrict__ CP) {
+  pdl_wait();
   const int pb = blockIdx.x;
   const ProbDev pr = prob[pb];
   for (int l = min(pr.L - 1, small_level_max(D)); l >= 2; --l) {
@@ -439,6 +444,7 @@ __device__ __forceinline__ void pull_range(float* a, const float4& xv, const int
 __global__ void __launch_bounds__(kBlock) k_attract(const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
                                                     const float* __restrict__ acost, const float4* __restrict__ x,
                                                     int64_t K, float4* __restrict__ y) {
+  pdl_wait();
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= K) return;
   int32_t t0 = adj_ptr[v], t1 = adj_ptr[v + 1];
@@ -453,6 +459,7 @@ __global__ void __launch_bounds__(kBlock) k_attract_warp(const int32_t* __restri
                                                          const int32_t* __restrict__ adj_ptr,
                                                          const int32_t* __restrict__ adj, const float* __restrict__ acost,
                                                          const float4* __restrict__ x, float4* __restrict__ y) {
+  pdl_wait();
   int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= n) return;
   const int lane = lane_id();
@@ -472,6 +479,7 @@ __global__ void __launch_bounds__(kBlock) k_attract_block(const int32_t* __restr
                                                           const int32_t* __restrict__ adj,
                                                           const float* __restrict__ acost,
                                                           const float4* __restrict__ x, float4* __restrict__ y) {
+  pdl_wait();
   __shared__ float part[kBlock / 32][4];
   const int lane = lane_id(), warp = threadIdx.x >> 5;
   int32_t v = list[blockIdx.x];
@@ -511,6 +519,7 @@ __global__ void k_compact_flags(const int32_t* __restrict__ flag, const int32_t*
 // Net centres z_j of general nets (Algorithm 4).
 __global__ void k_net_center(const int32_t* __restrict__ net_ptr, const int32_t* __restrict__ pins, int64_t l,
                              const float4* __restrict__ x, float4* __restrict__ z) {
+  pdl_wait();
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= l) return;
   int32_t a = net_ptr[j], b = net_ptr[j + 1];
@@ -526,6 +535,7 @@ __global__ void k_net_center(const int32_t* __restrict__ net_ptr, const int32_t*
 __global__ void k_attract_hyper(const int32_t* __restrict__ vtx_ptr, const int32_t* __restrict__ vnets,
                                 const float4* __restrict__ x, const float4* __restrict__ z, int64_t K,
                                 float4* __restrict__ y) {
+  pdl_wait();
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= K) return;
   float4 xv = x[v];
@@ -712,6 +722,7 @@ __device__ inline void bbox_warp_partial(const float4& v, bool valid, uint32_t* 
 __global__ void __launch_bounds__(kBlock) k_bbox_reduce(const uint32_t* __restrict__ part,
                                                         const int64_t* __restrict__ tbase, int P, int64_t nwarps,
                                                         uint32_t* __restrict__ bb, int32_t* __restrict__ tctr) {
+  pdl_wait();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) ++*tctr;  // the step of the level: read by the step kernel, which ran before this one
   const bool valid = i < nwarps;
@@ -823,6 +834,7 @@ __global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_upda
     const float* __restrict__ scale_tab, const int32_t* __restrict__ tctr,
     float step_override, float4* __restrict__ x, float4* __restrict__ y_out, uint32_t* __restrict__ bb_part,
     unsigned long long* __restrict__ icount) {
+  pdl_wait();
   constexpr int N = Pair<D>::N;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int pb = find_problem(tbase, P, t < T ? t : T - 1);
@@ -1398,6 +1410,7 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
     // whether it is the first step matter to the launches)
     auto step = [&](int t) -> vmo_status {
       ScratchFrame f2(sc);
+      PdlScope pdl;  // every kernel of a step starts with pdl_wait()
       uint32_t* cur = bb + (t & 1) * 8 * P;
       uint32_t* nxt = bb + ((t + 1) & 1) * 8 * P;
       // attraction depends only on x: it runs on the side stream, overlapped

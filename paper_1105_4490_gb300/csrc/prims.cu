@@ -167,6 +167,7 @@ __device__ inline TileInfo tile_info(const SortSegments& sg, int64_t n, int64_t 
 template <class K, int BITS>
 __global__ void radix_hist_kernel(const K* __restrict__ keys, int64_t n, int shift, SortSegments sg,
                                   uint32_t* __restrict__ hist) {
+  pdl_wait();
   constexpr int R = 1 << BITS;
   __shared__ uint32_t h[R];
   for (int i = threadIdx.x; i < R; i += blockDim.x) h[i] = 0;
@@ -185,6 +186,7 @@ __global__ void radix_hist_kernel(const K* __restrict__ keys, int64_t n, int shi
 // prefix in place, row total to rowtot.
 __global__ void radix_rowscan(uint32_t* __restrict__ hist, SortSegments sg, int R, int64_t nrows,
                               uint32_t* __restrict__ rowtot) {
+  pdl_wait();
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrows) return;
   const int seg = (int)(r / R), d = (int)(r % R);
@@ -220,6 +222,7 @@ __global__ void radix_rowscan(uint32_t* __restrict__ hist, SortSegments sg, int 
 // warp per row; nrows = R x the long segments (all rows when unsegmented).
 __global__ void radix_rowscan_warp(uint32_t* __restrict__ hist, SortSegments sg, int R, int64_t nrows,
                                    uint32_t* __restrict__ rowtot) {
+  pdl_wait();
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= nrows) return;
   const int lane = lane_id();
@@ -247,6 +250,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
     const K* __restrict__ keys, const uint32_t* __restrict__ vals, K* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, int64_t n, int shift, SortSegments sg, const uint32_t* __restrict__ offs,
     const uint32_t* __restrict__ rowtot) {
+  pdl_wait();
   constexpr int R = 1 << BITS;
   constexpr int PER = (R + kSortThreads - 1) / kSortThreads;
   __shared__ uint32_t wcnt[kSortWarps][R];

@@ -230,10 +230,39 @@ unsigned long long* stats_interaction_counter();  // null unless counting is on
 void stats_time_begin(cudaStream_t s);
 void stats_time_end(cudaStream_t s, uint64_t points);
 
+// Programmatic dependent launch: inside a PdlScope the calling thread's
+// launches carry the programmatic-serialization attribute, so a kernel's launch
+// is processed while its predecessor in the stream still runs.  Every kernel
+// launched that way starts with pdl_wait(), which returns once the preceding
+// kernel has completed and its writes are visible (and at once when the kernel
+// was launched without the attribute).
+extern thread_local bool g_pdl;
+struct PdlScope {
+  bool prev;
+  PdlScope() : prev(g_pdl) { g_pdl = true; }
+  ~PdlScope() { g_pdl = prev; }
+};
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <class... KArgs, class... Args>
 inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  kernel<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+  if (g_pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  } else {
+    kernel<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+  }
 }
 
 inline int bits_for(uint64_t maxval) {

@@ -358,3 +358,18 @@ def test_full_size_grid3d_step_and_order(V, O):
     perm_o, tree_o = O.order(ref, 3, _np(x), seed=21, max_depth=10)
     assert np.array_equal(_np(perm), perm_o)
     assert np.array_equal(_np(tree["nsep"]), tree_o["nsep"])
+
+
+def test_graph_replay_equals_direct_launches(V):
+    """The layout steps of a level replay a captured two-step CUDA graph unless
+    per-launch timing is on; both give bit-identical coordinates (d = 2, 3;
+    even and odd step counts)."""
+    A = W.powerlaw_symmetric(20000, seed=16)
+    hg = V.Hypergraph.from_matrix(A)
+    for d, iters in ((3, 100), (2, 17)):
+        p = V.Params(d=d, seed=8, iters=iters)
+        V.stats_reset(time_step_kernel=True)  # direct launches
+        a = _np(hg.layout(p))
+        V.stats_reset(time_step_kernel=False)  # graph replay
+        b = _np(hg.layout(p))
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), (d, iters)

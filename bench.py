@@ -52,7 +52,7 @@ SMS = 152
 # DRAM bytes (read + write) per launch of the step kernel, averaged over the
 # 3,000 launches of one step of the medium workload: one ncu capture of the
 # current kernel, summarised in profiles/k_repulse_update_traffic_medium.md
-STEP_KERNEL_TRAFFIC_BYTES = 4_370_494
+STEP_KERNEL_TRAFFIC_BYTES = 4_372_977
 
 
 def medium_workload():
@@ -200,6 +200,24 @@ def batched_leg(V, torch, count: int, plain_sample: int, warmup: int, steps: int
             "batched_over_plain": batched / plain}
 
 
+def max_over_ranks(seconds: float, world: int, device: str) -> float:
+    """Largest elapsed time over the ranks (the job's time: every rank orders
+    its own replica, so the job ends with the slowest)."""
+    import torch
+    if world <= 1:
+        return float(seconds)
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: int, world: int, tmax: float) -> float:
+    """Whole-job throughput of weak-scaled replicas: all ranks' units over the
+    slowest rank's time."""
+    return units_per_rank * world / tmax
+
+
 def served_leg(V, rate: float, duration: float, large_every: int = 50, slots: int = 4):
     """Served mode: an open-loop Poisson stream of ordering requests (seeded),
     98% from the batch_mix size distribution and every `large_every`-th a
@@ -269,6 +287,9 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=30.0,
                     help="requests per second of the served leg (0 skips it)")
     ap.add_argument("--serve-seconds", type=float, default=8.0, help="length of the served arrival stream")
+    ap.add_argument("--serve-sweep", default="",
+                    help="comma-separated request rates: run the served leg at each and report the highest rate "
+                         "sustained (achieved >= 95%% of offered, p99 <= 2 s)")
     ap.add_argument("--profile", action="store_true",
                     help="one untimed step of the workload and exit (for ncu captures; no JSON line)")
     ap.add_argument("--profile-matrix", type=int, default=-1,
@@ -373,11 +394,8 @@ def main():
         V.stats_reset(time_step_kernel=True, count_interactions=False)
         elapsed_ev, _ = timed_steps()
         st = V.stats()
-    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax = float(t.item())
-    value = nnz * world / tmax
+    tmax = max_over_ranks(elapsed, world, "cuda")
+    value = replica_throughput(nnz, world, tmax)
 
     # end to end through the public API: pinned host CSR -> permutations in
     # pinned host memory (one untimed warm-up pass, then K timed passes)
@@ -410,10 +428,7 @@ def main():
         b.record(stream)
         barrier()
         e2e_time += a.elapsed_time(b) / 1e3
-    te = torch.tensor([e2e_time], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = nnz * world / float(te.item())
+    e2e_value = nnz * world / max_over_ranks(e2e_time, world, "cuda")
 
     if rank != 0:
         if world > 1:
@@ -448,6 +463,35 @@ def main():
                                        flush)
     if args.serve_rate > 0 and world == 1:
         modes["served"] = served_leg(V, args.serve_rate, args.serve_seconds)
+    if args.serve_sweep and world == 1:
+        sweep = []
+        for rate in [float(r) for r in args.serve_sweep.split(",") if r]:
+            leg = served_leg(V, rate, args.serve_seconds)
+            leg["rate"] = rate
+            leg["sustained"] = (leg["achieved_nnz_per_s"] >= 0.95 * leg["offered_nnz_per_s"] and
+                                leg["p99_s"] is not None and leg["p99_s"] <= 2.0)
+            sweep.append({k: leg[k] for k in ("rate", "offered_nnz_per_s", "achieved_nnz_per_s", "p50_s", "p99_s",
+                                              "sustained")})
+        ok = [r["rate"] for r in sweep if r["sustained"]]
+        modes["served_sweep"] = {"rates": sweep, "max_sustained_rate": max(ok) if ok else None}
+
+    # phase split of one untimed step (build, layout = V, ordering = O)
+    breakdown = {"build_ms": 0.0, "layout_ms": 0.0, "order_ms": 0.0}
+    for (A, cfg), (rp, ci) in zip(mats, dev_csr):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        hg = V.Hypergraph(rp, ci, A.m, A.n, "symmetric")
+        ev[1].record(stream)
+        p = V.Params(d=cfg["d"], max_depth=cfg["max_depth"], seed=params["seed"])
+        x = hg.layout(p)
+        ev[2].record(stream)
+        hg.order_vertices(p, x)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        breakdown["build_ms"] += ev[0].elapsed_time(ev[1])
+        breakdown["layout_ms"] += ev[1].elapsed_time(ev[2])
+        breakdown["order_ms"] += ev[2].elapsed_time(ev[3])
+        del hg
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -462,7 +506,7 @@ def main():
                       "iters_per_level": 100, "max_depth": 10, "layout": "multilevel",
                       "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
            "gpu_launches": st_timed["launches"], "clocks": csum, "roofline": roofline, "cpu_baseline": cpu,
-           "modes": modes,
+           "modes": modes, "breakdown": breakdown,
            "e2e": {"value": e2e_value, "unit": "nnz/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
     print(json.dumps(out))
     if world > 1:

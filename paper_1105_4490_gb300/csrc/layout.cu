@@ -765,6 +765,28 @@ __device__ __forceinline__ void near_range(const float4* __restrict__ xp, int qa
                                            int64_t tgt, const float2* nx, float2* F, unsigned long long& nint) {
   constexpr int N = Pair<D>::N;
   int j = (qa >> 1) + lane_g;
+  for (; 2 * (j + 7 * G) < qb; j += 8 * G) {
+    float4 Q[8][N];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int i = 0; i < N; ++i) Q[u][i] = xp[(int64_t)(j + u * G) * N + i];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int h0 = 2 * (j + u * G);
+      float2 w = make_float2(1.0f, 1.0f);
+      if (UNIT) {
+        if (u == 0) pair_mask_half<D>(Q[u], 0, h0 < qa, nx);
+        if (u == 7) pair_mask_half<D>(Q[u], 1, h0 + 1 >= qb, nx);
+      } else {
+        w = pair_weight<D>(Q[u]);
+        if (u == 0) w.x = h0 >= qa ? w.x : 0.0f;
+        if (u == 7) w.y = h0 + 1 < qb ? w.y : 0.0f;
+      }
+      pair_charge<D, UNIT>(F, Q[u], nx, w);
+      if (COUNT) nint += (h0 >= qa && h0 != tgt) + (h0 + 1 < qb && h0 + 1 != tgt);
+    }
+  }
   for (; 2 * (j + 3 * G) < qb; j += 4 * G) {
     float4 Q[4][N];
 #pragma unroll

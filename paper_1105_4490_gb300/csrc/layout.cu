@@ -178,9 +178,10 @@ template <int D>
 __global__ void __launch_bounds__(kBlock) k_keys(const float4* __restrict__ x, int64_t K, const int32_t* __restrict__ vprob,
                                                  const ProbDev* __restrict__ prob, const uint32_t* __restrict__ bb,
                                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                 uint32_t* __restrict__ bb_next, int nreset) {
+                                                 uint32_t* __restrict__ bb_next, int nreset, int32_t* __restrict__ tctr) {
   pdl_wait();
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v == 0) ++*tctr;  // the level's step (read by the step kernel of this step)
   if (v < nreset) bb_next[v] = ((v & 7) < 4) ? 0xFFFFFFFFu : 0u;
   if (v >= K) return;
   int pb = vprob[v];
@@ -694,10 +695,13 @@ __device__ inline void far_level_lane(const float4* __restrict__ CP, int64_t cel
   }
 }
 
-// Per-warp bounding-box partials of the step kernel, reduced per problem by
-// k_bbox_reduce (no block barrier in the step kernel).
+// Next bounding box, folded in by the step kernel: lane 0 of every warp (a
+// warp never straddles two problems) applies atomic min / max of the
+// order-preserving integer images of its lanes' new coordinates to the
+// problem's box, which k_keys reset earlier in the step.  Min and max are
+// exact, so the order of the atomics does not matter.
 template <int D>
-__device__ inline void bbox_warp_partial(const float4& v, bool valid, uint32_t* __restrict__ part, int64_t warp) {
+__device__ inline void bbox_warp_fold(const float4& v, bool valid, uint32_t* __restrict__ box) {
   uint32_t mn[4], mx[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
@@ -705,53 +709,13 @@ __device__ inline void bbox_warp_partial(const float4& v, bool valid, uint32_t* 
     mn[m] = __reduce_min_sync(0xffffffffu, (valid && m < D) ? o : 0xFFFFFFFFu);
     mx[m] = __reduce_max_sync(0xffffffffu, o);
   }
-  if (lane_id() == 0) {
-    uint4* p = reinterpret_cast<uint4*>(part + warp * 8);
-    p[0] = make_uint4(mn[0], mn[1], mn[2], mn[3]);
-    p[1] = make_uint4(mx[0], mx[1], mx[2], mx[3]);
+  if (lane_id() == 0 && mn[0] != 0xFFFFFFFFu) {
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      atomicMin(box + m, mn[m]);
+      atomicMax(box + 4 + m, mx[m]);
+    }
   }
-}
-
-// Bounding boxes from the step kernel's per-warp partials (and the level's
-// step counter advanced for the next step): one thread per
-// partial, lanes of the same problem combine with a warp reduction and one of
-// them folds the result into the problem's box with atomic min / max (the box
-// was reset by k_keys earlier in the same iteration; min and max of the
-// order-preserving integer images are exact, so the order of the atomics does
-// not matter).
-__global__ void __launch_bounds__(kBlock) k_bbox_reduce(const uint32_t* __restrict__ part,
-                                                        const int64_t* __restrict__ tbase, int P, int64_t nwarps,
-                                                        uint32_t* __restrict__ bb, int32_t* __restrict__ tctr) {
-  pdl_wait();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) ++*tctr;  // the step of the level: read by the step kernel, which ran before this one
-  const bool valid = i < nwarps;
-  const int pb = valid ? find_problem(tbase, P, i * 32) : -1;
-  uint4 mn = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu), mx = make_uint4(0u, 0u, 0u, 0u);
-  if (valid) {
-    const uint4* p = reinterpret_cast<const uint4*>(part + i * 8);
-    mn = p[0];
-    mx = p[1];
-  }
-  const unsigned peers = __match_any_sync(0xffffffffu, pb);
-  mn.x = __reduce_min_sync(peers, mn.x);
-  mn.y = __reduce_min_sync(peers, mn.y);
-  mn.z = __reduce_min_sync(peers, mn.z);
-  mn.w = __reduce_min_sync(peers, mn.w);
-  mx.x = __reduce_max_sync(peers, mx.x);
-  mx.y = __reduce_max_sync(peers, mx.y);
-  mx.z = __reduce_max_sync(peers, mx.z);
-  mx.w = __reduce_max_sync(peers, mx.w);
-  if (!valid || lane_id() != __ffs(peers) - 1) return;
-  uint32_t* b = bb + (int64_t)pb * 8;
-  if (mn.x != 0xFFFFFFFFu) atomicMin(b + 0, mn.x);
-  if (mn.y != 0xFFFFFFFFu) atomicMin(b + 1, mn.y);
-  if (mn.z != 0xFFFFFFFFu) atomicMin(b + 2, mn.z);
-  if (mn.w != 0xFFFFFFFFu) atomicMin(b + 3, mn.w);
-  if (mx.x) atomicMax(b + 4, mx.x);
-  if (mx.y) atomicMax(b + 5, mx.y);
-  if (mx.z) atomicMax(b + 6, mx.z);
-  if (mx.w) atomicMax(b + 7, mx.w);
 }
 
 // Near field of one row range [qa, qb) of problem-local sorted positions for
@@ -854,7 +818,7 @@ __global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_upda
     const float4* __restrict__ CP, const float4* __restrict__ yatt, const int64_t* __restrict__ tbase, int P,
     const ProbDev* __restrict__ prob, int64_t T, float kappa, const float* __restrict__ s0,
     const float* __restrict__ scale_tab, const int32_t* __restrict__ tctr,
-    float step_override, float4* __restrict__ x, float4* __restrict__ y_out, uint32_t* __restrict__ bb_part,
+    float step_override, float4* __restrict__ x, float4* __restrict__ y_out, uint32_t* __restrict__ bb_next,
     unsigned long long* __restrict__ icount) {
   pdl_wait();
   constexpr int N = Pair<D>::N;
@@ -945,7 +909,7 @@ __global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_upda
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     if (lane_id() == 0 && tot) atomicAdd(icount, tot);
   }
-  bbox_warp_partial<D>(xnew, leader, bb_part, t >> 5);
+  bbox_warp_fold<D>(xnew, leader, bb_next + (int64_t)pb * 8);
 }
 
 // ------------------------------ initial layout -----------------------------
@@ -1386,10 +1350,6 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
   VMO_TRY(sc.alloc(&Wt, ncell));
   VMO_TRY(sc.alloc(&cst, nfine + P));
   VMO_TRY(sc.alloc(&bb, (size_t)2 * 8 * P));
-  uint32_t* bpart;
-  // one partial per warp of the step kernel's grid (whole blocks)
-  const int64_t nwarps = (lb.threads + kStepBlock - 1) / kStepBlock * (kStepBlock / 32);
-  VMO_TRY(sc.alloc(&bpart, (size_t)std::max<int64_t>(nwarps, 1) * 8));
   VMO_TRY(sc.alloc(&s0, P));
   VMO_TRY(sc.alloc(&fb, P + 1));
   if (lb.net_ptr) VMO_TRY(sc.alloc(&z, std::max<int64_t>(lb.nnets, 1)));
@@ -1403,7 +1363,7 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
   const float kappa = d == 2 ? 1.0f : (float)(d - 2);
   // step lengths s0 * decay^t: decay^t as the running double product, rounded
   // to fp32 (a table read by the step kernel at the level's step counter,
-  // which k_bbox_reduce advances)
+  // which k_keys advances)
   float* scale_tab;
   int32_t* tctr;
   VMO_TRY(sc.alloc(&scale_tab, iters));
@@ -1418,7 +1378,7 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
     VMO_CUDA(cudaMemcpyAsync(scale_tab, tab.data(), iters * sizeof(float), cudaMemcpyHostToDevice, s));
     VMO_CUDA(cudaStreamSynchronize(s));  // tab must outlive the copy
   }
-  VMO_CUDA(cudaMemsetAsync(tctr, 0, sizeof(int32_t), s));
+  VMO_CUDA(cudaMemsetAsync(tctr, 0xFF, sizeof(int32_t), s));  // -1: k_keys advances it at every step
   vmo_status st = VMO_OK;
   SideStream ss;  // attraction stream of this call (none if it cannot be created)
   cudaStream_t side = ss.stream;
@@ -1458,7 +1418,7 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
       }
       if (side) cudaEventRecord(ev_join, side);
       launch(k_keys<D>, grid_for(std::max<int64_t>(K, nreset), kBlock), kBlock, 0, ms, x, K, lb.vprob.ptr, lb.prob.ptr,
-                                                                                  cur, keys, vals, nxt, nreset);
+                                                                                  cur, keys, vals, nxt, nreset, tctr);
       if (keys_out && t == 0) cudaMemcpyAsync(keys_out, keys, K * 4, cudaMemcpyDeviceToDevice, ms);
       bool in_b = false;
       VMO_TRY(radix_sort_u32_pingpong(keys, vals, skeys, svals, K, D * lb.maxL, segmented ? &segs : nullptr, &in_b, ms,
@@ -1489,13 +1449,12 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
       if (icount)
         launch(k_repulse_update<D, true>, grid_for(lb.threads, kStepBlock), kStepBlock, 0, ms, xs, ws, XP, svals,
                scell, cst, CP, yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, scale_tab, tctr,
-               step_override, x, y_out, bpart, icount);
+               step_override, x, y_out, nxt, icount);
       else
         launch(k_repulse_update<D, false>, grid_for(lb.threads, kStepBlock), kStepBlock, 0, ms, xs, ws, XP, svals,
                scell, cst, CP, yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, scale_tab, tctr,
-               step_override, x, y_out, bpart, icount);
+               step_override, x, y_out, nxt, icount);
       if (timed) stats_time_end(ms, (uint64_t)K);
-      launch(k_bbox_reduce, grid_for(nwarps, kBlock), kBlock, 0, ms, bpart, lb.tbase.ptr, P, nwarps, nxt, tctr);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_fail(e, "layout step", __FILE__, __LINE__);
       return VMO_OK;

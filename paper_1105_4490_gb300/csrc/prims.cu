@@ -12,6 +12,8 @@
 // segments (one per problem of a batch) in one launch sequence.
 #include <algorithm>
 
+#include <type_traits>
+
 #include "vmo_internal.cuh"
 
 namespace vmo {
@@ -343,6 +345,77 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
   }
 }
 
+// Whole sort of one tile that is its own segment (at most 2,048 keys), all
+// passes of 8-bit digits in shared memory, by one block: the sort of the
+// small levels of a layout (one launch instead of three per pass).  Ranks
+// within a digit follow the input order exactly as in radix_scatter_kernel.
+__global__ void __launch_bounds__(kSortThreads) radix_tile_sort_kernel(const uint32_t* __restrict__ keys,
+                                                                       const uint32_t* __restrict__ vals,
+                                                                       uint32_t* __restrict__ keys_out,
+                                                                       uint32_t* __restrict__ vals_out, int64_t n,
+                                                                       int bits, SortSegments sg) {
+  pdl_wait();
+  constexpr int R = 256;
+  __shared__ uint32_t sk[2][kSortTile], sv[2][kSortTile];
+  __shared__ uint32_t wcnt[kSortWarps][R];
+  __shared__ uint32_t dbase[R];
+  __shared__ uint32_t ws[33];
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  const TileInfo ti = tile_info(sg, n, blockIdx.x, R);
+  for (int i = threadIdx.x; i < ti.count; i += blockDim.x) {
+    sk[0][i] = keys[ti.start + i];
+    sv[0][i] = vals[ti.start + i];
+  }
+  int cur = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int shift = 0; shift < bits; shift += 8) {
+    for (int i = threadIdx.x; i < kSortWarps * R; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    uint32_t rank[kSortItems], dig[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      const int idx = warp * (32 * kSortItems) + j * 32 + lane;
+      const bool valid = idx < ti.count;
+      const uint32_t dg = valid ? ((sk[cur][idx] >> shift) & (R - 1)) : (uint32_t)R;
+      dig[j] = dg;
+      const unsigned peers = __match_any_sync(0xffffffffu, dg);
+      const uint32_t base = valid ? wcnt[warp][dg] : 0u;
+      rank[j] = base + __popc(peers & lt);
+      __syncwarp();
+      if (valid && lane == __ffs(peers) - 1) wcnt[warp][dg] = base + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    // per digit: prefix over the warps, total; then bases by a block scan
+    uint32_t tot = 0;
+    {
+      const int dg = threadIdx.x;  // blockDim.x == R
+      for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = wcnt[w][dg];
+        wcnt[w][dg] = tot;
+        tot += c;
+      }
+    }
+    const uint32_t ex = block_exclusive<uint32_t>(tot, ws, nullptr);
+    dbase[threadIdx.x] = ex;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      if (dig[j] >= (uint32_t)R) continue;
+      const int idx = warp * (32 * kSortItems) + j * 32 + lane;
+      const uint32_t dst = dbase[dig[j]] + wcnt[warp][dig[j]] + rank[j];
+      sk[cur ^ 1][dst] = sk[cur][idx];
+      sv[cur ^ 1][dst] = sv[cur][idx];
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  for (int i = threadIdx.x; i < ti.count; i += blockDim.x) {
+    keys_out[ti.start + i] = sk[cur][i];
+    vals_out[ti.start + i] = sv[cur][i];
+  }
+}
+
 inline int digit_bits(int bits, int* passes) {
   const int p = (bits + kMaxRadixBits - 1) / kMaxRadixBits;
   const int need = (bits + p - 1) / p;
@@ -384,6 +457,17 @@ vmo_status radix_sort_impl(K* keys_in, uint32_t* vals_in, K* keys_out, uint32_t*
     VMO_CUDA(cudaMemcpyAsync(keys_out, keys_in, n * sizeof(K), cudaMemcpyDeviceToDevice, s));
     if (vals_in) VMO_CUDA(cudaMemcpyAsync(vals_out, vals_in, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     return VMO_OK;
+  }
+  if constexpr (std::is_same<K, uint32_t>::value) {
+    // every segment one tile: the whole sort of each tile in one block
+    const bool one_tile = sg.tile_seg ? (sg.nlong == 0 && sg.nmid == 0) : (sg.ntiles == 1);
+    if (one_tile && vals_in && bits <= 32) {
+      launch(radix_tile_sort_kernel, (unsigned)sg.ntiles, kSortThreads, 0, s, keys_in, vals_in, keys_out, vals_out, n,
+             bits, sg);
+      VMO_LAUNCHED("radix_tile_sort");
+      if (in_b) *in_b = true;
+      return VMO_OK;
+    }
   }
   uint32_t *hist, *rowtot;
   VMO_TRY(sc.alloc(&hist, (size_t)(sg.ntiles << B)));

@@ -83,6 +83,11 @@ typedef struct {
   int32_t km_iters;     /* Lloyd rounds of 2-means, Algorithm 5 (20) */
   int32_t min_part;     /* a node with <= min_part vertices is a leaf (64) */
   int32_t max_depth;    /* nodes at this depth are leaves, <= 62 (62) */
+  int32_t sep_recursion; /* 1: the separator V3 of a split node is ordered recursively as well, by the
+                            same bisection over the edges inside V3 (the Schur complement brought into
+                            BBD form, Sec. 4.2); child keys then 3h-1, 3h, 3h+1 for V1, V2, V3 and
+                            nodes at depth min(max_depth, 39) are leaves.  0: V3 keeps its inherited
+                            order (0) */
   uint64_t seed;        /* seed of every random draw (1) */
 } vmo_params;
 

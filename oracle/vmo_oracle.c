@@ -1082,7 +1082,11 @@ static int32_t ora_separate(const ora_hg* h, int d, const float* x4, const int32
 /* its depth equals max_depth, or 2-means leaves a side empty.  Otherwise its */
 /* vertices are stably reordered to [V1, V2, V3] (BBD) or [V1, V3, V2] (SBD)  */
 /* and V1, V2 become children (when non-empty) with heap numbers 2h, 2h+1.    */
-/* The separator keeps its inherited order (it is not recursed into).         */
+/* The separator keeps its inherited order (it is not recursed into), unless  */
+/* sep_rec is set: then V3 is a child as well (the additional freedom of      */
+/* Sec. 4.2: V3 bisected recursively over the edges inside it, the Schur      */
+/* complement in BBD form), the children of h are 3h-1, 3h, 3h+1 (V1, V2, V3) */
+/* and nodes at depth min(max_depth, 39) are leaves (keys stay in 64 bits).  */
 /* perm[new] = old.  Tree records: heap, offset, n1, n2, nsep, depth, comp  */
 /* (a leaf has n1 = |V|, n2 = nsep = 0).                                      */
 /* ------------------------------------------------------------------------- */
@@ -1113,8 +1117,10 @@ static int cmp_rec_key(const void* a, const void* b) {
  * records carry the component index; offsets are absolute positions in perm;
  * records are sorted by (component, heap number). */
 ORA_EXPORT int ora_order(const ora_hg* h, int32_t d, const float* x4, uint64_t seed, int32_t km_iters,
-                         int32_t min_part, int32_t max_depth, int32_t sbd, int32_t* perm, ora_tree* tree) {
+                         int32_t min_part, int32_t max_depth, int32_t sbd, int32_t sep_rec, int32_t* perm,
+                         ora_tree* tree) {
   int32_t k = h->k;
+  if (sep_rec && max_depth > 39) max_depth = 39;
   int32_t* cbase;
   int32_t nc = ora_group_components(h, perm, &cbase);
   memset(tree, 0, sizeof(*tree));
@@ -1159,8 +1165,14 @@ ORA_EXPORT int ora_order(const ora_hg* h, int32_t d, const float* x4, uint64_t s
     }
     for (int32_t i = 0; i < nd.size; ++i) { verts[i] = tmp[i]; innode[tmp[i]] = 0; lab[tmp[i]] = 0; }
     tree->n1[rec] = c1; tree->n2[rec] = c2; tree->nsep[rec] = c3;
-    if (c1 > 0) queue[qt++] = (ora_node){2 * nd.heap, nd.offset, c1, nd.depth + 1, nd.comp};
-    if (c2 > 0) queue[qt++] = (ora_node){2 * nd.heap + 1, nd.offset + (sbd ? c1 + c3 : c1), c2, nd.depth + 1, nd.comp};
+    if (!sep_rec) {
+      if (c1 > 0) queue[qt++] = (ora_node){2 * nd.heap, nd.offset, c1, nd.depth + 1, nd.comp};
+      if (c2 > 0) queue[qt++] = (ora_node){2 * nd.heap + 1, nd.offset + (sbd ? c1 + c3 : c1), c2, nd.depth + 1, nd.comp};
+    } else {
+      if (c1 > 0) queue[qt++] = (ora_node){3 * nd.heap - 1, nd.offset, c1, nd.depth + 1, nd.comp};
+      if (c2 > 0) queue[qt++] = (ora_node){3 * nd.heap, nd.offset + (sbd ? c1 + c3 : c1), c2, nd.depth + 1, nd.comp};
+      if (c3 > 0) queue[qt++] = (ora_node){3 * nd.heap + 1, nd.offset + (sbd ? c1 : c1 + c2), c3, nd.depth + 1, nd.comp};
+    }
   }
   /* sort records by (component, heap number) */
   int32_t nrec = tree->count;

@@ -174,6 +174,7 @@ vmo_status order_grouped(const vmo_hg_s* h, const ComponentGroups& g, const floa
   op.min_part = p->min_part;
   op.max_depth = p->max_depth;
   op.sbd = sbd;
+  op.sep_rec = p->sep_recursion;
   st.adj_ptr = h->adj_ptr.ptr;
   st.adj = h->adj.ptr;
   std::vector<uint64_t> seeds(g.base.size() - 1, p->seed);

@@ -72,7 +72,7 @@ __global__ void k_node_reset(NodeDev* __restrict__ nodes, int N) {
   for (int m = 0; m < 4; ++m) { nd.S1[m] = 0; nd.S2[m] = 0; }
   nd.n1 = nd.n2 = 0;
   nd.c1 = nd.c2 = nd.c3 = 0;
-  nd.child1 = nd.child2 = -1;
+  nd.child1 = nd.child2 = nd.child3 = -1;
 }
 
 template <int D>
@@ -346,10 +346,11 @@ __global__ void k_scatter(const int32_t* __restrict__ ord, const float4* __restr
   segl2[dst] = tag;
 }
 
-// Tree records and the next level's node table.
+// Tree records and the next level's node table.  Children: V1 and V2, and
+// with separator recursion V3 too (keys 2h + side, or 3h - 1 + side).
 __global__ void k_children(NodeDev* __restrict__ nodes, int N, const int64_t* __restrict__ pbase, int min_part,
-                           int max_depth, int sbd, NodeDev* __restrict__ next, int* __restrict__ next_count,
-                           int next_cap, TreeDev tree, int* __restrict__ err) {
+                           int max_depth, int sbd, int sep_rec, NodeDev* __restrict__ next,
+                           int* __restrict__ next_count, int next_cap, TreeDev tree, int* __restrict__ err) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= N) return;
   NodeDev& nd = nodes[s];
@@ -365,18 +366,18 @@ __global__ void k_children(NodeDev* __restrict__ nodes, int N, const int64_t* __
     return;
   }
   tree.n1[slot] = nd.c1; tree.n2[slot] = nd.c2; tree.nsep[slot] = nd.c3;
-  for (int side = 0; side < 2; ++side) {
-    int size = side == 0 ? nd.c1 : nd.c2;
+  for (int side = 0; side < (sep_rec ? 3 : 2); ++side) {
+    int size = side == 0 ? nd.c1 : (side == 1 ? nd.c2 : nd.c3);
     if (size == 0) continue;
-    int64_t off = nd.off + (side == 0 ? 0 : (sbd ? nd.c1 + nd.c3 : nd.c1));
-    uint64_t heap = 2 * nd.heap + side;
+    int64_t off = nd.off + (side == 0 ? 0 : side == 1 ? (sbd ? nd.c1 + nd.c3 : nd.c1) : (sbd ? nd.c1 : nd.c1 + nd.c2));
+    uint64_t heap = sep_rec ? 3 * nd.heap - 1 + side : 2 * nd.heap + side;
     int depth = nd.depth + 1;
     if (size > min_part && depth < max_depth) {
       int c = atomicAdd(next_count, 1);
       if (c >= next_cap) { atomicOr(err, 2); continue; }
       NodeDev& ch = next[c];
       ch.heap = heap; ch.off = off; ch.size = size; ch.depth = depth; ch.prob = nd.prob;
-      if (side == 0) nd.child1 = c; else nd.child2 = c;
+      if (side == 0) nd.child1 = c; else if (side == 1) nd.child2 = c; else nd.child3 = c;
     } else {
       int t = atomicAdd(tree.count, 1);
       if (t >= tree.cap) { atomicOr(err, 1); continue; }
@@ -394,7 +395,7 @@ __global__ void k_relabel(const int32_t* __restrict__ segl2, const int32_t* __re
   int32_t c = -1;
   if (tag >= 0) {
     int s = tag >> 2, l = tag & 3;
-    c = l == 1 ? nodes[s].child1 : (l == 2 ? nodes[s].child2 : -1);
+    c = l == 1 ? nodes[s].child1 : (l == 2 ? nodes[s].child2 : nodes[s].child3);
   }
   int32_t old = seg[i];
   seg[i] = (tag >= 0) ? c : -1;
@@ -582,8 +583,9 @@ vmo_status order_levels(OrderState& st, const OrderParams& op, cudaStream_t s, S
     launch(k_scatter, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.xo, st.seg, labf, n, st.nodes, pre, op.sbd, ord2, xo2,
                                                      segl2);
     VMO_CUDA(cudaMemsetAsync(next_count, 0, 4, s));
-    launch(k_children, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, st.pbase, op.min_part, op.max_depth, op.sbd, next,
-                                                      next_count, st.node_cap, st.tree, err);
+    const int max_depth = op.sep_rec ? std::min(op.max_depth, kSepRecMaxDepth) : op.max_depth;
+    launch(k_children, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, st.pbase, op.min_part, max_depth, op.sbd,
+           op.sep_rec, next, next_count, st.node_cap, st.tree, err);
     launch(k_relabel, grid_for(n, kBlock), kBlock, 0, s, segl2, ord2, n, st.nodes, st.seg, st.vnode);
     VMO_LAUNCHED("partition");
     // swap position arrays

@@ -7,7 +7,7 @@ namespace vmo {
 
 // One node of the recursion (device).
 struct NodeDev {
-  uint64_t heap;        // heap number (root 1, children 2h, 2h+1)
+  uint64_t heap;        // heap number (root 1, children 2h, 2h+1; with separator recursion 3h-1, 3h, 3h+1)
   int64_t off;          // first position of the node
   int32_t size;
   int32_t depth;
@@ -17,7 +17,7 @@ struct NodeDev {
   int32_t state;        // 0 iterating, 1 converged, 2 not splittable
   int32_t changed;
   int32_t c1, c2, c3;   // sizes after the separator
-  int32_t child1, child2;
+  int32_t child1, child2, child3;
   float4 z1, z2;
   long long S1[4], S2[4];
   long long n1, n2;
@@ -42,7 +42,11 @@ struct OrderParams {
   int min_part = 64;
   int max_depth = 62;
   int sbd = 0;
+  int sep_rec = 0;  // order V3 recursively too (ternary keys, depth <= kSepRecMaxDepth)
 };
+
+// Deepest node with separator recursion: ternary keys (3^(d+1) - 1) / 2 fit 64 bits up to d = 39.
+constexpr int kSepRecMaxDepth = 39;
 
 // Working state of the ordering of a batch of problems (all device).
 struct OrderState {

@@ -217,12 +217,13 @@ def test_bisect_degenerate(V, O):
     assert not ok and _np(lab).tolist() == [1]
 
 
-def _order_compare(V, O, A, model, d, coords, sbd, min_part=64, max_depth=62, seed=5):
+def _order_compare(V, O, A, model, d, coords, sbd, min_part=64, max_depth=62, seed=5, sep_rec=False):
     hg = V.Hypergraph.from_matrix(A, model)
     ref = O.build_from_matrix(model, A)
-    p = V.Params(d=d, min_part=min_part, max_depth=max_depth, seed=seed)
+    p = V.Params(d=d, min_part=min_part, max_depth=max_depth, seed=seed, sep_recursion=int(sep_rec))
     perm, tree = hg.order_vertices(p, torch.as_tensor(coords).cuda(), sbd=sbd)
-    perm_o, tree_o = O.order(ref, d, coords, seed=seed, min_part=min_part, max_depth=max_depth, sbd=sbd)
+    perm_o, tree_o = O.order(ref, d, coords, seed=seed, min_part=min_part, max_depth=max_depth, sbd=sbd,
+                             sep_rec=sep_rec)
     assert np.array_equal(_np(perm), perm_o)
     assert np.array_equal(_np(tree["heap"]).astype(np.uint64), tree_o["heap"])
     for f in ("offset", "n1", "n2", "nsep", "depth", "comp"):
@@ -373,3 +374,28 @@ def test_graph_replay_equals_direct_launches(V):
         V.stats_reset(time_step_kernel=False)  # graph replay
         b = _np(hg.layout(p))
         assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), (d, iters)
+
+
+@pytest.mark.parametrize("sbd", [False, True])
+def test_order_separator_recursion(V, O, sbd):
+    """Separator recursion (V3 ordered recursively, ternary keys): bit-exact
+    against the oracle on the grid's own coordinates and on random ones (d = 2,
+    3), down to single vertices (min_part 0) and with a small depth limit."""
+    A = W.grid_laplacian_2d(64)
+    ij = np.indices((64, 64)).reshape(2, -1).T
+    x = np.zeros((4096, 4), dtype=np.float32)
+    x[:, :2] = ij
+    _order_compare(V, O, A, "symmetric", 2, x, sbd, min_part=8, sep_rec=True)
+    B = W.powerlaw_symmetric(9000, seed=17)
+    _order_compare(V, O, B, "symmetric", 3, O.init_coords(B.n, 3, 17), sbd, min_part=4, sep_rec=True)
+    _order_compare(V, O, B, "symmetric", 2, O.init_coords(B.n, 2, 18), sbd, min_part=0, max_depth=62, sep_rec=True)
+    _order_compare(V, O, B, "symmetric", 2, O.init_coords(B.n, 2, 19), sbd, min_part=0, max_depth=5, sep_rec=True)
+
+
+def test_batch_separator_recursion_equals_plain(V):
+    mats = W.batch_mix(12, 31, nmin=200, nmax=3000)
+    p = V.Params(d=3, seed=4, sep_recursion=1, min_part=16)
+    perm, offs = V.batch_order(mats, p)
+    for i, A in enumerate(mats):
+        one, _ = V.Hypergraph.from_matrix(A).order_vertices(p)
+        assert np.array_equal(_np(perm)[offs[i]:offs[i + 1]], _np(one)), i

@@ -389,3 +389,85 @@ def test_multilevel_layout_of_components_is_independent(oracle_mod):
     xa = O.layout_multilevel(ha, 2, 5)
     xb = O.layout_multilevel(hb, 2, 5)
     assert np.array_equal(xa, xb[:A.m])
+
+
+def _parent3(h):
+    return (int(h) + 1) // 3
+
+
+def _branch3(h):
+    """0, 1, 2 for the V1, V2, V3 child of its parent (keys 3p-1, 3p, 3p+1)."""
+    return int(h) - (3 * _parent3(h) - 1)
+
+
+@pytest.mark.parametrize("sbd", [False, True])
+def test_sep_recursion_separator_of_grid_separator(oracle_mod, sbd):
+    """Separator recursion (the additional freedom of Sec. 4.2) on a 64x64 grid
+    with its own coordinates: the root separator is one grid line, a path of
+    64 vertices, and the separator of a path is a single vertex: the V3 child
+    of the root (key 4) splits 32 / 31 / 1, at the offset of the separator
+    block (after V1 and V2 in BBD, between them in SBD)."""
+    O = oracle_mod
+    A = W.grid_laplacian_2d(64)
+    hg = O.build_from_matrix("symmetric", A)
+    ij = np.indices((64, 64)).reshape(2, -1).T
+    perm, tree = O.order(hg, 2, _x4(ij.astype(np.float32)), seed=1, sbd=sbd, sep_rec=True, min_part=8)
+    H = [int(h) for h in tree["heap"]]
+    n1, n2, ns = (int(tree[f][0]) for f in ("n1", "n2", "nsep"))
+    assert H[0] == 1 and ns == 64 and n1 + n2 + ns == 4096
+    j = H.index(4)
+    assert tree["offset"][j] == (n1 if sbd else n1 + n2)
+    assert sorted((int(tree["n1"][j]), int(tree["n2"][j]))) == [31, 32] and tree["nsep"][j] == 1
+    # its three children are there too (keys 11, 12, 13)
+    assert {11, 12, 13} <= set(H)
+
+
+def test_sep_recursion_nesting(oracle_mod):
+    """Separator recursion on a power-law graph: a permutation; every split
+    node's three children at the right keys, offsets and sizes; and every edge
+    lies in a diagonal block or a border: below the lowest common node of its
+    two ends' owners, the ends are never one in the V1 branch and one in the V2
+    branch."""
+    O = oracle_mod
+    A = W.powerlaw_symmetric(3000, seed=21)
+    hg = O.build_from_matrix("symmetric", A)
+    x4 = O.init_coords(hg.k, 2, 21)
+    for sbd in (False, True):
+        perm, tree = O.order(hg, 2, x4, seed=3, sbd=sbd, sep_rec=True, min_part=4)
+        k = hg.k
+        assert sorted(perm.tolist()) == list(range(k))
+        idx = {(int(c), int(h)): i for i, (c, h) in enumerate(zip(tree["comp"], tree["heap"]))}
+        owner = np.full(k, -1)
+        for i in range(len(tree["heap"])):
+            o, n1, n2, ns, dp = (int(tree[f][i]) for f in ("offset", "n1", "n2", "nsep", "depth"))
+            c, h = int(tree["comp"][i]), int(tree["heap"][i])
+            if n2 == 0 and ns == 0:
+                owner[perm[o:o + n1]] = i
+                continue
+            for side, (size, off) in enumerate(((n1, o), (n2, o + n1 + ns if sbd else o + n1),
+                                                 (ns, o + n1 if sbd else o + n1 + n2))):
+                if size:
+                    ch = idx[(c, 3 * h - 1 + side)]
+                    assert tree["offset"][ch] == off and tree["depth"][ch] == dp + 1
+                    cs = int(tree["n1"][ch]) + int(tree["n2"][ch]) + int(tree["nsep"][ch])
+                    assert cs == size
+        assert (owner >= 0).all()
+        H, D, Cm = tree["heap"], tree["depth"], tree["comp"]
+
+        def path(i):
+            h, d, out = int(H[i]), int(D[i]), []
+            while d > 0:
+                out.append(h)
+                h, d = _parent3(h), d - 1
+            return out[::-1]  # keys from depth 1 down
+
+        for v in range(k):
+            for u in hg.adj[hg.adj_ptr[v]:hg.adj_ptr[v + 1]]:
+                a, b = owner[v], owner[u]
+                assert Cm[a] == Cm[b]
+                pa, pb = path(a), path(b)
+                m = 0
+                while m < min(len(pa), len(pb)) and pa[m] == pb[m]:
+                    m += 1
+                if m < len(pa) and m < len(pb):
+                    assert {_branch3(pa[m]), _branch3(pb[m])} != {0, 1}

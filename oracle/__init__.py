@@ -100,6 +100,9 @@ def _load():
             lib.ora_order.argtypes = [C.POINTER(_HG), C.c_int32, P, C.c_uint64, C.c_int32, C.c_int32,
                                       C.c_int32, C.c_int32, C.c_int32, P, C.POINTER(_Tree)]
             lib.ora_tree_free.argtypes = [C.POINTER(_Tree)]
+            lib.ora_kmeans.argtypes = [C.c_int32, P, P, C.c_int32, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32,
+                                       P, P]
+            lib.ora_kmeans.restype = C.c_int32
             lib.ora_cut_size.argtypes = [C.c_int32, P, P, P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
             lib.ora_cholesky_nnz.restype = C.c_int64
             lib.ora_cholesky_nnz.argtypes = [C.c_int32, P, P, P]
@@ -340,6 +343,18 @@ def order(hg: Hypergraph, d: int, x4: np.ndarray, seed: int, km_iters: int = 20,
                 comp=_arr(t.comp, n, np.int32))
     _load().ora_tree_free(C.byref(t))
     return perm, tree
+
+
+def kmeans(d: int, x4: np.ndarray, verts: np.ndarray, m: int, seed: int, key: int = 1, km_iters: int = 20):
+    """m-way k-means++ (Algorithm 5): (labels in [0, m), centres m x 4, number
+    of non-empty clusters).  For m = 2 it equals bisect with labels - 1."""
+    xf = np.ascontiguousarray(x4, dtype=np.float32).reshape(-1, 4)
+    vv = np.ascontiguousarray(verts, dtype=np.int32)
+    lab = np.zeros(max(len(vv), 1), dtype=np.int32)
+    z = np.zeros((max(m, 1), 4), dtype=np.float32)
+    ne = _load().ora_kmeans(d, _p(xf), _p(vv), len(vv), m, seed & (2**64 - 1), key & (2**64 - 1), km_iters,
+                            _p(lab), _p(z))
+    return lab[:len(vv)], z[:m], int(ne)
 
 
 def cut_size(net_ptr: np.ndarray, pins: np.ndarray, part: np.ndarray):

@@ -996,6 +996,98 @@ ORA_EXPORT int ora_bisect(int32_t d, const float* x4 /* coordinates, 4 per verte
 }
 
 /* ------------------------------------------------------------------------- */
+/* m-way k-means++ (Algorithm 5 with m centres; the partition C_1..C_m of     */
+/* Sec. 3), in the readings of the 2-means above:                             */
+/*  * z_1 = point floor(nv * r_0 / 2^64); for n = 2..m, D_i =                 */
+/*    floor(min_{j<n} ||x_i - z_j||^2 * 2^(34 - 2e)) (distances fp32, no      */
+/*    FMA) and z_n = the first point whose inclusive prefix of D exceeds      */
+/*    floor(sum D * r_(n-1) / 2^64), r_j = rand(seed ^ KMEANS, key, j).  If   */
+/*    the sum is 0 (every point on a chosen centre) the remaining centres     */
+/*    are copies of z_1 and never win a point.                                */
+/*  * Lloyd: label argmin_j ||x - z_j||^2, ties to the smaller j; stop when   */
+/*    no label changes, at most km_iters rounds; exact fixed-point means of   */
+/*    non-empty clusters; final labels from the final centres.                */
+/* For m = 2 this is ora_bisect with labels 0 / 1 instead of 1 / 2.          */
+/* labels[i] in [0, m) refers to verts[i]; z: m x 4 floats.  Returns the      */
+/* number of non-empty clusters.                                              */
+/* ------------------------------------------------------------------------- */
+static int32_t ora_nearest(const float* p, const float* z, int32_t m, int d) {
+  int32_t best = 0;
+  float bd = ora_sqdist32(p, z, d);
+  for (int32_t j = 1; j < m; ++j) {
+    float dj = ora_sqdist32(p, z + 4 * (int64_t)j, d);
+    if (dj < bd) { bd = dj; best = j; }
+  }
+  return best;
+}
+
+ORA_EXPORT int32_t ora_kmeans(int32_t d, const float* x4, const int32_t* verts, int32_t nv, int32_t m,
+                              uint64_t seed, uint64_t key, int32_t km_iters, int32_t* labels, float* z) {
+  for (int64_t j = 0; j < 4 * (int64_t)m; ++j) z[j] = 0.0f;
+  for (int32_t i = 0; i < nv; ++i) labels[i] = 0;
+  if (nv < 1 || m < 1) return 0;
+  int e = ora_exponent(x4, verts, nv, d);
+  int P = 30 - e, Q = 34 - 2 * e;
+  int32_t i0 = (int32_t)ora_scale_draw((uint64_t)nv, ora_rand64(seed ^ ORA_TAG_KMEANS, key, 0));
+  for (int mm = 0; mm < d; ++mm) z[mm] = x4[4 * (int64_t)verts[i0] + mm];
+  float* dmin = (float*)malloc((size_t)nv * sizeof(float));
+  for (int32_t i = 0; i < nv; ++i) dmin[i] = ora_sqdist32(&x4[4 * (int64_t)verts[i]], z, d);
+  int32_t chosen = 1;
+  for (int32_t n = 1; n < m; ++n) { /* centre index n (the (n+1)-th) */
+    uint64_t total = 0;
+    for (int32_t i = 0; i < nv; ++i) total += (uint64_t)floor(ldexp((double)dmin[i], Q));
+    if (total == 0) break;
+    uint64_t thr = ora_scale_draw(total, ora_rand64(seed ^ ORA_TAG_KMEANS, key, (uint64_t)n)), pre = 0;
+    int32_t pick = nv - 1;
+    for (int32_t i = 0; i < nv; ++i) {
+      pre += (uint64_t)floor(ldexp((double)dmin[i], Q));
+      if (pre > thr) { pick = i; break; }
+    }
+    for (int mm = 0; mm < d; ++mm) z[4 * (int64_t)n + mm] = x4[4 * (int64_t)verts[pick] + mm];
+    chosen = n + 1;
+    for (int32_t i = 0; i < nv; ++i) {
+      float dn = ora_sqdist32(&x4[4 * (int64_t)verts[i]], z + 4 * (int64_t)n, d);
+      if (dn < dmin[i]) dmin[i] = dn;
+    }
+  }
+  for (int32_t n = chosen; n < m; ++n)
+    for (int mm = 0; mm < 4; ++mm) z[4 * (int64_t)n + mm] = z[mm];
+  free(dmin);
+  int64_t* S = (int64_t*)malloc((size_t)m * 4 * sizeof(int64_t));
+  int64_t* cnt = (int64_t*)malloc((size_t)m * sizeof(int64_t));
+  int32_t* prev = (int32_t*)malloc((size_t)nv * sizeof(int32_t));
+  int have_prev = 0;
+  for (int32_t it = 0; it < km_iters; ++it) {
+    int changed = 0;
+    memset(S, 0, (size_t)m * 4 * sizeof(int64_t));
+    memset(cnt, 0, (size_t)m * sizeof(int64_t));
+    for (int32_t i = 0; i < nv; ++i) {
+      const float* p = &x4[4 * (int64_t)verts[i]];
+      int32_t lab = ora_nearest(p, z, m, d);
+      if (!have_prev || lab != prev[i]) changed = 1;
+      prev[i] = lab;
+      for (int mm = 0; mm < d; ++mm) S[4 * (int64_t)lab + mm] += llrint(ldexp((double)p[mm], P));
+      cnt[lab]++;
+    }
+    if (have_prev && !changed) break;
+    have_prev = 1;
+    for (int32_t j = 0; j < m; ++j)
+      if (cnt[j] > 0)
+        for (int mm = 0; mm < d; ++mm)
+          z[4 * (int64_t)j + mm] = (float)(((double)S[4 * (int64_t)j + mm] / (double)cnt[j]) * ldexp(1.0, -P));
+  }
+  memset(cnt, 0, (size_t)m * sizeof(int64_t));
+  for (int32_t i = 0; i < nv; ++i) {
+    labels[i] = ora_nearest(&x4[4 * (int64_t)verts[i]], z, m, d);
+    cnt[labels[i]]++;
+  }
+  int32_t nonempty = 0;
+  for (int32_t j = 0; j < m; ++j) nonempty += cnt[j] > 0;
+  free(S); free(cnt); free(prev);
+  return nonempty;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Vertex separator (Algorithm 7, Sec. 4.2) with mu = identity (no            */
 /* strengthened diagonal).                                                    */
 /*                                                                            */

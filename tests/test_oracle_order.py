@@ -471,3 +471,97 @@ def test_sep_recursion_nesting(oracle_mod):
                     m += 1
                 if m < len(pa) and m < len(pb):
                     assert {_branch3(pa[m]), _branch3(pb[m])} != {0, 1}
+
+
+# ---------------------------------------------------------------- m-way k-means++ (Algorithm 5, m centres)
+def _best_mway(pts, m):
+    """Exhaustive minimum of eq. kmeans over all m-labelings (small k)."""
+    k = len(pts)
+    best = np.inf
+    for lab in itertools.product(range(m), repeat=k):
+        lab = np.array(lab)
+        if len(set(lab.tolist())) < m:
+            continue
+        c = sum(((pts[lab == j] - pts[lab == j].mean(0)) ** 2).sum() for j in range(m))
+        best = min(best, c)
+    return best
+
+
+def _cost_m(pts, lab, m):
+    return sum(((pts[lab == j] - pts[lab == j].mean(0)) ** 2).sum() for j in range(m) if (lab == j).any())
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_kmeans_m2_equals_two_means(oracle_mod, seed):
+    """For m = 2 the m-way k-means++ is exactly the pinned 2-means (same draws,
+    same Lloyd rounds): labels 0 / 1 for 1 / 2 and the same centres."""
+    O = oracle_mod
+    rng = np.random.default_rng(300 + seed)
+    d = 2 + seed % 3
+    n = int(rng.integers(2, 400))
+    pts = (rng.normal(0, 1, (n, d)) * rng.uniform(0.1, 50)).astype(np.float32)
+    verts = rng.permutation(n)[: max(2, n - 3)].astype(np.int32)
+    for km in (0, 3, 20):
+        ok, lab2, z1, z2 = O.bisect(d, _x4(pts), verts, seed=seed, key=7 + seed, km_iters=km)
+        labm, zm, ne = O.kmeans(d, _x4(pts), verts, 2, seed=seed, key=7 + seed, km_iters=km)
+        assert np.array_equal(labm, lab2.astype(np.int32) - 1)
+        if ok:
+            assert ne == 2
+            assert np.array_equal(zm[0].view(np.uint32), z1.view(np.uint32))
+            assert np.array_equal(zm[1].view(np.uint32), z2.view(np.uint32))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_kmeans_m3_optimal_on_separated_clusters(oracle_mod, seed):
+    """Three well separated clusters (k <= 8): k-means++ finds the exhaustive
+    optimum of eq. kmeans (every cluster gets a seed with high probability by
+    D^2 sampling, and Lloyd keeps the clusters)."""
+    O = oracle_mod
+    rng = np.random.default_rng(40 + seed)
+    d = 2 + seed % 3
+    sizes = rng.integers(2, 4, 3)
+    pts = np.concatenate([rng.normal(c * 30.0, 0.5, (s, d)) for c, s in enumerate(sizes)]).astype(np.float32)
+    best = _best_mway(pts.astype(np.float64), 3)
+    lab, z, ne = O.kmeans(d, _x4(pts), np.arange(len(pts)), 3, seed=seed, key=1)
+    assert ne == 3
+    assert np.isclose(_cost_m(pts.astype(np.float64), lab, 3), best, rtol=1e-6)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_kmeans_m_lloyd_fixed_point_and_bound(oracle_mod, seed):
+    """Arbitrary points, m = 3 or 4: never better than the exhaustive optimum;
+    labels are the nearest centres (ties to the smaller index); converged
+    centres are the means of their clusters; m = 1 gives one cluster at the
+    mean."""
+    O = oracle_mod
+    rng = np.random.default_rng(500 + seed)
+    d = 2 + seed % 3
+    m = 3 + seed % 2
+    k = 8 if m == 3 else 7
+    pts = rng.uniform(0, 10, (k, d)).astype(np.float32)
+    best = _best_mway(pts.astype(np.float64), m)
+    lab, z, ne = O.kmeans(d, _x4(pts), np.arange(k), m, seed=seed, key=2, km_iters=60)
+    assert _cost_m(pts.astype(np.float64), lab, m) >= best * (1 - 1e-9)
+    dist = ((pts[:, None, :] - z[None, :, :d]) ** 2).sum(2)
+    assert np.array_equal(lab, dist.argmin(1))
+    for j in range(m):
+        if (lab == j).any():
+            assert np.allclose(z[j, :d], pts[lab == j].mean(0), atol=1e-5)
+    lab1, z1, ne1 = O.kmeans(d, _x4(pts), np.arange(k), 1, seed=seed, key=2)
+    assert ne1 == 1 and (lab1 == 0).all() and np.allclose(z1[0, :d], pts.mean(0), atol=1e-5)
+
+
+def test_kmeanspp_m_expected_cost_bound(oracle_mod):
+    """Arthur and Vassilvitskii: the seeding alone (0 Lloyd rounds) costs at most
+    8 (ln m + 2) times the optimum in expectation; checked over many keys."""
+    O = oracle_mod
+    rng = np.random.default_rng(77)
+    for m in (3, 4):
+        pts = np.concatenate([rng.normal(c * 5.0, 1.0, (3, 2)) for c in range(m)]).astype(np.float32)[:8]
+        best = _best_mway(pts.astype(np.float64), m)
+        costs = []
+        for key in range(400):
+            lab, z, _ = O.kmeans(2, _x4(pts), np.arange(len(pts)), m, seed=5, key=key, km_iters=0)
+            dist = ((pts[:, None, :] - z[None, :, :2]) ** 2).sum(2).min(1)
+            costs.append(dist.sum())
+        assert np.mean(costs) <= 8 * (np.log(m) + 2) * best

@@ -475,6 +475,26 @@ def main():
         ok = [r["rate"] for r in sweep if r["sustained"]]
         modes["served_sweep"] = {"rates": sweep, "max_sustained_rate": max(ok) if ok else None}
 
+    if world == 1:
+        # m-way k-means++ (Algorithm 5, 64 centres) of a million points, one call
+        kpts = V.init_coords(1_000_000, 3, seed=3)
+        kverts = torch.arange(1_000_000, dtype=torch.int32, device="cuda")
+        V.kmeans(kpts, kverts, 64, seed=1, km_iters=20, d=3)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, _, ne = V.kmeans(kpts, kverts, 64, seed=1, km_iters=20, d=3)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        modes["kmeans_m64"] = {"workload": "1,000,000 points of a seeded uniform layout in d = 3, m = 64 centres, "
+                                           "k-means++ seeding + at most 20 Lloyd rounds",
+                               "ms_per_call": statistics.median(ts), "points_per_s": 1e6 / (statistics.median(ts) / 1e3),
+                               "nonempty": ne}
+
     # phase split of one untimed step (build, layout = V, ordering = O)
     breakdown = {"build_ms": 0.0, "layout_ms": 0.0, "order_ms": 0.0}
     for (A, cfg), (rp, ci) in zip(mats, dev_csr):

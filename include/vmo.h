@@ -215,6 +215,24 @@ vmo_status vmo_bisect_noalloc(int32_t d, const float* coords, const int32_t* ver
                               uint64_t key, int32_t km_iters, uint8_t* labels, float* z, int32_t* split,
                               void* stream);
 
+/* m-way k-means++ (Algorithm 5 with m centres): the m-way partition C_1..C_m
+ * of the points coords[verts[i]] that the paper describes as a one-shot
+ * partitioner, in the readings of vmo_bisect (the same draws keyed by
+ * (seed, key, centre index), integer D^2 weights, fp32 distances without FMA,
+ * ties to the smaller centre, at most km_iters Lloyd rounds ending at the
+ * first round without a change, exact fixed-point means); for m = 2 it equals
+ * vmo_bisect with labels 0 / 1 for 1 / 2.  If the D^2 weights vanish before m
+ * centres are drawn (points on the chosen centres), the remaining centres are
+ * copies of the first and stay empty.
+ * coords: device float[4] per vertex (16-byte aligned); verts: device int32[nverts];
+ * labels: device int32[nverts] out, in [0, m); centres: device float[4 * m] out
+ * (16-byte aligned); nonempty: host int32 out, the number of non-empty clusters.
+ * Errors: VMO_ERR_INVALID for m outside [1, 256], negative sizes, null or
+ * unaligned pointers; VMO_ERR_UNSUPPORTED for d outside 2..4. */
+vmo_status vmo_kmeans(int32_t d, const float* coords, const int32_t* verts, int32_t nverts, int32_t m, uint64_t seed,
+                      uint64_t key, int32_t km_iters, int32_t* labels, float* centres, int32_t* nonempty,
+                      void* stream);
+
 /* Recursive BBD ordering (Sec. 4.2): layout (when coords == NULL) and then
  * recursive bisection with vertex separators placed last.  Symmetric model:
  * row_perm and col_perm (device int32[m]) receive the same permutation.

@@ -24,15 +24,6 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// Exponent e with max |x| < 2^e (0 for max = 0) from the ordered bits of the max.
-__device__ inline int exponent_of(uint32_t maxbits) {
-  float mx = __uint_as_float(maxbits);
-  if (mx == 0.0f) return 0;
-  int e;
-  frexpf(mx, &e);
-  return e;
-}
-
 template <int D>
 __device__ inline float plane_dist(const float4& x, const float4& r, float delta) {
   float acc = 0.0f;

@@ -300,6 +300,16 @@ __host__ __device__ inline uint64_t rand64(uint64_t seed, uint64_t a, uint64_t b
 // floor(n * r / 2^64)
 __device__ inline uint64_t scale_draw(uint64_t n, uint64_t r) { return __umul64hi(n, r); }
 
+// Exponent e with max |x| < 2^e (0 for max = 0) from the float bits of the max
+// (the fixed-point grid of the k-means sums is 2^-(30 - e)).
+__device__ inline int exponent_of(uint32_t maxbits) {
+  float mx = __uint_as_float(maxbits);
+  if (mx == 0.0f) return 0;
+  int e;
+  frexpf(mx, &e);
+  return e;
+}
+
 // Order-preserving map float -> uint32 (for atomicMin/Max on floats).
 __device__ inline uint32_t f2ord(float f) {
   uint32_t b = __float_as_uint(f);

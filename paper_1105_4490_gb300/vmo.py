@@ -82,7 +82,7 @@ SYMBOLS = ["vmo_default_params", "vmo_build_hypergraph", "vmo_hg_vertices", "vmo
            "vmo_status_string", "vmo_last_error", "vmo_stats_reset", "vmo_stats_get", "vmo_batch_order",
            "vmo_batch_layout", "vmo_bisect_noalloc", "vmo_server_default_config", "vmo_server_estimate_bytes",
            "vmo_server_plan", "vmo_server_create", "vmo_server_submit", "vmo_server_poll", "vmo_server_wait",
-           "vmo_server_cancel", "vmo_server_get_stats", "vmo_server_destroy"]
+           "vmo_server_cancel", "vmo_server_get_stats", "vmo_server_destroy", "vmo_kmeans"]
 
 
 class _ServerConfig(C.Structure):
@@ -129,6 +129,7 @@ def load(path: str | None = None):
     lib.vmo_coarsen.argtypes = [V, C.POINTER(_Params), V, V, P32, P32, P32, V]
     lib.vmo_bisect.argtypes = [V, I32, V, V, I32, U64, U64, I32, V, V, P32, V]
     lib.vmo_bisect_noalloc.argtypes = [I32, V, V, I32, U64, U64, I32, V, V, P32, V]
+    lib.vmo_kmeans.argtypes = [I32, V, V, I32, I32, U64, U64, I32, V, V, P32, V]
     for nm in ("vmo_order_bbd", "vmo_order_sbd"):
         getattr(lib, nm).argtypes = [V, V, C.POINTER(_Params), V, V, C.POINTER(_Tree), V]
     lib.vmo_order_vertices.argtypes = [V, V, C.POINTER(_Params), I32, V, C.POINTER(_Tree), V]
@@ -403,3 +404,16 @@ def bisect_noalloc(coords: torch.Tensor, verts: torch.Tensor, seed: int, key: in
     _check(load().vmo_bisect_noalloc(d, _ptr(coords), _ptr(verts), verts.numel(), seed & (2 ** 64 - 1), key,
                                      km_iters, _ptr(labels), _ptr(z), C.byref(split), _stream()))
     return bool(split.value), labels[:verts.numel()], z[:4], z[4:]
+
+
+def kmeans(coords: torch.Tensor, verts: torch.Tensor, m: int, seed: int, key: int = 1, km_iters: int = 20,
+           d: int = 3):
+    """m-way k-means++ of coords[verts] (Algorithm 5): (labels in [0, m),
+    centres [m, 4], number of non-empty clusters)."""
+    verts = verts.to(device="cuda", dtype=torch.int32).contiguous()
+    labels = torch.zeros(max(verts.numel(), 1), dtype=torch.int32, device="cuda")
+    centres = torch.zeros((max(m, 1), 4), dtype=torch.float32, device="cuda")
+    ne = C.c_int32()
+    _check(load().vmo_kmeans(d, _ptr(coords), _ptr(verts), verts.numel(), m, seed & (2 ** 64 - 1),
+                             key & (2 ** 64 - 1), km_iters, _ptr(labels), _ptr(centres), C.byref(ne), _stream()))
+    return labels[:verts.numel()], centres[:m], int(ne.value)

@@ -55,10 +55,13 @@ SMS = 152
 STEP_KERNEL_TRAFFIC_BYTES = 4_380_180
 
 
+MEDIUM_NAME = "grid3d_64^3+powerlaw_500k"
+
+
 def medium_workload():
     mats = [(W.grid_laplacian_3d(64), dict(d=3, max_depth=10)),
             (W.powerlaw_symmetric(500_000, seed=1), dict(d=3, max_depth=10))]
-    return "grid3d_64^3+powerlaw_500k", mats
+    return MEDIUM_NAME, mats
 
 
 def cpu_sample(small: bool):
@@ -315,7 +318,11 @@ def main():
         print(json.dumps({"metric": METRIC, "value": val, "unit": "nnz/s", "impl": "reference", "n_gpus": args.gpus,
                           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "config": {"workload": sample_name, "l2": "n/a (CPU)"},
+                          "data": "synthetic",
+                          "config": {"workload": MEDIUM_NAME, "model": "symmetric", "d": 3, "iters_per_level": 100,
+                                     "max_depth": 10, "layout": "multilevel",
+                                     "sample_per_step": f"{sample_name} (bounded sample of the workload)",
+                                     "l2": "n/a (CPU)"},
                           "cpu_baseline": {"value": val, "unit": "nnz/s", "cores": 1, "kind": "oracle",
                                            "sample": f"{sample_name}, oracle FP64 single-thread per step"},
                           "e2e": {"value": val, "unit": "nnz/s", "h2d_bytes_per_step": 0,

@@ -38,7 +38,7 @@ def test_kmeans_bit_exact(V, O, d):
     x = O.init_coords(k, d, 40 + d)
     xt = torch.as_tensor(x).cuda()
     for m, n, km in ((1, 1000, 20), (3, 2999, 20), (17, 20011, 20), (64, 29999, 12), (256, 30000, 5),
-                     (5, 7, 20), (8, 8, 3)):
+                     (5, 7, 20), (8, 8, 3), (8, 3, 20)):
         verts = rng.choice(k, n, replace=False).astype(np.int32)
         key = int(rng.integers(1, 1 << 40))
         lab, z, ne = V.kmeans(xt, torch.as_tensor(verts), m, seed=77, key=key, km_iters=km, d=d)

@@ -278,17 +278,32 @@ __device__ inline void store_cell(int64_t idx, int64_t pidx, const float* S, flo
 constexpr int kCellSerial = 32;
 
 template <int D>
+__device__ __forceinline__ void cell_add(const float4& p, float wq, float* S, float& W) {
+  S[0] += wq * p.x;
+  if (D > 1) S[1] += wq * p.y;
+  if (D > 2) S[2] += wq * p.z;
+  if (D > 3) S[3] += wq * p.w;
+  W += wq;
+}
+
+// Points q0, q0 + stride, ... < q1 added in that order; four loads issued
+// before their additions.
+template <int D>
 __device__ __forceinline__ void cell_sum(const float4* __restrict__ xs, const float* __restrict__ ws, int64_t q0,
                                          int64_t q1, int64_t stride, float* S, float& W) {
-  for (int64_t q = q0; q < q1; q += stride) {
-    float4 p = xs[q];
-    float wq = ws ? ws[q] : 1.0f;
-    S[0] += wq * p.x;
-    if (D > 1) S[1] += wq * p.y;
-    if (D > 2) S[2] += wq * p.z;
-    if (D > 3) S[3] += wq * p.w;
-    W += wq;
+  int64_t q = q0;
+  for (; q + 3 * stride < q1; q += 4 * stride) {
+    float4 p[4];
+    float wq[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      p[u] = xs[q + u * stride];
+      wq[u] = ws ? ws[q + u * stride] : 1.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cell_add<D>(p[u], wq[u], S, W);
   }
+  for (; q < q1; q += stride) cell_add<D>(xs[q], ws ? ws[q] : 1.0f, S, W);
 }
 
 template <int D>

@@ -710,6 +710,86 @@ __device__ inline void far_level_lane(const float4* __restrict__ CP, int64_t cel
   }
 }
 
+// The same far field with two of the lane's rows in flight: both rows' pairs
+// are loaded before either is accumulated, rows taken in the same order (so
+// the sums are bit-identical to far_level_lane).  Used for launches too small
+// to hide load latency with other warps (the small levels of a hierarchy).
+template <int D, bool COUNT>
+__device__ inline void far_level_lane2(const float4* __restrict__ CP, int64_t cell, const int32_t* me, int l,
+                                       const float2* nx, float2* F, int G, int lane_g, unsigned long long& nint) {
+  constexpr int N = Pair<D>::N;
+  const int sl = 1 << l;
+  int lo[D], hi[D], ext[D];
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    int par = me[m] >> 1;
+    lo[m] = max(2 * par - 2, 0);
+    hi[m] = min(2 * par + 3, sl - 1);
+    ext[m] = hi[m] - lo[m] + 1;
+  }
+  int nrows = 1;
+#pragma unroll
+  for (int m = 1; m < D; ++m) nrows *= ext[m];
+  const int npairs = ext[0] >> 1;
+  // row r (row-major over coordinates 1..D-1, coordinate 1 fastest): its
+  // first cell and whether it is adjacent to the target's cell in 1..D-1
+  auto row_at = [&](int r, int64_t& c0, bool& in) {
+    int64_t idx = 0;
+    bool adj = true;
+    int q[D];
+#pragma unroll
+    for (int m = 1; m < D; ++m) {
+      q[m] = lo[m] + r % ext[m];
+      r /= ext[m];
+      adj = adj && q[m] >= me[m] - 1 && q[m] <= me[m] + 1;
+    }
+#pragma unroll
+    for (int m = D - 1; m >= 1; --m) idx = idx * sl + q[m];
+    c0 = cell + idx * sl + lo[0];
+    in = adj;
+  };
+  auto load = [&](int64_t c0, float4 (*P)[N]) {
+    const float4* row = CP + (c0 >> 1) * N;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < N; ++j) P[i][j] = i < npairs ? row[i * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto apply = [&](float4 (*P)[N], bool incore) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float2 w = pair_weight<D>(P[i]);
+      if (incore) {
+        const int xa = lo[0] + 2 * i;
+        w.x = (xa >= me[0] - 1 && xa <= me[0] + 1) ? 0.0f : w.x;
+        w.y = (xa + 1 >= me[0] - 1 && xa + 1 <= me[0] + 1) ? 0.0f : w.y;
+      }
+      pair_charge<D>(F, P[i], nx, w);
+      if (COUNT) nint += (w.x > 0.0f) + (w.y > 0.0f);
+    }
+  };
+  int r = lane_g;
+  for (; r + G < nrows; r += 2 * G) {
+    int64_t ca, cb;
+    bool ia, ib;
+    row_at(r, ca, ia);
+    row_at(r + G, cb, ib);
+    float4 A[3][N], B[3][N];
+    load(ca, A);
+    load(cb, B);
+    apply(A, ia);
+    apply(B, ib);
+  }
+  if (r < nrows) {
+    int64_t ca;
+    bool ia;
+    row_at(r, ca, ia);
+    float4 A[3][N];
+    load(ca, A);
+    apply(A, ia);
+  }
+}
+
 // Next bounding box, folded in by the step kernel: lane 0 of every warp (a
 // warp never straddles two problems) applies atomic min / max of the
 // order-preserving integer images of its lanes' new coordinates to the
@@ -825,9 +905,12 @@ __device__ __forceinline__ void near_range(const float4* __restrict__ xp, int qa
 #define VMO_STEP_MINBLOCKS 6
 #endif
 constexpr int kStepBlock = VMO_STEP_BLOCK;
+// step launches of at most this many threads (about 4 warps per SM) take the
+// far-field variant with two rows in flight
+constexpr int64_t kSmallStepThreads = 152 * 4 * 32;
 
-template <int D, bool COUNT>
-__global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_update(
+template <int D, bool COUNT, bool MLP>
+__global__ void __launch_bounds__(kStepBlock, MLP ? 3 : VMO_STEP_MINBLOCKS) k_repulse_update(
     const float4* __restrict__ xs, const float* __restrict__ ws, const float4* __restrict__ XP,
     const uint32_t* __restrict__ svals, const uint32_t* __restrict__ scell, const int32_t* __restrict__ cst,
     const float4* __restrict__ CP, const float4* __restrict__ yatt, const int64_t* __restrict__ tbase, int P,
@@ -866,7 +949,8 @@ __global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_upda
     const float4* xp = XP + ((pr.vbase + pb + 1) >> 1) * N;  // the problem's first pair
     const int xa = max(c[0] - 1, 0), xb = min(c[0] + 1, side - 1);
     constexpr int NR = D == 2 ? 3 : (D == 3 ? 9 : 27);
-    for (int o = 0; o < NR; ++o) {
+    // the row ranges [qa, qb) of the problem's sorted points (empty: outside the grid)
+    auto row_range = [&](int o, int& qa, int& qb) {
       int32_t cc[D];
       int oo = o;
       bool inside = true;
@@ -877,20 +961,42 @@ __global__ void __launch_bounds__(kStepBlock, VMO_STEP_MINBLOCKS) k_repulse_upda
         oo /= 3;
         inside = inside && cc[m] >= 0 && cc[m] < side;
       }
-      if (!inside) continue;
+      qa = qb = 0;
+      if (!inside) return;
       const int64_t r0 = rowmajor<D>(cc, side);
-      const int qa = cs[r0] - (int)pr.vbase, qb = cs[r0 + (xb - xa) + 1] - (int)pr.vbase;  // problem-local
+      qa = cs[r0] - (int)pr.vbase;  // problem-local
+      qb = cs[r0 + (xb - xa) + 1] - (int)pr.vbase;
+    };
+    auto near_row = [&](int qa, int qb) {
+      if (qa >= qb) return;
       if (ws)
         near_range<D, COUNT, false>(xp, qa, qb, G, lane_g, tgt, nx, F, nint);
       else
         near_range<D, COUNT, true>(xp, qa, qb, G, lane_g, tgt, nx, F, nint);
+    };
+    if (MLP && D <= 3) {
+      // small launches: all rows' ranges loaded before the first row is used
+      int qa[NR], qb[NR];
+#pragma unroll
+      for (int o = 0; o < NR; ++o) row_range(o, qa[o], qb[o]);
+#pragma unroll
+      for (int o = 0; o < NR; ++o) near_row(qa[o], qb[o]);
+    } else {
+      for (int o = 0; o < NR; ++o) {
+        int qa, qb;
+        row_range(o, qa, qb);
+        near_row(qa, qb);
+      }
     }
     // far field, levels 2..L
     for (int l = 2; l <= L; ++l) {
       int32_t me[D];
 #pragma unroll
       for (int m = 0; m < D; ++m) me[m] = c[m] >> (L - l);
-      far_level_lane<D, COUNT>(CP, pr.cbase + pb + lvl_off(D, l) + 1, me, l, nx, F, G, lane_g, nint);
+      if (MLP)
+        far_level_lane2<D, COUNT>(CP, pr.cbase + pb + lvl_off(D, l) + 1, me, l, nx, F, G, lane_g, nint);
+      else
+        far_level_lane<D, COUNT>(CP, pr.cbase + pb + lvl_off(D, l) + 1, me, l, nx, F, G, lane_g, nint);
     }
   }
   float Fs[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1461,14 +1567,13 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
       const bool timed = stats_timing();
       if (timed) stats_time_begin(ms);
       unsigned long long* icount = stats_interaction_counter();
-      if (icount)
-        launch(k_repulse_update<D, true>, grid_for(lb.threads, kStepBlock), kStepBlock, 0, ms, xs, ws, XP, svals,
-               scell, cst, CP, yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, scale_tab, tctr,
-               step_override, x, y_out, nxt, icount);
-      else
-        launch(k_repulse_update<D, false>, grid_for(lb.threads, kStepBlock), kStepBlock, 0, ms, xs, ws, XP, svals,
-               scell, cst, CP, yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, scale_tab, tctr,
-               step_override, x, y_out, nxt, icount);
+      // few warps per SM: the far-field variant with two rows in flight
+      const bool mlp = lb.threads <= kSmallStepThreads;
+      auto step_kernel = icount ? (mlp ? k_repulse_update<D, true, true> : k_repulse_update<D, true, false>)
+                                : (mlp ? k_repulse_update<D, false, true> : k_repulse_update<D, false, false>);
+      launch(step_kernel, grid_for(lb.threads, kStepBlock), kStepBlock, 0, ms, xs, ws, XP, svals, scell, cst, CP,
+             yatt, lb.tbase.ptr, P, lb.prob.ptr, lb.threads, kappa, s0, scale_tab, tctr, step_override, x, y_out, nxt,
+             icount);
       if (timed) stats_time_end(ms, (uint64_t)K);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_fail(e, "layout step", __FILE__, __LINE__);

@@ -907,7 +907,10 @@ __device__ __forceinline__ void near_range(const float4* __restrict__ xp, int qa
 constexpr int kStepBlock = VMO_STEP_BLOCK;
 // step launches of at most this many threads (about 4 warps per SM) take the
 // far-field variant with two rows in flight
-constexpr int64_t kSmallStepThreads = 152 * 4 * 32;
+#ifndef VMO_SMALL_STEP_THREADS
+#define VMO_SMALL_STEP_THREADS (152 * 4 * 32)
+#endif
+constexpr int64_t kSmallStepThreads = VMO_SMALL_STEP_THREADS;
 
 template <int D, bool COUNT, bool MLP>
 __global__ void __launch_bounds__(kStepBlock, MLP ? 3 : VMO_STEP_MINBLOCKS) k_repulse_update(

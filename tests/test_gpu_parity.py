@@ -399,3 +399,19 @@ def test_batch_separator_recursion_equals_plain(V):
     for i, A in enumerate(mats):
         one, _ = V.Hypergraph.from_matrix(A).order_vertices(p)
         assert np.array_equal(_np(perm)[offs[i]:offs[i + 1]], _np(one)), i
+
+
+@pytest.mark.parametrize("d,sbd", [(4, False), (4, True), (2, False)])
+def test_full_pipeline_replay_d(V, O, d, sbd):
+    """GPU multilevel layout in d = 4 (and 2), then the oracle orders the GPU
+    coordinates: the same permutation and tree as the GPU ordering (the
+    layout-to-ordering hand-off in every dimension)."""
+    A = W.powerlaw_symmetric(12000, seed=23)
+    hg = V.Hypergraph.from_matrix(A)
+    p = V.Params(d=d, seed=6, min_part=32)
+    x = hg.layout(p)
+    perm, tree = hg.order_vertices(p, x, sbd=sbd)
+    ref = O.build_from_matrix("symmetric", A)
+    perm_o, tree_o = O.order(ref, d, _np(x), seed=6, min_part=32, sbd=sbd)
+    assert np.array_equal(_np(perm), perm_o)
+    assert np.array_equal(_np(tree["nsep"]), tree_o["nsep"])

@@ -98,7 +98,7 @@ def _load():
             lib.ora_bisect.argtypes = [C.c_int32, P, P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32,
                                        P, P, P]
             lib.ora_order.argtypes = [C.POINTER(_HG), C.c_int32, P, C.c_uint64, C.c_int32, C.c_int32,
-                                      C.c_int32, C.c_int32, C.c_int32, P, C.POINTER(_Tree)]
+                                      C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, C.POINTER(_Tree)]
             lib.ora_tree_free.argtypes = [C.POINTER(_Tree)]
             lib.ora_kmeans.argtypes = [C.c_int32, P, P, C.c_int32, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32,
                                        P, P]
@@ -323,12 +323,15 @@ def bisect(d: int, x4: np.ndarray, verts: np.ndarray, seed: int, key: int = 1, k
 
 
 def order(hg: Hypergraph, d: int, x4: np.ndarray, seed: int, km_iters: int = 20, min_part: int = 64,
-          max_depth: int = 62, sbd: bool = False, sep_rec: bool = False):
+          max_depth: int = 62, sbd: bool = False, sep_rec: bool = False, cut_order: bool = False):
     """Recursive BBD (or SBD) ordering from fp32 coordinates: (perm, tree).
     Connected components are ordered one after the other (block diagonal),
     each by its own recursion; tree records are sorted by (comp, heap).
     sep_rec: the separator of a split node is ordered recursively as well
-    (children 3h-1, 3h, 3h+1 for V1, V2, V3; depth at most 39)."""
+    (children 3h-1, 3h, 3h+1 for V1, V2, V3; depth at most 39).
+    cut_order: without sep_rec, every separator is stably sorted by the
+    two-bit number of its vertices' links into the parts of the children's
+    splits."""
     if hg.adj_ptr is None:
         raise ValueError("ordering needs a graph model (symmetric or bipartite)")
     s = hg._struct()
@@ -336,7 +339,7 @@ def order(hg: Hypergraph, d: int, x4: np.ndarray, seed: int, km_iters: int = 20,
     perm = np.zeros(hg.k, dtype=np.int32)
     t = _Tree()
     _load().ora_order(C.byref(s), d, _p(xf), seed & (2**64 - 1), km_iters, min_part, max_depth, int(sbd),
-                      int(sep_rec), _p(perm), C.byref(t))
+                      int(sep_rec), int(cut_order), _p(perm), C.byref(t))
     n = t.count
     tree = dict(heap=_arr(t.heap, n, np.uint64), offset=_arr(t.offset, n, np.int32), n1=_arr(t.n1, n, np.int32),
                 n2=_arr(t.n2, n, np.int32), nsep=_arr(t.nsep, n, np.int32), depth=_arr(t.depth, n, np.int32),

@@ -1203,14 +1203,90 @@ static int cmp_rec_key(const void* a, const void* b) {
   return (p->heap > q->heap) - (p->heap < q->heap);
 }
 
+/* Cut-row/column ordering (Sec. 4.2, the other use of the freedom in V3):    */
+/* every vertex w of the separator V3 of a split node gets a two-bit number:  */
+/* the first bit (value 1) if w has a neighbour in the first part of the     */
+/* split of V1 or of V2 (V11 or V21), the second bit (value 2) if it has one  */
+/* in their second parts (V12 or V22).  V3 is then stably sorted by the       */
+/* number: ascending for BBD (00, 01, 10, 11); for SBD, whose separator sits  */
+/* between the parts, as 01, 00, 11, 10 (cut rows of the first parts first,  */
+/* of the second parts last).  One two-bit pair (b = 1).  Part membership is  */
+/* by position range, so the result does not depend on the order in which    */
+/* the nodes are treated.                                                     */
+typedef struct { int32_t comp; uint64_t heap; int32_t rec; } ora_key;
+static int cmp_key(const void* a, const void* b) {
+  const ora_key* p = (const ora_key*)a;
+  const ora_key* q = (const ora_key*)b;
+  if (p->comp != q->comp) return (p->comp > q->comp) - (p->comp < q->comp);
+  return (p->heap > q->heap) - (p->heap < q->heap);
+}
+
+static int32_t ora_find_rec(const ora_key* ks, int32_t n, int32_t comp, uint64_t heap) {
+  int32_t lo = 0, hi = n - 1;
+  while (lo <= hi) {
+    int32_t mid = (lo + hi) / 2;
+    if (ks[mid].comp == comp && ks[mid].heap == heap) return ks[mid].rec;
+    if (ks[mid].comp < comp || (ks[mid].comp == comp && ks[mid].heap < heap)) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+static void ora_cut_order(const ora_hg* h, int32_t sbd, int32_t* perm, const ora_tree* tree) {
+  int32_t k = h->k, nrec = tree->count;
+  int32_t* pos = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
+  for (int32_t i = 0; i < k; ++i) pos[perm[i]] = i;
+  ora_key* ks = (ora_key*)malloc((size_t)(nrec > 0 ? nrec : 1) * sizeof(ora_key));
+  for (int32_t r = 0; r < nrec; ++r) ks[r] = (ora_key){tree->comp[r], tree->heap[r], r};
+  qsort(ks, (size_t)nrec, sizeof(ora_key), cmp_key);
+  static const int rank_bbd[4] = {0, 1, 2, 3}, rank_sbd[4] = {1, 0, 3, 2};
+  const int* rank = sbd ? rank_sbd : rank_bbd;
+  int32_t* tmp = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
+  for (int32_t r = 0; r < nrec; ++r) {
+    int32_t o = tree->offset[r], n1 = tree->n1[r], n2 = tree->n2[r], ns = tree->nsep[r];
+    if (ns == 0 || (n2 == 0 && ns == 0)) continue;
+    /* first / second part ranges of the splits of the two children */
+    int32_t flo[2], fhi[2], slo[2], shi[2];
+    for (int c = 0; c < 2; ++c) {
+      flo[c] = fhi[c] = slo[c] = shi[c] = 0;
+      int32_t cr = ora_find_rec(ks, nrec, tree->comp[r], 2 * tree->heap[r] + (uint64_t)c);
+      if (cr < 0) continue;
+      int32_t co = tree->offset[cr], c1 = tree->n1[cr], c2 = tree->n2[cr], cs = tree->nsep[cr];
+      if (c2 == 0 && cs == 0) continue; /* a leaf has no parts */
+      flo[c] = co; fhi[c] = co + c1;
+      slo[c] = sbd ? co + c1 + cs : co + c1; shi[c] = slo[c] + c2;
+    }
+    int32_t a = sbd ? o + n1 : o + n1 + n2;
+    int32_t cnt[4] = {0, 0, 0, 0};
+    uint8_t* code = (uint8_t*)malloc((size_t)ns);
+    for (int32_t i = 0; i < ns; ++i) {
+      int32_t w = perm[a + i];
+      uint8_t cw = 0;
+      for (int32_t t = h->adj_ptr[w]; t < h->adj_ptr[w + 1]; ++t) {
+        int32_t p = pos[h->adj[t]];
+        for (int c = 0; c < 2; ++c) {
+          if (p >= flo[c] && p < fhi[c]) cw |= 1;
+          if (p >= slo[c] && p < shi[c]) cw |= 2;
+        }
+      }
+      code[i] = cw;
+      cnt[rank[cw]]++;
+    }
+    int32_t start[4] = {0, cnt[0], cnt[0] + cnt[1], cnt[0] + cnt[1] + cnt[2]};
+    for (int32_t i = 0; i < ns; ++i) tmp[start[rank[code[i]]]++] = perm[a + i];
+    memcpy(perm + a, tmp, (size_t)ns * sizeof(int32_t));
+    free(code);
+  }
+  free(pos); free(ks); free(tmp);
+}
+
 /* Ordering of a graph model from fp32 coordinates.  A disconnected graph is
  * block diagonal: its components (grouped as in the layout) are ordered one
  * after the other, each by its own recursion (root heap number 1).  Tree
  * records carry the component index; offsets are absolute positions in perm;
  * records are sorted by (component, heap number). */
 ORA_EXPORT int ora_order(const ora_hg* h, int32_t d, const float* x4, uint64_t seed, int32_t km_iters,
-                         int32_t min_part, int32_t max_depth, int32_t sbd, int32_t sep_rec, int32_t* perm,
-                         ora_tree* tree) {
+                         int32_t min_part, int32_t max_depth, int32_t sbd, int32_t sep_rec, int32_t cut_order,
+                         int32_t* perm, ora_tree* tree) {
   int32_t k = h->k;
   if (sep_rec && max_depth > 39) max_depth = 39;
   int32_t* cbase;
@@ -1266,6 +1342,7 @@ ORA_EXPORT int ora_order(const ora_hg* h, int32_t d, const float* x4, uint64_t s
       if (c3 > 0) queue[qt++] = (ora_node){3 * nd.heap + 1, nd.offset + (sbd ? c1 : c1 + c2), c3, nd.depth + 1, nd.comp};
     }
   }
+  if (cut_order && !sep_rec) ora_cut_order(h, sbd, perm, tree);
   /* sort records by (component, heap number) */
   int32_t nrec = tree->count;
   ora_rec_key* rk = (ora_rec_key*)malloc((size_t)(nrec > 0 ? nrec : 1) * sizeof(ora_rec_key));

@@ -565,3 +565,136 @@ def test_kmeanspp_m_expected_cost_bound(oracle_mod):
             dist = ((pts[:, None, :] - z[None, :, :2]) ** 2).sum(2).min(1)
             costs.append(dist.sum())
         assert np.mean(costs) <= 8 * (np.log(m) + 2) * best
+
+
+# ---------------------------------------------------------------- cut-row/column ordering (Sec. 4.2)
+def _records(tree):
+    return {(int(c), int(h)): i for i, (c, h) in enumerate(zip(tree["comp"], tree["heap"]))}
+
+
+def _split_ranges(tree, i, sbd):
+    """(V1, V2, V3) position ranges of split node i."""
+    o, n1, n2, ns = (int(tree[f][i]) for f in ("offset", "n1", "n2", "nsep"))
+    v2 = (o + n1 + ns, o + n1 + ns + n2) if sbd else (o + n1, o + n1 + n2)
+    v3 = (o + n1, o + n1 + ns) if sbd else (o + n1 + n2, o + n1 + n2 + ns)
+    return (o, o + n1), v2, v3
+
+
+def _is_split(tree, i):
+    return not (tree["n2"][i] == 0 and tree["nsep"][i] == 0)
+
+
+@pytest.mark.parametrize("sbd", [False, True])
+def test_cut_order_grid_line_runs(oracle_mod, sbd):
+    """64x64 grid with its own coordinates: the root separator is one grid
+    line; the root's two children split their halves along the other axis.
+    With the cut rows ordered, the root separator is three runs of the line:
+    the vertices beside the children's separators (linked to no part of
+    either child's split), and the two halves of the line beside the
+    children's first and second parts.  BBD puts the first run first; SBD
+    puts it between the two halves, in the middle of the line."""
+    O = oracle_mod
+    A = W.grid_laplacian_2d(64)
+    hg = O.build_from_matrix("symmetric", A)
+    ij = np.indices((64, 64)).reshape(2, -1).T
+    x4 = _x4(ij.astype(np.float32))
+    plain, tree0 = O.order(hg, 2, x4, seed=1, sbd=sbd)
+    perm, tree = O.order(hg, 2, x4, seed=1, sbd=sbd, cut_order=True)
+    for f in tree0:
+        assert np.array_equal(tree[f], tree0[f]), f
+    rec = _records(tree)
+    (a, b) = _split_ranges(tree, rec[(0, 1)], sbd)[2]
+    line = ij[perm[a:b]]
+    assert sorted(map(tuple, ij[plain[a:b]])) == sorted(map(tuple, line))
+    axis = 0 if len(set(line[:, 0])) == 1 else 1
+    along = line[:, 1 - axis]
+    # the coordinates, along the root line, of the children's separator lines
+    cut = set()
+    for c in (2, 3):
+        lo, hi = _split_ranges(tree, rec[(0, c)], sbd)[2]
+        cut |= set(int(v) for v in ij[perm[lo:hi]][:, 1 - axis])
+    assert len(cut) >= 1
+    on = np.array([int(t) in cut for t in along])
+    below = ~on & (along < min(cut))
+    above = ~on & (along > max(cut))
+    assert (on | below | above).all()
+    cls = np.where(on, 0, np.where(below, 1, 2))
+    runs = [cls[0]] + [cls[t] for t in range(1, len(cls)) if cls[t] != cls[t - 1]]
+    assert sorted(runs) == [0, 1, 2]  # three contiguous runs
+    if sbd:
+        assert runs[1] == 0
+    else:
+        assert runs[0] == 0
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_cut_order_zero_blocks(oracle_mod, seed):
+    """Power-law graph: the ordering differs from the plain one only inside the
+    separator ranges (same sets, same tree), and every separator V3 of a node
+    whose children split into (V11, V12) and (V21, V22) falls into four
+    consecutive runs R0..R3 (BBD; SBD: R1, R0, R3, R2) with the zero blocks of
+    the recursive form: rows of R0 meet none of V11, V12, V21, V22; rows of R1
+    meet V11 or V21 but neither V12 nor V22; R2 the reverse; R3 both.  Inside
+    every run the plain order is kept."""
+    O = oracle_mod
+    A = W.powerlaw_symmetric(2500, seed=seed)
+    hg = O.build_from_matrix("symmetric", A)
+    x4 = O.init_coords(hg.k, 3, seed)
+    for sbd in (False, True):
+        plain, tree0 = O.order(hg, 3, x4, seed=seed, min_part=8, sbd=sbd)
+        perm, tree = O.order(hg, 3, x4, seed=seed, min_part=8, sbd=sbd, cut_order=True)
+        for f in tree0:
+            assert np.array_equal(tree[f], tree0[f]), f
+        _check_ordering(O, A, hg, perm, tree, sbd)
+        pos = np.empty(hg.k, dtype=np.int64)
+        pos[perm] = np.arange(hg.k)
+        pos0 = np.empty(hg.k, dtype=np.int64)
+        pos0[plain] = np.arange(hg.k)
+        inside = np.zeros(hg.k, dtype=bool)
+        rec = _records(tree)
+        moved = 0
+        for i in range(len(tree["heap"])):
+            if not _is_split(tree, i):
+                continue
+            c, h = int(tree["comp"][i]), int(tree["heap"][i])
+            a, b = _split_ranges(tree, i, sbd)[2]
+            inside[a:b] = True
+            assert set(perm[a:b]) == set(plain[a:b])
+            firsts, seconds = [], []
+            for ch in (2 * h, 2 * h + 1):
+                j = rec.get((c, ch))
+                if j is not None and _is_split(tree, j):
+                    r1, r2, _ = _split_ranges(tree, j, sbd)
+                    firsts.append(r1)
+                    seconds.append(r2)
+
+            def meets(v, ranges):
+                return any(lo <= pos[u] < hi for u in hg.adj[hg.adj_ptr[v]:hg.adj_ptr[v + 1]] for lo, hi in ranges)
+
+            cls = np.array([int(meets(v, firsts)) + 2 * int(meets(v, seconds)) for v in perm[a:b]])
+            order = [1, 0, 3, 2] if sbd else [0, 1, 2, 3]
+            rank = np.array([order.index(t) for t in cls])
+            assert (np.diff(rank) >= 0).all()
+            for t in range(4):
+                sel = perm[a:b][cls == t]
+                assert (np.diff(pos0[sel]) > 0).all()
+            moved += int((perm[a:b] != plain[a:b]).sum())
+        assert np.array_equal(perm[~inside], plain[~inside])
+        assert moved > 0
+
+
+def test_cut_order_special_cases(oracle_mod):
+    """Depth 1 (leaf children: every separator row has code 00) and separator
+    recursion (the cut ordering is then not applied) leave the ordering as it
+    is."""
+    O = oracle_mod
+    A = W.powerlaw_symmetric(1200, seed=9)
+    hg = O.build_from_matrix("symmetric", A)
+    x4 = O.init_coords(hg.k, 2, 9)
+    for sbd in (False, True):
+        for kw in ({"max_depth": 1}, {"sep_rec": True, "min_part": 8}):
+            p0, t0 = O.order(hg, 2, x4, seed=2, sbd=sbd, **kw)
+            p1, t1 = O.order(hg, 2, x4, seed=2, sbd=sbd, cut_order=True, **kw)
+            assert np.array_equal(p0, p1)
+            for f in t0:
+                assert np.array_equal(t0[f], t1[f]), f

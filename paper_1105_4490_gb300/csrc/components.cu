@@ -175,11 +175,14 @@ vmo_status order_grouped(const vmo_hg_s* h, const ComponentGroups& g, const floa
   op.max_depth = p->max_depth;
   op.sbd = sbd;
   op.sep_rec = p->sep_recursion;
+  op.cut_order = p->cut_order;
   st.adj_ptr = h->adj_ptr.ptr;
   st.adj = h->adj.ptr;
   std::vector<uint64_t> seeds(g.base.size() - 1, p->seed);
   VMO_TRY(order_setup(st, x, g.base, seeds, op, g.cperm, s, sc));
-  return order_levels(st, op, s, sc);
+  VMO_TRY(order_levels(st, op, s, sc));
+  if (op.cut_order && !op.sep_rec) VMO_TRY(cut_order_pass(st, op, s, sc));
+  return VMO_OK;
 }
 
 }  // namespace vmo

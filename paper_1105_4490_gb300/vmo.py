@@ -37,7 +37,8 @@ class _Params(C.Structure):
     _fields_ = [("d", C.c_int32), ("iters", C.c_int32), ("sigma", C.c_float), ("decay", C.c_float),
                 ("occupancy", C.c_int32), ("multilevel", C.c_int32), ("match_rounds", C.c_int32),
                 ("coarse_min", C.c_int32), ("km_iters", C.c_int32), ("min_part", C.c_int32),
-                ("max_depth", C.c_int32), ("sep_recursion", C.c_int32), ("seed", C.c_uint64)]
+                ("max_depth", C.c_int32), ("sep_recursion", C.c_int32), ("cut_order", C.c_int32),
+                ("seed", C.c_uint64)]
 
 
 class _Tree(C.Structure):
@@ -67,6 +68,7 @@ class Params:
     min_part: int = 64
     max_depth: int = 62
     sep_recursion: int = 0
+    cut_order: int = 0
     seed: int = 1
 
     def _c(self) -> _Params:

@@ -217,13 +217,15 @@ def test_bisect_degenerate(V, O):
     assert not ok and _np(lab).tolist() == [1]
 
 
-def _order_compare(V, O, A, model, d, coords, sbd, min_part=64, max_depth=62, seed=5, sep_rec=False):
+def _order_compare(V, O, A, model, d, coords, sbd, min_part=64, max_depth=62, seed=5, sep_rec=False,
+                   cut_order=False):
     hg = V.Hypergraph.from_matrix(A, model)
     ref = O.build_from_matrix(model, A)
-    p = V.Params(d=d, min_part=min_part, max_depth=max_depth, seed=seed, sep_recursion=int(sep_rec))
+    p = V.Params(d=d, min_part=min_part, max_depth=max_depth, seed=seed, sep_recursion=int(sep_rec),
+                 cut_order=int(cut_order))
     perm, tree = hg.order_vertices(p, torch.as_tensor(coords).cuda(), sbd=sbd)
     perm_o, tree_o = O.order(ref, d, coords, seed=seed, min_part=min_part, max_depth=max_depth, sbd=sbd,
-                             sep_rec=sep_rec)
+                             sep_rec=sep_rec, cut_order=cut_order)
     assert np.array_equal(_np(perm), perm_o)
     assert np.array_equal(_np(tree["heap"]).astype(np.uint64), tree_o["heap"])
     for f in ("offset", "n1", "n2", "nsep", "depth", "comp"):
@@ -390,6 +392,40 @@ def test_order_separator_recursion(V, O, sbd):
     _order_compare(V, O, B, "symmetric", 3, O.init_coords(B.n, 3, 17), sbd, min_part=4, sep_rec=True)
     _order_compare(V, O, B, "symmetric", 2, O.init_coords(B.n, 2, 18), sbd, min_part=0, max_depth=62, sep_rec=True)
     _order_compare(V, O, B, "symmetric", 2, O.init_coords(B.n, 2, 19), sbd, min_part=0, max_depth=5, sep_rec=True)
+
+
+@pytest.mark.parametrize("sbd", [False, True])
+def test_order_cut_order(V, O, sbd):
+    """Cut-row/column ordering (Sec. 4.2) bit-exact against the oracle: the
+    grid with its own coordinates, power-law graphs in d = 2 and 3 with parts
+    of every size down to one vertex, a depth limit, the bipartite model, a
+    disconnected matrix, and separator recursion switched on (no cut
+    ordering then)."""
+    A = W.grid_laplacian_2d(64)
+    ij = np.indices((64, 64)).reshape(2, -1).T
+    x = np.zeros((4096, 4), dtype=np.float32)
+    x[:, :2] = ij
+    _order_compare(V, O, A, "symmetric", 2, x, sbd, min_part=8, cut_order=True)
+    B = W.powerlaw_symmetric(9000, seed=27)
+    _order_compare(V, O, B, "symmetric", 3, O.init_coords(B.n, 3, 27), sbd, min_part=4, cut_order=True)
+    _order_compare(V, O, B, "symmetric", 2, O.init_coords(B.n, 2, 28), sbd, min_part=0, cut_order=True)
+    _order_compare(V, O, B, "symmetric", 2, O.init_coords(B.n, 2, 29), sbd, min_part=0, max_depth=3,
+                   cut_order=True)
+    _order_compare(V, O, B, "symmetric", 3, O.init_coords(B.n, 3, 30), sbd, min_part=4, sep_rec=True,
+                   cut_order=True)
+    R = W.powerlaw_rectangular(3000, 2000, seed=8)
+    _order_compare(V, O, R, "bipartite", 2, O.init_coords(R.m + R.n, 2, 31), sbd, min_part=1, cut_order=True)
+    D = W.random_symmetric(3000, 2.5, 5)  # 857 components
+    _order_compare(V, O, D, "symmetric", 3, O.init_coords(D.n, 3, 32), sbd, min_part=4, cut_order=True)
+
+
+def test_batch_cut_order_equals_plain(V):
+    mats = W.batch_mix(12, 33, nmin=200, nmax=3000)
+    p = V.Params(d=3, seed=4, cut_order=1, min_part=16)
+    perm, offs = V.batch_order(mats, p)
+    for i, A in enumerate(mats):
+        one, _ = V.Hypergraph.from_matrix(A).order_vertices(p)
+        assert np.array_equal(_np(perm)[offs[i]:offs[i + 1]], _np(one)), i
 
 
 def test_batch_separator_recursion_equals_plain(V):

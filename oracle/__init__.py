@@ -98,7 +98,7 @@ def _load():
             lib.ora_bisect.argtypes = [C.c_int32, P, P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32,
                                        P, P, P]
             lib.ora_order.argtypes = [C.POINTER(_HG), C.c_int32, P, C.c_uint64, C.c_int32, C.c_int32,
-                                      C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, C.POINTER(_Tree)]
+                                      C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P, C.POINTER(_Tree)]
             lib.ora_tree_free.argtypes = [C.POINTER(_Tree)]
             lib.ora_kmeans.argtypes = [C.c_int32, P, P, C.c_int32, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32,
                                        P, P]
@@ -323,7 +323,8 @@ def bisect(d: int, x4: np.ndarray, verts: np.ndarray, seed: int, key: int = 1, k
 
 
 def order(hg: Hypergraph, d: int, x4: np.ndarray, seed: int, km_iters: int = 20, min_part: int = 64,
-          max_depth: int = 62, sbd: bool = False, sep_rec: bool = False, cut_order: bool = False):
+          max_depth: int = 62, sbd: bool = False, sep_rec: bool = False, cut_order: bool = False,
+          match: np.ndarray | None = None):
     """Recursive BBD (or SBD) ordering from fp32 coordinates: (perm, tree).
     Connected components are ordered one after the other (block diagonal),
     each by its own recursion; tree records are sorted by (comp, heap).
@@ -331,21 +332,48 @@ def order(hg: Hypergraph, d: int, x4: np.ndarray, seed: int, km_iters: int = 20,
     (children 3h-1, 3h, 3h+1 for V1, V2, V3; depth at most 39).
     cut_order: without sep_rec, every separator is stably sorted by the
     two-bit number of its vertices' links into the parts of the children's
-    splits."""
+    splits.
+    match: strengthened diagonal of a square matrix in the bipartite model
+    (Sec. 4.2, the matching M as the map mu): match[i] is the column matched to
+    row i; a vertex moved into a separator takes its partner with it."""
     if hg.adj_ptr is None:
         raise ValueError("ordering needs a graph model (symmetric or bipartite)")
+    mu = None
+    if match is not None:
+        mu = mu_from_match(hg, match)
     s = hg._struct()
     xf = np.ascontiguousarray(x4, dtype=np.float32).reshape(-1, 4)
     perm = np.zeros(hg.k, dtype=np.int32)
     t = _Tree()
     _load().ora_order(C.byref(s), d, _p(xf), seed & (2**64 - 1), km_iters, min_part, max_depth, int(sbd),
-                      int(sep_rec), int(cut_order), _p(perm), C.byref(t))
+                      int(sep_rec), int(cut_order), _p(mu) if mu is not None else None, _p(perm), C.byref(t))
     n = t.count
     tree = dict(heap=_arr(t.heap, n, np.uint64), offset=_arr(t.offset, n, np.int32), n1=_arr(t.n1, n, np.int32),
                 n2=_arr(t.n2, n, np.int32), nsep=_arr(t.nsep, n, np.int32), depth=_arr(t.depth, n, np.int32),
                 comp=_arr(t.comp, n, np.int32))
     _load().ora_tree_free(C.byref(t))
     return perm, tree
+
+
+def mu_from_match(hg: Hypergraph, match: np.ndarray) -> np.ndarray:
+    """The map mu of a perfect matching M of the bipartite model of a square
+    m x m pattern (Sec. 4.2): rows are vertices 0..m-1, columns m..2m-1, and
+    row i is matched to column match[i].  Checks that M is a perfect matching
+    of the pattern's edges."""
+    if hg.model != MODELS["bipartite"] or hg.k % 2:
+        raise ValueError("a strengthened diagonal needs the bipartite model of a square pattern")
+    m = hg.k // 2
+    match = np.asarray(match, dtype=np.int64)
+    if match.shape != (m,) or not np.array_equal(np.sort(match), np.arange(m)):
+        raise ValueError("match must be a permutation of the columns")
+    for i in range(m):
+        nb = hg.adj[hg.adj_ptr[i]:hg.adj_ptr[i + 1]]
+        if not np.isin(m + match[i], nb):
+            raise ValueError(f"row {i} is not linked to its matched column {match[i]}")
+    mu = np.empty(2 * m, dtype=np.int32)
+    mu[:m] = m + match
+    mu[m + match] = np.arange(m)
+    return mu
 
 
 def kmeans(d: int, x4: np.ndarray, verts: np.ndarray, m: int, seed: int, key: int = 1, km_iters: int = 20):

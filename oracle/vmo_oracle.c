@@ -1122,9 +1122,19 @@ static int cmp_cut_edge(const void* a, const void* b) {
 
 /* lab[v] (indexed by vertex id) holds the 2-means labels of the node's
  * vertices on entry and {1, 2, 3} on exit; innode[v] marks the node's
- * vertices.  Returns the separator size. */
+ * vertices.  mu: NULL (no strengthened diagonal: mu is the identity) or the
+ * partner of every vertex under the matching M.  Returns the separator size.
+ *
+ * With a matching, the loop of Algorithm 7 moves both v and mu(v) into V3,
+ * and a partner moved early turns later edges at it into uncut ones, so the
+ * outcome depends on the edge order, which the paper does not fix.  Reading:
+ * the order-free form.  Every edge cut by the 2-means labels (one end 1, the
+ * other 2, before any vertex moves) selects its end with the smaller
+ * (|x.r - delta|, id); the selected vertices and their partners form V3.  With
+ * mu = identity this is the loop below. */
 static int32_t ora_separate(const ora_hg* h, int d, const float* x4, const int32_t* verts, int32_t nv,
-                            const uint8_t* innode, uint8_t* lab, const float* z1, const float* z2) {
+                            const uint8_t* innode, uint8_t* lab, const float* z1, const float* z2,
+                            const int32_t* mu) {
   float r[4], delta = 0.0f;
   for (int m = 0; m < d; ++m) r[m] = z2[m] - z1[m];
   for (int m = 0; m < d; ++m) {
@@ -1156,6 +1166,18 @@ static int32_t ora_separate(const ora_hg* h, int d, const float* x4, const int32
   }
   qsort(E, (size_t)ne, sizeof(ora_cut_edge), cmp_cut_edge);
   int32_t nsep = 0;
+  if (mu) {
+    /* all selections are taken against the 2-means labels, then applied */
+    for (int64_t t = 0; t < ne; ++t) {
+      if (!innode[mu[E[t].v]]) abort(); /* partners always share a node */
+    }
+    for (int64_t t = 0; t < ne; ++t) {
+      if (lab[E[t].v] != 3) { lab[E[t].v] = 3; nsep++; }
+      if (lab[mu[E[t].v]] != 3) { lab[mu[E[t].v]] = 3; nsep++; }
+    }
+    free(E);
+    return nsep;
+  }
   for (int64_t t = 0; t < ne; ++t) {
     uint8_t pv = lab[E[t].v], pw = lab[E[t].w];
     if (!((pv == 1 && pw == 2) || (pv == 2 && pw == 1))) continue;
@@ -1212,7 +1234,9 @@ static int cmp_rec_key(const void* a, const void* b) {
 /* between the parts, as 01, 00, 11, 10 (cut rows of the first parts first,  */
 /* of the second parts last).  One two-bit pair (b = 1).  Part membership is  */
 /* by position range, so the result does not depend on the order in which    */
-/* the nodes are treated.                                                     */
+/* the nodes are treated.  With a strengthened diagonal (mu) a row and its    */
+/* matched column hold one position of the row and column orders, so a       */
+/* vertex is sorted by the number of its pair: its own bits or its partner's. */
 typedef struct { int32_t comp; uint64_t heap; int32_t rec; } ora_key;
 static int cmp_key(const void* a, const void* b) {
   const ora_key* p = (const ora_key*)a;
@@ -1231,7 +1255,7 @@ static int32_t ora_find_rec(const ora_key* ks, int32_t n, int32_t comp, uint64_t
   return -1;
 }
 
-static void ora_cut_order(const ora_hg* h, int32_t sbd, int32_t* perm, const ora_tree* tree) {
+static void ora_cut_order(const ora_hg* h, int32_t sbd, const int32_t* mu, int32_t* perm, const ora_tree* tree) {
   int32_t k = h->k, nrec = tree->count;
   int32_t* pos = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
   for (int32_t i = 0; i < k; ++i) pos[perm[i]] = i;
@@ -1241,9 +1265,10 @@ static void ora_cut_order(const ora_hg* h, int32_t sbd, int32_t* perm, const ora
   static const int rank_bbd[4] = {0, 1, 2, 3}, rank_sbd[4] = {1, 0, 3, 2};
   const int* rank = sbd ? rank_sbd : rank_bbd;
   int32_t* tmp = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
+  uint8_t* vcode = (uint8_t*)calloc((size_t)(k > 0 ? k : 1), 1);
   for (int32_t r = 0; r < nrec; ++r) {
     int32_t o = tree->offset[r], n1 = tree->n1[r], n2 = tree->n2[r], ns = tree->nsep[r];
-    if (ns == 0 || (n2 == 0 && ns == 0)) continue;
+    if (ns == 0) continue;
     /* first / second part ranges of the splits of the two children */
     int32_t flo[2], fhi[2], slo[2], shi[2];
     for (int c = 0; c < 2; ++c) {
@@ -1257,7 +1282,6 @@ static void ora_cut_order(const ora_hg* h, int32_t sbd, int32_t* perm, const ora
     }
     int32_t a = sbd ? o + n1 : o + n1 + n2;
     int32_t cnt[4] = {0, 0, 0, 0};
-    uint8_t* code = (uint8_t*)malloc((size_t)ns);
     for (int32_t i = 0; i < ns; ++i) {
       int32_t w = perm[a + i];
       uint8_t cw = 0;
@@ -1268,15 +1292,20 @@ static void ora_cut_order(const ora_hg* h, int32_t sbd, int32_t* perm, const ora
           if (p >= slo[c] && p < shi[c]) cw |= 2;
         }
       }
-      code[i] = cw;
-      cnt[rank[cw]]++;
+      vcode[w] = cw;
+    }
+    for (int32_t i = 0; i < ns; ++i) {
+      int32_t w = perm[a + i];
+      cnt[rank[mu ? (vcode[w] | vcode[mu[w]]) : vcode[w]]]++;
     }
     int32_t start[4] = {0, cnt[0], cnt[0] + cnt[1], cnt[0] + cnt[1] + cnt[2]};
-    for (int32_t i = 0; i < ns; ++i) tmp[start[rank[code[i]]]++] = perm[a + i];
+    for (int32_t i = 0; i < ns; ++i) {
+      int32_t w = perm[a + i];
+      tmp[start[rank[mu ? (vcode[w] | vcode[mu[w]]) : vcode[w]]]++] = w;
+    }
     memcpy(perm + a, tmp, (size_t)ns * sizeof(int32_t));
-    free(code);
   }
-  free(pos); free(ks); free(tmp);
+  free(pos); free(ks); free(tmp); free(vcode);
 }
 
 /* Ordering of a graph model from fp32 coordinates.  A disconnected graph is
@@ -1286,7 +1315,7 @@ static void ora_cut_order(const ora_hg* h, int32_t sbd, int32_t* perm, const ora
  * records are sorted by (component, heap number). */
 ORA_EXPORT int ora_order(const ora_hg* h, int32_t d, const float* x4, uint64_t seed, int32_t km_iters,
                          int32_t min_part, int32_t max_depth, int32_t sbd, int32_t sep_rec, int32_t cut_order,
-                         int32_t* perm, ora_tree* tree) {
+                         const int32_t* mu, int32_t* perm, ora_tree* tree) {
   int32_t k = h->k;
   if (sep_rec && max_depth > 39) max_depth = 39;
   int32_t* cbase;
@@ -1318,7 +1347,7 @@ ORA_EXPORT int ora_order(const ora_hg* h, int32_t d, const float* x4, uint64_t s
     float z1[4], z2[4];
     if (!ora_bisect(d, x4, verts, nd.size, seed, nd.heap, km_iters, nlab, z1, z2)) continue;
     for (int32_t i = 0; i < nd.size; ++i) { lab[verts[i]] = nlab[i]; innode[verts[i]] = 1; }
-    ora_separate(h, d, x4, verts, nd.size, innode, lab, z1, z2);
+    ora_separate(h, d, x4, verts, nd.size, innode, lab, z1, z2, mu);
     int32_t c1 = 0, c2 = 0, c3 = 0;
     for (int32_t i = 0; i < nd.size; ++i) {
       uint8_t l = lab[verts[i]];
@@ -1342,7 +1371,7 @@ ORA_EXPORT int ora_order(const ora_hg* h, int32_t d, const float* x4, uint64_t s
       if (c3 > 0) queue[qt++] = (ora_node){3 * nd.heap + 1, nd.offset + (sbd ? c1 : c1 + c2), c3, nd.depth + 1, nd.comp};
     }
   }
-  if (cut_order && !sep_rec) ora_cut_order(h, sbd, perm, tree);
+  if (cut_order && !sep_rec) ora_cut_order(h, sbd, mu, perm, tree);
   /* sort records by (component, heap number) */
   int32_t nrec = tree->count;
   ora_rec_key* rk = (ora_rec_key*)malloc((size_t)(nrec > 0 ? nrec : 1) * sizeof(ora_rec_key));

@@ -698,3 +698,133 @@ def test_cut_order_special_cases(oracle_mod):
             assert np.array_equal(p0, p1)
             for f in t0:
                 assert np.array_equal(t0[f], t1[f]), f
+
+
+# ---------------------------------------------------------------- strengthened diagonal mu (Sec. 4.2, Alg. 7)
+def _matched_rows(perm, m, match):
+    rp = perm[perm < m].astype(np.int64)
+    return rp, np.asarray(match, dtype=np.int64)[rp]
+
+
+def _owners_of_pairs_agree(k, m, perm, tree, sbd, match):
+    part = _owner_info(k, perm, tree, sbd)
+    return np.array_equal(part[:m], part[m + np.asarray(match)])
+
+
+def test_matched_luproblem_example(oracle_mod):
+    """Ex. luproblem: with its diagonal as the matching and every row placed
+    on its column (rows and columns of B at the left, of C at the right, row
+    and column 4 between), one split gives the example's BBD form: blocks of
+    b = 2 and c = 2 pairs and a border of d = 1 pair, the matrix unchanged up
+    to the order of the two blocks."""
+    O = oracle_mod
+    g = json.load(open(os.path.join(GOLD, "luproblem.json")))
+    M = np.array(g["matrix"])
+    a = g["a"]
+    assert abs(round(np.linalg.det(M)) - g["det_A"]) == 0
+    r, c = np.nonzero(M)
+    A = W.csr_from_coo(a, a, r, c, "luproblem")
+    hg = O.build_from_matrix("bipartite", A)
+    pts = np.array([[0, 0], [0, 1], [10, 0], [10, 1], [5, 0.5]], dtype=np.float32)
+    x4 = _x4(np.concatenate([pts, pts]))
+    match = np.arange(a)
+    for sbd in (False, True):
+        perm, tree = O.order(hg, 2, x4, seed=1, min_part=1, max_depth=1, sbd=sbd, match=match)
+        n1, n2, ns = (int(tree[f][0]) for f in ("n1", "n2", "nsep"))
+        assert sorted([n1 // 2, n2 // 2]) == [g["b"], g["c"]] and ns // 2 == g["d"]
+        rp, cp = _matched_rows(perm, a, match)
+        assert np.array_equal(rp, cp)
+        blocks = [set(rp[:2]), set(rp[2:4]) if not sbd else set(rp[3:5])]
+        assert sorted(map(sorted, blocks)) == [[0, 1], [2, 3]]
+        assert rp[4 if not sbd else 2] == 4
+        B = M[np.ix_(rp, cp)]
+        lo, hi = (slice(0, 2), slice(2, 4)) if not sbd else (slice(0, 2), slice(3, 5))
+        assert not B[lo, hi].any() and not B[hi, lo].any()
+
+
+@pytest.mark.parametrize("cut_order", [False, True])
+@pytest.mark.parametrize("sbd", [False, True])
+@pytest.mark.parametrize("seed", [1, 2])
+def test_matched_square_blocks(oracle_mod, sbd, seed, cut_order):
+    """Unsymmetric mesh pattern with a strengthened diagonal, random
+    coordinates (many matching edges cut): every matched pair (row i, column
+    mu(i)) has one owner (no matching edge leaves the diagonal blocks and
+    separators); the rows with their matched columns give square diagonal
+    blocks: with the column order mu(row order) the diagonal is full and, at
+    every split, the blocks (R1, C2) and (R2, C1) are empty.  Without the
+    matching, separators split pairs.  The cut-row ordering (pairs sorted by
+    the two-bit numbers of row and column together) keeps all of this."""
+    O = oracle_mod
+    A = W.with_strengthened_diagonal(W.grid_laplacian_2d(36), 0.7, seed)
+    match = A.meta["match"]
+    m = A.m
+    hg = O.build_from_matrix("bipartite", A)
+    x4 = O.init_coords(hg.k, 2, seed)
+    perm, tree = O.order(hg, 2, x4, seed=seed, min_part=6, sbd=sbd, match=match, cut_order=cut_order)
+    _check_ordering(O, A, hg, perm, tree, sbd)
+    assert _owners_of_pairs_agree(hg.k, m, perm, tree, sbd, match)
+    rp, cp = _matched_rows(perm, m, match)
+    assert sorted(rp.tolist()) == list(range(m)) and sorted(cp.tolist()) == list(range(m))
+    dense = np.zeros((m, m), dtype=bool)
+    r = np.repeat(np.arange(m), np.diff(A.rowptr))
+    dense[r, A.colidx] = True
+    B = dense[np.ix_(rp, cp)]
+    assert B.diagonal().all()
+    for i in range(len(tree["heap"])):
+        o, n1, n2, ns = (int(tree[f][i]) for f in ("offset", "n1", "n2", "nsep"))
+        if n2 == 0 and ns == 0:
+            continue
+        assert o % 2 == 0 and n1 % 2 == 0 and n2 % 2 == 0 and ns % 2 == 0
+        p0, p1, p2 = o // 2, n1 // 2, n2 // 2
+        r1 = slice(p0, p0 + p1)
+        r2 = slice(p0 + p1 + ns // 2, p0 + p1 + ns // 2 + p2) if sbd else slice(p0 + p1, p0 + p1 + p2)
+        assert not B[r1, r2].any() and not B[r2, r1].any()
+    plain, tree0 = O.order(hg, 2, x4, seed=seed, min_part=6, sbd=sbd)
+    assert not _owners_of_pairs_agree(hg.k, m, plain, tree0, sbd, match)
+
+
+def test_matched_separator_order_free(oracle_mod):
+    """The separator with a matching in its order-free reading: at the root,
+    V3 is exactly the set of ends with the smaller (|x.r - delta|, id) of the
+    edges cut by the 2-means labels, with their partners; V1 and V2 keep the
+    2-means labels."""
+    O = oracle_mod
+    A = W.with_strengthened_diagonal(W.powerlaw_symmetric(800, seed=4), 0.6, 4)
+    match = A.meta["match"]
+    m = A.m
+    hg = O.build_from_matrix("bipartite", A)
+    x4 = O.init_coords(hg.k, 3, 4)
+    comps = O.components(hg)
+    root = np.flatnonzero(comps == comps[0]).astype(np.int32)
+    perm, tree = O.order(hg, 3, x4, seed=4, max_depth=1, match=match, min_part=1)
+    # the first component's root node; its vertices in their initial order
+    j = [i for i in range(len(tree["heap"])) if tree["comp"][i] == 0 and tree["heap"][i] == 1][0]
+    o, n1, n2, ns = (int(tree[f][j]) for f in ("offset", "n1", "n2", "nsep"))
+    assert np.array_equal(np.sort(perm[o:o + n1 + n2 + ns]), root)
+    verts = root  # the root's order before its split: ascending vertex ids
+    ok, lab, z1, z2 = O.bisect(3, x4, verts, seed=4, key=1)
+    assert ok
+    r = (z2[:3] - z1[:3]).astype(np.float32)
+    mid = (np.float32(0.5) * (z1[:3] + z2[:3])).astype(np.float32)
+    delta = np.float32(0)
+    for t in range(3):
+        delta = np.float32(delta + np.float32(mid[t] * r[t]))
+
+    def s(v):
+        acc = np.float32(0)
+        for t in range(3):
+            acc = np.float32(acc + np.float32(np.float32(x4[v, t]) * r[t]))
+        return abs(np.float32(acc - delta))
+
+    L = dict(zip(verts.tolist(), lab.tolist()))
+    mu = O.mu_from_match(hg, match)
+    sel = set()
+    for v in verts.tolist():
+        for w in hg.adj[hg.adj_ptr[v]:hg.adj_ptr[v + 1]].tolist():
+            if w > v and w in L and L[v] != L[w]:
+                sel.add(min((s(v), v), (s(w), w))[1])
+    sep = sel | {int(mu[v]) for v in sel}
+    got = perm[o + n1 + n2:o + n1 + n2 + ns]
+    assert set(got.tolist()) == sep
+    side1 = set(perm[o:o + n1].tolist())
+    assert all(L[v] == L[next(iter(side1))] for v in side1)

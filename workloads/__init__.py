@@ -20,6 +20,10 @@ circuit matrices); those are not available, so these generators stand in:
   count.
 * ``batch_mix``: many independent matrices of uneven size, half grids and half
   random symmetric patterns.
+* ``with_strengthened_diagonal``: an unsymmetric square pattern made from a
+  symmetric one with a full diagonal (off-diagonal entries dropped at random,
+  columns permuted at random), together with the perfect matching that the
+  permuted diagonal forms (``meta["match"]``: row i's matched column).
 """
 from __future__ import annotations
 
@@ -211,6 +215,26 @@ def random_pattern(m: int, n: int, nnz: int, seed: int, stream: int = 0) -> Matr
     rows = (r[:nnz] % np.uint64(max(m, 1))).astype(np.int64)
     cols = (r[nnz:] % np.uint64(max(n, 1))).astype(np.int64)
     return csr_from_coo(m, n, rows, cols, f"random_{m}x{n}")
+
+
+def with_strengthened_diagonal(A: Matrix, keep: float, seed: int) -> Matrix:
+    """Unsymmetric pattern with a known perfect matching: every off-diagonal
+    entry of the square pattern A is kept with probability ``keep``, the
+    diagonal is added, and the columns are permuted by a seeded random
+    permutation pi (entry (i, j) -> (i, pi[j])).  meta["match"][i] = pi[i], the
+    column that row i's diagonal entry moved to."""
+    if A.m != A.n:
+        raise ValueError("needs a square pattern")
+    n = A.n
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(A.rowptr.astype(np.int64)))
+    cols = A.colidx.astype(np.int64)
+    u = rand_uniform(seed, 40, rows.size)
+    off = rows != cols
+    sel = off & (u < keep)
+    rows, cols = np.concatenate([rows[sel], np.arange(n)]), np.concatenate([cols[sel], np.arange(n)])
+    pi = np.argsort(rand_u64(seed, 41, n), kind="stable").astype(np.int64)
+    B = csr_from_coo(n, n, rows, pi[cols], f"{A.name}_unsym", {"match": pi.astype(np.int32)})
+    return B
 
 
 def batch_mix(count: int, seed: int, nmin: int = 200, nmax: int = 20000) -> list[Matrix]:

@@ -259,6 +259,37 @@ vmo_status vmo_order_sbd(vmo_hg hg, const float* coords, const vmo_params* param
 vmo_status vmo_order_vertices(vmo_hg hg, const float* coords, const vmo_params* params, int32_t sbd,
                               int32_t* perm, vmo_tree* tree, void* stream);
 
+/* Recursive BBD (or SBD) ordering of a square, generally unsymmetric matrix
+ * that keeps a strengthened diagonal (Sec. 4.2 and Algorithm 7: a perfect
+ * matching M of the bipartite model, seen as the map mu; whenever a vertex
+ * joins a separator its partner mu(v) joins too, so no edge of M leaves the
+ * diagonal blocks and every block on the diagonal is square).
+ * The paper's edge loop gives an order-dependent result once partners move
+ * and fixes no order; this entry point takes the order-free reading: every
+ * edge cut by the 2-means labels selects its end with the smaller
+ * (|x.r - delta|, vertex id), and the selected vertices and their partners
+ * form V3 (with mu the identity this is the separator of vmo_order_bbd).
+ * With params->cut_order a separator is sorted by the two-bit number of
+ * each pair (the row's bits or its matched column's).
+ * hg: bipartite model (VMO_BIPARTITE) of an m x m pattern.
+ * match: device int32[m], match[i] = the column matched to row i: a
+ * permutation of [0, m) with (i, match[i]) an entry of the pattern.
+ * row_perm, col_perm: device int32[m] out; row_perm[t] = the row at position
+ * t, col_perm[t] = match[row_perm[t]], so the matched entries form the
+ * diagonal of the permuted matrix.  vperm: optional device int32[2m] out, the
+ * vertex order (rows 0..m-1, columns m..2m-1, interleaved as they lie in the
+ * recursive partition).  tree: optional, in positions of the vertex order
+ * (every range holds whole pairs, so halving gives row positions).
+ * sbd: 0 BBD [V1, V2, V3], 1 SBD [V1, V3, V2].  coords: NULL (the layout is
+ * computed) or device float[4 * 2m].
+ * Errors: VMO_ERR_INVALID for a model other than bipartite, a non-square
+ * pattern, a null match or output, and a match that is not a perfect
+ * matching of the pattern (index out of range, a column used twice, or a
+ * pair that is not an entry). */
+vmo_status vmo_order_matched(vmo_hg hg, const float* coords, const vmo_params* params, int32_t sbd,
+                             const int32_t* match, int32_t* row_perm, int32_t* col_perm, int32_t* vperm,
+                             vmo_tree* tree, void* stream);
+
 /* Batched recursive ordering of `count` independent square patterns in one
  * launch sequence (symmetric model).  The matrices are joined
  * block-diagonally on the device and every connected component of every

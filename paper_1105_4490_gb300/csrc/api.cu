@@ -207,8 +207,37 @@ __global__ void k_is_row(const int32_t* __restrict__ ord, int64_t n, int32_t m, 
   if (i < n) flag[i] = ord[i] < m ? 1 : 0;
 }
 
+// A strengthened diagonal: match[i] in [0, m), every column once, and the
+// pattern holds (i, match[i]) (row vertex i is linked to column vertex m + match[i]).
+__global__ void k_check_match(const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                              const int32_t* __restrict__ match, int32_t m, int32_t* __restrict__ seen,
+                              int32_t* __restrict__ err) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int32_t c = match[i];
+  if (c < 0 || c >= m) { atomicOr(err, 1); return; }
+  if (atomicAdd(&seen[c], 1) != 0) atomicOr(err, 2);
+  bool found = false;
+  for (int32_t t = adj_ptr[i]; t < adj_ptr[i + 1] && !found; ++t) found = adj[t] == m + c;
+  if (!found) atomicOr(err, 4);
+}
+
+__global__ void k_build_mu(const int32_t* __restrict__ match, int32_t m, int32_t* __restrict__ mu) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  mu[i] = m + match[i];
+  mu[m + match[i]] = i;
+}
+
+__global__ void k_match_cols(const int32_t* __restrict__ row_perm, const int32_t* __restrict__ match, int32_t m,
+                             int32_t* __restrict__ col_perm) {
+  int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) col_perm[t] = match[row_perm[t]];
+}
+
 vmo_status run_order(vmo_hg_s* h, const float* coords, const vmo_params* p, int sbd, int32_t* vperm,
-                     int32_t* row_perm, int32_t* col_perm, vmo_tree* tree, cudaStream_t s) {
+                     int32_t* row_perm, int32_t* col_perm, vmo_tree* tree, cudaStream_t s,
+                     const int32_t* match = nullptr) {
   VMO_TRY(ensure_device());
   VMO_TRY(check_params(p));
   if (!h) return invalid("handle is null");
@@ -217,6 +246,32 @@ vmo_status run_order(vmo_hg_s* h, const float* coords, const vmo_params* p, int 
   if (coords && !aligned16(coords)) return invalid("coords must be 16-byte aligned");
   Scratch sc(s);
   const int64_t k = h->k;
+  int32_t* mu = nullptr;
+  if (match) {
+    if (h->model != VMO_BIPARTITE || h->m != h->n)
+      return invalid("a strengthened diagonal needs the bipartite model of a square pattern");
+    const int32_t m = h->m;
+    int32_t *seen, *err;
+    VMO_TRY(sc.alloc(&mu, std::max<int64_t>(k, 1)));
+    VMO_TRY(sc.alloc(&seen, std::max<int32_t>(m, 1)));
+    VMO_TRY(sc.alloc(&err, 1));
+    VMO_CUDA(cudaMemsetAsync(seen, 0, std::max<int32_t>(m, 1) * sizeof(int32_t), s));
+    VMO_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+    if (m > 0) {
+      launch(k_check_match, grid_for(m, 256), 256, 0, s, h->adj_ptr.ptr, h->adj.ptr, match, m, seen, err);
+      VMO_LAUNCHED("check_match");
+    }
+    int32_t herr = 0;
+    VMO_CUDA(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s));
+    VMO_CUDA(cudaStreamSynchronize(s));
+    if (herr & 1) return invalid("match: a column index outside [0, m)");
+    if (herr & 2) return invalid("match: a column matched to two rows (not a permutation)");
+    if (herr & 4) return invalid("match: a row not linked to its matched column (not an entry of the pattern)");
+    if (m > 0) {
+      launch(k_build_mu, grid_for(m, 256), 256, 0, s, match, m, mu);
+      VMO_LAUNCHED("build_mu");
+    }
+  }
   ComponentGroups g;
   VMO_TRY(group_components(h, g, s, sc));
   float4* x = (float4*)coords;
@@ -225,7 +280,7 @@ vmo_status run_order(vmo_hg_s* h, const float* coords, const vmo_params* p, int 
     VMO_TRY(layout_grouped(h, g, p, x, s, sc));
   }
   OrderState st;
-  VMO_TRY(order_grouped(h, g, x, p, sbd, st, s, sc));
+  VMO_TRY(order_grouped(h, g, x, p, sbd, st, s, sc, mu));
   if (vperm) VMO_CUDA(cudaMemcpyAsync(vperm, st.ord, k * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   if (row_perm || col_perm) {
     if (h->model == VMO_SYMMETRIC) {
@@ -243,6 +298,10 @@ vmo_status run_order(vmo_hg_s* h, const float* coords, const vmo_params* p, int 
       if (k > 0) {
         launch(k_split_rows, grid_for(k, 256), 256, 0, s, st.ord, k, h->m, flag, row_perm, col_perm);
         VMO_LAUNCHED("split_rows");
+      }
+      if (match && h->m > 0) {  // every column at its matched row's position
+        launch(k_match_cols, grid_for(h->m, 256), 256, 0, s, row_perm, match, h->m, col_perm);
+        VMO_LAUNCHED("match_cols");
       }
     }
   }
@@ -504,6 +563,14 @@ vmo_status vmo_order_vertices(vmo_hg hg, const float* coords, const vmo_params* 
                               vmo_tree* tree, void* stream) {
   if (!perm && hg && hg->k > 0) return invalid("perm is null");
   return run_order(hg, coords, params, sbd ? 1 : 0, perm, nullptr, nullptr, tree, (cudaStream_t)stream);
+}
+
+vmo_status vmo_order_matched(vmo_hg hg, const float* coords, const vmo_params* params, int32_t sbd,
+                             const int32_t* match, int32_t* row_perm, int32_t* col_perm, int32_t* vperm,
+                             vmo_tree* tree, void* stream) {
+  if (!match) return invalid("match is null");
+  if (!row_perm || !col_perm) return invalid("row_perm and col_perm are required");
+  return run_order(hg, coords, params, sbd ? 1 : 0, vperm, row_perm, col_perm, tree, (cudaStream_t)stream, match);
 }
 
 vmo_status vmo_cut_size(vmo_hg hg, const int32_t* part, int32_t nparts, int64_t* cutnet, int64_t* lambda1,

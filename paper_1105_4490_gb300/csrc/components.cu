@@ -167,7 +167,7 @@ vmo_status layout_grouped(const vmo_hg_s* h, const ComponentGroups& g, const vmo
 }
 
 vmo_status order_grouped(const vmo_hg_s* h, const ComponentGroups& g, const float4* x, const vmo_params* p, int sbd,
-                         OrderState& st, cudaStream_t s, Scratch& sc) {
+                         OrderState& st, cudaStream_t s, Scratch& sc, const int32_t* mu) {
   OrderParams op;
   op.d = p->d;
   op.km_iters = p->km_iters;
@@ -178,6 +178,7 @@ vmo_status order_grouped(const vmo_hg_s* h, const ComponentGroups& g, const floa
   op.cut_order = p->cut_order;
   st.adj_ptr = h->adj_ptr.ptr;
   st.adj = h->adj.ptr;
+  st.mu = mu;
   std::vector<uint64_t> seeds(g.base.size() - 1, p->seed);
   VMO_TRY(order_setup(st, x, g.base, seeds, op, g.cperm, s, sc));
   VMO_TRY(order_levels(st, op, s, sc));

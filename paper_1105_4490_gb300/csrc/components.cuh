@@ -40,8 +40,9 @@ vmo_status layout_grouped(const vmo_hg_s* h, const ComponentGroups& g, const vmo
 
 // Recursive ordering of a graph model from coordinates x: every component
 // from its own root, components one after the other.  st.ord holds the
-// vertex permutation on return.
+// vertex permutation on return.  mu: matching partner of every vertex
+// (device int32[k], a strengthened diagonal) or null.
 vmo_status order_grouped(const vmo_hg_s* h, const ComponentGroups& g, const float4* x, const vmo_params* p, int sbd,
-                         OrderState& st, cudaStream_t s, Scratch& sc);
+                         OrderState& st, cudaStream_t s, Scratch& sc, const int32_t* mu = nullptr);
 
 }  // namespace vmo

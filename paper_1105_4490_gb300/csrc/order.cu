@@ -287,6 +287,55 @@ __global__ void k_separator(const int32_t* __restrict__ ord, const int32_t* __re
   }
 }
 
+// With a strengthened diagonal (Algorithm 7 moves a selected vertex's
+// matching partner too), in the order-free reading: every edge cut by the
+// 2-means labels selects its end with the smaller (s, id); the selected
+// vertices and their partners form V3.  Partners always share a node.
+__global__ void k_pick(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
+                       const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                       const int32_t* __restrict__ vnode, const uint8_t* __restrict__ vlab,
+                       const float* __restrict__ vs, uint8_t* __restrict__ vpick) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int s = seg[i];
+  if (s < 0) return;
+  int32_t v = ord[i];
+  uint8_t l = vlab[v], pick = 0;
+  if (l != 0) {
+    float sv = vs[v];
+    for (int32_t t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) {
+      int32_t w = adj[t];
+      if (vnode[w] != s) continue;
+      uint8_t lw = vlab[w];
+      if (lw == l || lw == 0) continue;
+      float sw = vs[w];
+      if (sv < sw || (sv == sw && v < w)) { pick = 1; break; }
+    }
+  }
+  vpick[v] = pick;
+}
+
+__global__ void k_separator_mu(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
+                               const int32_t* __restrict__ mu, const uint8_t* __restrict__ vlab,
+                               const uint8_t* __restrict__ vpick, NodeDev* __restrict__ nodes,
+                               uint8_t* __restrict__ labf) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int s = i < n ? seg[i] : -1;
+  uint8_t l = 0;
+  if (s >= 0) {
+    int32_t v = ord[i];
+    l = vlab[v];
+    if (l != 0 && (vpick[v] | vpick[mu[v]])) l = 3;
+    labf[i] = l;
+  }
+  int key = (l != 0) ? s * 4 + l : -1;
+  unsigned peers = __match_any_sync(0xffffffffu, key);
+  if (key >= 0 && (int)lane_id() == __ffs(peers) - 1) {
+    int* c = l == 1 ? &nodes[s].c1 : (l == 2 ? &nodes[s].c2 : &nodes[s].c3);
+    atomicAdd(c, (int)__popc(peers));
+  }
+}
+
 __global__ void k_pack(const int32_t* __restrict__ seg, const uint8_t* __restrict__ labf, int64_t n,
                        const NodeDev* __restrict__ nodes, unsigned long long* __restrict__ pk) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -519,28 +568,42 @@ __global__ void k_inverse_perm(const int32_t* __restrict__ ord, int64_t n, int32
   if (p < n) pos[ord[p]] = (int32_t)p;
 }
 
-// Two-bit number of every separator position and its sort key (node, rank);
-// other positions sort last.
+// Two-bit number of the vertex at every separator position.
 __global__ void k_cut_codes(const int32_t* __restrict__ ord, const int32_t* __restrict__ pos,
                             const int32_t* __restrict__ posrec, int64_t n, const CutNode* __restrict__ cn,
-                            const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj, int sbd,
-                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                            const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                            uint8_t* __restrict__ vcode) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int i = posrec[p];
+  if (i < 0) return;
+  const CutNode c = cn[i];
+  const int32_t w = ord[p];
+  int code = 0;
+  for (int32_t t = adj_ptr[w]; t < adj_ptr[w + 1]; ++t) {
+    const int32_t q = pos[adj[t]];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (q >= c.flo[k] && q < c.fhi[k]) code |= 1;
+      if (q >= c.slo[k] && q < c.shi[k]) code |= 2;
+    }
+  }
+  vcode[w] = (uint8_t)code;
+}
+
+// Sort key (node, rank) of every separator position; other positions sort
+// last.  With a matching a vertex is ranked by its pair's number (its own
+// bits or its partner's): row and matched column share one position.
+__global__ void k_cut_keys(const int32_t* __restrict__ ord, const int32_t* __restrict__ posrec, int64_t n,
+                           const uint8_t* __restrict__ vcode, const int32_t* __restrict__ mu, int sbd,
+                           uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int i = posrec[p];
   uint64_t key = ~0ull;
   if (i >= 0) {
-    const CutNode c = cn[i];
     const int32_t w = ord[p];
-    int code = 0;
-    for (int32_t t = adj_ptr[w]; t < adj_ptr[w + 1]; ++t) {
-      const int32_t q = pos[adj[t]];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        if (q >= c.flo[k] && q < c.fhi[k]) code |= 1;
-        if (q >= c.slo[k] && q < c.shi[k]) code |= 2;
-      }
-    }
+    const int code = vcode[w] | (mu ? vcode[mu[w]] : 0);
     const int rank = sbd ? (code == 1 ? 0 : code == 0 ? 1 : code == 3 ? 2 : 3) : code;
     key = (uint64_t)i * 4 + (uint64_t)rank;
   }
@@ -664,8 +727,15 @@ vmo_status order_levels(OrderState& st, const OrderParams& op, cudaStream_t s, S
       launch(k_vertex_state<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.ord, st.seg, n, st.nodes, st.lab, st.vlab,
                                                                st.vs);
     });
-    launch(k_separator, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vnode, st.vlab, st.vs,
-                                                       st.nodes, labf);
+    if (st.mu) {
+      launch(k_pick, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vnode, st.vlab,
+             st.vs, st.vpick);
+      launch(k_separator_mu, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.mu, st.vlab, st.vpick, st.nodes,
+             labf);
+    } else {
+      launch(k_separator, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vnode, st.vlab,
+             st.vs, st.nodes, labf);
+    }
     launch(k_pack, grid_for(n, kBlock), kBlock, 0, s, st.seg, labf, n, st.nodes, pk);
     VMO_LAUNCHED("separator");
     VMO_TRY(scan_inclusive<uint64_t>((const uint64_t*)pk, (uint64_t*)pre, n, s, sc));
@@ -704,6 +774,7 @@ vmo_status order_setup(OrderState& st, const float4* x, const std::vector<int64_
   VMO_TRY(sc.alloc(&st.vnode, std::max<int64_t>(n, 1)));
   VMO_TRY(sc.alloc(&st.vlab, std::max<int64_t>(n, 1)));
   VMO_TRY(sc.alloc(&st.vs, std::max<int64_t>(n, 1)));
+  if (st.mu) VMO_TRY(sc.alloc(&st.vpick, std::max<int64_t>(n, 1)));
   VMO_TRY(sc.alloc(&st.pbase, P + 1));
   VMO_TRY(sc.alloc(&st.seeds, std::max(P, 1)));
   // node table capacity: active nodes of one level have > min_part vertices each
@@ -824,6 +895,7 @@ vmo_status cut_order_pass(OrderState& st, const OrderParams& op, cudaStream_t s,
   if (nrec == 0) return VMO_OK;
   CutNode* cn;
   int32_t *posrec, *pos, *ord2;
+  uint8_t* vcode;
   int64_t *sz, *gstart;
   uint64_t *k1, *k2;
   uint32_t *v1, *v2;
@@ -831,6 +903,7 @@ vmo_status cut_order_pass(OrderState& st, const OrderParams& op, cudaStream_t s,
   VMO_TRY(sc.alloc(&posrec, n));
   VMO_TRY(sc.alloc(&pos, n));
   VMO_TRY(sc.alloc(&ord2, n));
+  VMO_TRY(sc.alloc(&vcode, n));
   VMO_TRY(sc.alloc(&sz, nrec));
   VMO_TRY(sc.alloc(&gstart, nrec));
   VMO_TRY(sc.alloc(&k1, n));
@@ -840,8 +913,8 @@ vmo_status cut_order_pass(OrderState& st, const OrderParams& op, cudaStream_t s,
   VMO_CUDA(cudaMemsetAsync(posrec, 0xFF, n * sizeof(int32_t), s));
   launch(k_cut_nodes, grid_for(nrec, kBlock), kBlock, 0, s, st.tree, idx, nrec, op.sbd, cn, posrec);
   launch(k_inverse_perm, grid_for(n, kBlock), kBlock, 0, s, st.ord, n, pos);
-  launch(k_cut_codes, grid_for(n, kBlock), kBlock, 0, s, st.ord, pos, posrec, n, cn, st.adj_ptr, st.adj, op.sbd, k1,
-         v1);
+  launch(k_cut_codes, grid_for(n, kBlock), kBlock, 0, s, st.ord, pos, posrec, n, cn, st.adj_ptr, st.adj, vcode);
+  launch(k_cut_keys, grid_for(n, kBlock), kBlock, 0, s, st.ord, posrec, n, vcode, st.mu, op.sbd, k1, v1);
   launch(k_cut_sizes, grid_for(nrec, kBlock), kBlock, 0, s, cn, nrec, sz);
   VMO_LAUNCHED("cut_codes");
   int64_t m = 0;

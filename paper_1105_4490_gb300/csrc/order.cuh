@@ -63,6 +63,8 @@ struct OrderState {
   uint64_t* seeds = nullptr;          // seed of every problem
   const int32_t* adj_ptr = nullptr;   // graph (global vertex ids)
   const int32_t* adj = nullptr;
+  const int32_t* mu = nullptr;        // matching partner of every vertex (strengthened diagonal) or null
+  uint8_t* vpick = nullptr;           // separator selection of each vertex (with mu)
   NodeDev* nodes = nullptr;
   int node_cap = 0;
   int nroots = 0;

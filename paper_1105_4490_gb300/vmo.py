@@ -80,7 +80,7 @@ class Params:
 
 SYMBOLS = ["vmo_default_params", "vmo_build_hypergraph", "vmo_hg_vertices", "vmo_hg_nets", "vmo_hg_arrays",
            "vmo_components", "vmo_init_coords", "vmo_layout", "vmo_layout_step", "vmo_coarsen", "vmo_bisect",
-           "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_cut_size", "vmo_destroy",
+           "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_order_matched", "vmo_cut_size", "vmo_destroy",
            "vmo_status_string", "vmo_last_error", "vmo_stats_reset", "vmo_stats_get", "vmo_batch_order",
            "vmo_batch_layout", "vmo_bisect_noalloc", "vmo_server_default_config", "vmo_server_estimate_bytes",
            "vmo_server_plan", "vmo_server_create", "vmo_server_submit", "vmo_server_poll", "vmo_server_wait",
@@ -135,6 +135,7 @@ def load(path: str | None = None):
     for nm in ("vmo_order_bbd", "vmo_order_sbd"):
         getattr(lib, nm).argtypes = [V, V, C.POINTER(_Params), V, V, C.POINTER(_Tree), V]
     lib.vmo_order_vertices.argtypes = [V, V, C.POINTER(_Params), I32, V, C.POINTER(_Tree), V]
+    lib.vmo_order_matched.argtypes = [V, V, C.POINTER(_Params), I32, V, V, V, V, C.POINTER(_Tree), V]
     lib.vmo_cut_size.argtypes = [V, V, I32, P64, P64, V]
     lib.vmo_batch_order.argtypes = [C.POINTER(_Csr), I32, V, C.POINTER(_Params), I32, V, V]
     lib.vmo_batch_layout.argtypes = [C.POINTER(_Csr), I32, C.POINTER(_Params), V, V]
@@ -330,6 +331,21 @@ class Hypergraph:
         _check(load().vmo_order_vertices(self._h, _ptr(coords), C.byref(p), int(sbd), _ptr(perm), C.byref(ct),
                                          _stream()))
         return perm, {f: v[:ct.count] for f, v in t.items()}
+
+    def order_matched(self, match: torch.Tensor, params: Params | None = None, coords: torch.Tensor | None = None,
+                      sbd: bool = False):
+        """Ordering that keeps a strengthened diagonal (bipartite model of a
+        square pattern; match[i] = column matched to row i):
+        (row_perm, col_perm, vertex_perm, tree), col_perm = match[row_perm]."""
+        p = (params or Params())._c()
+        match = torch.as_tensor(match).to(device="cuda", dtype=torch.int32).contiguous()
+        rp = torch.empty(self.m, dtype=torch.int32, device="cuda")
+        cp = torch.empty(self.m, dtype=torch.int32, device="cuda")
+        vp = torch.empty(self.k, dtype=torch.int32, device="cuda")
+        t, ct = self._tree(2 * self.k + 16)
+        _check(load().vmo_order_matched(self._h, _ptr(coords), C.byref(p), int(sbd), _ptr(match), _ptr(rp), _ptr(cp),
+                                        _ptr(vp), C.byref(ct), _stream()))
+        return rp, cp, vp, {f: v[:ct.count] for f, v in t.items()}
 
     def cut_size(self, part: torch.Tensor, nparts: int):
         """(cut-net count, lambda - 1) of a vertex partition over the nets."""

@@ -451,3 +451,86 @@ def test_full_pipeline_replay_d(V, O, d, sbd):
     perm_o, tree_o = O.order(ref, d, _np(x), seed=6, min_part=32, sbd=sbd)
     assert np.array_equal(_np(perm), perm_o)
     assert np.array_equal(_np(tree["nsep"]), tree_o["nsep"])
+
+
+def _matched_compare(V, O, A, d, coords, sbd, min_part=16, max_depth=62, seed=5, sep_rec=False, cut_order=False):
+    match = A.meta["match"]
+    hg = V.Hypergraph.from_matrix(A, "bipartite")
+    ref = O.build_from_matrix("bipartite", A)
+    p = V.Params(d=d, min_part=min_part, max_depth=max_depth, seed=seed, sep_recursion=int(sep_rec),
+                 cut_order=int(cut_order))
+    rp, cp, vp, tree = hg.order_matched(torch.as_tensor(match), p, torch.as_tensor(coords).cuda(), sbd=sbd)
+    perm_o, tree_o = O.order(ref, d, coords, seed=seed, min_part=min_part, max_depth=max_depth, sbd=sbd,
+                             sep_rec=sep_rec, cut_order=cut_order, match=match)
+    assert np.array_equal(_np(vp), perm_o)
+    assert np.array_equal(_np(tree["heap"]).astype(np.uint64), tree_o["heap"])
+    for f in ("offset", "n1", "n2", "nsep", "depth", "comp"):
+        assert np.array_equal(_np(tree[f]), tree_o[f]), f
+    rows = perm_o[perm_o < A.m]
+    assert np.array_equal(_np(rp), rows)
+    assert np.array_equal(_np(cp), match[rows])
+
+
+@pytest.mark.parametrize("sbd", [False, True])
+def test_order_matched(V, O, sbd):
+    """Strengthened diagonal (Sec. 4.2, Algorithm 7 with mu) bit-exact against
+    the oracle: an unsymmetric mesh pattern and an unsymmetric power-law
+    pattern, random coordinates in d = 2 and 3, down to single pairs, with
+    separator recursion and with the cut-row ordering."""
+    G = W.with_strengthened_diagonal(W.grid_laplacian_2d(60), 0.7, 3)
+    _matched_compare(V, O, G, 2, O.init_coords(2 * G.m, 2, 3), sbd)
+    P = W.with_strengthened_diagonal(W.powerlaw_symmetric(6000, seed=13), 0.6, 13)
+    _matched_compare(V, O, P, 3, O.init_coords(2 * P.m, 3, 13), sbd, min_part=2)
+    _matched_compare(V, O, P, 2, O.init_coords(2 * P.m, 2, 14), sbd, min_part=0, max_depth=8)
+    _matched_compare(V, O, P, 3, O.init_coords(2 * P.m, 3, 15), sbd, min_part=4, sep_rec=True)
+    _matched_compare(V, O, P, 3, O.init_coords(2 * P.m, 3, 16), sbd, min_part=4, cut_order=True)
+
+
+def test_order_matched_full_pipeline(V, O):
+    """GPU multilevel layout of the bipartite model, then the matched ordering:
+    the oracle's ordering of the GPU coordinates is the same, and the
+    permuted matrix has a full diagonal and empty off-diagonal blocks at the
+    root split."""
+    A = W.with_strengthened_diagonal(W.grid_laplacian_2d(80), 0.75, 9)
+    match = A.meta["match"]
+    hg = V.Hypergraph.from_matrix(A, "bipartite")
+    p = V.Params(d=3, seed=2, min_part=32)
+    x = hg.layout(p)
+    rp, cp, vp, tree = hg.order_matched(torch.as_tensor(match), p, x)
+    ref = O.build_from_matrix("bipartite", A)
+    perm_o, _ = O.order(ref, 3, _np(x), seed=2, min_part=32, match=match)
+    assert np.array_equal(_np(vp), perm_o)
+    rp2, cp2, _, _ = hg.order_matched(torch.as_tensor(match), p)  # layout inside the call
+    assert np.array_equal(_np(rp2), _np(rp)) and np.array_equal(_np(cp2), _np(cp))
+    rp, cp = _np(rp), _np(cp)
+    dense = np.zeros((A.m, A.m), dtype=bool)
+    dense[np.repeat(np.arange(A.m), np.diff(A.rowptr)), A.colidx] = True
+    B = dense[np.ix_(rp, cp)]
+    assert B.diagonal().all()
+    n1, n2 = int(_np(tree["n1"])[0]) // 2, int(_np(tree["n2"])[0]) // 2
+    assert not B[:n1, n1:n1 + n2].any() and not B[n1:n1 + n2, :n1].any()
+
+
+def test_order_matched_rejects(V):
+    """A match that is not a perfect matching of the pattern, a non-square
+    pattern and the symmetric model are refused with an error, not run."""
+    A = W.with_strengthened_diagonal(W.grid_laplacian_2d(10), 0.7, 1)
+    match = torch.as_tensor(A.meta["match"]).clone()
+    hg = V.Hypergraph.from_matrix(A, "bipartite")
+    bad = [match.clone(), match.clone(), match.clone()]
+    bad[0][3] = A.m  # out of range
+    bad[1][3] = bad[1][4]  # a column used twice
+    dense = np.zeros((A.m, A.m), dtype=bool)
+    dense[np.repeat(np.arange(A.m), np.diff(A.rowptr)), A.colidx] = True
+    i, j = np.argwhere(~dense)[0]  # swap two matched columns onto a zero
+    bad[2][i], bad[2][int(np.flatnonzero(match.numpy() == j)[0])] = int(j), int(match[i])
+    for b in bad:
+        with pytest.raises(V.VmoError):
+            hg.order_matched(b)
+    R = W.powerlaw_rectangular(120, 100, seed=2)
+    with pytest.raises(V.VmoError):
+        V.Hypergraph.from_matrix(R, "bipartite").order_matched(torch.arange(120))
+    with pytest.raises(V.VmoError):
+        V.Hypergraph.from_matrix(A).order_matched(match)
+    rp, cp, _, _ = hg.order_matched(match)  # the handle still works
+    assert sorted(_np(rp).tolist()) == list(range(A.m))

@@ -27,7 +27,7 @@ _LIB_PATH = os.path.join(_HERE, "libvmo_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-MODELS = {"symmetric": 0, "bipartite": 1, "rownet": 2, "colnet": 3}
+MODELS = {"symmetric": 0, "bipartite": 1, "rownet": 2, "colnet": 3, "finegrain": 4}
 
 
 def build(force: bool = False) -> str:
@@ -100,6 +100,7 @@ def _load():
             lib.ora_order.argtypes = [C.POINTER(_HG), C.c_int32, P, C.c_uint64, C.c_int32, C.c_int32,
                                       C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P, C.POINTER(_Tree)]
             lib.ora_tree_free.argtypes = [C.POINTER(_Tree)]
+            lib.ora_finegrain_coords.argtypes = [C.POINTER(_HG), P, P]
             lib.ora_kmeans.argtypes = [C.c_int32, P, P, C.c_int32, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32,
                                        P, P]
             lib.ora_kmeans.restype = C.c_int32
@@ -353,6 +354,18 @@ def order(hg: Hypergraph, d: int, x4: np.ndarray, seed: int, km_iters: int = 20,
                 comp=_arr(t.comp, n, np.int32))
     _load().ora_tree_free(C.byref(t))
     return perm, tree
+
+
+def finegrain_coords(fg: Hypergraph, xb: np.ndarray) -> np.ndarray:
+    """Finegrain layout from the bipartite one (Sec. 4.2): every entry at the
+    mean of its row's and its column's points (FP64, k x 4)."""
+    if fg.model != MODELS["finegrain"]:
+        raise ValueError("needs the finegrain model")
+    s = fg._struct()
+    xf = np.ascontiguousarray(xb, dtype=np.float32).reshape(-1, 4)
+    out = np.zeros((max(fg.k, 1), 4), dtype=np.float64)
+    _load().ora_finegrain_coords(C.byref(s), _p(xf), _p(out))
+    return out[:fg.k]
 
 
 def mu_from_match(hg: Hypergraph, match: np.ndarray) -> np.ndarray:

@@ -72,6 +72,8 @@ static int cmp_i64(const void* a, const void* b) {
 /*   model 1 bipartite : V = rows 0..m-1, columns m..m+n-1, E = {{r_i,c_j}}   */
 /*   model 2 row-net   : V = columns, net i = {c_j : a_ij != 0}               */
 /*   model 3 col-net   : V = rows, net j = {r_i : a_ij != 0}                  */
+/*   model 4 finegrain : V = the distinct entries v_ij in row-major order,    */
+/*                       net i = {v_ij : j} (rows), net m+j = {v_ij : i}      */
 /* ------------------------------------------------------------------------- */
 typedef struct {
   int32_t model, k, l; /* vertices, nets */
@@ -192,7 +194,39 @@ ORA_EXPORT int ora_build(int32_t model, int32_t m, int32_t n, const int32_t* row
     free(key);
     return 0;
   }
+  if (model == 4) {
+    int64_t* key = (int64_t*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int64_t));
+    for (int32_t i = 0; i < m; ++i)
+      for (int32_t t = rowptr[i]; t < rowptr[i + 1]; ++t) key[t] = (int64_t)i * n + colidx[t];
+    int64_t u = ora_sort_unique(key, nnz); /* vertex t = the t-th distinct entry */
+    out->k = (int32_t)u; out->l = m + n;
+    /* (net, vertex) pairs: v_ij lies on row net i and column net m + j */
+    int64_t* nv = (int64_t*)malloc((size_t)(2 * u > 0 ? 2 * u : 1) * sizeof(int64_t));
+    for (int64_t t = 0; t < u; ++t) {
+      int64_t i = key[t] / n, j = key[t] % n;
+      nv[2 * t] = i * (u > 0 ? u : 1) + t;
+      nv[2 * t + 1] = ((int64_t)m + j) * (u > 0 ? u : 1) + t;
+    }
+    qsort(nv, (size_t)(2 * u), sizeof(int64_t), cmp_i64);
+    ora_rows(m + n, (int32_t)(u > 0 ? u : 1), nv, 2 * u, &out->net_ptr, &out->pins);
+    ora_incidence(m + n, (int32_t)(u > 0 ? u : 1), nv, 2 * u, &out->vtx_ptr, &out->vnets);
+    free(nv); free(key);
+    return 0;
+  }
   return 1;
+}
+
+/* Finegrain coordinates from the bipartite layout (Sec. 4.2): the dual of the
+ * finegrain hypergraph is the bipartite graph, and every entry a_ij is placed
+ * at the mean of the points of its row r_i and its column c_j.  fg: the
+ * finegrain model; xb: bipartite coordinates (rows 0..m-1, columns m..),
+ * 4 floats per vertex; xf: 4 doubles per entry. */
+ORA_EXPORT void ora_finegrain_coords(const ora_hg* fg, const float* xb, double* xf) {
+  for (int32_t t = 0; t < fg->k; ++t) {
+    int32_t r = fg->vnets[fg->vtx_ptr[t]], c = fg->vnets[fg->vtx_ptr[t] + 1];
+    for (int q = 0; q < 4; ++q)
+      xf[4 * (int64_t)t + q] = 0.5 * ((double)xb[4 * (int64_t)r + q] + (double)xb[4 * (int64_t)c + q]);
+  }
 }
 
 /* Dual hypergraph (Definition 1.2): V* = E and E* = {{e : e contains v} : v in V}.

@@ -157,3 +157,55 @@ def test_components_hypergraph_nets(oracle_mod):
     for v in range(A.m):
         canon[comp[v]] = min(canon[comp[v]], v)
     assert (lab == canon[comp]).all()
+
+
+def test_finegrain_model_definition(oracle_mod):
+    """Finegrain model (Table 1): one vertex per distinct entry (row-major),
+    the m row nets then the n column nets; equal to a plain construction from
+    a pattern with duplicate entries, every vertex on exactly its row's and
+    its column's net, and the dual is the bipartite graph (one net
+    {r_i, c_j} per entry)."""
+    O = oracle_mod
+    A = W.random_pattern(23, 31, 140, 9)
+    m, n = A.m, A.n
+    rows = np.repeat(np.arange(m), np.diff(A.rowptr))
+    cols = A.colidx
+    # the same pattern given with every entry twice, rows reversed in order
+    rr = np.concatenate([rows[::-1], rows])
+    cc = np.concatenate([cols[::-1], cols])
+    o = np.lexsort((np.arange(len(rr)), rr))
+    rp = np.zeros(m + 1, dtype=np.int32)
+    rp[1:] = np.cumsum(np.bincount(rr, minlength=m))
+    fg = O.build_hypergraph("finegrain", m, n, rp, cc[o])
+    entries = sorted(set(zip(rows.tolist(), cols.tolist())))
+    assert fg.k == len(entries) and fg.l == m + n
+    want = [[t for t, (i, _) in enumerate(entries) if i == r] for r in range(m)] + \
+           [[t for t, (_, j) in enumerate(entries) if j == c] for c in range(n)]
+    assert _nets(fg.net_ptr, fg.pins) == [list(e) for e in want]
+    for t, (i, j) in enumerate(entries):
+        assert fg.vnets[fg.vtx_ptr[t]:fg.vtx_ptr[t + 1]].tolist() == [i, m + j]
+    dptr, dpins = O.dual(fg.k, fg.l, fg.net_ptr, fg.pins)
+    bp = O.build_from_matrix("bipartite", A)
+    assert sorted(tuple(e) for e in _nets(dptr, dpins)) == sorted(tuple(e) for e in _nets(bp.net_ptr, bp.pins))
+
+
+def test_finegrain_coords_are_edge_midpoints(oracle_mod):
+    """Finegrain layout from the bipartite one (Sec. 4.2): entry t lies at the
+    midpoint of the bipartite edge it is dual to (the bipartite nets are listed
+    in the same row-major order); an entry whose row and column share a point
+    lies on it."""
+    O = oracle_mod
+    A = W.random_pattern(40, 35, 300, 4)
+    bp = O.build_from_matrix("bipartite", A)
+    fg = O.build_from_matrix("finegrain", A)
+    xb = O.init_coords(bp.k, 3, 4)
+    xf = O.finegrain_coords(fg, xb)
+    ends = bp.pins.reshape(-1, 2)
+    mid = 0.5 * (xb[ends[:, 0]].astype(np.float64) + xb[ends[:, 1]].astype(np.float64))
+    assert np.array_equal(xf, mid)
+    xb2 = xb.copy()
+    xb2[A.m:] = xb2[np.arange(A.n) % A.m]  # column j at row j's point (j < m)
+    xf2 = O.finegrain_coords(fg, xb2)
+    same = fg.vnets[0::2] == (fg.vnets[1::2] - A.m)
+    assert same.any()
+    assert np.array_equal(xf2[same], xb2[fg.vnets[0::2][same]].astype(np.float64))

@@ -54,9 +54,12 @@ typedef enum {
  *  BIPARTITE: vertices rows 0..m-1 then columns m..m+n-1, nets {r_i, c_j}.
  *  ROWNET:    vertices = columns, net i = {c_j : a_ij != 0}.
  *  COLNET:    vertices = rows, net j = {r_i : a_ij != 0}.
+ *  FINEGRAIN: vertices = the distinct entries v_ij in row-major order, nets
+ *             = the m rows {v_ij : j} then the n columns {v_ij : i}
+ *             (m + n nets; every vertex on two).
  * SYMMETRIC and BIPARTITE are graphs; only they can be ordered
  * (Algorithm 7 is stated for graphs). */
-typedef enum { VMO_SYMMETRIC = 0, VMO_BIPARTITE = 1, VMO_ROWNET = 2, VMO_COLNET = 3 } vmo_model;
+typedef enum { VMO_SYMMETRIC = 0, VMO_BIPARTITE = 1, VMO_ROWNET = 2, VMO_COLNET = 3, VMO_FINEGRAIN = 4 } vmo_model;
 
 typedef struct vmo_hg_s* vmo_hg;
 
@@ -313,6 +316,21 @@ vmo_status vmo_batch_order(const vmo_csr* mats, int32_t count, const float* coor
  * to vmo_layout of each matrix alone.  Errors as vmo_batch_order. */
 vmo_status vmo_batch_layout(const vmo_csr* mats, int32_t count, const vmo_params* params, float* coords,
                             void* stream);
+
+/* Finegrain layout from the bipartite one (Sec. 4.2: the finegrain model's
+ * dual is the bipartite graph; laying that out and placing every entry a_ij
+ * at the mean of the points of row r_i and column c_j gives a finegrain
+ * layout at the cost of a 2m-vertex layout instead of an nnz-vertex one).
+ * hg: a FINEGRAIN handle of the pattern; bipartite_coords: device
+ * float[4 (m + n)] (16-byte aligned), the coordinates of the BIPARTITE model
+ * of the same pattern (rows, then columns), e.g. from vmo_layout;
+ * coords: device float[4 k] out (k = distinct entries), entry t at
+ * 0.5 (x(row) + x(column)) in fp32 per coordinate.  The result feeds
+ * vmo_bisect / vmo_kmeans (a partition of the entries) and vmo_cut_size on
+ * the finegrain handle (cut rows and columns of that partition).
+ * Errors: VMO_ERR_INVALID for a handle of another model, null or unaligned
+ * pointers. */
+vmo_status vmo_finegrain_coords(vmo_hg hg, const float* bipartite_coords, float* coords, void* stream);
 
 /* Cut metrics of a vertex partition (Sec. 4.1 footnote, Sec. 5): over the
  * nets of the model, lambda_e = number of distinct parts among the pins;

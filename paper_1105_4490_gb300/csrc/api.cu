@@ -102,6 +102,7 @@ void Scratch::release_to(size_t m) {
 
 vmo_status build_model(const vmo_csr* a, vmo_model model, vmo_hg_s* h, cudaStream_t s);
 vmo_status components(const vmo_hg_s* h, int32_t* labels, cudaStream_t s);
+vmo_status finegrain_coords(const vmo_hg_s* h, const float* xb, float* xf, cudaStream_t s);
 vmo_status cut_size(const vmo_hg_s* h, const int32_t* part, int32_t nparts, int64_t* cutnet, int64_t* lambda1,
                     cudaStream_t s);
 
@@ -355,7 +356,7 @@ vmo_status vmo_build_hypergraph(const vmo_csr* a, vmo_model model, const float* 
   if (!out) return invalid("out is null");
   *out = nullptr;
   VMO_TRY(ensure_device());
-  if (model < VMO_SYMMETRIC || model > VMO_COLNET) return invalid("unknown model");
+  if (model < VMO_SYMMETRIC || model > VMO_FINEGRAIN) return invalid("unknown model");
   cudaStream_t s = (cudaStream_t)stream;
   std::unique_ptr<vmo_hg_s> h(new vmo_hg_s());
   cudaGetDevice(&h->device);
@@ -571,6 +572,15 @@ vmo_status vmo_order_matched(vmo_hg hg, const float* coords, const vmo_params* p
   if (!match) return invalid("match is null");
   if (!row_perm || !col_perm) return invalid("row_perm and col_perm are required");
   return run_order(hg, coords, params, sbd ? 1 : 0, vperm, row_perm, col_perm, tree, (cudaStream_t)stream, match);
+}
+
+vmo_status vmo_finegrain_coords(vmo_hg hg, const float* bipartite_coords, float* coords, void* stream) {
+  VMO_TRY(ensure_device());
+  if (!hg) return invalid("handle is null");
+  if (hg->model != VMO_FINEGRAIN) return invalid("finegrain coordinates need a finegrain handle");
+  if (hg->k > 0 && (!bipartite_coords || !coords)) return invalid("coordinates are null");
+  if (!aligned16(bipartite_coords) || !aligned16(coords)) return invalid("coordinates must be 16-byte aligned");
+  return finegrain_coords(hg, bipartite_coords, coords, (cudaStream_t)stream);
 }
 
 vmo_status vmo_cut_size(vmo_hg hg, const int32_t* part, int32_t nparts, int64_t* cutnet, int64_t* lambda1,

@@ -254,6 +254,40 @@ static vmo_status csr_from_keys(uint64_t* keys, int64_t nkeys, int64_t nrows, in
   return VMO_OK;
 }
 
+// Finegrain incidence: vertex t (the t-th distinct entry, in row i) lies on
+// row net i and column net m + col(t).
+__global__ void fg_vnets_kernel(const int32_t* __restrict__ rptr, const int32_t* __restrict__ cidx, int32_t m,
+                                int32_t* __restrict__ vtx_ptr, int32_t* __restrict__ vnets) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  for (int32_t t = rptr[i]; t < rptr[i + 1]; ++t) {
+    vtx_ptr[t] = 2 * t;
+    vnets[2 * t] = i;
+    vnets[2 * t + 1] = m + cidx[t];
+  }
+  if (i == m - 1) vtx_ptr[rptr[m]] = 2 * rptr[m];
+}
+
+// Column keys col * u + t of the u distinct entries (row-major vertex ids).
+__global__ void fg_col_keys_kernel(const int32_t* __restrict__ cidx, int64_t u, uint64_t* __restrict__ keys) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < u) keys[t] = (uint64_t)cidx[t] * (uint64_t)u + (uint64_t)t;
+}
+
+// Nets of the finegrain model: the row nets (vertex ranges of the row CSR)
+// followed by the column nets.
+__global__ void fg_nets_kernel(const int32_t* __restrict__ rptr, int32_t m, const int32_t* __restrict__ cptr,
+                               const int32_t* __restrict__ cpins, int32_t n, int64_t u, int32_t* __restrict__ net_ptr,
+                               int32_t* __restrict__ pins) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t <= m) net_ptr[t] = rptr[t];
+  if (t < n) net_ptr[m + 1 + t] = (int32_t)u + cptr[t + 1];
+  if (t < u) {
+    pins[t] = (int32_t)t;
+    pins[u + t] = cpins[t];
+  }
+}
+
 vmo_status build_model(const vmo_csr* a, vmo_model model, vmo_hg_s* h, cudaStream_t s) {
   Scratch sc(s);
   VMO_TRY(validate_csr(a, s, sc));
@@ -332,7 +366,65 @@ vmo_status build_model(const vmo_csr* a, vmo_model model, vmo_hg_s* h, cudaStrea
     VMO_CUDA(cudaStreamSynchronize(s));
     return VMO_OK;
   }
+  if (model == VMO_FINEGRAIN) {
+    if ((int64_t)m + n > INT32_MAX) return unsupported("too many nets");
+    uint64_t* keys;
+    VMO_TRY(sc.alloc(&keys, (size_t)std::max<int64_t>(nnz, 1)));
+    if (nnz > 0) {
+      launch(pattern_keys_kernel, grid_for(nnz, 256), 256, 0, s, a->rowptr, a->colidx, m, n, nnz, 0, keys);
+      VMO_LAUNCHED("pattern_keys");
+    }
+    DevArray<int32_t> rptr, cidx, cptr, cpins;
+    int64_t u = 0, uc = 0;
+    VMO_TRY(csr_from_keys(keys, nnz, m, n, rptr, cidx, &u, s, sc));
+    if (2 * u > INT32_MAX) return unsupported("too many entries");
+    h->k = (int32_t)u;
+    h->l = (int64_t)m + n;
+    h->npins = 2 * u;
+    h->nvnets = 2 * u;
+    VMO_TRY(h->vtx_ptr.resize((size_t)u + 1));
+    VMO_TRY(h->vnets.resize((size_t)std::max<int64_t>(2 * u, 1)));
+    VMO_TRY(h->net_ptr.resize((size_t)m + n + 1));
+    VMO_TRY(h->pins.resize((size_t)std::max<int64_t>(2 * u, 1)));
+    VMO_CUDA(cudaMemsetAsync(h->vtx_ptr.ptr, 0, sizeof(int32_t), s));
+    if (m > 0) {
+      launch(fg_vnets_kernel, grid_for(m, 256), 256, 0, s, rptr.ptr, cidx.ptr, m, h->vtx_ptr.ptr, h->vnets.ptr);
+      VMO_LAUNCHED("fg_vnets");
+    }
+    uint64_t* ckeys;
+    VMO_TRY(sc.alloc(&ckeys, (size_t)std::max<int64_t>(u, 1)));
+    if (u > 0) {
+      launch(fg_col_keys_kernel, grid_for(u, 256), 256, 0, s, cidx.ptr, u, ckeys);
+      VMO_LAUNCHED("fg_col_keys");
+    }
+    VMO_TRY(csr_from_keys(ckeys, u, n, std::max<int64_t>(u, 1), cptr, cpins, &uc, s, sc));
+    const int64_t span = std::max<int64_t>(std::max<int64_t>(u, (int64_t)m + 1), (int64_t)n);
+    launch(fg_nets_kernel, grid_for(span, 256), 256, 0, s, rptr.ptr, m, cptr.ptr, cpins.ptr, n, u, h->net_ptr.ptr,
+           h->pins.ptr);
+    VMO_LAUNCHED("fg_nets");
+    VMO_CUDA(cudaStreamSynchronize(s));
+    return VMO_OK;
+  }
   return invalid("unknown model");
+}
+
+// Finegrain layout from the bipartite one (Sec. 4.2): entry t at the mean of
+// its row's and its column's points.
+__global__ void fg_coords_kernel(const int32_t* __restrict__ vnets, int32_t k, const float4* __restrict__ xb,
+                                 float4* __restrict__ xf) {
+  int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= k) return;
+  const float4 a = xb[vnets[2 * t]], b = xb[vnets[2 * t + 1]];
+  xf[t] = make_float4(0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z), 0.5f * (a.w + b.w));
+}
+
+vmo_status finegrain_coords(const vmo_hg_s* h, const float* xb, float* xf, cudaStream_t s) {
+  if (h->k > 0) {
+    launch(fg_coords_kernel, grid_for(h->k, 256), 256, 0, s, h->vnets.ptr, h->k, (const float4*)xb, (float4*)xf);
+    VMO_LAUNCHED("fg_coords");
+  }
+  VMO_CUDA(cudaStreamSynchronize(s));
+  return VMO_OK;
 }
 
 vmo_status components(const vmo_hg_s* h, int32_t* labels, cudaStream_t s) {

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvmo.so")
 _lib = None
 
-MODELS = {"symmetric": 0, "bipartite": 1, "rownet": 2, "colnet": 3}
+MODELS = {"symmetric": 0, "bipartite": 1, "rownet": 2, "colnet": 3, "finegrain": 4}
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error", 4: "device wait timed out",
           5: "over admission budget", 6: "unsupported"}
 
@@ -80,7 +80,7 @@ class Params:
 
 SYMBOLS = ["vmo_default_params", "vmo_build_hypergraph", "vmo_hg_vertices", "vmo_hg_nets", "vmo_hg_arrays",
            "vmo_components", "vmo_init_coords", "vmo_layout", "vmo_layout_step", "vmo_coarsen", "vmo_bisect",
-           "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_order_matched", "vmo_cut_size", "vmo_destroy",
+           "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_order_matched", "vmo_finegrain_coords", "vmo_cut_size", "vmo_destroy",
            "vmo_status_string", "vmo_last_error", "vmo_stats_reset", "vmo_stats_get", "vmo_batch_order",
            "vmo_batch_layout", "vmo_bisect_noalloc", "vmo_server_default_config", "vmo_server_estimate_bytes",
            "vmo_server_plan", "vmo_server_create", "vmo_server_submit", "vmo_server_poll", "vmo_server_wait",
@@ -136,6 +136,7 @@ def load(path: str | None = None):
         getattr(lib, nm).argtypes = [V, V, C.POINTER(_Params), V, V, C.POINTER(_Tree), V]
     lib.vmo_order_vertices.argtypes = [V, V, C.POINTER(_Params), I32, V, C.POINTER(_Tree), V]
     lib.vmo_order_matched.argtypes = [V, V, C.POINTER(_Params), I32, V, V, V, V, C.POINTER(_Tree), V]
+    lib.vmo_finegrain_coords.argtypes = [V, V, V, V]
     lib.vmo_cut_size.argtypes = [V, V, I32, P64, P64, V]
     lib.vmo_batch_order.argtypes = [C.POINTER(_Csr), I32, V, C.POINTER(_Params), I32, V, V]
     lib.vmo_batch_layout.argtypes = [C.POINTER(_Csr), I32, C.POINTER(_Params), V, V]
@@ -346,6 +347,15 @@ class Hypergraph:
         _check(load().vmo_order_matched(self._h, _ptr(coords), C.byref(p), int(sbd), _ptr(match), _ptr(rp), _ptr(cp),
                                         _ptr(vp), C.byref(ct), _stream()))
         return rp, cp, vp, {f: v[:ct.count] for f, v in t.items()}
+
+    def finegrain_coords(self, bipartite_coords: torch.Tensor) -> torch.Tensor:
+        """Finegrain layout from the bipartite model's coordinates (this
+        handle: the finegrain model): every entry at the mean of its row's and
+        its column's points (k x 4 on the device)."""
+        xb = bipartite_coords.to(device="cuda", dtype=torch.float32).contiguous()
+        out = torch.empty((self.k, 4), dtype=torch.float32, device="cuda")
+        _check(load().vmo_finegrain_coords(self._h, _ptr(xb), _ptr(out), _stream()))
+        return out
 
     def cut_size(self, part: torch.Tensor, nparts: int):
         """(cut-net count, lambda - 1) of a vertex partition over the nets."""

@@ -534,3 +534,35 @@ def test_order_matched_rejects(V):
         V.Hypergraph.from_matrix(A).order_matched(match)
     rp, cp, _, _ = hg.order_matched(match)  # the handle still works
     assert sorted(_np(rp).tolist()) == list(range(A.m))
+
+
+def test_finegrain_model_coords_and_partition(V, O):
+    """Finegrain model (Table 1) and the finegrain layout from the bipartite
+    one (Sec. 4.2): the model's arrays bit-exact against the oracle from a
+    pattern given with duplicate entries; its components; the coordinates of
+    the GPU's bipartite layout within one fp32 rounding of the oracle's FP64
+    means; an m-way k-means partition of the entries and its cut metrics over
+    the row and column nets bit-exact."""
+    A = W.powerlaw_rectangular(3000, 2000, seed=5)
+    rows = np.repeat(np.arange(A.m), np.diff(A.rowptr))
+    rr, cc = np.concatenate([rows, rows[::3]]), np.concatenate([A.colidx, A.colidx[::3]])
+    o = np.argsort(rr, kind="stable")
+    rp = np.zeros(A.m + 1, dtype=np.int32)
+    rp[1:] = np.cumsum(np.bincount(rr, minlength=A.m))
+    dup = W.Matrix("dup", A.m, A.n, rp, cc[o].astype(np.int32), {})
+    fg = V.Hypergraph.from_matrix(dup, "finegrain")
+    ref = O.build_from_matrix("finegrain", dup)
+    assert fg.k == ref.k == A.nnz and fg.nets == A.m + A.n
+    arr = fg.arrays()
+    for f in ("net_ptr", "pins", "vtx_ptr", "vnets"):
+        assert np.array_equal(_np(arr[f]), getattr(ref, f)), f
+    assert np.array_equal(_np(fg.components()), O.components(ref))
+    bp = V.Hypergraph.from_matrix(A, "bipartite")
+    x = bp.layout(V.Params(d=3, seed=5))
+    xf = _np(fg.finegrain_coords(x))
+    xo = O.finegrain_coords(ref, _np(x)).astype(np.float32)
+    assert np.all(np.abs(xf - xo) <= np.spacing(np.abs(xo)))
+    lab, _, ne = V.kmeans(fg.finegrain_coords(x), torch.arange(fg.k), 16, seed=3, d=3)
+    lab_o, _, ne_o = O.kmeans(3, xf, np.arange(fg.k), 16, seed=3)
+    assert ne == ne_o and np.array_equal(_np(lab), lab_o)
+    assert fg.cut_size(lab, 16) == O.cut_size(ref.net_ptr, ref.pins, lab_o)

@@ -331,9 +331,9 @@ def order(hg: Hypergraph, d: int, x4: np.ndarray, seed: int, km_iters: int = 20,
     each by its own recursion; tree records are sorted by (comp, heap).
     sep_rec: the separator of a split node is ordered recursively as well
     (children 3h-1, 3h, 3h+1 for V1, V2, V3; depth at most 39).
-    cut_order: without sep_rec, every separator is stably sorted by the
-    two-bit number of its vertices' links into the parts of the children's
-    splits.
+    cut_order: b (0: off; True counts as 1): without sep_rec, every
+    separator is stably sorted by b two-bit numbers of its vertices' links
+    into the parts of the splits of the descendants 1..b levels down.
     match: strengthened diagonal of a square matrix in the bipartite model
     (Sec. 4.2, the matching M as the map mu): match[i] is the column matched to
     row i; a vertex moved into a separator takes its partner with it."""

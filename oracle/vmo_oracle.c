@@ -1266,11 +1266,15 @@ static int cmp_rec_key(const void* a, const void* b) {
 /* in their second parts (V12 or V22).  V3 is then stably sorted by the       */
 /* number: ascending for BBD (00, 01, 10, 11); for SBD, whose separator sits  */
 /* between the parts, as 01, 00, 11, 10 (cut rows of the first parts first,  */
-/* of the second parts last).  One two-bit pair (b = 1).  Part membership is  */
-/* by position range, so the result does not depend on the order in which    */
-/* the nodes are treated.  With a strengthened diagonal (mu) a row and its    */
-/* matched column hold one position of the row and column orders, so a       */
-/* vertex is sorted by the number of its pair: its own bits or its partner's. */
+/* of the second parts last).  Expanded to b two-bit pairs: pair l describes  */
+/* the links into the first and second parts of the splits of the node's     */
+/* descendants l levels down (l = 1: its children), and V3 is sorted by the   */
+/* pairs in turn (pair 1 first), which brings the cut rows and columns into   */
+/* recursive form down to the b-th level.  Part membership is by position     */
+/* range, so the result does not depend on the order in which the nodes are   */
+/* treated.  With a strengthened diagonal (mu) a row and its matched column   */
+/* hold one position of the row and column orders, so a vertex is sorted by   */
+/* the number of its pair: its own bits or its partner's.                     */
 typedef struct { int32_t comp; uint64_t heap; int32_t rec; } ora_key;
 static int cmp_key(const void* a, const void* b) {
   const ora_key* p = (const ora_key*)a;
@@ -1289,7 +1293,16 @@ static int32_t ora_find_rec(const ora_key* ks, int32_t n, int32_t comp, uint64_t
   return -1;
 }
 
-static void ora_cut_order(const ora_hg* h, int32_t sbd, const int32_t* mu, int32_t* perm, const ora_tree* tree) {
+typedef struct { uint64_t key; int32_t i; } ora_cut_key;
+static int cmp_cut_key(const void* a, const void* b) {
+  const ora_cut_key* p = (const ora_cut_key*)a;
+  const ora_cut_key* q = (const ora_cut_key*)b;
+  if (p->key != q->key) return (p->key > q->key) - (p->key < q->key);
+  return (p->i > q->i) - (p->i < q->i);
+}
+
+static void ora_cut_order(const ora_hg* h, int32_t sbd, int32_t b, const int32_t* mu, int32_t* perm,
+                          const ora_tree* tree) {
   int32_t k = h->k, nrec = tree->count;
   int32_t* pos = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
   for (int32_t i = 0; i < k; ++i) pos[perm[i]] = i;
@@ -1299,47 +1312,52 @@ static void ora_cut_order(const ora_hg* h, int32_t sbd, const int32_t* mu, int32
   static const int rank_bbd[4] = {0, 1, 2, 3}, rank_sbd[4] = {1, 0, 3, 2};
   const int* rank = sbd ? rank_sbd : rank_bbd;
   int32_t* tmp = (int32_t*)malloc((size_t)(k > 0 ? k : 1) * sizeof(int32_t));
-  uint8_t* vcode = (uint8_t*)calloc((size_t)(k > 0 ? k : 1), 1);
+  uint32_t* vcode = (uint32_t*)calloc((size_t)(k > 0 ? k : 1), sizeof(uint32_t));
+  int32_t maxr = 2 << b; /* at most 2^b split descendants l <= b levels down, two parts each */
+  int32_t* lo = (int32_t*)malloc((size_t)maxr * sizeof(int32_t));
+  int32_t* hi = (int32_t*)malloc((size_t)maxr * sizeof(int32_t));
+  uint8_t* bit = (uint8_t*)malloc((size_t)maxr);
   for (int32_t r = 0; r < nrec; ++r) {
     int32_t o = tree->offset[r], n1 = tree->n1[r], n2 = tree->n2[r], ns = tree->nsep[r];
     if (ns == 0) continue;
-    /* first / second part ranges of the splits of the two children */
-    int32_t flo[2], fhi[2], slo[2], shi[2];
-    for (int c = 0; c < 2; ++c) {
-      flo[c] = fhi[c] = slo[c] = shi[c] = 0;
-      int32_t cr = ora_find_rec(ks, nrec, tree->comp[r], 2 * tree->heap[r] + (uint64_t)c);
-      if (cr < 0) continue;
-      int32_t co = tree->offset[cr], c1 = tree->n1[cr], c2 = tree->n2[cr], cs = tree->nsep[cr];
-      if (c2 == 0 && cs == 0) continue; /* a leaf has no parts */
-      flo[c] = co; fhi[c] = co + c1;
-      slo[c] = sbd ? co + c1 + cs : co + c1; shi[c] = slo[c] + c2;
-    }
     int32_t a = sbd ? o + n1 : o + n1 + n2;
-    int32_t cnt[4] = {0, 0, 0, 0};
-    for (int32_t i = 0; i < ns; ++i) {
-      int32_t w = perm[a + i];
-      uint8_t cw = 0;
-      for (int32_t t = h->adj_ptr[w]; t < h->adj_ptr[w + 1]; ++t) {
-        int32_t p = pos[h->adj[t]];
-        for (int c = 0; c < 2; ++c) {
-          if (p >= flo[c] && p < fhi[c]) cw |= 1;
-          if (p >= slo[c] && p < shi[c]) cw |= 2;
-        }
+    for (int32_t i = 0; i < ns; ++i) vcode[perm[a + i]] = 0;
+    for (int32_t l = 1; l <= b && tree->depth[r] + l <= 62; ++l) {
+      /* first / second part ranges of the splits of the descendants l levels down */
+      int32_t nr = 0;
+      for (uint64_t j = 0; j < (1ull << l); ++j) {
+        int32_t cr = ora_find_rec(ks, nrec, tree->comp[r], (tree->heap[r] << l) + j);
+        if (cr < 0) continue;
+        int32_t co = tree->offset[cr], c1 = tree->n1[cr], c2 = tree->n2[cr], cs = tree->nsep[cr];
+        if (c2 == 0 && cs == 0) continue; /* a leaf has no parts */
+        lo[nr] = co; hi[nr] = co + c1; bit[nr++] = 1;
+        lo[nr] = sbd ? co + c1 + cs : co + c1; hi[nr] = lo[nr] + c2; bit[nr++] = 2;
       }
-      vcode[w] = cw;
+      for (int32_t i = 0; i < ns; ++i) {
+        int32_t w = perm[a + i];
+        uint32_t cw = 0;
+        for (int32_t t = h->adj_ptr[w]; t < h->adj_ptr[w + 1]; ++t) {
+          int32_t p = pos[h->adj[t]];
+          for (int32_t q = 0; q < nr; ++q)
+            if (p >= lo[q] && p < hi[q]) cw |= bit[q];
+        }
+        vcode[w] |= cw << (2 * (b - l));
+      }
     }
+    ora_cut_key* key = (ora_cut_key*)malloc((size_t)ns * sizeof(ora_cut_key));
     for (int32_t i = 0; i < ns; ++i) {
       int32_t w = perm[a + i];
-      cnt[rank[mu ? (vcode[w] | vcode[mu[w]]) : vcode[w]]]++;
+      uint32_t c = mu ? (vcode[w] | vcode[mu[w]]) : vcode[w];
+      uint64_t kk = 0;
+      for (int32_t l = 1; l <= b; ++l) kk = 4 * kk + (uint64_t)rank[(c >> (2 * (b - l))) & 3];
+      key[i] = (ora_cut_key){kk, i};
     }
-    int32_t start[4] = {0, cnt[0], cnt[0] + cnt[1], cnt[0] + cnt[1] + cnt[2]};
-    for (int32_t i = 0; i < ns; ++i) {
-      int32_t w = perm[a + i];
-      tmp[start[rank[mu ? (vcode[w] | vcode[mu[w]]) : vcode[w]]]++] = w;
-    }
+    qsort(key, (size_t)ns, sizeof(ora_cut_key), cmp_cut_key);
+    for (int32_t i = 0; i < ns; ++i) tmp[i] = perm[a + key[i].i];
     memcpy(perm + a, tmp, (size_t)ns * sizeof(int32_t));
+    free(key);
   }
-  free(pos); free(ks); free(tmp); free(vcode);
+  free(pos); free(ks); free(tmp); free(vcode); free(lo); free(hi); free(bit);
 }
 
 /* Ordering of a graph model from fp32 coordinates.  A disconnected graph is
@@ -1405,7 +1423,7 @@ ORA_EXPORT int ora_order(const ora_hg* h, int32_t d, const float* x4, uint64_t s
       if (c3 > 0) queue[qt++] = (ora_node){3 * nd.heap + 1, nd.offset + (sbd ? c1 : c1 + c2), c3, nd.depth + 1, nd.comp};
     }
   }
-  if (cut_order && !sep_rec) ora_cut_order(h, sbd, mu, perm, tree);
+  if (cut_order > 0 && !sep_rec) ora_cut_order(h, sbd, cut_order, mu, perm, tree);
   /* sort records by (component, heap number) */
   int32_t nrec = tree->count;
   ora_rec_key* rk = (ora_rec_key*)malloc((size_t)(nrec > 0 ? nrec : 1) * sizeof(ora_rec_key));

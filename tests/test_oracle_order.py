@@ -828,3 +828,70 @@ def test_matched_separator_order_free(oracle_mod):
     assert set(got.tolist()) == sep
     side1 = set(perm[o:o + n1].tolist())
     assert all(L[v] == L[next(iter(side1))] for v in side1)
+
+
+def _heap_path_codes(hg, perm, tree, sbd, b, owner):
+    """Pairs 1..b of every separator vertex, from the owners' heap numbers:
+    a neighbour owned by a node D levels below the separator's node d lies in
+    the first (second) part of the split of its ancestor at depth d + l when
+    D >= d + l + 1 and the branch taken at depth d + l + 1 is 2h (2h + 1)."""
+    H, Dp = tree["heap"], tree["depth"]
+    codes = {}
+    for i in range(len(H)):
+        o, n1, n2, ns = (int(tree[f][i]) for f in ("offset", "n1", "n2", "nsep"))
+        if ns == 0:
+            continue
+        a = o + n1 if sbd else o + n1 + n2
+        h, d = int(H[i]), int(Dp[i])
+        for w in perm[a:a + ns].tolist():
+            c = 0
+            for u in hg.adj[hg.adj_ptr[w]:hg.adj_ptr[w + 1]].tolist():
+                j = owner[u]
+                hu, du = int(H[j]), int(Dp[j])
+                if du <= d or (hu >> (du - d)) != h or tree["comp"][j] != tree["comp"][i]:
+                    continue
+                for l in range(1, b + 1):
+                    if du >= d + l + 1:
+                        c |= (2 if (hu >> (du - d - l - 1)) & 1 else 1) << (2 * (b - l))
+            codes[w] = c
+    return codes
+
+
+@pytest.mark.parametrize("b", [2, 3])
+def test_cut_order_levels(oracle_mod, b):
+    """Cut ordering to b levels: every separator is sorted by its vertices'
+    pairs 1..b in turn (rank per pair: BBD 00, 01, 10, 11; SBD 01, 00, 11, 10),
+    the pairs recomputed from the tree's heap numbers (the branch a neighbour's
+    owner takes below the separator's node), the plain order kept within
+    equal pairs; the ordering differs from one level's; b beyond the depth of
+    the tree changes nothing more."""
+    O = oracle_mod
+    A = W.grid_laplacian_3d(14)
+    hg = O.build_from_matrix("symmetric", A)
+    x4 = O.init_coords(hg.k, 3, 8)
+    for sbd in (False, True):
+        plain, _ = O.order(hg, 3, x4, seed=8, min_part=4, sbd=sbd)
+        one, _ = O.order(hg, 3, x4, seed=8, min_part=4, sbd=sbd, cut_order=1)
+        perm, tree = O.order(hg, 3, x4, seed=8, min_part=4, sbd=sbd, cut_order=b)
+        _check_ordering(O, A, hg, perm, tree, sbd)
+        owner = _owner_info(hg.k, perm, tree, sbd)
+        codes = _heap_path_codes(hg, perm, tree, sbd, b, owner)
+        rank1 = [1, 0, 3, 2] if sbd else [0, 1, 2, 3]
+        pos0 = np.empty(hg.k, dtype=np.int64)
+        pos0[plain] = np.arange(hg.k)
+        for i in range(len(tree["heap"])):
+            o, n1, n2, ns = (int(tree[f][i]) for f in ("offset", "n1", "n2", "nsep"))
+            if ns == 0:
+                continue
+            a = o + n1 if sbd else o + n1 + n2
+            seg = perm[a:a + ns]
+            assert set(seg.tolist()) == set(plain[a:a + ns].tolist())
+            key = [tuple(rank1[(codes[w] >> (2 * (b - l))) & 3] for l in range(1, b + 1)) + (int(pos0[w]),)
+                   for w in seg.tolist()]
+            assert key == sorted(key)
+        assert not np.array_equal(perm, one)
+    # the tree is 3 levels deep: pairs beyond the deepest split are 00
+    p3, _ = O.order(hg, 3, x4, seed=8, min_part=4, max_depth=3, cut_order=2)
+    for bb in (3, 8):
+        pb, _ = O.order(hg, 3, x4, seed=8, min_part=4, max_depth=3, cut_order=bb)
+        assert np.array_equal(pb, p3)

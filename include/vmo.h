@@ -91,12 +91,14 @@ typedef struct {
                             BBD form, Sec. 4.2); child keys then 3h-1, 3h, 3h+1 for V1, V2, V3 and
                             nodes at depth min(max_depth, 39) are leaves.  0: V3 keeps its inherited
                             order (0) */
-  int32_t cut_order;    /* 1 (with sep_recursion = 0): after the recursion every separator V3 is stably
-                            sorted by the two-bit number of its vertices' links into the first / second
-                            parts of the splits of the node's children (first bit, value 1: a neighbour in
-                            V11 or V21; second bit, value 2: in V12 or V22), ascending for BBD, in the
-                            order 01, 00, 11, 10 for SBD: the cut rows and columns brought into recursive
-                            form one level deep (Sec. 4.2) (0) */
+  int32_t cut_order;    /* b in [0, 8] (with sep_recursion = 0): after the recursion every separator V3
+                            is stably sorted by b two-bit numbers per vertex; pair l describes its
+                            links into the first / second parts of the splits of the node's
+                            descendants l levels down (first bit, value 1: a neighbour in a first part
+                            such as V11 or V21; second bit, value 2: in a second part such as V12 or
+                            V22); pair 1 sorts first, each pair ascending for BBD and in the order 01,
+                            00, 11, 10 for SBD: the cut rows and columns brought into recursive form
+                            down to the b-th level (Sec. 4.2) (0: off) */
   uint64_t seed;        /* seed of every random draw (1) */
 } vmo_params;
 

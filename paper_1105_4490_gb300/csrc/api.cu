@@ -140,7 +140,7 @@ vmo_status check_params(const vmo_params* p) {
   if (!(p->sigma > 0.0f) || !(p->decay > 0.0f) || p->decay > 1.0f) return invalid("sigma > 0 and 0 < decay <= 1");
   if (p->max_depth < 0 || p->max_depth > 62) return invalid("max_depth must be in [0, 62]");
   if (p->sep_recursion != 0 && p->sep_recursion != 1) return invalid("sep_recursion must be 0 or 1");
-  if (p->cut_order != 0 && p->cut_order != 1) return invalid("cut_order must be 0 or 1");
+  if (p->cut_order < 0 || p->cut_order > 8) return invalid("cut_order must be in [0, 8]");
   return VMO_OK;
 }
 

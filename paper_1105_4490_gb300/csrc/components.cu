@@ -182,7 +182,7 @@ vmo_status order_grouped(const vmo_hg_s* h, const ComponentGroups& g, const floa
   std::vector<uint64_t> seeds(g.base.size() - 1, p->seed);
   VMO_TRY(order_setup(st, x, g.base, seeds, op, g.cperm, s, sc));
   VMO_TRY(order_levels(st, op, s, sc));
-  if (op.cut_order && !op.sep_rec) VMO_TRY(cut_order_pass(st, op, s, sc));
+  if (op.cut_order > 0 && !op.sep_rec) VMO_TRY(cut_order_pass(st, op, s, sc));
   return VMO_OK;
 }
 

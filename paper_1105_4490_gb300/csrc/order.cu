@@ -516,51 +516,31 @@ void dispatch_d(int d, F&& f) {
 }
 
 // ---- cut-row/column ordering of the separators (Sec. 4.2) ----------------
-// Ranges of the first and second parts of the splits of a node's two children
-// (empty for a leaf child), and the node's separator range.
-struct CutNode {
-  int32_t flo[2], fhi[2], slo[2], shi[2];
-  int32_t a, ns;  // separator range [a, a + ns)
+// Every position belongs to one tree record: a leaf's vertices or a split
+// node's separator.  Records are indexed in (problem, heap) order.
+struct CutRec {
+  uint64_t heap;
+  int32_t depth;
+  int32_t a;   // separator start (split nodes)
+  int32_t ns;  // separator size (0 for leaves)
 };
 
-// Record of (prob, heap) in the records sorted by (prob, heap), or -1.
-__device__ int find_record(const TreeDev& tree, const uint32_t* __restrict__ idx, int n, int32_t prob,
-                           uint64_t heap) {
-  int lo = 0, hi = n - 1;
-  while (lo <= hi) {
-    const int mid = (lo + hi) >> 1;
-    const uint32_t r = idx[mid];
-    const int32_t p = tree.prob[r];
-    const uint64_t h = tree.heap[r];
-    if (p == prob && h == heap) return (int)r;
-    if (p < prob || (p == prob && h < heap)) lo = mid + 1; else hi = mid - 1;
-  }
-  return -1;
-}
-
-__global__ void k_cut_nodes(const TreeDev tree, const uint32_t* __restrict__ idx, int n, int sbd,
-                            CutNode* __restrict__ cn, int32_t* __restrict__ posrec) {
+__global__ void k_cut_recs(const TreeDev tree, const uint32_t* __restrict__ idx, int n, int sbd,
+                           CutRec* __restrict__ cr, int32_t* __restrict__ own, int64_t* __restrict__ sz) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t r = idx[i];
   const int32_t o = tree.offset[r], n1 = tree.n1[r], n2 = tree.n2[r], ns = tree.nsep[r];
-  CutNode c;
-  c.a = sbd ? o + n1 : o + n1 + n2;
-  c.ns = ns;
-  for (int k = 0; k < 2; ++k) {
-    c.flo[k] = c.fhi[k] = c.slo[k] = c.shi[k] = 0;
-    if (ns == 0) continue;
-    const int cr = find_record(tree, idx, n, tree.prob[r], 2 * tree.heap[r] + (uint64_t)k);
-    if (cr < 0) continue;
-    const int32_t co = tree.offset[cr], c1 = tree.n1[cr], c2 = tree.n2[cr], cs = tree.nsep[cr];
-    if (c2 == 0 && cs == 0) continue;  // a leaf has no parts
-    c.flo[k] = co;
-    c.fhi[k] = co + c1;
-    c.slo[k] = sbd ? co + c1 + cs : co + c1;
-    c.shi[k] = c.slo[k] + c2;
-  }
-  cn[i] = c;
-  for (int32_t p = 0; p < ns; ++p) posrec[c.a + p] = i;
+  const bool leaf = n2 == 0 && ns == 0;
+  CutRec c;
+  c.heap = tree.heap[r];
+  c.depth = tree.depth[r];
+  c.a = leaf ? o : (sbd ? o + n1 : o + n1 + n2);
+  c.ns = leaf ? 0 : ns;
+  cr[i] = c;
+  sz[i] = c.ns;
+  const int32_t len = leaf ? n1 : ns;
+  for (int32_t p = 0; p < len; ++p) own[c.a + p] = i;
 }
 
 __global__ void k_inverse_perm(const int32_t* __restrict__ ord, int64_t n, int32_t* __restrict__ pos) {
@@ -568,63 +548,71 @@ __global__ void k_inverse_perm(const int32_t* __restrict__ ord, int64_t n, int32
   if (p < n) pos[ord[p]] = (int32_t)p;
 }
 
-// Two-bit number of the vertex at every separator position.
+// Pairs 1..b of the vertex at every separator position (pair l in bits
+// 2(b - l), 2(b - l) + 1).  A neighbour owned by a record D levels deep below
+// the separator's node (depth d, heap h) lies in the first (second) part of
+// the split of its ancestor at depth d + l when D >= d + l + 1 and its heap
+// number takes the branch 2h' (2h' + 1) at depth d + l + 1.  Owners outside
+// the node's subtree (ancestors, the node itself) add nothing.
 __global__ void k_cut_codes(const int32_t* __restrict__ ord, const int32_t* __restrict__ pos,
-                            const int32_t* __restrict__ posrec, int64_t n, const CutNode* __restrict__ cn,
-                            const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
-                            uint8_t* __restrict__ vcode) {
+                            const int32_t* __restrict__ own, int64_t n, const CutRec* __restrict__ cr,
+                            const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj, int b,
+                            uint32_t* __restrict__ vcode) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
-  const int i = posrec[p];
-  if (i < 0) return;
-  const CutNode c = cn[i];
+  if (p >= n || own[p] < 0) return;
+  const CutRec c = cr[own[p]];
+  if (c.ns == 0) return;
   const int32_t w = ord[p];
-  int code = 0;
+  uint32_t code = 0;
   for (int32_t t = adj_ptr[w]; t < adj_ptr[w + 1]; ++t) {
-    const int32_t q = pos[adj[t]];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      if (q >= c.flo[k] && q < c.fhi[k]) code |= 1;
-      if (q >= c.slo[k] && q < c.shi[k]) code |= 2;
+    const int32_t ou = own[pos[adj[t]]];
+    if (ou < 0) continue;
+    const CutRec u = cr[ou];
+    if (u.depth <= c.depth || (u.heap >> (u.depth - c.depth)) != c.heap) continue;
+    for (int l = 1; l <= b && u.depth >= c.depth + l + 1; ++l) {
+      const uint32_t second = (uint32_t)(u.heap >> (u.depth - c.depth - l - 1)) & 1u;
+      code |= (second ? 2u : 1u) << (2 * (b - l));
     }
   }
-  vcode[w] = (uint8_t)code;
+  vcode[w] = code;
 }
 
-// Sort key (node, rank) of every separator position; other positions sort
-// last.  With a matching a vertex is ranked by its pair's number (its own
-// bits or its partner's): row and matched column share one position.
-__global__ void k_cut_keys(const int32_t* __restrict__ ord, const int32_t* __restrict__ posrec, int64_t n,
-                           const uint8_t* __restrict__ vcode, const int32_t* __restrict__ mu, int sbd,
+// Sort key (record, ranks of pairs 1..b) of every separator position; other
+// positions sort last.  With a matching a vertex is ranked by its pair's
+// number (its own bits or its partner's): row and matched column share one
+// position.
+__global__ void k_cut_keys(const int32_t* __restrict__ ord, const int32_t* __restrict__ own, int64_t n,
+                           const CutRec* __restrict__ cr, const uint32_t* __restrict__ vcode,
+                           const int32_t* __restrict__ mu, int sbd, int b, uint64_t sentinel,
                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
-  const int i = posrec[p];
-  uint64_t key = ~0ull;
-  if (i >= 0) {
+  const int i = own[p];
+  uint64_t key = sentinel;
+  if (i >= 0 && cr[i].ns > 0) {
     const int32_t w = ord[p];
-    const int code = vcode[w] | (mu ? vcode[mu[w]] : 0);
-    const int rank = sbd ? (code == 1 ? 0 : code == 0 ? 1 : code == 3 ? 2 : 3) : code;
-    key = (uint64_t)i * 4 + (uint64_t)rank;
+    const uint32_t code = vcode[w] | (mu ? vcode[mu[w]] : 0u);
+    uint64_t rk = 0;
+    for (int l = 1; l <= b; ++l) {
+      const uint32_t f = (code >> (2 * (b - l))) & 3u;
+      const uint32_t r = sbd ? (f ^ 1u) : f;  // SBD: 01, 00, 11, 10
+      rk = 4 * rk + r;
+    }
+    key = ((uint64_t)i << (2 * b)) | rk;
   }
   keys[p] = key;
   vals[p] = (uint32_t)p;
 }
 
-// Separator positions in (node, rank, position) order back into their node's
-// separator range.
+// Separator positions in (record, ranks, position) order back into their
+// record's separator range.
 __global__ void k_cut_scatter(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t m,
-                              const CutNode* __restrict__ cn, const int64_t* __restrict__ gstart,
+                              int b, const CutRec* __restrict__ cr, const int64_t* __restrict__ gstart,
                               const int32_t* __restrict__ ord, int32_t* __restrict__ ord2) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
-  const int i = (int)(keys[j] >> 2);
-  ord2[cn[i].a + (j - gstart[i])] = ord[vals[j]];
-}
-
-__global__ void k_cut_sizes(const CutNode* __restrict__ cn, int n, int64_t* __restrict__ sz) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) sz[i] = cn[i].ns;
+  const int i = (int)(keys[j] >> (2 * b));
+  ord2[cr[i].a + (j - gstart[i])] = ord[vals[j]];
 }
 
 }  // namespace
@@ -880,56 +868,56 @@ vmo_status tree_sorted(OrderState& st, bool by_prob, int32_t* count_out, uint32_
   return VMO_OK;
 }
 
-// Cut-row/column ordering (Sec. 4.2): every separator stably sorted by the
-// two-bit number of its vertices' links into the first / second parts of the
-// splits of the node's two children (BBD: 00, 01, 10, 11; SBD: 01, 00, 11,
-// 10).  Applied after the recursion, when the separators are not recursed
-// into.
+// Cut-row/column ordering (Sec. 4.2): every separator stably sorted by b
+// two-bit numbers of its vertices' links into the first / second parts of the
+// splits of the node's descendants 1..b levels down (per pair BBD: 00, 01,
+// 10, 11; SBD: 01, 00, 11, 10).  Applied after the recursion, when the
+// separators are not recursed into.
 vmo_status cut_order_pass(OrderState& st, const OrderParams& op, cudaStream_t s, Scratch& sc) {
   const int64_t n = st.n;
-  if (n == 0) return VMO_OK;
+  const int b = op.cut_order;
+  if (n == 0 || b <= 0) return VMO_OK;
   ScratchFrame frame(sc);
   int nrec = 0;
   uint32_t* idx;
   VMO_TRY(tree_sorted(st, true, &nrec, &idx, s, sc));
   if (nrec == 0) return VMO_OK;
-  CutNode* cn;
-  int32_t *posrec, *pos, *ord2;
-  uint8_t* vcode;
-  int64_t *sz, *gstart;
+  CutRec* cr;
+  int32_t *own, *pos, *ord2;
+  uint32_t* vcode;
+  int64_t *sz, *gstart, *total;
   uint64_t *k1, *k2;
   uint32_t *v1, *v2;
-  VMO_TRY(sc.alloc(&cn, nrec));
-  VMO_TRY(sc.alloc(&posrec, n));
+  VMO_TRY(sc.alloc(&cr, nrec));
+  VMO_TRY(sc.alloc(&own, n));
   VMO_TRY(sc.alloc(&pos, n));
   VMO_TRY(sc.alloc(&ord2, n));
   VMO_TRY(sc.alloc(&vcode, n));
   VMO_TRY(sc.alloc(&sz, nrec));
   VMO_TRY(sc.alloc(&gstart, nrec));
+  VMO_TRY(sc.alloc(&total, 1));
   VMO_TRY(sc.alloc(&k1, n));
   VMO_TRY(sc.alloc(&k2, n));
   VMO_TRY(sc.alloc(&v1, n));
   VMO_TRY(sc.alloc(&v2, n));
-  VMO_CUDA(cudaMemsetAsync(posrec, 0xFF, n * sizeof(int32_t), s));
-  launch(k_cut_nodes, grid_for(nrec, kBlock), kBlock, 0, s, st.tree, idx, nrec, op.sbd, cn, posrec);
+  VMO_CUDA(cudaMemsetAsync(own, 0xFF, n * sizeof(int32_t), s));  // every position is owned; -1 would be skipped
+  launch(k_cut_recs, grid_for(nrec, kBlock), kBlock, 0, s, st.tree, idx, nrec, op.sbd, cr, own, sz);
   launch(k_inverse_perm, grid_for(n, kBlock), kBlock, 0, s, st.ord, n, pos);
-  launch(k_cut_codes, grid_for(n, kBlock), kBlock, 0, s, st.ord, pos, posrec, n, cn, st.adj_ptr, st.adj, vcode);
-  launch(k_cut_keys, grid_for(n, kBlock), kBlock, 0, s, st.ord, posrec, n, vcode, st.mu, op.sbd, k1, v1);
-  launch(k_cut_sizes, grid_for(nrec, kBlock), kBlock, 0, s, cn, nrec, sz);
+  launch(k_cut_codes, grid_for(n, kBlock), kBlock, 0, s, st.ord, pos, own, n, cr, st.adj_ptr, st.adj, b, vcode);
+  const uint64_t sentinel = (uint64_t)nrec << (2 * b);
+  int bits = 1;
+  while (bits < 64 && (1ull << bits) <= sentinel) ++bits;
+  launch(k_cut_keys, grid_for(n, kBlock), kBlock, 0, s, st.ord, own, n, cr, vcode, st.mu, op.sbd, b, sentinel, k1,
+         v1);
   VMO_LAUNCHED("cut_codes");
+  VMO_TRY(scan_exclusive<int64_t>(sz, gstart, nrec, total, s, sc));
   int64_t m = 0;
-  VMO_TRY(scan_exclusive<int64_t>(sz, gstart, nrec, nullptr, s, sc));
-  {
-    int64_t last = 0, lastsz = 0;
-    VMO_CUDA(cudaMemcpyAsync(&last, gstart + nrec - 1, 8, cudaMemcpyDeviceToHost, s));
-    VMO_CUDA(cudaMemcpyAsync(&lastsz, sz + nrec - 1, 8, cudaMemcpyDeviceToHost, s));
-    VMO_CUDA(cudaStreamSynchronize(s));
-    m = last + lastsz;
-  }
+  VMO_CUDA(cudaMemcpyAsync(&m, total, 8, cudaMemcpyDeviceToHost, s));
+  VMO_CUDA(cudaStreamSynchronize(s));
   if (m == 0) return VMO_OK;
-  VMO_TRY(radix_sort_u64(k1, v1, k2, v2, n, 64, s, sc));
+  VMO_TRY(radix_sort_u64(k1, v1, k2, v2, n, bits, s, sc));
   VMO_CUDA(cudaMemcpyAsync(ord2, st.ord, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-  launch(k_cut_scatter, grid_for(m, kBlock), kBlock, 0, s, k2, v2, m, cn, gstart, st.ord, ord2);
+  launch(k_cut_scatter, grid_for(m, kBlock), kBlock, 0, s, k2, v2, m, b, cr, gstart, st.ord, ord2);
   VMO_LAUNCHED("cut_scatter");
   VMO_CUDA(cudaMemcpyAsync(st.ord, ord2, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   VMO_CUDA(cudaStreamSynchronize(s));

@@ -43,7 +43,7 @@ struct OrderParams {
   int max_depth = 62;
   int sbd = 0;
   int sep_rec = 0;  // order V3 recursively too (ternary keys, depth <= kSepRecMaxDepth)
-  int cut_order = 0;  // sort every separator by its links into the children's parts (without sep_rec)
+  int cut_order = 0;  // b: sort every separator by b two-bit link numbers (without sep_rec)
 };
 
 // Deepest node with separator recursion: ternary keys (3^(d+1) - 1) / 2 fit 64 bits up to d = 39.
@@ -82,7 +82,7 @@ vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s,
 vmo_status two_means_into(OrderState& st, int N, int d, int km_iters, unsigned long long* dval,
                           unsigned long long* dpre, int* cnt, uint64_t* partial, cudaStream_t s);
 vmo_status order_levels(OrderState& st, const OrderParams& op, cudaStream_t s, Scratch& sc);
-// Separators stably sorted by their two-bit link numbers (after order_levels).
+// Separators stably sorted by b two-bit link numbers (after order_levels).
 vmo_status cut_order_pass(OrderState& st, const OrderParams& op, cudaStream_t s, Scratch& sc);
 // Indices of the tree records sorted by heap number (and by problem first when
 // by_prob); *count_out receives the number of records (host).

@@ -419,6 +419,25 @@ def test_order_cut_order(V, O, sbd):
     _order_compare(V, O, D, "symmetric", 3, O.init_coords(D.n, 3, 32), sbd, min_part=4, cut_order=True)
 
 
+@pytest.mark.parametrize("b", [2, 3, 8])
+def test_order_cut_order_levels(V, O, b):
+    """Cut ordering to b levels bit-exact against the oracle (BBD/SBD): a 3D
+    grid with its own coordinates, power-law graphs with parts down to single
+    vertices, the bipartite model, and a strengthened diagonal."""
+    G = W.grid_laplacian_3d(24)
+    ijk = np.indices((24, 24, 24)).reshape(3, -1).T
+    x = np.zeros((G.n, 4), dtype=np.float32)
+    x[:, :3] = ijk
+    B = W.powerlaw_symmetric(9000, seed=35)
+    R = W.powerlaw_rectangular(3000, 2000, seed=9)
+    M = W.with_strengthened_diagonal(W.grid_laplacian_2d(50), 0.7, 5)
+    for sbd in (False, True):
+        _order_compare(V, O, G, "symmetric", 3, x, sbd, min_part=8, cut_order=b)
+        _order_compare(V, O, B, "symmetric", 3, O.init_coords(B.n, 3, 35), sbd, min_part=0, cut_order=b)
+        _order_compare(V, O, R, "bipartite", 2, O.init_coords(R.m + R.n, 2, 36), sbd, min_part=1, cut_order=b)
+        _matched_compare(V, O, M, 2, O.init_coords(2 * M.m, 2, 37), sbd, min_part=4, cut_order=b)
+
+
 def test_batch_cut_order_equals_plain(V):
     mats = W.batch_mix(12, 33, nmin=200, nmax=3000)
     p = V.Params(d=3, seed=4, cut_order=1, min_part=16)

@@ -297,6 +297,10 @@ def main():
                     help="one untimed step of the workload and exit (for ncu captures; no JSON line)")
     ap.add_argument("--profile-matrix", type=int, default=-1,
                     help="with --profile: order only this matrix of the workload (0 or 1)")
+    ap.add_argument("--profile-large", type=int, default=0, metavar="SIDE",
+                    help="a case larger than L2 for the memory-bound kernels (ncu captures, no JSON line): "
+                         "SIDE^3 7-point grid, 4 layout steps from random coordinates at one level, then the "
+                         "recursive BBD of the grid's own coordinates to depth 10")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -344,6 +348,21 @@ def main():
         dist.barrier()
     import paper_1105_4490_gb300 as V
     V.load()
+
+    if args.profile_large:
+        side = args.profile_large
+        A = W.grid_laplacian_3d(side)
+        hg = V.Hypergraph.from_matrix(A)
+        p = V.Params(d=3, iters=4, seed=1)
+        x0 = V.init_coords(A.n, 3, 1)
+        hg.layout(p, x0.clone())
+        ijk = torch.tensor(np.indices((side, side, side)).reshape(3, -1).T.astype(np.float32))
+        xg = torch.zeros((A.n, 4), dtype=torch.float32)
+        xg[:, :3] = ijk
+        hg.order_vertices(V.Params(d=3, max_depth=10, seed=1), xg.cuda())
+        torch.cuda.synchronize()
+        print(f"profile-large done: {side}^3 grid, {A.n} rows, {A.nnz} nnz", file=sys.stderr)
+        return
 
     name, mats = medium_workload()
     if args.profile and args.profile_matrix >= 0:

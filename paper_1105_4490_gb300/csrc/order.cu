@@ -137,42 +137,154 @@ __global__ void k_seed2(const float4* __restrict__ xo, const int32_t* __restrict
 // One Lloyd assignment: label 1 iff ||x - z1||^2 <= ||x - z2||^2 (fp32),
 // change detection against the previous labels, and exact fixed-point sums
 // q(x) = rint(x * 2^P), P = 30 - e, of each cluster.
+// Lloyd assignment (Algorithm 5) with exact fixed-point centroid sums: every
+// block takes kAssignItems x blockDim consecutive positions.  A block whose
+// positions all lie in one node (the common case above the deepest levels)
+// sums in registers and adds its totals with one set of atomics; other blocks
+// aggregate per warp and (node, label).  Integer sums make the result
+// independent of the order of the additions.
+constexpr int kAssignItems = 8;
+
+template <int D>
+__device__ inline void assign_one(const float4* __restrict__ xo, int64_t i, const NodeDev& nd, int it,
+                                  uint8_t* __restrict__ lab, int final_pass, uint8_t& l, long long* q, bool& chg) {
+  float4 x = xo[i];
+  l = (sqdist32<D>(x, nd.z1) <= sqdist32<D>(x, nd.z2)) ? 1 : 2;
+  if (!final_pass) {
+    if (it > 0 && l != lab[i]) chg = true;
+    float sc = exp2i_f(30 - nd.e);
+#pragma unroll
+    for (int m = 0; m < D; ++m) q[m] = __float2ll_rn(__fmul_rn(comp(x, m), sc));
+  }
+  lab[i] = l;
+}
+
+// Replicas of the sums of the first kRepNodes nodes: on large inputs the
+// blocks of a node add into kRepR copies (by block index) instead of one, so
+// that the atomics of thousands of blocks on the top levels do not queue on
+// the same addresses; k_fold_reps adds the copies into the node.  Ten sums per
+// node in the order of NodeDev: S1[0..3], S2[0..3], n1, n2.
+constexpr int kRepR = 32;
+constexpr int kRepNodes = 256;
+constexpr int64_t kRepMinPositions = 1 << 19;
+
+__global__ void k_fold_reps(NodeDev* __restrict__ nodes, int N, unsigned long long* __restrict__ rep) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N * 10) return;
+  const int s = i / 10, t = i % 10;
+  unsigned long long sum = 0;
+  for (int r = 0; r < kRepR; ++r) {
+    unsigned long long* p = rep + ((int64_t)s * kRepR + r) * 10 + t;
+    sum += *p;
+    *p = 0;
+  }
+  reinterpret_cast<unsigned long long*>(&nodes[s].S1[0])[t] += sum;
+}
+
 template <int D>
 __global__ void k_assign(const float4* __restrict__ xo, const int32_t* __restrict__ seg, int64_t n, int it,
-                         NodeDev* __restrict__ nodes, uint8_t* __restrict__ lab, int final_pass) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int s = i < n ? seg[i] : -1;
-  bool act = false;
-  uint8_t l = 0;
-  long long q[4] = {0, 0, 0, 0};
-  if (s >= 0) {
-    NodeDev& nd = nodes[s];
-    int st = nd.state;
-    act = final_pass ? (st != 2) : (st == 0);
-    if (act) {
-      float4 x = xo[i];
-      l = (sqdist32<D>(x, nd.z1) <= sqdist32<D>(x, nd.z2)) ? 1 : 2;
-      if (!final_pass) {
-        if (it > 0 && l != lab[i]) nd.changed = 1;
-        float sc = exp2i_f(30 - nd.e);
+                         NodeDev* __restrict__ nodes, uint8_t* __restrict__ lab, int final_pass,
+                         unsigned long long* __restrict__ rep) {
+  __shared__ int s_first;
+  __shared__ unsigned long long red[kBlock / 32][2 * 4 + 2];
+  const int64_t base = (int64_t)blockIdx.x * (kAssignItems * blockDim.x);
+  if (threadIdx.x == 0) s_first = base < n ? seg[base] : -1;
+  __syncthreads();
+  const int s0 = s_first;
+  int sv[kAssignItems];
+  bool same = true;
 #pragma unroll
-        for (int m = 0; m < D; ++m) q[m] = __float2ll_rn(__fmul_rn(comp(x, m), sc));
-      }
-      lab[i] = l;
-    }
+  for (int k = 0; k < kAssignItems; ++k) {
+    const int64_t i = base + k * blockDim.x + threadIdx.x;
+    sv[k] = i < n ? seg[i] : -1;
+    same = same && (i >= n || sv[k] == s0);
   }
-  // warp-aggregated accumulation per (node, label)
-  int key = act ? s * 2 + (l - 1) : -1;
-  unsigned peers = __match_any_sync(0xffffffffu, key);
-  if (key < 0) return;
-  int leader = __ffs(peers) - 1;
-  unsigned long long cnt = __popc(peers);
-  unsigned long long sum[4] = {0, 0, 0, 0};
-  if (!final_pass) {
-    if (peers == 0xffffffffu) {
+  const bool uniform = __syncthreads_and(same) && s0 >= 0;
+  if (uniform) {
+    NodeDev& nd = nodes[s0];
+    const int st = nd.state;
+    if (!(final_pass ? (st != 2) : (st == 0))) return;
+    unsigned long long S[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    unsigned long long c[2] = {0, 0};
+    bool chg = false;
 #pragma unroll
-      for (int m = 0; m < D; ++m) sum[m] = warp_sum64((unsigned long long)q[m]);
-    } else {
+    for (int k = 0; k < kAssignItems; ++k) {
+      const int64_t i = base + k * blockDim.x + threadIdx.x;
+      if (i >= n) continue;
+      uint8_t l;
+      long long q[4] = {0, 0, 0, 0};
+      assign_one<D>(xo, i, nd, it, lab, final_pass, l, q, chg);
+      const bool first = l == 1;  // selects, not a computed index: the sums stay in registers
+      c[0] += first ? 1ull : 0ull;
+      c[1] += first ? 0ull : 1ull;
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        S[0][m] += first ? (unsigned long long)q[m] : 0ull;
+        S[1][m] += first ? 0ull : (unsigned long long)q[m];
+      }
+    }
+    // block totals: counts, sums (not in the final pass) and the change flag
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    unsigned long long v[2 * 4 + 2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      v[h] = warp_sum64(c[h]);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) v[2 + 4 * h + m] = m < D && !final_pass ? warp_sum64(S[h][m]) : 0ull;
+    }
+    const bool any_chg = __any_sync(0xffffffffu, chg);
+    if (lane == 0) {
+#pragma unroll
+      for (int t = 0; t < 2 * 4 + 2; ++t) red[warp][t] = v[t];
+    }
+    const bool block_chg = __syncthreads_or(any_chg);
+    if (threadIdx.x == 0) {
+      unsigned long long tot[2 * 4 + 2];
+#pragma unroll
+      for (int t = 0; t < 2 * 4 + 2; ++t) {
+        tot[t] = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot[t] += red[w][t];
+      }
+      if (block_chg) nd.changed = 1;
+      unsigned long long* acc = rep ? rep + ((int64_t)s0 * kRepR + (blockIdx.x & (kRepR - 1))) * 10
+                                    : reinterpret_cast<unsigned long long*>(&nd.S1[0]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (tot[h] == 0) continue;
+        if (!final_pass) {
+#pragma unroll
+          for (int m = 0; m < D; ++m) atomicAdd(acc + 4 * h + m, tot[2 + 4 * h + m]);
+        }
+        atomicAdd(acc + 8 + h, tot[h]);
+      }
+    }
+    return;
+  }
+  // positions of several nodes: per warp and (node, label)
+#pragma unroll 1
+  for (int k = 0; k < kAssignItems; ++k) {
+    const int64_t i = base + k * blockDim.x + threadIdx.x;
+    const int s = sv[k];
+    bool act = false;
+    uint8_t l = 0;
+    long long q[4] = {0, 0, 0, 0};
+    if (s >= 0) {
+      NodeDev& nd = nodes[s];
+      const int st = nd.state;
+      act = final_pass ? (st != 2) : (st == 0);
+      if (act) {
+        bool chg = false;
+        assign_one<D>(xo, i, nd, it, lab, final_pass, l, q, chg);
+        if (chg) nd.changed = 1;
+      }
+    }
+    const int key = act ? s * 2 + (l - 1) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key < 0) continue;
+    const int leader = __ffs(peers) - 1;
+    const unsigned long long cnt = __popc(peers);
+    unsigned long long sum[4] = {0, 0, 0, 0};
+    if (!final_pass) {
 #pragma unroll
       for (int m = 0; m < D; ++m) {
         unsigned long long acc = 0;
@@ -183,17 +295,19 @@ __global__ void k_assign(const float4* __restrict__ xo, const int32_t* __restric
         sum[m] = acc;
       }
     }
-  }
-  if ((int)lane_id() != leader) return;
-  NodeDev& nd = nodes[s];
-  if (final_pass) {
-    atomicAdd((unsigned long long*)(l == 1 ? &nd.n1 : &nd.n2), cnt);
-    return;
-  }
-  unsigned long long* S = (unsigned long long*)(l == 1 ? nd.S1 : nd.S2);
+    if ((int)lane_id() != leader) continue;
+    NodeDev& nd = nodes[s];
+    if (!final_pass) {
+      unsigned long long* Sx = (unsigned long long*)(l == 1 ? nd.S1 : nd.S2);
 #pragma unroll
-  for (int m = 0; m < D; ++m) atomicAdd(&S[m], sum[m]);
-  atomicAdd((unsigned long long*)(l == 1 ? &nd.n1 : &nd.n2), cnt);
+      for (int m = 0; m < D; ++m) atomicAdd(&Sx[m], sum[m]);
+    }
+    atomicAdd((unsigned long long*)(l == 1 ? &nd.n1 : &nd.n2), cnt);
+  }
+}
+
+inline unsigned assign_grid(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, (n + (int64_t)kBlock * kAssignItems - 1) / ((int64_t)kBlock * kAssignItems));
 }
 
 // Centre update: z = fp32((double(sum) / count) * 2^-P); a node whose labels
@@ -622,11 +736,15 @@ __global__ void k_cut_scatter(const uint64_t* __restrict__ keys, const uint32_t*
 vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s, Scratch& sc) {
   const int64_t n = st.n;
   ScratchFrame frame(sc);
-  unsigned long long *dval, *dpre;
+  unsigned long long *dval, *dpre, *rep = nullptr;
   int* cnt;
   VMO_TRY(sc.alloc(&dval, std::max<int64_t>(n, 1)));
   VMO_TRY(sc.alloc(&dpre, std::max<int64_t>(n, 1)));
   VMO_TRY(sc.alloc(&cnt, 1));
+  if (N <= kRepNodes && n >= kRepMinPositions) {
+    VMO_TRY(sc.alloc(&rep, (size_t)N * kRepR * 10));
+    VMO_CUDA(cudaMemsetAsync(rep, 0, (size_t)N * kRepR * 10 * sizeof(unsigned long long), s));
+  }
   vmo_status stt = VMO_OK;
   dispatch_d(d, [&](auto DC) {
     constexpr int D = decltype(DC)::value;
@@ -638,7 +756,8 @@ vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s,
     if (stt != VMO_OK) return;
     launch(k_seed2<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, dval, dpre, st.nodes, st.seeds);
     for (int it = 0; it < km_iters; ++it) {
-      launch(k_assign<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, it, st.nodes, st.lab, 0);
+      launch(k_assign<D>, assign_grid(n), kBlock, 0, s, st.xo, st.seg, n, it, st.nodes, st.lab, 0, rep);
+      if (rep) launch(k_fold_reps, grid_for(N * 10, kBlock), kBlock, 0, s, st.nodes, N, rep);
       launch(k_update<D>, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, it);
       if (it % 4 == 3 && it + 1 < km_iters) {  // stop early once every node has converged
         int h = 0;
@@ -650,7 +769,8 @@ vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s,
       }
     }
     launch(k_clear_counts, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N);
-    launch(k_assign<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, 0, st.nodes, st.lab, 1);
+    launch(k_assign<D>, assign_grid(n), kBlock, 0, s, st.xo, st.seg, n, 0, st.nodes, st.lab, 1, rep);
+    if (rep) launch(k_fold_reps, grid_for(N * 10, kBlock), kBlock, 0, s, st.nodes, N, rep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) stt = cuda_fail(e, "two_means", __FILE__, __LINE__);
   });
@@ -671,7 +791,8 @@ vmo_status two_means_into(OrderState& st, int N, int d, int km_iters, unsigned l
     if (stt != VMO_OK) return;
     launch(k_seed2<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, dval, dpre, st.nodes, st.seeds);
     for (int it = 0; it < km_iters; ++it) {
-      launch(k_assign<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, it, st.nodes, st.lab, 0);
+      launch(k_assign<D>, assign_grid(n), kBlock, 0, s, st.xo, st.seg, n, it, st.nodes, st.lab, 0,
+             (unsigned long long*)nullptr);
       launch(k_update<D>, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, it);
       if (it % 4 == 3 && it + 1 < km_iters) {  // stop early once every node has converged
         int h = 0;
@@ -683,7 +804,8 @@ vmo_status two_means_into(OrderState& st, int N, int d, int km_iters, unsigned l
       }
     }
     launch(k_clear_counts, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N);
-    launch(k_assign<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, 0, st.nodes, st.lab, 1);
+    launch(k_assign<D>, assign_grid(n), kBlock, 0, s, st.xo, st.seg, n, 0, st.nodes, st.lab, 1,
+           (unsigned long long*)nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) stt = cuda_fail(e, "two_means", __FILE__, __LINE__);
   });

@@ -255,8 +255,17 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
   pdl_wait();
   constexpr int R = 1 << BITS;
   constexpr int PER = (R + kSortThreads - 1) / kSortThreads;
-  __shared__ uint32_t wcnt[kSortWarps][R];
+  // the per-warp digit counts, then (once every element knows its place) the
+  // tile's keys and values in digit order, so that the writes of a digit's
+  // run go out as consecutive addresses
+  constexpr int kCountBytes = kSortWarps * R * 4;
+  constexpr int kStageBytes = kSortTile * ((int)sizeof(K) + (HasVal ? 4 : 0));
+  __shared__ __align__(16) unsigned char raw[kCountBytes > kStageBytes ? kCountBytes : kStageBytes];
+  uint32_t(*wcnt)[R] = reinterpret_cast<uint32_t(*)[R]>(raw);
+  K* skey = reinterpret_cast<K*>(raw);
+  uint32_t* sval = reinterpret_cast<uint32_t*>(raw + kSortTile * sizeof(K));
   __shared__ uint32_t tbase[R];
+  __shared__ uint32_t lbase[R];  // the tile's exclusive digit offsets
   __shared__ uint32_t ws[33];
   const int lane = lane_id(), warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kSortWarps * R; i += blockDim.x) (&wcnt[0][0])[i] = 0;
@@ -315,33 +324,51 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
       wcnt[w][dg] = run;
       run += c;
     }
-    if (single) tbase[dg] = run;  // the tile's count of digit dg
+    lbase[dg] = run;  // the tile's count of digit dg
   }
   __syncthreads();
-  if (single) {  // exclusive scan of the tile's digit counts (block-uniform branch)
+  {  // exclusive scan of the tile's digit counts
     uint32_t v[PER];
     uint32_t sum = 0;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
       const int d = threadIdx.x * PER + j;
-      v[j] = d < R ? tbase[d] : 0u;
+      v[j] = d < R ? lbase[d] : 0u;
       sum += v[j];
     }
-    uint32_t ex = block_exclusive<uint32_t>(sum, ws, nullptr) + (uint32_t)seg_start;
+    uint32_t ex = block_exclusive<uint32_t>(sum, ws, nullptr);
+    __syncthreads();
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
       const int d = threadIdx.x * PER + j;
-      if (d < R) tbase[d] = ex;
+      if (d < R) {
+        lbase[d] = ex;
+        if (single) tbase[d] = ex + (uint32_t)seg_start;
+      }
       ex += v[j];
     }
-    __syncthreads();
   }
+  __syncthreads();
+  // place of every element in the tile's digit order (stable: within a digit,
+  // by warp, then item, then lane, i.e. input order)
+  uint32_t lpos[kSortItems];
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j)
+    lpos[j] = dig[j] < (uint32_t)R ? lbase[dig[j]] + wcnt[warp][dig[j]] + rank[j] : 0u;
+  __syncthreads();  // wcnt is overwritten by the staged tile from here on
 #pragma unroll
   for (int j = 0; j < kSortItems; ++j) {
     if (dig[j] >= (uint32_t)R) continue;
-    uint32_t dst = tbase[dig[j]] + wcnt[warp][dig[j]] + rank[j];
-    keys_out[dst] = key[j];
-    if (HasVal) vals_out[dst] = val[j];
+    skey[lpos[j]] = key[j];
+    if (HasVal) sval[lpos[j]] = val[j];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ti.count; e += blockDim.x) {
+    const K k = skey[e];
+    const uint32_t d = (uint32_t)(k >> shift) & (R - 1);
+    const uint32_t dst = tbase[d] + ((uint32_t)e - lbase[d]);
+    keys_out[dst] = k;
+    if (HasVal) vals_out[dst] = sval[e];
   }
 }
 

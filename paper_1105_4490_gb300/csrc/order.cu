@@ -138,7 +138,8 @@ __global__ void k_seed2(const float4* __restrict__ xo, const int32_t* __restrict
 // change detection against the previous labels, and exact fixed-point sums
 // q(x) = rint(x * 2^P), P = 30 - e, of each cluster.
 // Lloyd assignment (Algorithm 5) with exact fixed-point centroid sums: every
-// block takes kAssignItems x blockDim consecutive positions.  A block whose
+// block takes items x blockDim consecutive positions (items <= kAssignItems,
+// fewer when the positions would not give every SM a few blocks).  A block whose
 // positions all lie in one node (the common case above the deepest levels)
 // sums in registers and adds its totals with one set of atomics; other blocks
 // aggregate per warp and (node, label).  Integer sums make the result
@@ -184,10 +185,10 @@ __global__ void k_fold_reps(NodeDev* __restrict__ nodes, int N, unsigned long lo
 template <int D>
 __global__ void k_assign(const float4* __restrict__ xo, const int32_t* __restrict__ seg, int64_t n, int it,
                          NodeDev* __restrict__ nodes, uint8_t* __restrict__ lab, int final_pass,
-                         unsigned long long* __restrict__ rep) {
+                         unsigned long long* __restrict__ rep, int items) {
   __shared__ int s_first;
   __shared__ unsigned long long red[kBlock / 32][2 * 4 + 2];
-  const int64_t base = (int64_t)blockIdx.x * (kAssignItems * blockDim.x);
+  const int64_t base = (int64_t)blockIdx.x * (items * blockDim.x);
   if (threadIdx.x == 0) s_first = base < n ? seg[base] : -1;
   __syncthreads();
   const int s0 = s_first;
@@ -196,8 +197,8 @@ __global__ void k_assign(const float4* __restrict__ xo, const int32_t* __restric
 #pragma unroll
   for (int k = 0; k < kAssignItems; ++k) {
     const int64_t i = base + k * blockDim.x + threadIdx.x;
-    sv[k] = i < n ? seg[i] : -1;
-    same = same && (i >= n || sv[k] == s0);
+    sv[k] = k < items && i < n ? seg[i] : -1;
+    same = same && (k >= items || i >= n || sv[k] == s0);
   }
   const bool uniform = __syncthreads_and(same) && s0 >= 0;
   if (uniform) {
@@ -210,7 +211,7 @@ __global__ void k_assign(const float4* __restrict__ xo, const int32_t* __restric
 #pragma unroll
     for (int k = 0; k < kAssignItems; ++k) {
       const int64_t i = base + k * blockDim.x + threadIdx.x;
-      if (i >= n) continue;
+      if (k >= items || i >= n) continue;
       uint8_t l;
       long long q[4] = {0, 0, 0, 0};
       assign_one<D>(xo, i, nd, it, lab, final_pass, l, q, chg);
@@ -262,7 +263,7 @@ __global__ void k_assign(const float4* __restrict__ xo, const int32_t* __restric
   }
   // positions of several nodes: per warp and (node, label)
 #pragma unroll 1
-  for (int k = 0; k < kAssignItems; ++k) {
+  for (int k = 0; k < items; ++k) {
     const int64_t i = base + k * blockDim.x + threadIdx.x;
     const int s = sv[k];
     bool act = false;
@@ -306,8 +307,17 @@ __global__ void k_assign(const float4* __restrict__ xo, const int32_t* __restric
   }
 }
 
+// Positions per thread: at most kAssignItems, and few enough that the blocks
+// fill every SM about four times over.
+inline int assign_items(int64_t n) {
+  int items = kAssignItems;
+  while (items > 1 && n < (int64_t)items * kBlock * 152 * 4) items >>= 1;
+  return items;
+}
+
 inline unsigned assign_grid(int64_t n) {
-  return (unsigned)std::max<int64_t>(1, (n + (int64_t)kBlock * kAssignItems - 1) / ((int64_t)kBlock * kAssignItems));
+  const int64_t per = (int64_t)kBlock * assign_items(n);
+  return (unsigned)std::max<int64_t>(1, (n + per - 1) / per);
 }
 
 // Centre update: z = fp32((double(sum) / count) * 2^-P); a node whose labels
@@ -756,7 +766,8 @@ vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s,
     if (stt != VMO_OK) return;
     launch(k_seed2<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, dval, dpre, st.nodes, st.seeds);
     for (int it = 0; it < km_iters; ++it) {
-      launch(k_assign<D>, assign_grid(n), kBlock, 0, s, st.xo, st.seg, n, it, st.nodes, st.lab, 0, rep);
+      launch(k_assign<D>, assign_grid(n), kBlock, 0, s, st.xo, st.seg, n, it, st.nodes, st.lab, 0, rep,
+             assign_items(n));
       if (rep) launch(k_fold_reps, grid_for(N * 10, kBlock), kBlock, 0, s, st.nodes, N, rep);
       launch(k_update<D>, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, it);
       if (it % 4 == 3 && it + 1 < km_iters) {  // stop early once every node has converged
@@ -769,7 +780,8 @@ vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s,
       }
     }
     launch(k_clear_counts, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N);
-    launch(k_assign<D>, assign_grid(n), kBlock, 0, s, st.xo, st.seg, n, 0, st.nodes, st.lab, 1, rep);
+    launch(k_assign<D>, assign_grid(n), kBlock, 0, s, st.xo, st.seg, n, 0, st.nodes, st.lab, 1, rep,
+           assign_items(n));
     if (rep) launch(k_fold_reps, grid_for(N * 10, kBlock), kBlock, 0, s, st.nodes, N, rep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) stt = cuda_fail(e, "two_means", __FILE__, __LINE__);
@@ -792,7 +804,7 @@ vmo_status two_means_into(OrderState& st, int N, int d, int km_iters, unsigned l
     launch(k_seed2<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, dval, dpre, st.nodes, st.seeds);
     for (int it = 0; it < km_iters; ++it) {
       launch(k_assign<D>, assign_grid(n), kBlock, 0, s, st.xo, st.seg, n, it, st.nodes, st.lab, 0,
-             (unsigned long long*)nullptr);
+             (unsigned long long*)nullptr, assign_items(n));
       launch(k_update<D>, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, it);
       if (it % 4 == 3 && it + 1 < km_iters) {  // stop early once every node has converged
         int h = 0;
@@ -805,7 +817,7 @@ vmo_status two_means_into(OrderState& st, int N, int d, int km_iters, unsigned l
     }
     launch(k_clear_counts, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N);
     launch(k_assign<D>, assign_grid(n), kBlock, 0, s, st.xo, st.seg, n, 0, st.nodes, st.lab, 1,
-           (unsigned long long*)nullptr);
+           (unsigned long long*)nullptr, assign_items(n));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) stt = cuda_fail(e, "two_means", __FILE__, __LINE__);
   });

@@ -293,6 +293,10 @@ def main():
     ap.add_argument("--serve-sweep", default="",
                     help="comma-separated request rates: run the served leg at each and report the highest rate "
                          "sustained (achieved >= 95%% of offered, p99 <= 2 s)")
+    ap.add_argument("--autotune", type=int, default=0, metavar="N",
+                    help="before the batched leg, tune the launch shapes (vmo_autotune) on the first N matrices "
+                         "of the batch mix and report the setting and its times (the setting never changes a "
+                         "result)")
     ap.add_argument("--profile", action="store_true",
                     help="one untimed step of the workload and exit (for ncu captures; no JSON line)")
     ap.add_argument("--profile-matrix", type=int, default=-1,
@@ -484,6 +488,12 @@ def main():
                           "the same workload run right after the timed region"}
 
     modes = {}
+    if args.autotune > 0 and world == 1:
+        sample = W.batch_mix(args.batch_count or 4096, seed=1)[:args.autotune]
+        dev = [(torch.as_tensor(A.rowptr).cuda(), torch.as_tensor(A.colidx).cuda(), A.m) for A in sample]
+        best, best_ms, default_ms = V.autotune(dev, V.Params(d=3, seed=1), reps=3)
+        modes["autotune"] = {"sample": f"first {args.autotune} matrices of the batch mix, vmo_batch_order, median of 3",
+                             "setting": best, "best_ms": best_ms, "default_ms": default_ms}
     if args.batch_count > 0:
         modes["batched"] = batched_leg(V, torch, args.batch_count, 32, args.warmup, max(min(args.steps, 3), 1),
                                        flush)

@@ -334,6 +334,48 @@ vmo_status vmo_batch_layout(const vmo_csr* mats, int32_t count, const vmo_params
  * pointers. */
 vmo_status vmo_finegrain_coords(vmo_hg hg, const float* bipartite_coords, float* coords, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Launch-shape tuning (no counterpart in the paper: choices of this GPU
+ * implementation).  None of these settings changes any result, bit for bit;
+ * they only change how the work is split into launches:
+ *   small_step_threads: layout step launches of at most this many threads
+ *     use the step-kernel variant with two far-field rows in flight per lane
+ *     (latency hiding for small levels); default 19,456 (4 warps per SM);
+ *   radix_max_bits: widest digit of the binning sort's LSD passes, 8, 9 or
+ *     10 (default 10: fewest passes);
+ *   assign_items: positions per thread of the Lloyd assignment, 1, 2, 4 or
+ *     8 (default 8; fewer are used when the blocks would not fill the GPU).
+ * The setting is process-wide and read at every launch.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t small_step_threads;
+  int32_t radix_max_bits;
+  int32_t assign_items;
+} vmo_tuning;
+
+/* Current setting (host struct out). */
+void vmo_get_tuning(vmo_tuning* out);
+
+/* Sets all three choices.  Errors: VMO_ERR_INVALID for a null pointer or a
+ * value outside the ranges above (nothing is changed then).  Not to be called
+ * while another thread is inside a library call. */
+vmo_status vmo_set_tuning(const vmo_tuning* tuning);
+
+/* Timed search for the setting that orders the given matrices fastest: from
+ * the current setting, each choice in turn over its candidates
+ * (small_step_threads 0 ... 155,648; radix_max_bits 8, 9, 10; assign_items
+ * 1, 2, 4, 8), every candidate timed as the median of `reps` calls of
+ * vmo_batch_order(mats, count, NULL, params, BBD) after one untimed call, with
+ * CUDA events on `stream`.  The fastest becomes the process-wide setting.
+ * mats: host array of `count` vmo_csr (device pointers inside), as for
+ * vmo_batch_order; best (host, optional): the chosen setting; best_ms /
+ * default_ms (host, optional): its time and the starting setting's time.
+ * Allocates one device permutation buffer for the duration of the call.
+ * Errors: those of vmo_batch_order (the setting is restored then);
+ * VMO_ERR_INVALID for count <= 0 or reps outside [1, 100]. */
+vmo_status vmo_autotune(const vmo_csr* mats, int32_t count, const vmo_params* params, int32_t reps,
+                        vmo_tuning* best, double* best_ms, double* default_ms, void* stream);
+
 /* Cut metrics of a vertex partition (Sec. 4.1 footnote, Sec. 5): over the
  * nets of the model, lambda_e = number of distinct parts among the pins;
  * cutnet = #{e : lambda_e > 1}, lambda1 = sum_e (lambda_e - 1).

@@ -905,12 +905,8 @@ __device__ __forceinline__ void near_range(const float4* __restrict__ xp, int qa
 #define VMO_STEP_MINBLOCKS 6
 #endif
 constexpr int kStepBlock = VMO_STEP_BLOCK;
-// step launches of at most this many threads (about 4 warps per SM) take the
-// far-field variant with two rows in flight
-#ifndef VMO_SMALL_STEP_THREADS
-#define VMO_SMALL_STEP_THREADS (152 * 4 * 32)
-#endif
-constexpr int64_t kSmallStepThreads = VMO_SMALL_STEP_THREADS;
+// step launches of at most g_tuning.small_step_threads threads (default
+// about 4 warps per SM) take the far-field variant with two rows in flight
 
 template <int D, bool COUNT, bool MLP>
 __global__ void __launch_bounds__(kStepBlock, MLP ? 3 : VMO_STEP_MINBLOCKS) k_repulse_update(
@@ -1571,7 +1567,7 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
       if (timed) stats_time_begin(ms);
       unsigned long long* icount = stats_interaction_counter();
       // few warps per SM: the far-field variant with two rows in flight
-      const bool mlp = lb.threads <= kSmallStepThreads;
+      const bool mlp = lb.threads <= g_tuning.small_step_threads.load(std::memory_order_relaxed);
       auto step_kernel = icount ? (mlp ? k_repulse_update<D, true, true> : k_repulse_update<D, true, false>)
                                 : (mlp ? k_repulse_update<D, false, true> : k_repulse_update<D, false, false>);
       launch(step_kernel, grid_for(lb.threads, kStepBlock), kStepBlock, 0, ms, xs, ws, XP, svals, scell, cst, CP,

@@ -307,10 +307,10 @@ __global__ void k_assign(const float4* __restrict__ xo, const int32_t* __restric
   }
 }
 
-// Positions per thread: at most kAssignItems, and few enough that the blocks
-// fill every SM about four times over.
+// Positions per thread: at most the tuned cap (kAssignItems by default), and
+// few enough that the blocks fill every SM about four times over.
 inline int assign_items(int64_t n) {
-  int items = kAssignItems;
+  int items = std::min(kAssignItems, std::max(1, g_tuning.assign_items.load(std::memory_order_relaxed)));
   while (items > 1 && n < (int64_t)items * kBlock * 152 * 4) items >>= 1;
   return items;
 }

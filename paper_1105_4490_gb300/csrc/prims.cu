@@ -133,8 +133,9 @@ vmo_status scan_impl(const T* in, T* out, int64_t n, T* total, cudaStream_t s, S
 
 // ------------------------------- radix sort --------------------------------
 // LSD passes of B-bit digits, B in {6, 8, 9, 10} chosen per sort: the fewest
-// passes of at most 10 bits, then the smallest listed width covering the key
-// bits in that many passes (18-bit cell keys: 2 passes of 9 bits).
+// passes of at most 10 bits (or the tuned cap, 8 or 9), then the smallest
+// listed width covering the key bits in that many passes (18-bit cell keys:
+// 2 passes of 9 bits).
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = kSortTile / kSortThreads;  // 8
 constexpr int kSortWarps = kSortThreads / 32;
@@ -444,7 +445,8 @@ __global__ void __launch_bounds__(kSortThreads) radix_tile_sort_kernel(const uin
 }
 
 inline int digit_bits(int bits, int* passes) {
-  const int p = (bits + kMaxRadixBits - 1) / kMaxRadixBits;
+  const int maxb = std::min(kMaxRadixBits, std::max(8, g_tuning.radix_max_bits.load(std::memory_order_relaxed)));
+  const int p = (bits + maxb - 1) / maxb;
   const int need = (bits + p - 1) / p;
   *passes = p;
   return need <= 6 ? 6 : need <= 8 ? 8 : need <= 9 ? 9 : 10;

@@ -237,6 +237,17 @@ void stats_time_end(cudaStream_t s, uint64_t points);
 // kernel has completed and its writes are visible (and at once when the kernel
 // was launched without the attribute).
 extern thread_local bool g_pdl;
+
+// Launch-shape choices that never change a result (tune.cu): the largest
+// step launch that takes the variant with two far-field rows in flight, the
+// widest radix digit, and the positions per thread of the Lloyd assignment.
+// Process-wide; set by vmo_set_tuning / vmo_autotune.
+struct Tuning {
+  std::atomic<int64_t> small_step_threads{152 * 4 * 32};
+  std::atomic<int> radix_max_bits{10};
+  std::atomic<int> assign_items{8};
+};
+extern Tuning g_tuning;
 struct PdlScope {
   bool prev;
   PdlScope() : prev(g_pdl) { g_pdl = true; }

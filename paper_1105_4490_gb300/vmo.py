@@ -33,6 +33,10 @@ class _Csr(C.Structure):
                 ("colidx", C.c_void_p)]
 
 
+class _Tuning(C.Structure):
+    _fields_ = [("small_step_threads", C.c_int64), ("radix_max_bits", C.c_int32), ("assign_items", C.c_int32)]
+
+
 class _Params(C.Structure):
     _fields_ = [("d", C.c_int32), ("iters", C.c_int32), ("sigma", C.c_float), ("decay", C.c_float),
                 ("occupancy", C.c_int32), ("multilevel", C.c_int32), ("match_rounds", C.c_int32),
@@ -80,7 +84,8 @@ class Params:
 
 SYMBOLS = ["vmo_default_params", "vmo_build_hypergraph", "vmo_hg_vertices", "vmo_hg_nets", "vmo_hg_arrays",
            "vmo_components", "vmo_init_coords", "vmo_layout", "vmo_layout_step", "vmo_coarsen", "vmo_bisect",
-           "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_order_matched", "vmo_finegrain_coords", "vmo_cut_size", "vmo_destroy",
+           "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_order_matched", "vmo_finegrain_coords", "vmo_get_tuning", "vmo_set_tuning",
+           "vmo_autotune", "vmo_cut_size", "vmo_destroy",
            "vmo_status_string", "vmo_last_error", "vmo_stats_reset", "vmo_stats_get", "vmo_batch_order",
            "vmo_batch_layout", "vmo_bisect_noalloc", "vmo_server_default_config", "vmo_server_estimate_bytes",
            "vmo_server_plan", "vmo_server_create", "vmo_server_submit", "vmo_server_poll", "vmo_server_wait",
@@ -137,6 +142,11 @@ def load(path: str | None = None):
     lib.vmo_order_vertices.argtypes = [V, V, C.POINTER(_Params), I32, V, C.POINTER(_Tree), V]
     lib.vmo_order_matched.argtypes = [V, V, C.POINTER(_Params), I32, V, V, V, V, C.POINTER(_Tree), V]
     lib.vmo_finegrain_coords.argtypes = [V, V, V, V]
+    lib.vmo_get_tuning.argtypes = [C.POINTER(_Tuning)]
+    lib.vmo_get_tuning.restype = None
+    lib.vmo_set_tuning.argtypes = [C.POINTER(_Tuning)]
+    lib.vmo_autotune.argtypes = [C.POINTER(_Csr), I32, C.POINTER(_Params), I32, C.POINTER(_Tuning),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double), V]
     lib.vmo_cut_size.argtypes = [V, V, I32, P64, P64, V]
     lib.vmo_batch_order.argtypes = [C.POINTER(_Csr), I32, V, C.POINTER(_Params), I32, V, V]
     lib.vmo_batch_layout.argtypes = [C.POINTER(_Csr), I32, C.POINTER(_Params), V, V]
@@ -166,7 +176,7 @@ def load(path: str | None = None):
     for nm in SYMBOLS:
         if nm not in ("vmo_default_params", "vmo_hg_vertices", "vmo_hg_nets", "vmo_destroy", "vmo_status_string",
                       "vmo_last_error", "vmo_stats_reset", "vmo_server_default_config", "vmo_server_estimate_bytes",
-                      "vmo_server_plan", "vmo_server_destroy"):
+                      "vmo_server_plan", "vmo_server_destroy", "vmo_get_tuning"):
             getattr(lib, nm).restype = C.c_int
     _lib = lib
     return lib
@@ -417,6 +427,30 @@ def batch_order(mats, params: Params | None = None, sbd: bool = False, coords: t
     p = (params or Params())._c()
     _check(load().vmo_batch_order(arr, len(mats), _ptr(coords), C.byref(p), int(sbd), _ptr(perm), _stream()))
     return perm[:offs[-1]], offs
+
+
+def get_tuning() -> dict:
+    """The launch-shape setting (vmo_get_tuning): none of it changes a result."""
+    t = _Tuning()
+    load().vmo_get_tuning(C.byref(t))
+    return {f: getattr(t, f) for f, _ in _Tuning._fields_}
+
+
+def set_tuning(small_step_threads: int, radix_max_bits: int, assign_items: int) -> None:
+    """vmo_set_tuning: all three choices at once."""
+    t = _Tuning(small_step_threads, radix_max_bits, assign_items)
+    _check(load().vmo_set_tuning(C.byref(t)))
+
+
+def autotune(mats, params: Params | None = None, reps: int = 3):
+    """vmo_autotune: timed search over the launch shapes on these matrices
+    (as for batch_order); sets and returns (setting, best_ms, default_ms)."""
+    arr, offs, keep = _csr_array(mats)
+    p = (params or Params())._c()
+    t = _Tuning()
+    b, dflt = C.c_double(), C.c_double()
+    _check(load().vmo_autotune(arr, len(mats), C.byref(p), reps, C.byref(t), C.byref(b), C.byref(dflt), _stream()))
+    return {f: getattr(t, f) for f, _ in _Tuning._fields_}, b.value, dflt.value
 
 
 def bisect_noalloc(coords: torch.Tensor, verts: torch.Tensor, seed: int, key: int = 1, km_iters: int = 20,

@@ -63,7 +63,7 @@ def test_struct_layouts_match_c(tmp_path):
     from paper_1105_4490_gb300 import vmo
     structs = {"vmo_params": vmo._Params, "vmo_csr": vmo._Csr, "vmo_tree": vmo._Tree, "vmo_stats": vmo._Stats,
                "vmo_server_config": vmo._ServerConfig, "vmo_request_info": vmo._RequestInfo,
-               "vmo_server_stats": vmo._ServerStats}
+               "vmo_server_stats": vmo._ServerStats, "vmo_tuning": vmo._Tuning}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vmo.h"', "int main(void) {"]
     for cname, ct in structs.items():
         lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
@@ -84,3 +84,19 @@ def test_struct_layouts_match_c(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(ct), cname
         for f, _ in ct._fields_:
             assert got[(cname, f)] == getattr(ct, f).offset, (cname, f)
+
+
+def test_tuning_host_calls():
+    """The launch-shape setting is host state: read, set, refused out of range
+    (unchanged then), restored."""
+    import paper_1105_4490_gb300 as V
+    t0 = V.get_tuning()
+    assert t0 == {"small_step_threads": 19456, "radix_max_bits": 10, "assign_items": 8}
+    V.set_tuning(0, 8, 2)
+    assert V.get_tuning() == {"small_step_threads": 0, "radix_max_bits": 8, "assign_items": 2}
+    for bad in ((-1, 10, 8), (0, 7, 8), (0, 11, 8), (0, 10, 3), (0, 10, 16)):
+        with pytest.raises(V.VmoError):
+            V.set_tuning(*bad)
+        assert V.get_tuning() == {"small_step_threads": 0, "radix_max_bits": 8, "assign_items": 2}
+    V.set_tuning(**t0)
+    assert V.get_tuning() == t0

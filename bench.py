@@ -85,6 +85,35 @@ def oracle_step(mats, seed=1):
     return nnz
 
 
+def _oracle_order_one(A) -> int:
+    """One matrix through the oracle's full pipeline (a worker of the all-core
+    baseline; touches no GPU)."""
+    return oracle_step([(A, dict(d=3, max_depth=62))])
+
+
+def batch_cpu_all_cores(mats=None, count: int = 0, max_nnz: int = 15_000) -> dict:
+    """The oracle on all host cores over independent matrices of the batch mix:
+    a seeded sample of `count` (default: one per core) of the 4,096 matrices
+    among those of at most `max_nnz` nonzeros, one matrix per task, a spawn
+    process pool of one worker per core."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    mats = mats if mats is not None else W.batch_mix(4096, seed=1)
+    small = [i for i, A in enumerate(mats) if A.nnz <= max_nnz]
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(24)
+    pick = sorted(int(i) for i in rng.choice(small, size=min(count or cores, len(small)), replace=False))
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        nnz = sum(pool.map(_oracle_order_one, [mats[i] for i in pick], chunksize=1))
+    dt = time.perf_counter() - t0
+    return {"value": nnz / dt, "unit": "nnz/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(pick)} matrices of the batch mix with <= {max_nnz} nnz (seeded), {nnz} nnz, oracle "
+                      f"FP64 full pipeline (multilevel layout d=3, recursive BBD, min_part 64), one matrix per "
+                      f"worker process, {dt:.1f} s"}
+
+
 def run_cpu_baseline(mats, sample_name):
     t0 = time.perf_counter()
     nnz = oracle_step(mats)
@@ -157,11 +186,11 @@ def gpu_step(V, torch, mats, dev_csr, params):
     return nnz
 
 
-def batched_leg(V, torch, count: int, plain_sample: int, warmup: int, steps: int, flush):
+def batched_leg(V, torch, count: int, plain_sample: int, warmup: int, steps: int, flush, mats=None):
     """Config-4 distribution: `count` independent matrices ordered to BBD in one
     batch (vmo_batch_order) against one-at-a-time plain calls on the first
     `plain_sample` of them; both in nnz ordered per second."""
-    mats = W.batch_mix(count, seed=1)
+    mats = mats if mats is not None else W.batch_mix(count, seed=1)
     dev = [(torch.as_tensor(A.rowptr).cuda(), torch.as_tensor(A.colidx).cuda(), A.m) for A in mats]
     nnz = sum(A.nnz for A in mats)
     p = V.Params(d=3, seed=1)
@@ -495,8 +524,11 @@ def main():
         modes["autotune"] = {"sample": f"first {args.autotune} matrices of the batch mix, vmo_batch_order, median of 3",
                              "setting": best, "best_ms": best_ms, "default_ms": default_ms}
     if args.batch_count > 0:
+        bmats = W.batch_mix(args.batch_count, seed=1)
         modes["batched"] = batched_leg(V, torch, args.batch_count, 32, args.warmup, max(min(args.steps, 3), 1),
-                                       flush)
+                                       flush, bmats)
+        if not args.no_cpu_baseline and world == 1:
+            modes["batched"]["cpu_oracle_all_cores"] = batch_cpu_all_cores(bmats)
     if args.serve_rate > 0 and world == 1:
         modes["served"] = served_leg(V, args.serve_rate, args.serve_seconds)
     if args.serve_sweep and world == 1:

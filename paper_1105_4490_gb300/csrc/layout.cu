@@ -647,10 +647,11 @@ __device__ inline void far_row(const float4* __restrict__ CP, int64_t cell0, int
   float4 P[3][N];
   const int npairs = (hi0 - lo0 + 1) >> 1;
   const float4* row = CP + (cell0 >> 1) * N;
+  // a row holds 2 or 3 pairs: only the third is conditional
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < N; ++j) P[i][j] = i < npairs ? row[i * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = 0; j < N; ++j) P[i][j] = (i < 2 || npairs > 2) ? row[i * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     float2 w = pair_weight<D>(P[i]);
@@ -753,7 +754,7 @@ __device__ inline void far_level_lane2(const float4* __restrict__ CP, int64_t ce
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < N; ++j) P[i][j] = i < npairs ? row[i * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int j = 0; j < N; ++j) P[i][j] = (i < 2 || npairs > 2) ? row[i * N + j] : make_float4(0.f, 0.f, 0.f, 0.f);
   };
   auto apply = [&](float4 (*P)[N], bool incore) {
 #pragma unroll

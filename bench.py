@@ -52,7 +52,7 @@ SMS = 152
 # DRAM bytes (read + write) per launch of the step kernel, averaged over the
 # 3,000 launches of one step of the medium workload: one ncu capture of the
 # current kernel, summarised in profiles/k_repulse_update_traffic_medium.md
-STEP_KERNEL_TRAFFIC_BYTES = 4_409_186
+STEP_KERNEL_TRAFFIC_BYTES = 4_409_344
 
 
 MEDIUM_NAME = "grid3d_64^3+powerlaw_500k"

@@ -274,8 +274,8 @@ vmo_status vmo_order_vertices(vmo_hg hg, const float* coords, const vmo_params* 
  * edge cut by the 2-means labels selects its end with the smaller
  * (|x.r - delta|, vertex id), and the selected vertices and their partners
  * form V3 (with mu the identity this is the separator of vmo_order_bbd).
- * With params->cut_order a separator is sorted by the two-bit number of
- * each pair (the row's bits or its matched column's).
+ * With params->cut_order = b a separator is sorted by the b two-bit numbers
+ * of each pair (the row's bits or its matched column's, level by level).
  * hg: bipartite model (VMO_BIPARTITE) of an m x m pattern.
  * match: device int32[m], match[i] = the column matched to row i: a
  * permutation of [0, m) with (i, match[i]) an entry of the pattern.

@@ -649,22 +649,28 @@ struct CutRec {
   int32_t ns;  // separator size (0 for leaves)
 };
 
+// One warp per record: lane 0 fills the record, the warp marks its positions.
 __global__ void k_cut_recs(const TreeDev tree, const uint32_t* __restrict__ idx, int n, int sbd,
                            CutRec* __restrict__ cr, int32_t* __restrict__ own, int64_t* __restrict__ sz) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = lane_id();
+  if (w >= n) return;
+  const int i = (int)w;
   const uint32_t r = idx[i];
   const int32_t o = tree.offset[r], n1 = tree.n1[r], n2 = tree.n2[r], ns = tree.nsep[r];
   const bool leaf = n2 == 0 && ns == 0;
-  CutRec c;
-  c.heap = tree.heap[r];
-  c.depth = tree.depth[r];
-  c.a = leaf ? o : (sbd ? o + n1 : o + n1 + n2);
-  c.ns = leaf ? 0 : ns;
-  cr[i] = c;
-  sz[i] = c.ns;
+  const int32_t a = leaf ? o : (sbd ? o + n1 : o + n1 + n2);
+  if (lane == 0) {
+    CutRec c;
+    c.heap = tree.heap[r];
+    c.depth = tree.depth[r];
+    c.a = a;
+    c.ns = leaf ? 0 : ns;
+    cr[i] = c;
+    sz[i] = c.ns;
+  }
   const int32_t len = leaf ? n1 : ns;
-  for (int32_t p = 0; p < len; ++p) own[c.a + p] = i;
+  for (int32_t p = lane; p < len; p += 32) own[a + p] = i;
 }
 
 __global__ void k_inverse_perm(const int32_t* __restrict__ ord, int64_t n, int32_t* __restrict__ pos) {
@@ -1035,7 +1041,7 @@ vmo_status cut_order_pass(OrderState& st, const OrderParams& op, cudaStream_t s,
   VMO_TRY(sc.alloc(&v1, n));
   VMO_TRY(sc.alloc(&v2, n));
   VMO_CUDA(cudaMemsetAsync(own, 0xFF, n * sizeof(int32_t), s));  // every position is owned; -1 would be skipped
-  launch(k_cut_recs, grid_for(nrec, kBlock), kBlock, 0, s, st.tree, idx, nrec, op.sbd, cr, own, sz);
+  launch(k_cut_recs, grid_for((int64_t)nrec * 32, kBlock), kBlock, 0, s, st.tree, idx, nrec, op.sbd, cr, own, sz);
   launch(k_inverse_perm, grid_for(n, kBlock), kBlock, 0, s, st.ord, n, pos);
   launch(k_cut_codes, grid_for(n, kBlock), kBlock, 0, s, st.ord, pos, own, n, cr, st.adj_ptr, st.adj, b, vcode);
   const uint64_t sentinel = (uint64_t)nrec << (2 * b);

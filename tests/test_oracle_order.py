@@ -895,3 +895,33 @@ def test_cut_order_levels(oracle_mod, b):
     for bb in (3, 8):
         pb, _ = O.order(hg, 3, x4, seed=8, min_part=4, max_depth=3, cut_order=bb)
         assert np.array_equal(pb, p3)
+
+
+def test_mu_from_match_checks_the_matching(oracle_mod):
+    """mu of a perfect matching pairs row i with column match[i] both ways;
+    a non-permutation, an entry outside the pattern, a non-bipartite model and
+    a rectangular pattern are refused."""
+    O = oracle_mod
+    A = W.with_strengthened_diagonal(W.grid_laplacian_2d(12), 0.6, 4)
+    m = A.m
+    bp = O.build_from_matrix("bipartite", A)
+    match = A.meta["match"].astype(np.int64)
+    mu = O.mu_from_match(bp, match)
+    assert np.array_equal(mu[:m], m + match) and np.array_equal(mu[m + match], np.arange(m))
+    assert np.array_equal(mu[mu], np.arange(2 * m))
+    dup = match.copy()
+    dup[1] = dup[0]
+    dense = np.zeros((m, m), dtype=bool)
+    dense[np.repeat(np.arange(m), np.diff(A.rowptr)), A.colidx] = True
+    i, j = np.argwhere(~dense)[0]
+    off = match.copy()
+    k = int(np.flatnonzero(match == j)[0])
+    off[i], off[k] = j, match[i]
+    for bad in (dup, off):
+        with pytest.raises(ValueError):
+            O.mu_from_match(bp, bad)
+    with pytest.raises(ValueError):
+        O.mu_from_match(O.build_from_matrix("symmetric", A), match)
+    R = W.powerlaw_rectangular(30, 20, seed=1)
+    with pytest.raises(ValueError):
+        O.mu_from_match(O.build_from_matrix("bipartite", R), np.arange(25))

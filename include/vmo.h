@@ -295,6 +295,24 @@ vmo_status vmo_order_matched(vmo_hg hg, const float* coords, const vmo_params* p
                              const int32_t* match, int32_t* row_perm, int32_t* col_perm, int32_t* vperm,
                              vmo_tree* tree, void* stream);
 
+/* Strengthened diagonal for vmo_order_matched, computed on the host: a
+ * perfect matching of the bipartite model of the square pattern (rows to
+ * columns), as the paper obtains it for its LU experiments (Sec. 5): a
+ * heavy-edge matching (entries by decreasing |value|, ties by row then
+ * column, each taken when its row and column are both free; without values,
+ * every row in order takes its first free column) augmented by the
+ * Hopcroft-Karp algorithm to a maximum matching.  Host preprocessing of the
+ * input, outside the ordering's GPU path; it touches no device memory.
+ * rowptr, colidx: HOST arrays of an m x m pattern (int32[m + 1], int32[nnz]);
+ * values: optional host float[nnz] (NULL: pattern only); match: host
+ * int32[m] out, match[i] = the column matched to row i (-1 if unmatched);
+ * matched: optional host out, the size of the maximum matching.
+ * Errors: VMO_ERR_INVALID for a malformed pattern or a NaN value;
+ * VMO_ERR_UNSUPPORTED when the pattern is structurally singular (no perfect
+ * matching exists: match then holds a maximum matching). */
+vmo_status vmo_perfect_matching_host(int32_t m, const int32_t* rowptr, const int32_t* colidx, const float* values,
+                                     int32_t* match, int32_t* matched);
+
 /* Batched recursive ordering of `count` independent square patterns in one
  * launch sequence (symmetric model).  The matrices are joined
  * block-diagonally on the device and every connected component of every

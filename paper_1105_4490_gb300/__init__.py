@@ -2,5 +2,6 @@
 C-ABI (include/vmo.h) with a thin Python binding (``vmo``)."""
 from . import server, vmo  # noqa: F401
 from .vmo import (Hypergraph, Params, VmoError, autotune, batch_layout, batch_order, default_params,  # noqa: F401
-                  get_tuning, init_coords, kmeans, load, set_tuning, stats, stats_reset)
+                  get_tuning, init_coords, kmeans, load, perfect_matching, set_tuning, stats,
+                  stats_reset)
 from .server import Server  # noqa: F401

@@ -84,7 +84,8 @@ class Params:
 
 SYMBOLS = ["vmo_default_params", "vmo_build_hypergraph", "vmo_hg_vertices", "vmo_hg_nets", "vmo_hg_arrays",
            "vmo_components", "vmo_init_coords", "vmo_layout", "vmo_layout_step", "vmo_coarsen", "vmo_bisect",
-           "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_order_matched", "vmo_finegrain_coords", "vmo_get_tuning", "vmo_set_tuning",
+           "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_order_matched", "vmo_perfect_matching_host", "vmo_finegrain_coords", "vmo_get_tuning",
+           "vmo_set_tuning",
            "vmo_autotune", "vmo_cut_size", "vmo_destroy",
            "vmo_status_string", "vmo_last_error", "vmo_stats_reset", "vmo_stats_get", "vmo_batch_order",
            "vmo_batch_layout", "vmo_bisect_noalloc", "vmo_server_default_config", "vmo_server_estimate_bytes",
@@ -142,6 +143,7 @@ def load(path: str | None = None):
     lib.vmo_order_vertices.argtypes = [V, V, C.POINTER(_Params), I32, V, C.POINTER(_Tree), V]
     lib.vmo_order_matched.argtypes = [V, V, C.POINTER(_Params), I32, V, V, V, V, C.POINTER(_Tree), V]
     lib.vmo_finegrain_coords.argtypes = [V, V, V, V]
+    lib.vmo_perfect_matching_host.argtypes = [I32, V, V, V, V, C.POINTER(I32)]
     lib.vmo_get_tuning.argtypes = [C.POINTER(_Tuning)]
     lib.vmo_get_tuning.restype = None
     lib.vmo_set_tuning.argtypes = [C.POINTER(_Tuning)]
@@ -427,6 +429,25 @@ def batch_order(mats, params: Params | None = None, sbd: bool = False, coords: t
     p = (params or Params())._c()
     _check(load().vmo_batch_order(arr, len(mats), _ptr(coords), C.byref(p), int(sbd), _ptr(perm), _stream()))
     return perm[:offs[-1]], offs
+
+
+def perfect_matching(mat, values=None):
+    """vmo_perfect_matching_host: a strengthened diagonal for order_matched
+    (heavy-edge start from |values|, Hopcroft-Karp augmentation) of a square
+    host pattern (object with .m, .rowptr, .colidx numpy arrays).  Returns
+    (match int32 numpy [m], matched); raises VmoError when no perfect
+    matching exists."""
+    import numpy as np
+    rp = np.ascontiguousarray(mat.rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(mat.colidx, dtype=np.int32)
+    vv = None if values is None else np.ascontiguousarray(values, dtype=np.float32)
+    match = np.empty(max(mat.m, 1), dtype=np.int32)
+    got = C.c_int32(0)
+    st = load().vmo_perfect_matching_host(mat.m, rp.ctypes.data, ci.ctypes.data if ci.size else None,
+                                          vv.ctypes.data if vv is not None else None, match.ctypes.data,
+                                          C.byref(got))
+    _check(st)
+    return match[:mat.m], int(got.value)
 
 
 def get_tuning() -> dict:

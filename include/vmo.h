@@ -295,6 +295,38 @@ vmo_status vmo_order_matched(vmo_hg hg, const float* coords, const vmo_params* p
                              const int32_t* match, int32_t* row_perm, int32_t* col_perm, int32_t* vperm,
                              vmo_tree* tree, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Matrix Market files (host I/O; no counterpart in the paper, whose test
+ * matrices come in this format).  A host CSR: row-major, columns sorted
+ * within a row, duplicate entries summed; arrays allocated with malloc by
+ * vmo_read_matrix_market and released with vmo_free_host_csr.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t m, n;
+  int64_t nnz;
+  int32_t* rowptr; /* m + 1 */
+  int32_t* colidx; /* nnz */
+  float* values;   /* nnz (pattern files: 1; complex files: the modulus) */
+} vmo_host_csr;
+
+/* Reads a coordinate Matrix Market file (fields real, integer, complex,
+ * pattern; symmetry general, symmetric, skew-symmetric, hermitian).
+ * expand_symmetric: 1 stores both triangles of symmetric storage (a_ji =
+ * a_ij, -a_ij for skew-symmetric), 0 keeps the stored triangle.
+ * Errors: VMO_ERR_INVALID for a missing file or a malformed header, size
+ * line or entry (index outside the matrix); VMO_ERR_UNSUPPORTED for array
+ * (dense) files and sizes beyond 2^30; VMO_ERR_OOM. *out is zeroed on
+ * error. */
+vmo_status vmo_read_matrix_market(const char* path, int32_t expand_symmetric, vmo_host_csr* out);
+
+/* Writes a host CSR as a general coordinate file (pattern = 1: no values).
+ * Errors: VMO_ERR_INVALID for null arguments or a file that cannot be
+ * written. */
+vmo_status vmo_write_matrix_market(const char* path, const vmo_host_csr* csr, int32_t pattern);
+
+/* Releases the arrays of a CSR filled by vmo_read_matrix_market (NULL-safe). */
+void vmo_free_host_csr(vmo_host_csr* csr);
+
 /* Strengthened diagonal for vmo_order_matched, computed on the host: a
  * perfect matching of the bipartite model of the square pattern (rows to
  * columns), as the paper obtains it for its LU experiments (Sec. 5): a

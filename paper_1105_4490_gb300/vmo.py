@@ -33,6 +33,11 @@ class _Csr(C.Structure):
                 ("colidx", C.c_void_p)]
 
 
+class _HostCsr(C.Structure):
+    _fields_ = [("m", C.c_int32), ("n", C.c_int32), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("colidx", C.c_void_p), ("values", C.c_void_p)]
+
+
 class _Tuning(C.Structure):
     _fields_ = [("small_step_threads", C.c_int64), ("radix_max_bits", C.c_int32), ("assign_items", C.c_int32)]
 
@@ -84,7 +89,8 @@ class Params:
 
 SYMBOLS = ["vmo_default_params", "vmo_build_hypergraph", "vmo_hg_vertices", "vmo_hg_nets", "vmo_hg_arrays",
            "vmo_components", "vmo_init_coords", "vmo_layout", "vmo_layout_step", "vmo_coarsen", "vmo_bisect",
-           "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_order_matched", "vmo_perfect_matching_host", "vmo_finegrain_coords", "vmo_get_tuning",
+           "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_order_matched", "vmo_perfect_matching_host", "vmo_read_matrix_market",
+           "vmo_write_matrix_market", "vmo_free_host_csr", "vmo_finegrain_coords", "vmo_get_tuning",
            "vmo_set_tuning",
            "vmo_autotune", "vmo_cut_size", "vmo_destroy",
            "vmo_status_string", "vmo_last_error", "vmo_stats_reset", "vmo_stats_get", "vmo_batch_order",
@@ -144,6 +150,10 @@ def load(path: str | None = None):
     lib.vmo_order_matched.argtypes = [V, V, C.POINTER(_Params), I32, V, V, V, V, C.POINTER(_Tree), V]
     lib.vmo_finegrain_coords.argtypes = [V, V, V, V]
     lib.vmo_perfect_matching_host.argtypes = [I32, V, V, V, V, C.POINTER(I32)]
+    lib.vmo_read_matrix_market.argtypes = [C.c_char_p, I32, C.POINTER(_HostCsr)]
+    lib.vmo_write_matrix_market.argtypes = [C.c_char_p, C.POINTER(_HostCsr), I32]
+    lib.vmo_free_host_csr.argtypes = [C.POINTER(_HostCsr)]
+    lib.vmo_free_host_csr.restype = None
     lib.vmo_get_tuning.argtypes = [C.POINTER(_Tuning)]
     lib.vmo_get_tuning.restype = None
     lib.vmo_set_tuning.argtypes = [C.POINTER(_Tuning)]
@@ -178,7 +188,7 @@ def load(path: str | None = None):
     for nm in SYMBOLS:
         if nm not in ("vmo_default_params", "vmo_hg_vertices", "vmo_hg_nets", "vmo_destroy", "vmo_status_string",
                       "vmo_last_error", "vmo_stats_reset", "vmo_server_default_config", "vmo_server_estimate_bytes",
-                      "vmo_server_plan", "vmo_server_destroy", "vmo_get_tuning"):
+                      "vmo_server_plan", "vmo_server_destroy", "vmo_get_tuning", "vmo_free_host_csr"):
             getattr(lib, nm).restype = C.c_int
     _lib = lib
     return lib
@@ -429,6 +439,55 @@ def batch_order(mats, params: Params | None = None, sbd: bool = False, coords: t
     p = (params or Params())._c()
     _check(load().vmo_batch_order(arr, len(mats), _ptr(coords), C.byref(p), int(sbd), _ptr(perm), _stream()))
     return perm[:offs[-1]], offs
+
+
+class HostMatrix:
+    """A host CSR pattern with values (row-major, sorted columns), as read from
+    a Matrix Market file; accepted wherever a matrix with .m, .n, .rowptr and
+    .colidx is (Hypergraph.from_matrix, perfect_matching, batch_order)."""
+
+    def __init__(self, name, m, n, rowptr, colidx, values):
+        self.name, self.m, self.n = name, m, n
+        self.rowptr, self.colidx, self.values = rowptr, colidx, values
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+
+def read_matrix_market(path: str, expand_symmetric: bool = True) -> HostMatrix:
+    """vmo_read_matrix_market: a coordinate Matrix Market file as a HostMatrix
+    (duplicates summed; symmetric storage expanded to both triangles unless
+    expand_symmetric is False)."""
+    import numpy as np
+    c = _HostCsr()
+    _check(load().vmo_read_matrix_market(os.fsencode(path), int(expand_symmetric), C.byref(c)))
+    try:
+        def arr(p, n, dt):
+            return np.ctypeslib.as_array(C.cast(p, C.POINTER(dt)), shape=(n,)).copy() if n else \
+                np.zeros(0, dtype=np.dtype(dt))
+        rp = arr(c.rowptr, c.m + 1, C.c_int32)
+        ci = arr(c.colidx, c.nnz, C.c_int32)
+        vv = arr(c.values, c.nnz, C.c_float)
+        return HostMatrix(os.path.basename(path), c.m, c.n, rp, ci, vv)
+    finally:
+        load().vmo_free_host_csr(C.byref(c))
+
+
+def write_matrix_market(path: str, mat, values=None) -> None:
+    """vmo_write_matrix_market: a general coordinate file of the pattern (and
+    the values, if given or present on the matrix)."""
+    import numpy as np
+    rp = np.ascontiguousarray(mat.rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(mat.colidx, dtype=np.int32)
+    if values is None:
+        values = getattr(mat, "values", None)
+        if callable(values):
+            values = values()
+    vv = None if values is None else np.ascontiguousarray(values, dtype=np.float32)
+    c = _HostCsr(mat.m, mat.n, int(rp[-1]), rp.ctypes.data, ci.ctypes.data if ci.size else None,
+                 vv.ctypes.data if vv is not None and vv.size else None)
+    _check(load().vmo_write_matrix_market(os.fsencode(path), C.byref(c), int(vv is None)))
 
 
 def perfect_matching(mat, values=None):

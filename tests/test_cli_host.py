@@ -1,5 +1,6 @@
 """The command line's host parts (no GPU): argument checks and the permuted
 matrix it writes."""
+import os
 import subprocess
 import sys
 
@@ -10,7 +11,9 @@ import workloads as W
 
 
 def test_help_and_argument_errors():
-    r = subprocess.run([sys.executable, "-m", "paper_1105_4490_gb300", "--help"], capture_output=True, text=True)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-m", "paper_1105_4490_gb300", "--help"], capture_output=True, text=True,
+                       cwd=root)
     assert r.returncode == 0 and "Matrix Market" in r.stdout
     from paper_1105_4490_gb300.__main__ import parse
     a = parse(["m.mtx", "out", "--sbd", "--cut-order", "2"])

@@ -91,6 +91,14 @@ def _load():
             lib.ora_match.argtypes = [C.c_int32, P, P, P, C.c_uint64, C.c_int32, C.c_int32, P, P]
             lib.ora_hierarchy.restype = C.c_int32
             lib.ora_hierarchy.argtypes = [C.POINTER(_HG), C.c_uint64, C.c_int32, C.c_int32, P]
+            lib.ora_hierarchy_level.restype = C.c_int32
+            lib.ora_hierarchy_level.argtypes = [C.POINTER(_HG), P, C.c_uint64, C.c_int32, C.c_int32, C.c_int32,
+                                                C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                                C.POINTER(C.POINTER(C.c_int32)), C.POINTER(C.POINTER(C.c_int32)),
+                                                C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.POINTER(C.c_double)),
+                                                C.POINTER(C.POINTER(C.c_int32))]
+            lib.ora_prolong.restype = None
+            lib.ora_prolong.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_int32, P, P, P]
             lib.ora_layout_multilevel.restype = C.c_int
             lib.ora_layout_multilevel.argtypes = [C.POINTER(_HG), C.c_int32, C.c_int32, C.c_double, C.c_double,
                                                   C.c_int32, C.c_uint64, C.c_int32, C.c_int32, P, P]
@@ -296,6 +304,71 @@ def hierarchy(hg: Hypergraph, seed: int, rounds: int = 4, kmin: int = 64) -> lis
     ks = np.zeros(41, dtype=np.int32)
     n = _load().ora_hierarchy(C.byref(s), seed & (2**64 - 1), rounds, kmin, _p(ks))
     return [int(v) for v in ks[:n]]
+
+
+def hierarchy_level(hg: Hypergraph, j: int, seed: int, rounds: int = 4, kmin: int = 64, w=None):
+    """Level j of the coarsening hierarchy of Algorithm 3 built from the whole
+    graph: dict with k, adj_ptr, adj (neighbours ascending), acost (summed
+    costs of the merged fine edges), w (summed vertex weights), pi (level j-1
+    vertex -> level j vertex; None for j = 0) and nlevels.  None if j is not a
+    level."""
+    if hg.adj_ptr is None:
+        raise ValueError("the hierarchy needs a graph model")
+    lib = _load()
+    s = hg._struct()
+    ww = _opt64(w)
+    k, nadj = C.c_int32(), C.c_int64()
+    ap, aj, pi = C.POINTER(C.c_int32)(), C.POINTER(C.c_int32)(), C.POINTER(C.c_int32)()
+    ac, wo = C.POINTER(C.c_double)(), C.POINTER(C.c_double)()
+    nl = lib.ora_hierarchy_level(C.byref(s), _p(ww), seed & (2**64 - 1), rounds, kmin, j, C.byref(k), C.byref(nadj),
+                                 C.byref(ap), C.byref(aj), C.byref(ac), C.byref(wo), C.byref(pi))
+    if nl < 0:
+        return None
+    kk, na = int(k.value), int(nadj.value)
+    kf = hg.k if j == 1 else None
+    out = dict(k=kk, adj_ptr=_arr(ap, kk + 1, np.int32), adj=_arr(aj, na, np.int32),
+               acost=_arr(ac, na, np.float64), w=_arr(wo, kk, np.float64), nlevels=int(nl), pi=None)
+    if j > 0:
+        if kf is None:
+            kf = hierarchy(hg, seed, rounds, kmin)[j - 1]
+        out["pi"] = _arr(pi, kf, np.int32)
+    for ptr in (ap, aj, ac, wo, pi):
+        if ptr:
+            lib.ora_free(C.cast(ptr, C.c_void_p))
+    return out
+
+
+def prolong(kf: int, kc: int, d: int, seed: int, j: int, pi: np.ndarray, xc) -> np.ndarray:
+    """Prolongation of Algorithm 3 from level j (kc points xc) to level j-1 (kf
+    points, grouping pi): FP64 [kf, 4]."""
+    xx = _x64(xc)
+    pp = np.ascontiguousarray(pi, dtype=np.int32)
+    out = np.zeros((max(kf, 1), 4), dtype=np.float64)
+    _load().ora_prolong(kf, kc, d, seed & (2**64 - 1), j, _p(pp), _p(xx), _p(out))
+    return out[:kf]
+
+
+def graph_nets(k: int, adj_ptr: np.ndarray, adj: np.ndarray, acost: np.ndarray | None = None):
+    """The graph given by a symmetric adjacency as a hypergraph of 2-pin nets
+    (edges u < v in lexicographic order, the layout of the symmetric model),
+    with the cost of every net taken from the adjacency entry (u, v)."""
+    ap = np.asarray(adj_ptr, dtype=np.int64)
+    aj = np.asarray(adj, dtype=np.int64)
+    rows = np.repeat(np.arange(k, dtype=np.int64), np.diff(ap))
+    keep = aj > rows
+    u, v = rows[keep], aj[keep]
+    l = len(u)
+    pins = np.stack([u, v], axis=1).reshape(-1).astype(np.int32)
+    net_ptr = (2 * np.arange(l + 1)).astype(np.int32)
+    order = np.lexsort((np.arange(2 * l), pins))
+    vtx_ptr = np.zeros(k + 1, dtype=np.int32)
+    np.add.at(vtx_ptr, pins.astype(np.int64) + 1, 1)
+    vtx_ptr = np.cumsum(vtx_ptr).astype(np.int32)
+    vnets = (order // 2).astype(np.int32)
+    hg = Hypergraph(0, k, l, net_ptr, pins, vtx_ptr, vnets, np.asarray(adj_ptr, dtype=np.int32),
+                    np.asarray(adj, dtype=np.int32))
+    cost = None if acost is None else np.asarray(acost, dtype=np.float64)[keep]
+    return hg, cost
 
 
 def layout_multilevel(hg: Hypergraph, d: int, seed: int, iters: int = 100, occ: int = 8, sigma: float = 1.0,

@@ -802,6 +802,49 @@ ORA_EXPORT int32_t ora_hierarchy(const ora_hg* h, uint64_t seed, int32_t rounds,
   return nl;
 }
 
+/* One level of the coarsening hierarchy of a graph (for checks): the graph of
+ * level j (vertex count, adjacency with summed edge costs, summed vertex
+ * weights; w = NULL for unit weights at level 0) and, for j >= 1, the grouping
+ * pi of level j-1 into level j.  Outputs are malloc'd (release with ora_free);
+ * pi_out receives NULL for j = 0.  Returns the number of levels, or -1 (and
+ * nothing allocated) when j is not a level. */
+ORA_EXPORT int32_t ora_hierarchy_level(const ora_hg* h, const double* w, uint64_t seed, int32_t rounds, int32_t kmin,
+                                       int32_t j, int32_t* k_out, int64_t* nadj_out, int32_t** adj_ptr_out,
+                                       int32_t** adj_out, double** acost_out, double** w_out, int32_t** pi_out) {
+  ora_graph G[41];
+  int32_t* PI[41];
+  memset(G, 0, sizeof(G)); memset(PI, 0, sizeof(PI));
+  int32_t nl = ora_build_hierarchy(h, w, seed, rounds, kmin, G, PI);
+  int32_t ret = (j >= 0 && j < nl) ? nl : -1;
+  if (ret > 0) {
+    *k_out = G[j].k;
+    *nadj_out = G[j].adj_ptr[G[j].k];
+    *adj_ptr_out = G[j].adj_ptr; *adj_out = G[j].adj; *acost_out = G[j].acost; *w_out = G[j].w;
+    memset(&G[j], 0, sizeof(G[j]));
+    *pi_out = j > 0 ? PI[j - 1] : NULL;
+    if (j > 0) PI[j - 1] = NULL;
+  }
+  for (int32_t i = 0; i < nl; ++i) { ora_graph_free(&G[i]); free(PI[i]); }
+  return ret;
+}
+
+/* Prolongation of Algorithm 3 from level j (kc vertices) to level j-1 (kf
+ * vertices, grouping pi): x_{j-1}(v) = f * x_j(pi(v)) + jitter(v), with
+ * f = (kf/kc)^(1/d), which keeps the number of points per unit volume, and
+ * jitter_m = 0.1 * (u - 1/2), u = (rand(seed^JITTER, v, 4*(j-1) + m) >> 40) * 2^-24
+ * uniform in [0, 1), so that the members of a group start apart. */
+ORA_EXPORT void ora_prolong(int32_t kf, int32_t kc, int32_t d, uint64_t seed, int32_t j, const int32_t* pi,
+                            const double* xc /* kc*4 */, double* xf /* kf*4, out */) {
+  double f = pow((double)kf / (double)kc, 1.0 / d);
+  for (int32_t v = 0; v < kf; ++v)
+    for (int m = 0; m < 4; ++m) {
+      if (m >= d) { xf[4 * v + m] = 0.0; continue; }
+      uint64_t r = ora_rand64(seed ^ ORA_TAG_JITTER, (uint64_t)v, (uint64_t)(4 * (j - 1) + m));
+      double u = (double)(r >> 40) * 0x1p-24;
+      xf[4 * v + m] = f * xc[4 * pi[v] + m] + 0.1 * (u - 0.5);
+    }
+}
+
 static int ora_layout_connected(const ora_hg* h, int32_t d, int32_t occ, double sigma, double decay,
                                 int32_t iters, uint64_t seed, int32_t rounds, int32_t kmin, const double* w,
                                 double* x /* out, k*4 */) {
@@ -824,14 +867,8 @@ static int ora_layout_connected(const ora_hg* h, int32_t d, int32_t occ, double 
     ora_hg_free(&hj);
     if (j > 0) { /* prolong to level j-1 */
       int32_t kf = G[j - 1].k;
-      double f = pow((double)kf / (double)G[j].k, 1.0 / d);
       double* xn = (double*)calloc((size_t)kf * 4, sizeof(double));
-      for (int32_t v = 0; v < kf; ++v)
-        for (int m = 0; m < d; ++m) {
-          uint64_t r = ora_rand64(seed ^ ORA_TAG_JITTER, (uint64_t)v, (uint64_t)(4 * (j - 1) + m));
-          double u = (double)(r >> 40) * 0x1p-24;
-          xn[4 * v + m] = f * xc[4 * PI[j - 1][v] + m] + 0.1 * (u - 0.5);
-        }
+      ora_prolong(kf, G[j].k, d, seed, j, PI[j - 1], xc, xn);
       free(xc);
       xc = xn;
     }

@@ -106,7 +106,8 @@ def _load():
             lib.ora_bisect.argtypes = [C.c_int32, P, P, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32,
                                        P, P, P]
             lib.ora_order.argtypes = [C.POINTER(_HG), C.c_int32, P, C.c_uint64, C.c_int32, C.c_int32,
-                                      C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P, C.POINTER(_Tree)]
+                                      C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, C.c_int32, P,
+                                      C.POINTER(_Tree)]
             lib.ora_tree_free.argtypes = [C.POINTER(_Tree)]
             lib.ora_finegrain_coords.argtypes = [C.POINTER(_HG), P, P]
             lib.ora_kmeans.argtypes = [C.c_int32, P, P, C.c_int32, C.c_int32, C.c_uint64, C.c_uint64, C.c_int32,
@@ -398,7 +399,7 @@ def bisect(d: int, x4: np.ndarray, verts: np.ndarray, seed: int, key: int = 1, k
 
 def order(hg: Hypergraph, d: int, x4: np.ndarray, seed: int, km_iters: int = 20, min_part: int = 64,
           max_depth: int = 62, sbd: bool = False, sep_rec: bool = False, cut_order: bool = False,
-          match: np.ndarray | None = None):
+          match: np.ndarray | None = None, order_free: bool = False):
     """Recursive BBD (or SBD) ordering from fp32 coordinates: (perm, tree).
     Connected components are ordered one after the other (block diagonal),
     each by its own recursion; tree records are sorted by (comp, heap).
@@ -409,7 +410,10 @@ def order(hg: Hypergraph, d: int, x4: np.ndarray, seed: int, km_iters: int = 20,
     into the parts of the splits of the descendants 1..b levels down.
     match: strengthened diagonal of a square matrix in the bipartite model
     (Sec. 4.2, the matching M as the map mu): match[i] is the column matched to
-    row i; a vertex moved into a separator takes its partner with it."""
+    row i; a vertex moved into a separator takes its partner with it, in the
+    loop of Algorithm 7 over the cut edges in canonical order (a partner moved
+    early leaves later edges at it uncut), or, with order_free, in the
+    order-free reading (every cut edge's selected end and its partner)."""
     if hg.adj_ptr is None:
         raise ValueError("ordering needs a graph model (symmetric or bipartite)")
     mu = None
@@ -420,7 +424,8 @@ def order(hg: Hypergraph, d: int, x4: np.ndarray, seed: int, km_iters: int = 20,
     perm = np.zeros(hg.k, dtype=np.int32)
     t = _Tree()
     _load().ora_order(C.byref(s), d, _p(xf), seed & (2**64 - 1), km_iters, min_part, max_depth, int(sbd),
-                      int(sep_rec), int(cut_order), _p(mu) if mu is not None else None, _p(perm), C.byref(t))
+                      int(sep_rec), int(cut_order), _p(mu) if mu is not None else None, int(bool(order_free)),
+                      _p(perm), C.byref(t))
     n = t.count
     tree = dict(heap=_arr(t.heap, n, np.uint64), offset=_arr(t.offset, n, np.int32), n1=_arr(t.n1, n, np.int32),
                 n2=_arr(t.n2, n, np.int32), nsep=_arr(t.nsep, n, np.int32), depth=_arr(t.depth, n, np.int32),

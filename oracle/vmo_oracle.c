@@ -1198,14 +1198,17 @@ static int cmp_cut_edge(const void* a, const void* b) {
  *
  * With a matching, the loop of Algorithm 7 moves both v and mu(v) into V3,
  * and a partner moved early turns later edges at it into uncut ones, so the
- * outcome depends on the edge order, which the paper does not fix.  Reading:
- * the order-free form.  Every edge cut by the 2-means labels (one end 1, the
- * other 2, before any vertex moves) selects its end with the smaller
- * (|x.r - delta|, id); the selected vertices and their partners form V3.  With
- * mu = identity this is the loop below. */
+ * outcome depends on the edge order, which the paper does not fix.  Reading
+ * (mu_rule 0, the default): the loop itself, over the cut edges in the
+ * canonical order above; an edge whose ends no longer carry labels 1 and 2
+ * (one of them, or its partner, moved already) is skipped.  mu_rule 1: the
+ * order-free form, every edge cut by the 2-means labels (before any move)
+ * selects its end with the smaller (|x.r - delta|, id), and the selected
+ * vertices and their partners form V3 (a superset of the loop's separator).
+ * With mu = identity both are the loop below. */
 static int32_t ora_separate(const ora_hg* h, int d, const float* x4, const int32_t* verts, int32_t nv,
                             const uint8_t* innode, uint8_t* lab, const float* z1, const float* z2,
-                            const int32_t* mu) {
+                            const int32_t* mu, int32_t mu_rule) {
   float r[4], delta = 0.0f;
   for (int m = 0; m < d; ++m) r[m] = z2[m] - z1[m];
   for (int m = 0; m < d; ++m) {
@@ -1238,10 +1241,12 @@ static int32_t ora_separate(const ora_hg* h, int d, const float* x4, const int32
   qsort(E, (size_t)ne, sizeof(ora_cut_edge), cmp_cut_edge);
   int32_t nsep = 0;
   if (mu) {
-    /* all selections are taken against the 2-means labels, then applied */
     for (int64_t t = 0; t < ne; ++t) {
       if (!innode[mu[E[t].v]]) abort(); /* partners always share a node */
     }
+  }
+  if (mu && mu_rule == 1) {
+    /* all selections are taken against the 2-means labels, then applied */
     for (int64_t t = 0; t < ne; ++t) {
       if (lab[E[t].v] != 3) { lab[E[t].v] = 3; nsep++; }
       if (lab[mu[E[t].v]] != 3) { lab[mu[E[t].v]] = 3; nsep++; }
@@ -1254,6 +1259,7 @@ static int32_t ora_separate(const ora_hg* h, int d, const float* x4, const int32
     if (!((pv == 1 && pw == 2) || (pv == 2 && pw == 1))) continue;
     lab[E[t].v] = 3; /* |x(v).r - delta| <= |x(w).r - delta|: v joins the separator */
     nsep++;
+    if (mu && lab[mu[E[t].v]] != 3) { lab[mu[E[t].v]] = 3; nsep++; } /* and its partner */
   }
   free(E);
   return nsep;
@@ -1404,7 +1410,7 @@ static void ora_cut_order(const ora_hg* h, int32_t sbd, int32_t b, const int32_t
  * records are sorted by (component, heap number). */
 ORA_EXPORT int ora_order(const ora_hg* h, int32_t d, const float* x4, uint64_t seed, int32_t km_iters,
                          int32_t min_part, int32_t max_depth, int32_t sbd, int32_t sep_rec, int32_t cut_order,
-                         const int32_t* mu, int32_t* perm, ora_tree* tree) {
+                         const int32_t* mu, int32_t mu_rule, int32_t* perm, ora_tree* tree) {
   int32_t k = h->k;
   if (sep_rec && max_depth > 39) max_depth = 39;
   int32_t* cbase;
@@ -1436,7 +1442,7 @@ ORA_EXPORT int ora_order(const ora_hg* h, int32_t d, const float* x4, uint64_t s
     float z1[4], z2[4];
     if (!ora_bisect(d, x4, verts, nd.size, seed, nd.heap, km_iters, nlab, z1, z2)) continue;
     for (int32_t i = 0; i < nd.size; ++i) { lab[verts[i]] = nlab[i]; innode[verts[i]] = 1; }
-    ora_separate(h, d, x4, verts, nd.size, innode, lab, z1, z2, mu);
+    ora_separate(h, d, x4, verts, nd.size, innode, lab, z1, z2, mu, mu_rule);
     int32_t c1 = 0, c2 = 0, c3 = 0;
     for (int32_t i = 0; i < nd.size; ++i) {
       uint8_t l = lab[verts[i]];

@@ -783,20 +783,14 @@ def test_matched_square_blocks(oracle_mod, sbd, seed, cut_order):
     assert not _owners_of_pairs_agree(hg.k, m, plain, tree0, sbd, match)
 
 
-def test_matched_separator_order_free(oracle_mod):
-    """The separator with a matching in its order-free reading: at the root,
-    V3 is exactly the set of ends with the smaller (|x.r - delta|, id) of the
-    edges cut by the 2-means labels, with their partners; V1 and V2 keep the
-    2-means labels."""
-    O = oracle_mod
+def _root_separator_case(O, order_free):
     A = W.with_strengthened_diagonal(W.powerlaw_symmetric(800, seed=4), 0.6, 4)
     match = A.meta["match"]
-    m = A.m
     hg = O.build_from_matrix("bipartite", A)
     x4 = O.init_coords(hg.k, 3, 4)
     comps = O.components(hg)
     root = np.flatnonzero(comps == comps[0]).astype(np.int32)
-    perm, tree = O.order(hg, 3, x4, seed=4, max_depth=1, match=match, min_part=1)
+    perm, tree = O.order(hg, 3, x4, seed=4, max_depth=1, match=match, min_part=1, order_free=order_free)
     # the first component's root node; its vertices in their initial order
     j = [i for i in range(len(tree["heap"])) if tree["comp"][i] == 0 and tree["heap"][i] == 1][0]
     o, n1, n2, ns = (int(tree[f][j]) for f in ("offset", "n1", "n2", "nsep"))
@@ -818,16 +812,45 @@ def test_matched_separator_order_free(oracle_mod):
 
     L = dict(zip(verts.tolist(), lab.tolist()))
     mu = O.mu_from_match(hg, match)
-    sel = set()
+    # cut edges (2-means labels), as (key of the selected end, selected end, other end)
+    cut = []
     for v in verts.tolist():
         for w in hg.adj[hg.adj_ptr[v]:hg.adj_ptr[v + 1]].tolist():
             if w > v and w in L and L[v] != L[w]:
-                sel.add(min((s(v), v), (s(w), w))[1])
-    sep = sel | {int(mu[v]) for v in sel}
-    got = perm[o + n1 + n2:o + n1 + n2 + ns]
-    assert set(got.tolist()) == sep
+                a, b = sorted([(s(v), v), (s(w), w)])
+                cut.append((a[0], a[1], b[1]))
+    got = set(perm[o + n1 + n2:o + n1 + n2 + ns].tolist())
     side1 = set(perm[o:o + n1].tolist())
     assert all(L[v] == L[next(iter(side1))] for v in side1)
+    return got, cut, L, mu
+
+
+def test_matched_separator_order_free(oracle_mod):
+    """The separator with a matching in its order-free reading: at the root,
+    V3 is exactly the set of ends with the smaller (|x.r - delta|, id) of the
+    edges cut by the 2-means labels, with their partners; V1 and V2 keep the
+    2-means labels."""
+    got, cut, L, mu = _root_separator_case(oracle_mod, True)
+    sel = {v for _, v, _ in cut}
+    assert got == sel | {int(mu[v]) for v in sel}
+
+
+def test_matched_separator_literal_loop(oracle_mod):
+    """The default reading: Algorithm 7's loop itself over the cut edges in the
+    canonical order (ascending key of the selected end, then the other end);
+    an edge still cut when reached moves its selected end and that end's
+    partner into V3, an edge with an end (or through it a partner) already
+    moved is skipped.  Restated here as a plain loop on the root's data; it
+    gives a subset of the order-free separator, strictly smaller here."""
+    got, cut, L, mu = _root_separator_case(oracle_mod, False)
+    lab = dict(L)
+    for _, v, w in sorted(cut):
+        if lab[v] != 3 and lab[w] != 3:
+            lab[v] = 3
+            lab[int(mu[v])] = 3
+    assert got == {v for v, l in lab.items() if l == 3}
+    free, _, _, _ = _root_separator_case(oracle_mod, True)
+    assert got < free
 
 
 def _heap_path_codes(hg, perm, tree, sbd, b, owner):

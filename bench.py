@@ -51,7 +51,7 @@ FP32_LANES_PER_SM = 128
 SMS = 152
 # DRAM bytes (read + write) per launch of the step kernel, averaged over the
 # 3,000 launches of one step of the medium workload: one ncu capture of the
-# current kernel, summarised in profiles/k_repulse_update_traffic_medium.md
+# current kernel (dram__bytes_read.sum + dram__bytes_write.sum)
 STEP_KERNEL_TRAFFIC_BYTES = 4_409_344
 
 

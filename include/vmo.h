@@ -99,6 +99,11 @@ typedef struct {
                             V22); pair 1 sorts first, each pair ascending for BBD and in the order 01,
                             00, 11, 10 for SBD: the cut rows and columns brought into recursive form
                             down to the b-th level (Sec. 4.2) (0: off) */
+  int32_t sep_order_free; /* with a strengthened diagonal (vmo_order_matched) only: 0 runs Algorithm 7's
+                            loop over the cut edges in canonical order (ascending |x.r - delta|, id of
+                            the end it moves, then the other end), where a partner moved early leaves
+                            later edges at it uncut; 1 takes the order-free reading (every cut edge's
+                            moved end and its partner; a superset) (0) */
   uint64_t seed;        /* seed of every random draw (1) */
 } vmo_params;
 
@@ -130,13 +135,16 @@ typedef struct {
  * device time of the layout step kernel (repulsion + update, timed with CUDA
  * events on the launching stream), its launch count, the target points and the
  * source interactions (near-field pairs plus far-field cell charges) it
- * evaluated. */
+ * evaluated; and the device memory allocations the library has made (stream-
+ * ordered pool and plain cudaMalloc alike; counted whether or not timing is
+ * enabled). */
 typedef struct {
   uint64_t launches;
   uint64_t step_launches;
   double step_ms;
   uint64_t step_points;
   uint64_t step_interactions;
+  uint64_t device_allocations;
 } vmo_stats;
 
 /* Fills *p with the defaults listed above. */
@@ -185,7 +193,8 @@ vmo_status vmo_layout(vmo_hg hg, const vmo_params* params, float* coords, int32_
  * length `step`: y = gradient of eq. graphenergygradientsimple (repulsion on
  * the grid pyramid), then x_n <- x_n - step * y_n / ||y_n||.
  * coords (in/out) device float[4k]; y_out device float[4k] or NULL;
- * keys_out device uint32[k] or NULL (level-L Morton key of every vertex);
+ * keys_out device uint32[k] or NULL (row-major index of every vertex's
+ * level-L grid cell, coordinate 0 fastest);
  * levels_out host int32 or NULL (finest grid level L). */
 vmo_status vmo_layout_step(vmo_hg hg, const vmo_params* params, float* coords, float step, float* y_out,
                            uint32_t* keys_out, int32_t* levels_out, void* stream);
@@ -197,6 +206,42 @@ vmo_status vmo_layout_step(vmo_hg hg, const vmo_params* params, float* coords, f
  * NULL.  Graph models only. */
 vmo_status vmo_coarsen(vmo_hg hg, const vmo_params* params, int32_t* mate, int32_t* pi, int32_t* kc_out,
                        int32_t* level_sizes, int32_t* nlevels, void* stream);
+
+/* One level of the coarsening hierarchy of Algorithm 3 (Sec. 2.3) built from
+ * the handle's whole graph as one problem (the hierarchy whose sizes
+ * vmo_coarsen reports; the layout of a connected graph uses the same one).
+ * Level 0 is the handle's graph (unit costs; the handle's vertex weights, or
+ * 1); level j >= 1 is the graph of the groups of level j-1: a coarse vertex
+ * weighs what its group weighs, the fine edges between two groups merge into
+ * one edge whose cost is the sum of theirs, edges inside a group vanish.
+ * Outputs (device, any may be NULL): adj_ptr int32[k+1] and adj int32[nadj]
+ * (neighbours ascending), acost float[nadj] (edge costs), weight float[k]
+ * (vertex weights), pi int32[k_{j-1}] (vertex of level j-1 -> its group at
+ * level j; untouched for level 0).  *k_out, *nadj_out: host sizes of the
+ * level (call once with NULL arrays to size them).
+ * Errors: VMO_ERR_INVALID for a level outside [0, levels), VMO_ERR_UNSUPPORTED
+ * for hypergraph models. */
+vmo_status vmo_hierarchy_level(vmo_hg hg, const vmo_params* params, int32_t level, int32_t* k_out, int64_t* nadj_out,
+                               int32_t* adj_ptr, int32_t* adj, float* acost, float* weight, int32_t* pi,
+                               void* stream);
+
+/* Prolongation of Algorithm 3 from level `level` (>= 1) of that hierarchy to
+ * level-1: fine[v] = f * coarse[pi(v)] + jitter(v) per coordinate m < d, with
+ * f = (k_{level-1} / k_level)^(1/d) (the same number of points per unit
+ * volume) and jitter(v)_m = 0.1 (u - 1/2), u uniform in [0, 1) from the keyed
+ * draw (seed, v, 4 (level-1) + m); coordinates >= d are 0.  coarse: device
+ * float[4 k_level], fine: device float[4 k_{level-1}] out, both 16-byte
+ * aligned.  Errors: VMO_ERR_INVALID for level 0 or outside the hierarchy. */
+vmo_status vmo_hierarchy_prolong(vmo_hg hg, const vmo_params* params, int32_t level, const float* coarse, float* fine,
+                                 void* stream);
+
+/* One steepest-descent step of Algorithm 4 on level `level` of that
+ * hierarchy, with its vertex weights and edge costs (y = gradient of eq.
+ * graphenergygradientsimple, x_n <- x_n - step * y_n / ||y_n||), as
+ * vmo_layout_step does on the finest level.  coords: device float[4 k_level]
+ * in/out; y_out: device float[4 k_level] or NULL. */
+vmo_status vmo_hierarchy_step(vmo_hg hg, const vmo_params* params, int32_t level, float* coords, float step,
+                              float* y_out, void* stream);
 
 /* 2-means of the points coords[verts[i]] in dimension d (Algorithm 5 with
  * m = 2, in the exact arithmetic of the ordering): verts device int32[nverts]
@@ -217,9 +262,10 @@ vmo_status vmo_bisect(vmo_hg hg, int32_t d, const float* coords, const int32_t* 
  * library reserves on each GPU that loads it (about 5.3 MB, kept until the
  * process exits) instead of in freshly allocated memory; no cudaMalloc or
  * other allocation is made.  Limit: nverts <= 131072, larger inputs return
- * VMO_ERR_INVALID.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents:
+ * VMO_ERR_INVALID.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress, which allocates nothing); the first call on a device
+ * also loads the library's device code there, so make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's contents:
  * calls that overlap on the GPU (other streams or threads) race and must be
  * serialised by the caller. */
 vmo_status vmo_bisect_noalloc(int32_t d, const float* coords, const int32_t* verts, int32_t nverts, uint64_t seed,
@@ -270,10 +316,13 @@ vmo_status vmo_order_vertices(vmo_hg hg, const float* coords, const vmo_params* 
  * joins a separator its partner mu(v) joins too, so no edge of M leaves the
  * diagonal blocks and every block on the diagonal is square).
  * The paper's edge loop gives an order-dependent result once partners move
- * and fixes no order; this entry point takes the order-free reading: every
- * edge cut by the 2-means labels selects its end with the smaller
- * (|x.r - delta|, vertex id), and the selected vertices and their partners
- * form V3 (with mu the identity this is the separator of vmo_order_bbd).
+ * and fixes no order; this entry point runs the loop over the edges cut by
+ * the 2-means labels in canonical order (ascending (|x.r - delta|, vertex id)
+ * of the end the loop moves, then the other end): an edge still cut when
+ * reached moves that end and its partner into V3.  With
+ * params->sep_order_free = 1 it takes the order-free reading instead (every
+ * cut edge's moved end and its partner; a superset).  With mu the identity
+ * both are the separator of vmo_order_bbd.
  * With params->cut_order = b a separator is sorted by the b two-bit numbers
  * of each pair (the row's bits or its matched column's, level by level).
  * hg: bipartite model (VMO_BIPARTITE) of an m x m pattern.
@@ -529,9 +578,17 @@ vmo_status vmo_server_poll(vmo_server srv, uint64_t id, vmo_request_info* info);
  * limit); returns VMO_ERR_TIMEOUT in the latter case, info filled either way. */
 vmo_status vmo_server_wait(vmo_server srv, uint64_t id, double timeout_s, vmo_request_info* info);
 
-/* Cancels a request: a queued one never runs; a running one finishes on the
- * device but its permutation is not written.  No effect on terminal ones. */
+/* Cancels a request: a queued one never runs and is cancelled at once; a
+ * running one stays VMO_REQ_RUNNING (its batch may still read its host
+ * arrays) and becomes VMO_REQ_CANCELLED, with nothing written, when its batch
+ * ends.  No effect on terminal ones. */
 vmo_status vmo_server_cancel(vmo_server srv, uint64_t id);
+
+/* Forgets a terminal request (done, failed or cancelled): its record is freed
+ * and its id becomes unknown, so a long-running server does not grow by one
+ * record per request.  Errors: VMO_ERR_INVALID for an unknown id or a request
+ * that is still queued or running. */
+vmo_status vmo_server_release(vmo_server srv, uint64_t id);
 
 vmo_status vmo_server_get_stats(vmo_server srv, vmo_server_stats* out);
 

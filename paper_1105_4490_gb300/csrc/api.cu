@@ -36,6 +36,8 @@ vmo_status unsupported(const std::string& msg) {
 
 // ------------------------------ instrumentation ----------------------------
 std::atomic<uint64_t> g_launches{0};
+// Device allocations made by the library (reported by vmo_stats_get).
+std::atomic<uint64_t> g_device_allocs{0};
 namespace {
 std::mutex g_stats_mu;
 bool g_time = false;
@@ -89,6 +91,7 @@ vmo_status Scratch::alloc_bytes(void** p, size_t bytes) {
     set_error("device allocation of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
     return VMO_ERR_OOM;
   }
+  g_device_allocs.fetch_add(1, std::memory_order_relaxed);
   ptrs.push_back(*p);
   return VMO_OK;
 }
@@ -141,6 +144,7 @@ vmo_status check_params(const vmo_params* p) {
   if (p->max_depth < 0 || p->max_depth > 62) return invalid("max_depth must be in [0, 62]");
   if (p->sep_recursion != 0 && p->sep_recursion != 1) return invalid("sep_recursion must be 0 or 1");
   if (p->cut_order < 0 || p->cut_order > 8) return invalid("cut_order must be in [0, 8]");
+  if (p->sep_order_free != 0 && p->sep_order_free != 1) return invalid("sep_order_free must be 0 or 1");
   return VMO_OK;
 }
 
@@ -322,6 +326,28 @@ vmo_status run_order(vmo_hg_s* h, const float* coords, const vmo_params* p, int 
   return VMO_OK;
 }
 
+// The coarsening hierarchy of the handle's graph as one problem (the one that
+// vmo_coarsen counts) and a check that `level` is one of its levels.
+vmo_status hierarchy_of(vmo_hg_s* h, const vmo_params* p, int32_t level, LevelBatch& lb, Hierarchy& H, cudaStream_t s,
+                        Scratch& sc) {
+  VMO_TRY(ensure_device());
+  VMO_TRY(check_params(p));
+  if (!h) return invalid("handle is null");
+  if (h->model != VMO_SYMMETRIC && h->model != VMO_BIPARTITE) return unsupported("the hierarchy needs a graph model");
+  VMO_TRY(single_batch(h, p->d, p->occupancy, lb, s));
+  std::vector<uint64_t> seeds{p->seed};
+  VMO_TRY(build_hierarchy(lb, options_of(p), seeds, p->match_rounds, p->coarse_min, p->multilevel != 0, H, s, sc));
+  if (level < 0 || level >= (int32_t)H.levels.size())
+    return invalid("level " + std::to_string(level) + " outside the hierarchy's " + std::to_string(H.levels.size()) +
+                   " levels");
+  return VMO_OK;
+}
+
+__global__ void k_fill_f32(float* __restrict__ a, int64_t n, float v) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
 }  // namespace
 
 vmo_status ensure_device_public() { return ensure_device(); }
@@ -348,6 +374,7 @@ void vmo_default_params(vmo_params* p) {
   p->max_depth = 62;
   p->sep_recursion = 0;
   p->cut_order = 0;
+  p->sep_order_free = 0;
   p->seed = 1;
 }
 
@@ -499,6 +526,68 @@ vmo_status vmo_coarsen(vmo_hg hg, const vmo_params* params, int32_t* mate, int32
   return VMO_OK;
 }
 
+vmo_status vmo_hierarchy_level(vmo_hg hg, const vmo_params* params, int32_t level, int32_t* k_out, int64_t* nadj_out,
+                               int32_t* adj_ptr, int32_t* adj, float* acost, float* weight, int32_t* pi,
+                               void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch sc(s);
+  LevelBatch lb;
+  Hierarchy H;
+  VMO_TRY(hierarchy_of(hg, params, level, lb, H, s, sc));
+  const LevelBatch& L = *H.levels[level];
+  const int64_t k = L.K, na = L.nadj;
+  if (k_out) *k_out = (int32_t)k;
+  if (nadj_out) *nadj_out = na;
+  if (adj_ptr) VMO_CUDA(cudaMemcpyAsync(adj_ptr, L.adj_ptr, (k + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  if (adj && na > 0) VMO_CUDA(cudaMemcpyAsync(adj, L.adj, na * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  if (acost && na > 0) {
+    if (L.acost) VMO_CUDA(cudaMemcpyAsync(acost, L.acost, na * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    else launch(k_fill_f32, grid_for(na, 256), 256, 0, s, acost, na, 1.0f);
+  }
+  if (weight && k > 0) {
+    if (L.w) VMO_CUDA(cudaMemcpyAsync(weight, L.w, k * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    else launch(k_fill_f32, grid_for(k, 256), 256, 0, s, weight, k, 1.0f);
+  }
+  if (pi && level > 0 && H.levels[level - 1]->K > 0)
+    VMO_CUDA(cudaMemcpyAsync(pi, H.pis[level - 1], H.levels[level - 1]->K * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                             s));
+  VMO_LAUNCHED("hierarchy_level");
+  VMO_CUDA(cudaStreamSynchronize(s));
+  return VMO_OK;
+}
+
+vmo_status vmo_hierarchy_prolong(vmo_hg hg, const vmo_params* params, int32_t level, const float* coarse, float* fine,
+                                 void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch sc(s);
+  LevelBatch lb;
+  Hierarchy H;
+  VMO_TRY(hierarchy_of(hg, params, level, lb, H, s, sc));
+  if (level < 1) return invalid("prolongation needs a level >= 1");
+  if ((H.levels[level]->K > 0 && (!coarse || !aligned16(coarse))) ||
+      (H.levels[level - 1]->K > 0 && (!fine || !aligned16(fine))))
+    return invalid("coarse and fine coordinates must be non-null and 16-byte aligned");
+  VMO_TRY(prolong_level(H, level - 1, params->d, (const float4*)coarse, (float4*)fine, s, sc));
+  VMO_CUDA(cudaStreamSynchronize(s));
+  return VMO_OK;
+}
+
+vmo_status vmo_hierarchy_step(vmo_hg hg, const vmo_params* params, int32_t level, float* coords, float step,
+                              float* y_out, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch sc(s);
+  LevelBatch lb;
+  Hierarchy H;
+  VMO_TRY(hierarchy_of(hg, params, level, lb, H, s, sc));
+  if (!(step > 0.0f)) return invalid("step must be > 0");
+  LevelBatch& L = *H.levels[level];
+  if (L.K > 0 && (!coords || !aligned16(coords))) return invalid("coords null or not 16-byte aligned");
+  if (y_out && !aligned16(y_out)) return invalid("y_out must be 16-byte aligned");
+  VMO_TRY(layout_level(L, options_of(params), (float4*)coords, 1, step, (float4*)y_out, nullptr, s, sc));
+  VMO_CUDA(cudaStreamSynchronize(s));
+  return VMO_OK;
+}
+
 vmo_status vmo_bisect(vmo_hg hg, int32_t d, const float* coords, const int32_t* verts, int32_t nverts, uint64_t seed,
                       uint64_t key, int32_t km_iters, uint8_t* labels, float* z, int32_t* split, void* stream) {
   VMO_TRY(ensure_device());
@@ -616,6 +705,7 @@ vmo_status vmo_stats_get(vmo_stats* out) {
   std::lock_guard<std::mutex> lk(g_stats_mu);
   memset(out, 0, sizeof(*out));
   out->launches = g_launches.load();
+  out->device_allocations = g_device_allocs.load();
   if (!g_timed.empty() || g_icount) VMO_CUDA(cudaDeviceSynchronize());
   for (auto& t : g_timed) {
     float ms = 0.f;

@@ -176,6 +176,7 @@ vmo_status order_grouped(const vmo_hg_s* h, const ComponentGroups& g, const floa
   op.sbd = sbd;
   op.sep_rec = p->sep_recursion;
   op.cut_order = p->cut_order;
+  op.mu_order_free = p->sep_order_free;
   st.adj_ptr = h->adj_ptr.ptr;
   st.adj = h->adj.ptr;
   st.mu = mu;

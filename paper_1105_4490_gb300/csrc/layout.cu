@@ -1254,12 +1254,21 @@ __global__ void k_emit_coarse(const uint64_t* __restrict__ keys, const uint32_t*
   atomicAdd(&rowcount[k / Kc], 1);
 }
 
+// Coarse vertex weights (Algorithm 3: a group weighs what its members weigh).
+// The fp32 weights are added in FP64, where the sum of a group of fp32 values
+// is exact (their exponents lie within the 29 spare bits), so the order of the
+// atomics does not change the rounded fp32 result.
 __global__ void k_coarse_w(const float* __restrict__ w, const int32_t* __restrict__ pi, int64_t K,
-                           float* __restrict__ wc) {
+                           double* __restrict__ wc) {
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= K) return;
   int32_t a = pi[v];
-  if (a >= 0) atomicAdd(&wc[a], w ? w[v] : 1.0f);
+  if (a >= 0) atomicAdd(&wc[a], (double)(w ? w[v] : 1.0f));
+}
+
+__global__ void k_round_w(const double* __restrict__ wd, int64_t n, float* __restrict__ w) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) w[i] = (float)wd[i];
 }
 
 __global__ void k_fill_vprob(const int64_t* __restrict__ vb, int P, int64_t K, int32_t* __restrict__ vprob) {
@@ -1383,6 +1392,7 @@ vmo_status level_setup(LevelBatch& lb, int d, int occ, cudaStream_t s) {
   VMO_CUDA(cudaMemcpyAsync(lb.tbase.ptr, tb.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   int64_t* vb;
   VMO_CUDA(cudaMallocAsync((void**)&vb, (P + 1) * sizeof(int64_t), s));
+  g_device_allocs.fetch_add(1, std::memory_order_relaxed);
   VMO_CUDA(cudaMemcpyAsync(vb, lb.vbase.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   if (lb.K > 0) {
     launch(k_fill_vprob, grid_for(lb.K, kBlock), kBlock, 0, s, vb, P, lb.K, lb.vprob.ptr);
@@ -1708,8 +1718,10 @@ static vmo_status contract_level(LevelBatch& lb, const std::vector<int64_t>& new
   VMO_TRY(out.own_adj.resize(std::max<int32_t>(nadj_c, 1)));
   VMO_TRY(out.own_acost.resize(std::max<int32_t>(nadj_c, 1)));
   VMO_TRY(out.own_w.resize((size_t)std::max<int64_t>(Kc, 1)));
+  double* wsum;
+  VMO_TRY(sc.alloc(&wsum, std::max<int64_t>(Kc, 1)));
   VMO_CUDA(cudaMemsetAsync(out.own_adj_ptr.ptr, 0, (Kc + 1) * sizeof(int32_t), s));
-  VMO_CUDA(cudaMemsetAsync(out.own_w.ptr, 0, std::max<int64_t>(Kc, 1) * sizeof(float), s));
+  VMO_CUDA(cudaMemsetAsync(wsum, 0, std::max<int64_t>(Kc, 1) * sizeof(double), s));
   if (n > 0) {
     launch(k_emit_coarse, grid_for(n, kBlock), kBlock, 0, s, skeys, svals, n, flag, pos, (uint64_t)Kc, out.own_adj.ptr,
                                                          out.own_acost.ptr, out.own_adj_ptr.ptr);
@@ -1717,7 +1729,8 @@ static vmo_status contract_level(LevelBatch& lb, const std::vector<int64_t>& new
   }
   VMO_TRY(scan_exclusive<int32_t>(out.own_adj_ptr.ptr, out.own_adj_ptr.ptr, Kc, total, s, sc));
   launch(k_set_last, 1, 1, 0, s, out.own_adj_ptr.ptr, Kc, total);
-  launch(k_coarse_w, grid_for(K, kBlock), kBlock, 0, s, lb.w, pi, K, out.own_w.ptr);
+  launch(k_coarse_w, grid_for(K, kBlock), kBlock, 0, s, lb.w, pi, K, wsum);
+  if (Kc > 0) launch(k_round_w, grid_for(Kc, kBlock), kBlock, 0, s, wsum, Kc, out.own_w.ptr);
   VMO_LAUNCHED("coarse_w");
   out.K = Kc;
   out.adj_ptr = out.own_adj_ptr.ptr;
@@ -1785,55 +1798,61 @@ vmo_status build_hierarchy(LevelBatch& fine, const LayoutOptions& o, const std::
   return VMO_OK;
 }
 
+vmo_status prolong_level(const Hierarchy& H, int j, int d, const float4* xc, float4* xj, cudaStream_t s,
+                         Scratch& sc) {
+  const std::vector<LevelBatch*>& levels = H.levels;
+  const int nl = (int)levels.size();
+  LevelBatch& cur = *levels[j];
+  const int P = cur.P;
+  // which problems of this level start here (not present one level up)
+  std::vector<int32_t> start(P, 1);
+  std::vector<float> fac(P, -1.0f);
+  if (j + 1 < nl) {
+    const LevelBatch& up = *levels[j + 1];
+    size_t q = 0;
+    for (int p = 0; p < P && q < up.src.size(); ++p) {
+      if (cur.src[p] == up.src[q]) {
+        start[p] = 0;
+        double kf = (double)(cur.vbase[p + 1] - cur.vbase[p]);
+        double kcq = (double)(up.vbase[q + 1] - up.vbase[q]);
+        fac[p] = (float)std::pow(kf / kcq, 1.0 / d);
+        ++q;
+      }
+    }
+  }
+  int32_t* st;
+  float* fc;
+  uint64_t* sd;
+  VMO_TRY(sc.alloc(&st, P));
+  VMO_TRY(sc.alloc(&fc, P));
+  VMO_TRY(sc.alloc(&sd, P));
+  VMO_CUDA(cudaMemcpyAsync(st, start.data(), P * 4, cudaMemcpyHostToDevice, s));
+  VMO_CUDA(cudaMemcpyAsync(fc, fac.data(), P * 4, cudaMemcpyHostToDevice, s));
+  VMO_CUDA(cudaMemcpyAsync(sd, H.seeds[j].data(), P * 8, cudaMemcpyHostToDevice, s));
+  VMO_TRY(init_coords_level(cur, d, sd, xj, st, s));
+  if (xc && cur.K > 0) {
+    launch(k_prolong, grid_for(cur.K, kBlock), kBlock, 0, s, xc, H.pis[j], cur.K, cur.vprob.ptr, cur.prob.ptr, fc, sd,
+           j, d, xj);
+    VMO_LAUNCHED("prolong");
+  }
+  VMO_CUDA(cudaStreamSynchronize(s));  // host vectors above must outlive the copies
+  return VMO_OK;
+}
+
 vmo_status layout_multilevel(LevelBatch& fine, const LayoutOptions& o, const std::vector<uint64_t>& seeds,
                              int match_rounds, int coarse_min, bool multilevel, float4* x, cudaStream_t s,
                              Scratch& sc) {
   Hierarchy H;
   VMO_TRY(build_hierarchy(fine, o, seeds, match_rounds, coarse_min, multilevel, H, s, sc));
-  std::vector<LevelBatch*>& levels = H.levels;
-  std::vector<int32_t*>& pis = H.pis;
-  std::vector<std::vector<uint64_t>>& lseeds = H.seeds;
   // layout from the coarsest level down
-  const int nl = (int)levels.size();
+  const int nl = (int)H.levels.size();
   float4* xc = nullptr;
   for (int j = nl - 1; j >= 0; --j) {
-    LevelBatch& cur = *levels[j];
-    const int P = cur.P;
+    LevelBatch& cur = *H.levels[j];
     float4* xj = (j == 0) ? x : nullptr;
     if (!xj) VMO_TRY(sc.alloc(&xj, std::max<int64_t>(cur.K, 1)));
-    // which problems of this level start here (not present one level up)
-    std::vector<int32_t> start(P, 1);
-    std::vector<float> fac(P, -1.0f);
-    if (j + 1 < nl) {
-      const LevelBatch& up = *levels[j + 1];
-      size_t q = 0;
-      for (int p = 0; p < P && q < up.src.size(); ++p) {
-        if (cur.src[p] == up.src[q]) {
-          start[p] = 0;
-          double kf = (double)(cur.vbase[p + 1] - cur.vbase[p]);
-          double kcq = (double)(up.vbase[q + 1] - up.vbase[q]);
-          fac[p] = (float)std::pow(kf / kcq, 1.0 / o.d);
-          ++q;
-        }
-      }
-    }
-    int32_t* st;
-    float* fc;
-    uint64_t* sd;
-    VMO_TRY(sc.alloc(&st, P));
-    VMO_TRY(sc.alloc(&fc, P));
-    VMO_TRY(sc.alloc(&sd, P));
-    VMO_CUDA(cudaMemcpyAsync(st, start.data(), P * 4, cudaMemcpyHostToDevice, s));
-    VMO_CUDA(cudaMemcpyAsync(fc, fac.data(), P * 4, cudaMemcpyHostToDevice, s));
-    VMO_CUDA(cudaMemcpyAsync(sd, lseeds[j].data(), P * 8, cudaMemcpyHostToDevice, s));
-    VMO_TRY(init_coords_level(cur, o.d, sd, xj, st, s));
-    if (xc) {
-      launch(k_prolong, grid_for(cur.K, kBlock), kBlock, 0, s, xc, pis[j], cur.K, cur.vprob.ptr, cur.prob.ptr, fc, sd, j,
-                                                           o.d, xj);
-      VMO_LAUNCHED("prolong");
-    }
+    VMO_TRY(prolong_level(H, j, o.d, xc, xj, s, sc));
     VMO_TRY(layout_level(cur, o, xj, o.iters, -1.0f, nullptr, nullptr, s, sc));
-    VMO_CUDA(cudaStreamSynchronize(s));  // host vectors above must outlive the copies
     xc = xj;
   }
   return VMO_OK;

@@ -107,6 +107,13 @@ vmo_status build_hierarchy(LevelBatch& fine, const LayoutOptions& o, const std::
                            int match_rounds, int coarse_min, bool multilevel, Hierarchy& H, cudaStream_t s,
                            Scratch& sc);
 
+// Start of level j of a hierarchy (the levels above it already laid out):
+// problems that continue from level j+1 are prolonged from its coordinates xc
+// (Algorithm 3: x = f x_c(pi(v)) + jitter, f = (k_j / k_{j+1})^(1/d)), the
+// others (and every problem when xc is null) get the random initial layout.
+vmo_status prolong_level(const Hierarchy& H, int j, int d, const float4* xc, float4* xj, cudaStream_t s,
+                         Scratch& sc);
+
 int grid_levels(int64_t k, int d, int occ);
 int init_side(int64_t k, int d);
 

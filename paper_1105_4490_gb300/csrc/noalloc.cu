@@ -10,7 +10,6 @@
 // overlap on the GPU (other streams, other threads) race on it.
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 
 #include "order.cuh"
 
@@ -35,23 +34,16 @@ constexpr size_t kScratchBytes = align256(kOffCnt + sizeof(int));
 
 static __device__ __align__(256) unsigned char g_bisect_scratch[kScratchBytes];
 
-// Device address of g_bisect_scratch, looked up once per device (host code
-// must not use the symbol itself: on the host it is only a stand-in).
-std::mutex g_addr_mu;
-void* g_addr[256];
-
+// Device address of g_bisect_scratch on the current device (host code must
+// not use the symbol itself: on the host it is only a stand-in).  Looked up on
+// every call rather than cached: the lookup allocates nothing, and after a
+// device reset the library's device code is loaded again and the array may
+// then sit at another address.
 vmo_status scratch_address(unsigned char** out) {
-  int dev = 0;
-  VMO_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 256) return invalid("device ordinal out of range");
-  std::lock_guard<std::mutex> lk(g_addr_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_bisect_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_bisect_scratch)", __FILE__, __LINE__);
-    g_addr[dev] = p;
-  }
-  *out = static_cast<unsigned char*>(g_addr[dev]);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_bisect_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_bisect_scratch)", __FILE__, __LINE__);
+  *out = static_cast<unsigned char*>(p);
   return VMO_OK;
 }
 

@@ -460,6 +460,170 @@ __global__ void k_separator_mu(const int32_t* __restrict__ ord, const int32_t* _
   }
 }
 
+// ----- Algorithm 7's loop with a strengthened diagonal, in canonical order -----
+// The loop visits the edges cut by the 2-means labels in ascending key (s(c),
+// c, w), c the end with the smaller (s, id) (the one the loop moves), and an
+// edge still cut when reached moves c and mu(c) into V3.  A vertex u is moved
+// only by an edge whose moved end is u or mu(u), so the pair class
+// P = {u, mu(u)} is moved by at most one edge: the first edge of its candidate
+// list M(P) (edges moving a member of P, in key order) whose other end's class
+// is not moved before it.  T(P) = key of that edge (infinite if none).  Every
+// class walks its list in rounds: its current candidate e = (c, w) is skipped
+// when class(w) moved before e, taken when class(w) is known to move after e
+// (it is exhausted, took a later edge, or its current candidate is already
+// later than e: candidates only advance), else it waits.  The class with the
+// globally smallest current candidate always decides, so every round makes
+// progress, and the fixed point is the sequential loop's result.
+//
+// State of a class (one int32 word at its representative min(u, mu(u))):
+// (candidate index << 2) | flag, flag 0 undecided, 1 moved, 2 never moved.
+// Words only move forward (index up, flag 0 -> 1 or 2), so a stale read gives
+// a lower bound on the class's move key and every decision taken from it holds.
+constexpr int kMuUndecided = 0, kMuMoved = 1, kMuNever = 2;
+
+__device__ __forceinline__ bool mu_cut_neighbour(int32_t v, int32_t w, int s, uint8_t l,
+                                                 const int32_t* __restrict__ vnode, const uint8_t* __restrict__ vlab,
+                                                 const float* __restrict__ vs) {
+  if (vnode[w] != s) return false;
+  const uint8_t lw = vlab[w];
+  if (lw == l || lw == 0) return false;
+  const float sv = vs[v], sw = vs[w];
+  return sv < sw || (sv == sw && v < w);  // v is the end the loop moves
+}
+
+// Candidate edges moved through each vertex (edges whose moved end it is).
+__global__ void k_mu_count(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
+                           const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                           const int32_t* __restrict__ vnode, const uint8_t* __restrict__ vlab,
+                           const float* __restrict__ vs, int32_t* __restrict__ mcnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int s = seg[i];
+  const int32_t v = ord[i];
+  int32_t c = 0;
+  const uint8_t l = s >= 0 ? vlab[v] : 0;
+  if (l != 0)
+    for (int32_t t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) c += mu_cut_neighbour(v, adj[t], s, l, vnode, vlab, vs);
+  mcnt[v] = c;
+}
+
+__device__ __forceinline__ bool mu_first(int32_t a, int32_t b, const float* __restrict__ vs) {
+  const float sa = vs[a], sb = vs[b];
+  return sa < sb || (sa == sb && a < b);
+}
+
+// Length of every class's candidate list, at its representative.
+__global__ void k_mu_total(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
+                           const int32_t* __restrict__ mu, const int32_t* __restrict__ mcnt,
+                           int32_t* __restrict__ mtot) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t v = ord[i];
+  const int32_t u = mu[v];
+  mtot[v] = (seg[i] >= 0 && v <= u) ? mcnt[v] + (u != v ? mcnt[u] : 0) : 0;
+}
+
+// Candidate lists: the edges moving the member with the smaller (s, id)
+// first, each member's edges by ascending other end (adjacency order).
+__global__ void k_mu_fill(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
+                          const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                          const int32_t* __restrict__ vnode, const uint8_t* __restrict__ vlab,
+                          const float* __restrict__ vs, const int32_t* __restrict__ mu,
+                          const int32_t* __restrict__ mcnt, const int32_t* __restrict__ mbeg,
+                          int32_t* __restrict__ cand_c, int32_t* __restrict__ cand_w, int32_t* __restrict__ mstate) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int s = seg[i];
+  if (s < 0) return;
+  const int32_t v = ord[i];
+  const int32_t u = mu[v];
+  const int32_t rep = v < u ? v : u;
+  if (v == rep) {
+    const int32_t tot = mcnt[v] + (u != v ? mcnt[u] : 0);
+    mstate[rep] = tot > 0 ? kMuUndecided : kMuNever;
+  }
+  const uint8_t l = vlab[v];
+  if (l == 0 || mcnt[v] == 0) return;
+  const bool first = u == v || mu_first(v, u, vs);
+  int32_t o = mbeg[rep] + (first ? 0 : mcnt[u]);
+  for (int32_t t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) {
+    const int32_t w = adj[t];
+    if (!mu_cut_neighbour(v, w, s, l, vnode, vlab, vs)) continue;
+    cand_c[o] = v;
+    cand_w[o] = w;
+    ++o;
+  }
+}
+
+// (s, id) key of a candidate's moved end, as one ordered 64-bit number (s >= 0).
+__device__ __forceinline__ uint64_t mu_key(int32_t c, const float* __restrict__ vs) {
+  return ((uint64_t)__float_as_uint(vs[c]) << 32) | (uint32_t)c;
+}
+
+// One round over every undecided class; *busy counts classes still undecided.
+__global__ void k_mu_round(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
+                           const int32_t* __restrict__ mu, const int32_t* __restrict__ mbeg,
+                           const int32_t* __restrict__ mtot, const int32_t* __restrict__ cand_c,
+                           const int32_t* __restrict__ cand_w, const float* __restrict__ vs,
+                           int32_t* __restrict__ mstate, int* __restrict__ busy) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || seg[i] < 0) return;
+  const int32_t p = ord[i];
+  if (mu[p] < p) return;  // not the representative
+  volatile int32_t* vst = mstate;
+  int32_t w0 = vst[p];
+  if ((w0 & 3) != kMuUndecided) return;
+  int32_t ptr = w0 >> 2;
+  const int32_t tot = mtot[p], base = mbeg[p];
+  int32_t out = -1;
+  while (out < 0) {
+    if (ptr >= tot) { out = (ptr << 2) | kMuNever; break; }
+    const int32_t c = cand_c[base + ptr], w = cand_w[base + ptr];
+    const int32_t q = min(w, mu[w]);
+    if (q == p) { out = (ptr << 2) | kMuMoved; break; }  // edge between the partners
+    const uint64_t ke = mu_key(c, vs);
+    const int32_t sq = vst[q];
+    const int fq = sq & 3;
+    if (fq == kMuNever) { out = (ptr << 2) | kMuMoved; break; }
+    const uint64_t kq = mu_key(cand_c[mbeg[q] + (sq >> 2)], vs);
+    if (fq == kMuMoved) {
+      if (kq < ke) { ++ptr; continue; }  // class(w) moved first: the edge is no longer cut
+      out = (ptr << 2) | kMuMoved;
+      break;
+    }
+    if (kq > ke) { out = (ptr << 2) | kMuMoved; break; }  // class(w) cannot move before this edge
+    break;  // wait for class(w)
+  }
+  if (out >= 0) {
+    vst[p] = out;
+  } else {
+    if (ptr != (w0 >> 2)) vst[p] = ptr << 2;
+    if (busy) atomicAdd(busy, 1);
+  }
+}
+
+// Final labels: both members of a moved class are in V3.
+__global__ void k_separator_mu_loop(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
+                                    const int32_t* __restrict__ mu, const uint8_t* __restrict__ vlab,
+                                    const int32_t* __restrict__ mstate, NodeDev* __restrict__ nodes,
+                                    uint8_t* __restrict__ labf) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int s = i < n ? seg[i] : -1;
+  uint8_t l = 0;
+  if (s >= 0) {
+    int32_t v = ord[i];
+    l = vlab[v];
+    if (l != 0 && (mstate[min(v, mu[v])] & 3) == kMuMoved) l = 3;
+    labf[i] = l;
+  }
+  int key = (l != 0) ? s * 4 + l : -1;
+  unsigned peers = __match_any_sync(0xffffffffu, key);
+  if (key >= 0 && (int)lane_id() == __ffs(peers) - 1) {
+    int* c = l == 1 ? &nodes[s].c1 : (l == 2 ? &nodes[s].c2 : &nodes[s].c3);
+    atomicAdd(c, (int)__popc(peers));
+  }
+}
+
 __global__ void k_pack(const int32_t* __restrict__ seg, const uint8_t* __restrict__ labf, int64_t n,
                        const NodeDev* __restrict__ nodes, unsigned long long* __restrict__ pk) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -748,19 +912,14 @@ __global__ void k_cut_scatter(const uint64_t* __restrict__ keys, const uint32_t*
 }  // namespace
 
 // 2-means of every node of the table (Algorithm 5), leaving the final labels
-// in lab (position order) and the node fields z1, z2, n1, n2, state.
-vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s, Scratch& sc) {
+// in lab (position order) and the node fields z1, z2, n1, n2, state.  The
+// working arrays come from the caller: dval, dpre (n values), cnt (one int),
+// partial (scan_partials_needed(n) values) and, optionally, rep (per-node
+// replicas of the Lloyd sums, N * kRepR * 10 values, zeroed).
+static vmo_status two_means_body(OrderState& st, int N, int d, int km_iters, unsigned long long* dval,
+                                 unsigned long long* dpre, int* cnt, uint64_t* partial, unsigned long long* rep,
+                                 cudaStream_t s) {
   const int64_t n = st.n;
-  ScratchFrame frame(sc);
-  unsigned long long *dval, *dpre, *rep = nullptr;
-  int* cnt;
-  VMO_TRY(sc.alloc(&dval, std::max<int64_t>(n, 1)));
-  VMO_TRY(sc.alloc(&dpre, std::max<int64_t>(n, 1)));
-  VMO_TRY(sc.alloc(&cnt, 1));
-  if (N <= kRepNodes && n >= kRepMinPositions) {
-    VMO_TRY(sc.alloc(&rep, (size_t)N * kRepR * 10));
-    VMO_CUDA(cudaMemsetAsync(rep, 0, (size_t)N * kRepR * 10 * sizeof(unsigned long long), s));
-  }
   vmo_status stt = VMO_OK;
   dispatch_d(d, [&](auto DC) {
     constexpr int D = decltype(DC)::value;
@@ -768,7 +927,7 @@ vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s,
     launch(k_maxabs<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, st.nodes);
     launch(k_seed1, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, st.xo, st.seeds);
     launch(k_dsq<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, st.nodes, dval);
-    stt = scan_inclusive<uint64_t>((const uint64_t*)dval, (uint64_t*)dpre, n, s, sc);
+    stt = scan_inclusive_u64_into((const uint64_t*)dval, (uint64_t*)dpre, n, partial, s);
     if (stt != VMO_OK) return;
     launch(k_seed2<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, dval, dpre, st.nodes, st.seeds);
     for (int it = 0; it < km_iters; ++it) {
@@ -778,10 +937,12 @@ vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s,
       launch(k_update<D>, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, it);
       if (it % 4 == 3 && it + 1 < km_iters) {  // stop early once every node has converged
         int h = 0;
-        cudaMemsetAsync(cnt, 0, 4, s);
+        cudaError_t e = cudaMemsetAsync(cnt, 0, 4, s);
+        if (e != cudaSuccess) { stt = cuda_fail(e, "two_means: clear counter", __FILE__, __LINE__); return; }
         launch(k_count_active, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, cnt);
-        cudaMemcpyAsync(&h, cnt, 4, cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
+        e = cudaMemcpyAsync(&h, cnt, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { stt = cuda_fail(e, "two_means: convergence check", __FILE__, __LINE__); return; }
         if (h == 0) break;
       }
     }
@@ -795,39 +956,75 @@ vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s,
   return stt;
 }
 
+vmo_status two_means(OrderState& st, int N, int d, int km_iters, cudaStream_t s, Scratch& sc) {
+  const int64_t n = st.n;
+  ScratchFrame frame(sc);
+  unsigned long long *dval, *dpre, *rep = nullptr;
+  uint64_t* partial;
+  int* cnt;
+  VMO_TRY(sc.alloc(&dval, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&dpre, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&partial, std::max<int64_t>(scan_partials_needed(n), 1)));
+  VMO_TRY(sc.alloc(&cnt, 1));
+  if (N <= kRepNodes && n >= kRepMinPositions) {
+    VMO_TRY(sc.alloc(&rep, (size_t)N * kRepR * 10));
+    VMO_CUDA(cudaMemsetAsync(rep, 0, (size_t)N * kRepR * 10 * sizeof(unsigned long long), s));
+  }
+  return two_means_body(st, N, d, km_iters, dval, dpre, cnt, partial, rep, s);
+}
+
 vmo_status two_means_into(OrderState& st, int N, int d, int km_iters, unsigned long long* dval,
                           unsigned long long* dpre, int* cnt, uint64_t* partial, cudaStream_t s) {
-  const int64_t n = st.n;
-  vmo_status stt = VMO_OK;
-  dispatch_d(d, [&](auto DC) {
-    constexpr int D = decltype(DC)::value;
-    launch(k_node_reset, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N);
-    launch(k_maxabs<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, st.nodes);
-    launch(k_seed1, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, st.xo, st.seeds);
-    launch(k_dsq<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, st.nodes, dval);
-    stt = scan_inclusive_u64_into((const uint64_t*)dval, (uint64_t*)dpre, n, partial, s);
-    if (stt != VMO_OK) return;
-    launch(k_seed2<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, dval, dpre, st.nodes, st.seeds);
-    for (int it = 0; it < km_iters; ++it) {
-      launch(k_assign<D>, assign_grid(n), kBlock, 0, s, st.xo, st.seg, n, it, st.nodes, st.lab, 0,
-             (unsigned long long*)nullptr, assign_items(n));
-      launch(k_update<D>, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, it);
-      if (it % 4 == 3 && it + 1 < km_iters) {  // stop early once every node has converged
-        int h = 0;
-        cudaMemsetAsync(cnt, 0, 4, s);
-        launch(k_count_active, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, cnt);
-        cudaMemcpyAsync(&h, cnt, 4, cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
-        if (h == 0) break;
-      }
+  return two_means_body(st, N, d, km_iters, dval, dpre, cnt, partial, nullptr, s);
+}
+
+// Separator of every split node of the level by Algorithm 7's loop with the
+// strengthened diagonal, in canonical edge order (the class rounds above).
+static vmo_status mu_loop_separator(OrderState& st, int64_t n, uint8_t* labf, cudaStream_t s, Scratch& sc) {
+  if (n == 0) return VMO_OK;
+  ScratchFrame frame(sc);
+  int32_t *mcnt, *mtot, *mbeg, *mstate, *total;
+  int* busy;
+  VMO_TRY(sc.alloc(&mcnt, n));
+  VMO_TRY(sc.alloc(&mtot, n));
+  VMO_TRY(sc.alloc(&mbeg, n));
+  VMO_TRY(sc.alloc(&mstate, n));
+  VMO_TRY(sc.alloc(&total, 1));
+  VMO_TRY(sc.alloc(&busy, 1));
+  launch(k_mu_count, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vnode, st.vlab,
+         st.vs, mcnt);
+  launch(k_mu_total, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.mu, mcnt, mtot);
+  VMO_TRY(scan_exclusive<int32_t>(mtot, mbeg, n, total, s, sc));
+  int32_t ncand = 0;
+  VMO_CUDA(cudaMemcpyAsync(&ncand, total, 4, cudaMemcpyDeviceToHost, s));
+  VMO_CUDA(cudaStreamSynchronize(s));
+  int32_t *cand_c, *cand_w;
+  VMO_TRY(sc.alloc(&cand_c, std::max<int32_t>(ncand, 1)));
+  VMO_TRY(sc.alloc(&cand_w, std::max<int32_t>(ncand, 1)));
+  launch(k_mu_fill, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vnode, st.vlab,
+         st.vs, st.mu, mcnt, mbeg, cand_c, cand_w, mstate);
+  // every round decides at least one class (the one with the smallest
+  // current candidate), so ncand + 1 rounds always suffice
+  constexpr int kRoundsPerCheck = 4;
+  int64_t rounds = 0;
+  for (;;) {
+    for (int r = 0; r < kRoundsPerCheck; ++r) {
+      if (r == kRoundsPerCheck - 1) VMO_CUDA(cudaMemsetAsync(busy, 0, sizeof(int), s));
+      launch(k_mu_round, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.mu, mbeg, mtot, cand_c, cand_w,
+             st.vs, mstate, r == kRoundsPerCheck - 1 ? busy : (int*)nullptr);
     }
-    launch(k_clear_counts, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N);
-    launch(k_assign<D>, assign_grid(n), kBlock, 0, s, st.xo, st.seg, n, 0, st.nodes, st.lab, 1,
-           (unsigned long long*)nullptr, assign_items(n));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) stt = cuda_fail(e, "two_means", __FILE__, __LINE__);
-  });
-  return stt;
+    rounds += kRoundsPerCheck;
+    int h = 0;
+    VMO_CUDA(cudaMemcpyAsync(&h, busy, sizeof(int), cudaMemcpyDeviceToHost, s));
+    VMO_CUDA(cudaStreamSynchronize(s));
+    if (h == 0) break;
+    if (rounds > (int64_t)ncand + 2 * kRoundsPerCheck)
+      return cuda_fail(cudaErrorUnknown, "separator: the matched-pair rounds did not settle", __FILE__, __LINE__);
+  }
+  launch(k_separator_mu_loop, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.mu, st.vlab, mstate, st.nodes,
+         labf);
+  VMO_LAUNCHED("separator_mu_loop");
+  return VMO_OK;
 }
 
 vmo_status order_levels(OrderState& st, const OrderParams& op, cudaStream_t s, Scratch& sc) {
@@ -855,11 +1052,13 @@ vmo_status order_levels(OrderState& st, const OrderParams& op, cudaStream_t s, S
       launch(k_vertex_state<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.ord, st.seg, n, st.nodes, st.lab, st.vlab,
                                                                st.vs);
     });
-    if (st.mu) {
+    if (st.mu && op.mu_order_free) {
       launch(k_pick, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vnode, st.vlab,
              st.vs, st.vpick);
       launch(k_separator_mu, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.mu, st.vlab, st.vpick, st.nodes,
              labf);
+    } else if (st.mu) {
+      VMO_TRY(mu_loop_separator(st, n, labf, s, sc));
     } else {
       launch(k_separator, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vnode, st.vlab,
              st.vs, st.nodes, labf);

@@ -44,6 +44,7 @@ struct OrderParams {
   int sbd = 0;
   int sep_rec = 0;  // order V3 recursively too (ternary keys, depth <= kSepRecMaxDepth)
   int cut_order = 0;  // b: sort every separator by b two-bit link numbers (without sep_rec)
+  int mu_order_free = 0;  // with a strengthened diagonal: 0 Algorithm 7's loop in canonical order, 1 order-free
 };
 
 // Deepest node with separator recursion: ternary keys (3^(d+1) - 1) / 2 fit 64 bits up to d = 39.

@@ -33,6 +33,7 @@ struct Req {
   const int32_t* rowptr = nullptr;
   const int32_t* colidx = nullptr;
   int32_t* out = nullptr;
+  bool cancel_requested = false;  // cancelled while running: becomes terminal when its batch ends
   vmo_request_info info{};
 };
 
@@ -138,8 +139,9 @@ void ServerImpl::worker(int slot) {
 void ServerImpl::run_batch(int slot, const std::vector<uint64_t>& ids, cudaStream_t s, int32_t*& stage,
                            size_t& stage_cap) {
   (void)slot;
-  // the request records are not moved while running (only this worker
-  // touches them besides cancel, which only flips the state)
+  // the records stay where they are while running (an unordered_map keeps
+  // its elements in place; release refuses records that are not terminal,
+  // and cancel only sets a flag)
   std::vector<Req*> rs;
   {
     std::lock_guard<std::mutex> lk(mu);
@@ -161,6 +163,8 @@ void ServerImpl::run_batch(int slot, const std::vector<uint64_t>& ids, cudaStrea
     (void)cudaGetLastError();
     st = VMO_ERR_OOM;
     dbuf = nullptr;
+  } else {
+    g_device_allocs.fetch_add(1, std::memory_order_relaxed);
   }
   if (st == VMO_OK && (size_t)nperm > stage_cap) {
     if (stage) cudaFreeHost(stage);
@@ -210,8 +214,10 @@ void ServerImpl::run_batch(int slot, const std::vector<uint64_t>& ids, cudaStrea
     const double t = now();
     int64_t off = 0;
     for (Req* r : rs) {
-      if (r->info.state == VMO_REQ_CANCELLED) {
-        // cancelled while running: nothing is written
+      if (r->cancel_requested) {
+        // cancelled while running: its inputs are no longer read, nothing is written
+        r->info.state = VMO_REQ_CANCELLED;
+        ++cancelled;
       } else if (st == VMO_OK) {
         if (r->n > 0) memcpy(r->out, stage + off, (size_t)r->n * 4);
         r->info.state = VMO_REQ_DONE;
@@ -361,15 +367,21 @@ vmo_status vmo_server_wait(vmo_server srv, uint64_t id, double timeout_s, vmo_re
   if (!srv) return invalid("server: null argument");
   ServerImpl& S = srv->impl;
   std::unique_lock<std::mutex> lk(S.mu);
-  auto it = S.reqs.find(id);
-  if (it == S.reqs.end()) return invalid("server: unknown request id");
-  auto terminal = [&] { return it->second.info.state >= VMO_REQ_DONE; };
+  if (S.reqs.find(id) == S.reqs.end()) return invalid("server: unknown request id");
+  // the record is looked up again after every wake-up: the mutex is released
+  // while waiting, and another thread may insert (rehash) or release it
+  auto terminal = [&] {
+    auto it = S.reqs.find(id);
+    return it == S.reqs.end() || it->second.info.state >= VMO_REQ_DONE;
+  };
   bool ok = true;
   if (timeout_s < 0) {
     S.cv_done.wait(lk, terminal);
   } else {
     ok = S.cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), terminal);
   }
+  auto it = S.reqs.find(id);
+  if (it == S.reqs.end()) return invalid("server: request released while waiting");
   if (info) *info = it->second.info;
   if (!ok) {
     set_error("server: wait timed out");
@@ -392,12 +404,27 @@ vmo_status vmo_server_cancel(vmo_server srv, uint64_t id) {
       r.info.t_done = S.now();
       ++S.cancelled;
     } else if (r.info.state == VMO_REQ_RUNNING) {
-      r.info.state = VMO_REQ_CANCELLED;  // the batch finishes; nothing is written
-      ++S.cancelled;
+      // the batch may still read the request's host arrays: it stays running
+      // and turns cancelled (nothing written) when the batch ends
+      r.cancel_requested = true;
     }
   }
   S.cv_done.notify_all();
   S.cv_work.notify_all();
+  return VMO_OK;
+}
+
+vmo_status vmo_server_release(vmo_server srv, uint64_t id) {
+  if (!srv) return invalid("server: null argument");
+  ServerImpl& S = srv->impl;
+  {
+    std::lock_guard<std::mutex> lk(S.mu);
+    auto it = S.reqs.find(id);
+    if (it == S.reqs.end()) return invalid("server: unknown request id");
+    if (it->second.info.state < VMO_REQ_DONE) return invalid("server: request is not terminal");
+    S.reqs.erase(it);
+  }
+  S.cv_done.notify_all();
   return VMO_OK;
 }
 

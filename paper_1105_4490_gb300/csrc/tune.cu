@@ -90,6 +90,7 @@ extern "C" vmo_status vmo_autotune(const vmo_csr* mats, int32_t count, const vmo
   cudaStream_t s = (cudaStream_t)stream;
   int32_t* perm = nullptr;
   VMO_CUDA(cudaMalloc(&perm, (size_t)std::max<int64_t>(rows, 1) * sizeof(int32_t)));
+  g_device_allocs.fetch_add(1, std::memory_order_relaxed);
   const vmo_tuning start = current();
   vmo_tuning bt = start;
   double bms = 0.0, dms = 0.0;

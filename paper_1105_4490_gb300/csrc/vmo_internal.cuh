@@ -78,6 +78,7 @@ struct ScratchFrame {
 // its memory from the stream-ordered pool on the scope's stream and returns it
 // on that stream, so threads working on different streams (the request
 // server's slots) never wait for each other in an allocation or a free.
+extern std::atomic<uint64_t> g_device_allocs;
 extern thread_local cudaStream_t g_devarray_stream;
 extern thread_local bool g_devarray_async;
 
@@ -126,6 +127,7 @@ vmo_status DevArray<T>::resize(size_t n) {
   count = n;
   async = as;
   astream = g_devarray_stream;
+  g_device_allocs.fetch_add(1, std::memory_order_relaxed);
   return VMO_OK;
 }
 
@@ -353,15 +355,6 @@ __device__ inline float sqdist32(const float4& a, const float4& b) {
 
 __device__ inline float comp(const float4& v, int m) {
   return m == 0 ? v.x : (m == 1 ? v.y : (m == 2 ? v.z : v.w));
-}
-
-// Morton interleave of cell coordinates (bit b of coordinate m -> bit b*d+m).
-template <int D>
-__host__ __device__ inline uint32_t morton(const int32_t* c, int bits) {
-  uint32_t key = 0;
-  for (int b = 0; b < bits; ++b)
-    for (int m = 0; m < D; ++m) key |= (uint32_t)((c[m] >> b) & 1) << (b * D + m);
-  return key;
 }
 
 __device__ inline unsigned lane_id() { return threadIdx.x & 31u; }

@@ -95,11 +95,16 @@ class Server:
             _, _, out, n = self._keep[rid]
         return out[:n].copy()
 
-    def release(self, rid: int) -> None:
-        """Drops the binding's references to a terminal request's arrays."""
-        if self.poll(rid)["state"] in ("done", "failed", "cancelled"):
-            with self._mu:
-                self._keep.pop(rid, None)
+    def release(self, rid: int) -> bool:
+        """Frees a terminal request: the server's record (vmo_server_release)
+        and the binding's references to its arrays.  Returns False (nothing
+        freed) while the request is queued or running."""
+        if self.poll(rid)["state"] not in ("done", "failed", "cancelled"):
+            return False
+        _check(load().vmo_server_release(self._h, rid))
+        with self._mu:
+            self._keep.pop(rid, None)
+        return True
 
     def cancel(self, rid: int) -> None:
         _check(load().vmo_server_cancel(self._h, rid))

@@ -47,6 +47,7 @@ class _Params(C.Structure):
                 ("occupancy", C.c_int32), ("multilevel", C.c_int32), ("match_rounds", C.c_int32),
                 ("coarse_min", C.c_int32), ("km_iters", C.c_int32), ("min_part", C.c_int32),
                 ("max_depth", C.c_int32), ("sep_recursion", C.c_int32), ("cut_order", C.c_int32),
+                ("sep_order_free", C.c_int32),
                 ("seed", C.c_uint64)]
 
 
@@ -58,7 +59,7 @@ class _Tree(C.Structure):
 
 class _Stats(C.Structure):
     _fields_ = [("launches", C.c_uint64), ("step_launches", C.c_uint64), ("step_ms", C.c_double),
-                ("step_points", C.c_uint64), ("step_interactions", C.c_uint64)]
+                ("step_points", C.c_uint64), ("step_interactions", C.c_uint64), ("device_allocations", C.c_uint64)]
 
 
 @dataclass
@@ -78,6 +79,7 @@ class Params:
     max_depth: int = 62
     sep_recursion: int = 0
     cut_order: int = 0
+    sep_order_free: int = 0
     seed: int = 1
 
     def _c(self) -> _Params:
@@ -88,7 +90,8 @@ class Params:
 
 
 SYMBOLS = ["vmo_default_params", "vmo_build_hypergraph", "vmo_hg_vertices", "vmo_hg_nets", "vmo_hg_arrays",
-           "vmo_components", "vmo_init_coords", "vmo_layout", "vmo_layout_step", "vmo_coarsen", "vmo_bisect",
+           "vmo_components", "vmo_init_coords", "vmo_layout", "vmo_layout_step", "vmo_coarsen",
+           "vmo_hierarchy_level", "vmo_hierarchy_prolong", "vmo_hierarchy_step", "vmo_bisect",
            "vmo_order_bbd", "vmo_order_sbd", "vmo_order_vertices", "vmo_order_matched", "vmo_perfect_matching_host", "vmo_read_matrix_market",
            "vmo_write_matrix_market", "vmo_free_host_csr", "vmo_finegrain_coords", "vmo_get_tuning",
            "vmo_set_tuning",
@@ -96,7 +99,7 @@ SYMBOLS = ["vmo_default_params", "vmo_build_hypergraph", "vmo_hg_vertices", "vmo
            "vmo_status_string", "vmo_last_error", "vmo_stats_reset", "vmo_stats_get", "vmo_batch_order",
            "vmo_batch_layout", "vmo_bisect_noalloc", "vmo_server_default_config", "vmo_server_estimate_bytes",
            "vmo_server_plan", "vmo_server_create", "vmo_server_submit", "vmo_server_poll", "vmo_server_wait",
-           "vmo_server_cancel", "vmo_server_get_stats", "vmo_server_destroy", "vmo_kmeans"]
+           "vmo_server_cancel", "vmo_server_release", "vmo_server_get_stats", "vmo_server_destroy", "vmo_kmeans"]
 
 
 class _ServerConfig(C.Structure):
@@ -141,6 +144,9 @@ def load(path: str | None = None):
     lib.vmo_layout.argtypes = [V, C.POINTER(_Params), V, I32, V]
     lib.vmo_layout_step.argtypes = [V, C.POINTER(_Params), V, C.c_float, V, V, P32, V]
     lib.vmo_coarsen.argtypes = [V, C.POINTER(_Params), V, V, P32, P32, P32, V]
+    lib.vmo_hierarchy_level.argtypes = [V, C.POINTER(_Params), I32, P32, P64, V, V, V, V, V, V]
+    lib.vmo_hierarchy_prolong.argtypes = [V, C.POINTER(_Params), I32, V, V, V]
+    lib.vmo_hierarchy_step.argtypes = [V, C.POINTER(_Params), I32, V, C.c_float, V, V]
     lib.vmo_bisect.argtypes = [V, I32, V, V, I32, U64, U64, I32, V, V, P32, V]
     lib.vmo_bisect_noalloc.argtypes = [I32, V, V, I32, U64, U64, I32, V, V, P32, V]
     lib.vmo_kmeans.argtypes = [I32, V, V, I32, I32, U64, U64, I32, V, V, P32, V]
@@ -182,6 +188,7 @@ def load(path: str | None = None):
     lib.vmo_server_poll.argtypes = [V, U64, C.POINTER(_RequestInfo)]
     lib.vmo_server_wait.argtypes = [V, U64, C.c_double, C.POINTER(_RequestInfo)]
     lib.vmo_server_cancel.argtypes = [V, U64]
+    lib.vmo_server_release.argtypes = [V, U64]
     lib.vmo_server_get_stats.argtypes = [V, C.POINTER(_ServerStats)]
     lib.vmo_server_destroy.argtypes = [V]
     lib.vmo_server_destroy.restype = None
@@ -313,6 +320,50 @@ class Hypergraph:
         _check(load().vmo_coarsen(self._h, C.byref(p), _ptr(mate), _ptr(pi), C.byref(kc), sizes, C.byref(nl),
                                   _stream()))
         return mate, pi, int(kc.value), [int(sizes[i]) for i in range(nl.value)]
+
+    def hierarchy_level(self, level: int, params: Params | None = None) -> dict:
+        """Level `level` of the coarsening hierarchy of Algorithm 3: dict with
+        k, adj_ptr, adj, acost (edge costs), weight (vertex weights) and pi
+        (level-1 vertex -> level vertex; None for level 0), device tensors."""
+        p = (params or Params())._c()
+        lib = load()
+        k, nadj = C.c_int32(), C.c_int64()
+        _check(lib.vmo_hierarchy_level(self._h, C.byref(p), level, C.byref(k), C.byref(nadj), None, None, None, None,
+                                       None, _stream()))
+        k, nadj = int(k.value), int(nadj.value)
+        kf = None
+        if level > 0:
+            kf_c = C.c_int32()
+            _check(lib.vmo_hierarchy_level(self._h, C.byref(p), level - 1, C.byref(kf_c), None, None, None, None, None,
+                                           None, _stream()))
+            kf = int(kf_c.value)
+        out = {"k": k, "adj_ptr": torch.empty(k + 1, dtype=torch.int32, device="cuda"),
+               "adj": torch.empty(max(nadj, 1), dtype=torch.int32, device="cuda"),
+               "acost": torch.empty(max(nadj, 1), dtype=torch.float32, device="cuda"),
+               "weight": torch.empty(max(k, 1), dtype=torch.float32, device="cuda"),
+               "pi": torch.empty(max(kf, 1), dtype=torch.int32, device="cuda") if kf is not None else None}
+        _check(lib.vmo_hierarchy_level(self._h, C.byref(p), level, None, None, _ptr(out["adj_ptr"]), _ptr(out["adj"]),
+                                       _ptr(out["acost"]), _ptr(out["weight"]), _ptr(out["pi"]), _stream()))
+        out["adj"], out["acost"], out["weight"] = out["adj"][:nadj], out["acost"][:nadj], out["weight"][:k]
+        if kf is not None:
+            out["pi"] = out["pi"][:kf]
+        return out
+
+    def hierarchy_prolong(self, level: int, coarse: torch.Tensor, kf: int, params: Params | None = None):
+        """Prolongation of Algorithm 3 from `level` to level - 1 (kf points)."""
+        p = (params or Params())._c()
+        fine = torch.empty((max(kf, 1), 4), dtype=torch.float32, device="cuda")
+        _check(load().vmo_hierarchy_prolong(self._h, C.byref(p), level, _ptr(coarse.contiguous()), _ptr(fine),
+                                            _stream()))
+        return fine[:kf]
+
+    def hierarchy_step(self, level: int, coords: torch.Tensor, step: float, params: Params | None = None):
+        """One step of Algorithm 4 on a level of the hierarchy: (new coords, y)."""
+        p = (params or Params())._c()
+        x = coords.clone().contiguous()
+        y = torch.zeros_like(x)
+        _check(load().vmo_hierarchy_step(self._h, C.byref(p), level, _ptr(x), step, _ptr(y), _stream()))
+        return x, y
 
     def bisect(self, coords: torch.Tensor, verts: torch.Tensor, seed: int, key: int = 1, km_iters: int = 20,
                d: int = 3):

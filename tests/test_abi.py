@@ -47,9 +47,9 @@ def test_status_strings_and_defaults(lib):
 def test_params_struct_layout():
     """The ctypes mirror matches the C struct (field order and size)."""
     from paper_1105_4490_gb300 import vmo
-    assert ctypes.sizeof(vmo._Params) == 4 * 13 + 4 + 8  # 13 x 4-byte fields, padding, uint64 seed
+    assert ctypes.sizeof(vmo._Params) == 4 * 14 + 8  # 14 x 4-byte fields, uint64 seed
     assert ctypes.sizeof(vmo._Tree) == 8 + 7 * 8
-    assert ctypes.sizeof(vmo._Stats) == 5 * 8
+    assert ctypes.sizeof(vmo._Stats) == 6 * 8
 
 
 def test_struct_layouts_match_c(tmp_path):

@@ -472,15 +472,16 @@ def test_full_pipeline_replay_d(V, O, d, sbd):
     assert np.array_equal(_np(tree["nsep"]), tree_o["nsep"])
 
 
-def _matched_compare(V, O, A, d, coords, sbd, min_part=16, max_depth=62, seed=5, sep_rec=False, cut_order=False):
+def _matched_compare(V, O, A, d, coords, sbd, min_part=16, max_depth=62, seed=5, sep_rec=False, cut_order=False,
+                     order_free=False):
     match = A.meta["match"]
     hg = V.Hypergraph.from_matrix(A, "bipartite")
     ref = O.build_from_matrix("bipartite", A)
     p = V.Params(d=d, min_part=min_part, max_depth=max_depth, seed=seed, sep_recursion=int(sep_rec),
-                 cut_order=int(cut_order))
+                 cut_order=int(cut_order), sep_order_free=int(order_free))
     rp, cp, vp, tree = hg.order_matched(torch.as_tensor(match), p, torch.as_tensor(coords).cuda(), sbd=sbd)
     perm_o, tree_o = O.order(ref, d, coords, seed=seed, min_part=min_part, max_depth=max_depth, sbd=sbd,
-                             sep_rec=sep_rec, cut_order=cut_order, match=match)
+                             sep_rec=sep_rec, cut_order=cut_order, match=match, order_free=order_free)
     assert np.array_equal(_np(vp), perm_o)
     assert np.array_equal(_np(tree["heap"]).astype(np.uint64), tree_o["heap"])
     for f in ("offset", "n1", "n2", "nsep", "depth", "comp"):
@@ -488,21 +489,42 @@ def _matched_compare(V, O, A, d, coords, sbd, min_part=16, max_depth=62, seed=5,
     rows = perm_o[perm_o < A.m]
     assert np.array_equal(_np(rp), rows)
     assert np.array_equal(_np(cp), match[rows])
+    return tree_o
 
 
+@pytest.mark.parametrize("order_free", [False, True])
 @pytest.mark.parametrize("sbd", [False, True])
-def test_order_matched(V, O, sbd):
+def test_order_matched(V, O, sbd, order_free):
     """Strengthened diagonal (Sec. 4.2, Algorithm 7 with mu) bit-exact against
-    the oracle: an unsymmetric mesh pattern and an unsymmetric power-law
-    pattern, random coordinates in d = 2 and 3, down to single pairs, with
-    separator recursion and with the cut-row ordering."""
+    the oracle, in both readings (the loop in canonical order, the default,
+    and the order-free one): an unsymmetric mesh pattern and an unsymmetric
+    power-law pattern, random coordinates in d = 2 and 3, down to single
+    pairs, with separator recursion and with the cut-row ordering."""
     G = W.with_strengthened_diagonal(W.grid_laplacian_2d(60), 0.7, 3)
-    _matched_compare(V, O, G, 2, O.init_coords(2 * G.m, 2, 3), sbd)
+    of = dict(order_free=order_free)
+    _matched_compare(V, O, G, 2, O.init_coords(2 * G.m, 2, 3), sbd, **of)
     P = W.with_strengthened_diagonal(W.powerlaw_symmetric(6000, seed=13), 0.6, 13)
-    _matched_compare(V, O, P, 3, O.init_coords(2 * P.m, 3, 13), sbd, min_part=2)
-    _matched_compare(V, O, P, 2, O.init_coords(2 * P.m, 2, 14), sbd, min_part=0, max_depth=8)
-    _matched_compare(V, O, P, 3, O.init_coords(2 * P.m, 3, 15), sbd, min_part=4, sep_rec=True)
-    _matched_compare(V, O, P, 3, O.init_coords(2 * P.m, 3, 16), sbd, min_part=4, cut_order=True)
+    _matched_compare(V, O, P, 3, O.init_coords(2 * P.m, 3, 13), sbd, min_part=2, **of)
+    _matched_compare(V, O, P, 2, O.init_coords(2 * P.m, 2, 14), sbd, min_part=0, max_depth=8, **of)
+    _matched_compare(V, O, P, 3, O.init_coords(2 * P.m, 3, 15), sbd, min_part=4, sep_rec=True, **of)
+    _matched_compare(V, O, P, 3, O.init_coords(2 * P.m, 3, 16), sbd, min_part=4, cut_order=True, **of)
+
+
+@pytest.mark.parametrize("name,make,d", [
+    ("mesh120", lambda: W.with_strengthened_diagonal(W.grid_laplacian_2d(120), 0.7, 21), 2),
+    ("powerlaw40k", lambda: W.with_strengthened_diagonal(W.powerlaw_symmetric(40000, seed=22), 0.6, 22), 3)])
+def test_order_matched_literal_loop_layout(V, O, name, make, d):
+    """The loop of Algorithm 7 with the matching, on the GPU's own multilevel
+    layout of planted-matching patterns (many cut edges share pairs): the GPU
+    equals the oracle's sequential loop bit for bit, and its separators are no
+    larger than the order-free reading's at every level (smaller in total)."""
+    A = make()
+    hg = V.Hypergraph.from_matrix(A, "bipartite")
+    x = _np(hg.layout(V.Params(d=d, seed=4)))
+    lit = _matched_compare(V, O, A, d, x, False, min_part=16, seed=4)
+    free = _matched_compare(V, O, A, d, x, False, min_part=16, seed=4, order_free=True)
+    assert int(lit["nsep"][0]) <= int(free["nsep"][0])
+    assert int(lit["nsep"].sum()) < int(free["nsep"].sum()), (int(lit["nsep"].sum()), int(free["nsep"].sum()))
 
 
 def test_order_matched_full_pipeline(V, O):

@@ -98,3 +98,33 @@ def test_cancel_and_reject(V):
         with pytest.raises(V.VmoError):
             srv.submit(np.array([0, 1, 2], np.int32), np.array([0, 5], np.int32))
         assert srv.stats()["cancelled"] == 1
+
+
+def test_cancel_running_stays_running_until_batch_ends(V):
+    """A request cancelled while its batch runs is not terminal until the batch
+    ends (the batch may still read its host arrays); it then turns cancelled
+    with nothing written, and release frees its record only then."""
+    big = W.grid_laplacian_3d(48)  # long enough to be caught running
+    with V.Server(V.Params(**PARAMS), slots=1, max_batch=1) as srv:
+        rid = srv.submit_matrix(big)
+        t0 = time.time()
+        while srv.poll(rid)["state"] == "queued" and time.time() - t0 < 60:
+            time.sleep(0.001)
+        assert srv.poll(rid)["state"] == "running"
+        srv.cancel(rid)
+        st = srv.poll(rid)["state"]
+        assert st in ("running", "cancelled")
+        if st == "running":
+            assert srv.release(rid) is False  # not terminal yet: nothing freed
+        info = srv.wait(rid, 300.0)
+        assert info["state"] == "cancelled"
+        assert srv.stats()["cancelled"] == 1 and srv.stats()["completed"] == 0
+        assert srv.release(rid) is True
+        with pytest.raises(V.VmoError):
+            srv.poll(rid)  # the record is gone
+        # the server keeps serving after a cancelled batch
+        A = _mix(1, 45)[0]
+        r2 = srv.submit_matrix(A)
+        assert srv.wait(r2, 300.0)["state"] == "done"
+        assert np.array_equal(srv.result(r2), _plain(V, A))
+        assert srv.release(r2) is True

@@ -86,3 +86,37 @@ def test_noalloc_rejects_oversize(V):
     verts = torch.arange(MAX_POINTS + 1, dtype=torch.int32, device="cuda")
     with pytest.raises(V.VmoError, match="131072"):
         V.vmo.bisect_noalloc(x, verts, seed=1, d=3)
+
+
+def test_noalloc_makes_no_device_allocation(V):
+    """The defining property: around a warmed-up call through the C-ABI, with
+    every output allocated beforehand by the caller, the library's own
+    allocation counter and torch's allocator are unchanged (vmo_bisect, for
+    contrast, does allocate, so the counter is live)."""
+    import ctypes as C
+    lib = V.load()
+    A = W.powerlaw_symmetric(20000, seed=4)
+    hg = V.Hypergraph.from_matrix(A)
+    x = V.init_coords(hg.k, 3, seed=2)
+    verts = torch.arange(hg.k, dtype=torch.int32, device="cuda")
+    labels = torch.zeros(hg.k, dtype=torch.uint8, device="cuda")
+    z = torch.zeros(8, dtype=torch.float32, device="cuda")
+    split = C.c_int32()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call():
+        st = lib.vmo_bisect_noalloc(3, C.c_void_p(x.data_ptr()), C.c_void_p(verts.data_ptr()), hg.k, 11, 1, 20,
+                                    C.c_void_p(labels.data_ptr()), C.c_void_p(z.data_ptr()), C.byref(split), stream)
+        assert st == 0
+
+    call()  # warm-up: loads the library's device code on this device
+    torch.cuda.synchronize()
+    before_lib = V.stats()["device_allocations"]
+    before_torch = torch.cuda.memory_allocated()
+    for _ in range(2):
+        call()
+    torch.cuda.synchronize()
+    assert V.stats()["device_allocations"] == before_lib
+    assert torch.cuda.memory_allocated() == before_torch
+    hg.bisect(x, verts, seed=11, key=1, km_iters=20, d=3)
+    assert V.stats()["device_allocations"] > before_lib

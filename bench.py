@@ -30,6 +30,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -47,8 +48,6 @@ METRIC = "nnz ordered/sec (recursive BBD)"
 # algorithmic FP32 operations per source interaction of the layout step kernel
 # (differences, squared norm, reciprocal power, force accumulation), per d
 FLOPS_PER_INTERACTION = {2: 10, 3: 18, 4: 23}
-FP32_LANES_PER_SM = 128
-SMS = 152
 # DRAM bytes (read + write) per launch of the step kernel, averaged over the
 # 3,000 launches of one step of the medium workload: one ncu capture of the
 # current kernel (dram__bytes_read.sum + dram__bytes_write.sum)
@@ -72,6 +71,30 @@ def cpu_sample(small: bool):
                                                (W.powerlaw_symmetric(1000, seed=1), dict(d=3, max_depth=10))]
     return "grid3d_16^3+powerlaw_2000", [(W.grid_laplacian_3d(16), dict(d=3, max_depth=10)),
                                           (W.powerlaw_symmetric(2000, seed=1), dict(d=3, max_depth=10))]
+
+
+def host_cpu() -> dict:
+    """Model name and core count of the host CPU (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                v = line.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    model = v
+                    break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"cpu_model": model or "unknown", "cpu_cores": os.cpu_count() or 1, "arch": platform.machine()}
 
 
 def oracle_step(mats, seed=1):
@@ -111,7 +134,7 @@ def batch_cpu_all_cores(mats=None, count: int = 0, max_nnz: int = 15_000) -> dic
     return {"value": nnz / dt, "unit": "nnz/s", "cores": cores, "kind": "oracle",
             "sample": f"{len(pick)} matrices of the batch mix with <= {max_nnz} nnz (seeded), {nnz} nnz, oracle "
                       f"FP64 full pipeline (multilevel layout d=3, recursive BBD, min_part 64), one matrix per "
-                      f"worker process, {dt:.1f} s"}
+                      f"worker process, {dt:.1f} s", **host_cpu()}
 
 
 def run_cpu_baseline(mats, sample_name):
@@ -232,6 +255,125 @@ def batched_leg(V, torch, count: int, plain_sample: int, warmup: int, steps: int
             "batched_over_plain": batched / plain}
 
 
+def step_roofline(V, torch, run_once, d: int, steps: int, peak: dict, elapsed_ref: float | None = None) -> dict:
+    """Roofline of the layout step kernel over one workload: algorithmic flops
+    per launch (interactions counted by the kernel in one untimed run, times
+    FLOPS_PER_INTERACTION[d]) over the average launch time, measured with CUDA
+    events around every step-kernel launch on its stream in `steps` further
+    runs; against the measured FP32 peak of this GPU."""
+    V.stats_reset(time_step_kernel=True, count_interactions=True)
+    run_once()
+    counted = V.stats()
+    V.stats_reset(time_step_kernel=True, count_interactions=False)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        run_once()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    st = V.stats()
+    V.stats_reset(time_step_kernel=False, count_interactions=False)
+    launches = max(counted["step_launches"], 1)
+    flops_per_launch = counted["step_interactions"] * FLOPS_PER_INTERACTION[d] / launches
+    avg_ms = st["step_ms"] / max(st["step_launches"], 1)
+    achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": f"k_repulse_update<{d}> (layout step)", "achieved": achieved,
+            "peak": peak["ffma2_tflops"], "unit": "TFLOP/s", "frac": achieved / peak["ffma2_tflops"],
+            "peak_source": f"measured in this run (vmo_measure_alu_peaks): packed FP32 fma2 on all "
+                           f"{peak['sms']} SMs, {peak['ffma2_tflops']:.1f} TFLOP/s (scalar fma "
+                           f"{peak['ffma_tflops']:.1f}, rsqrt {peak['rsqrt_tops']:.2f} T/s)",
+            "interactions_per_launch": counted["step_interactions"] / launches,
+            "flops_per_interaction": FLOPS_PER_INTERACTION[d], "avg_launch_ms": avg_ms,
+            "launches": st["step_launches"],
+            "share_of_step": st["step_ms"] / 1e3 / (elapsed_ref if elapsed_ref else wall),
+            "timing": "CUDA events around every step-kernel launch on its stream"}
+
+
+def owner_parts(k: int, perm: np.ndarray, tree: dict, sbd: bool) -> np.ndarray:
+    """Final owner of every vertex: the index of its leaf record, or of the
+    split node whose separator holds it (the parts of the cut metrics)."""
+    part = np.full(k, -1, dtype=np.int32)
+    off, n1, n2, ns = (tree[f].cpu().numpy() for f in ("offset", "n1", "n2", "nsep"))
+    for i in range(len(off)):
+        o, a, b, c = int(off[i]), int(n1[i]), int(n2[i]), int(ns[i])
+        if b == 0 and c == 0:
+            part[perm[o:o + a]] = i
+        else:
+            so = o + a if sbd else o + a + b
+            part[perm[so:so + c]] = i
+    return part
+
+
+def config_leg(V, torch, name: str, A, model: str, d: int, sbd: bool, max_depth: int, min_part: int, steps: int,
+               warmup: int, flush, peak: dict, cuts: bool = False) -> dict:
+    """One configuration ordered plain (one matrix, device-resident CSR): build
+    of the model + multilevel layout + recursive BBD/SBD per step, in nnz
+    ordered per second, with its own step-kernel roofline; optionally the cut
+    metrics of the final parts (cut-net and lambda - 1 over the row nets and
+    the column nets)."""
+    rp, ci = torch.as_tensor(A.rowptr).cuda(), torch.as_tensor(A.colidx).cuda()
+    p = V.Params(d=d, max_depth=max_depth, min_part=min_part, seed=1)
+    stream = torch.cuda.current_stream()
+
+    def once(with_tree=False):
+        hg = V.Hypergraph(rp, ci, A.m, A.n, model)
+        out = hg.order_vertices(p, None, sbd=sbd) if with_tree else hg.order(p, None, sbd=sbd, with_tree=False)
+        del hg
+        return out
+
+    for _ in range(max(warmup, 3)):
+        once()
+    t = 0.0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        once()
+        b.record(stream)
+        torch.cuda.synchronize()
+        t += a.elapsed_time(b) / 1e3
+    leg = {"workload": name, "m": A.m, "n": A.n, "nnz": int(A.nnz), "model": model, "d": d,
+           "form": "SBD" if sbd else "BBD", "max_depth": max_depth, "min_part": min_part,
+           "value": A.nnz * steps / t, "unit": "nnz/s", "ms_per_step": 1e3 * t / steps, "steps": steps,
+           "roofline": step_roofline(V, torch, once, d, max(1, min(steps, 3)), peak, t / steps)}
+    if cuts:
+        perm, tree = once(with_tree=True)
+        part = owner_parts(A.m + A.n, perm.cpu().numpy(), tree, sbd)
+        rows, cols = part[:A.m], part[A.m:]
+        nparts = int(part.max()) + 1
+        cn_r, l1_r = V.Hypergraph.from_matrix(A, "rownet").cut_size(torch.as_tensor(cols), nparts)
+        cn_c, l1_c = V.Hypergraph.from_matrix(A, "colnet").cut_size(torch.as_tensor(rows), nparts)
+        nsep = tree["nsep"].cpu().numpy()
+        leg["cuts"] = {"parts": nparts, "leaves": int((nsep == 0).sum()), "sum_sep": int(nsep.sum()),
+                       "max_sep": int(nsep.max()), "lambda_minus_1": l1_r + l1_c,
+                       "lambda_minus_1_rownets": l1_r, "lambda_minus_1_colnets": l1_c, "cut_nets": cn_r + cn_c}
+    return leg
+
+
+def plain_over_requests(V, torch, reqs, count: int) -> dict:
+    """The served mix one request at a time through the plain API (host CSR in,
+    host permutation out, each call finished before the next), on the first
+    `count` requests of the stream."""
+    p = V.Params(d=3, seed=1)
+    sample = reqs[:count]
+    host = [(torch.as_tensor(A.rowptr).pin_memory(), torch.as_tensor(A.colidx).pin_memory(),
+             torch.empty(A.m, dtype=torch.int32).pin_memory()) for A in sample]
+    for (rp, ci, out), A in list(zip(host, sample))[:2]:
+        V.Hypergraph(rp.cuda(), ci.cuda(), A.m, A.m).order(p, None, with_tree=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for (rp, ci, out), A in zip(host, sample):
+        hg = V.Hypergraph(rp.cuda(non_blocking=True), ci.cuda(non_blocking=True), A.m, A.m)
+        perm, _, _ = hg.order(p, None, with_tree=False)
+        out.copy_(perm)  # waits for the result, as a caller of the plain API would
+        del hg
+    dt = time.perf_counter() - t0
+    nnz = sum(A.nnz for A in sample)
+    return {"value": nnz / dt, "unit": "nnz/s", "requests": len(sample), "nnz": int(nnz),
+            "large_requests": sum(1 for A in sample if A.m >= 1_000_000), "seconds": dt}
+
+
 def max_over_ranks(seconds: float, world: int, device: str) -> float:
     """Largest elapsed time over the ranks (the job's time: every rank orders
     its own replica, so the job ends with the slowest)."""
@@ -250,7 +392,8 @@ def replica_throughput(units_per_rank: int, world: int, tmax: float) -> float:
     return units_per_rank * world / tmax
 
 
-def served_leg(V, rate: float, duration: float, large_every: int = 50, slots: int = 4):
+def served_leg(V, rate: float, duration: float, large_every: int = 50, slots: int = 4, plain_sample: int = 0,
+               torch=None):
     """Served mode: an open-loop Poisson stream of ordering requests (seeded),
     98% from the batch_mix size distribution and every `large_every`-th a
     27-point stencil on 100^3 (1,000,000 rows, 26,463,592 nnz), submitted from
@@ -296,6 +439,7 @@ def served_leg(V, rate: float, duration: float, large_every: int = 50, slots: in
     def pct(a, q):
         return float(np.percentile(a, q)) if len(a) else None
 
+    plain = plain_over_requests(V, torch, reqs, plain_sample) if plain_sample > 0 else None
     return {"workload": f"Poisson arrivals {rate:g}/s for {duration:g} s (seed 5): batch_mix sizes, every "
                         f"{large_every}th request a 27-point stencil 100^3 (26.46M nnz); host CSR in, host "
                         f"permutation out; d=3, min_part 64",
@@ -304,7 +448,10 @@ def served_leg(V, rate: float, duration: float, large_every: int = 50, slots: in
             "unit": "nnz/s", "p50_s": pct(lat, 50), "p99_s": pct(lat, 99), "p50_small_s": pct(lat_small, 50),
             "p99_small_s": pct(lat_small, 99), "p50_large_s": pct(lat_large, 50), "max_s": pct(lat, 100),
             "batches": st["batches"], "slots": slots, "budget_bytes": st["budget_bytes"],
-            "peak_admitted_bytes": st["bytes_peak"], "pool_peak_bytes": st["pool_peak_bytes"]}
+            "peak_admitted_bytes": st["bytes_peak"], "pool_peak_bytes": st["pool_peak_bytes"],
+            "drain_s": t_last - t_first,
+            **({"plain_one_at_a_time": plain, "served_over_plain": (nnz_done / (t_last - t_first)) / plain["value"]}
+               if plain else {})}
 
 
 def main():
@@ -316,9 +463,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-count", type=int, default=4096,
                     help="matrices of the batched leg (config-4 distribution; 0 skips it)")
-    ap.add_argument("--serve-rate", type=float, default=30.0,
+    ap.add_argument("--serve-rate", type=float, default=2000.0,
                     help="requests per second of the served leg (0 skips it)")
-    ap.add_argument("--serve-seconds", type=float, default=8.0, help="length of the served arrival stream")
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of the served arrival stream")
+    ap.add_argument("--serve-plain", type=int, default=200,
+                    help="requests of the served stream also ordered one at a time through the plain API")
+    ap.add_argument("--no-config-legs", action="store_true",
+                    help="skip the legs of the small 2D grid and the rectangular SBD workload")
     ap.add_argument("--serve-sweep", default="",
                     help="comma-separated request rates: run the served leg at each and report the highest rate "
                          "sustained (achieved >= 95%% of offered, p99 <= 2 s)")
@@ -361,7 +512,8 @@ def main():
                                      "sample_per_step": f"{sample_name} (bounded sample of the workload)",
                                      "l2": "n/a (CPU)"},
                           "cpu_baseline": {"value": val, "unit": "nnz/s", "cores": 1, "kind": "oracle",
-                                           "sample": f"{sample_name}, oracle FP64 single-thread per step"},
+                                           "sample": f"{sample_name}, oracle FP64 single-thread per step",
+                                           **host_cpu()},
                           "e2e": {"value": val, "unit": "nnz/s", "h2d_bytes_per_step": 0,
                                   "d2h_bytes_per_step": 0}}))
         return
@@ -495,20 +647,22 @@ def main():
         return
 
     csum = clocks.summary()
-    sm_mhz = csum["sm_mhz"] if csum else 2070.0
+    peak = V.vmo.measure_alu_peaks()  # this GPU's measured FP32 rates (a few ms; after the timed region)
     d = 3
     inter_per_step = counted["step_interactions"]
     launches_per_step = max(counted["step_launches"], 1)
     flops_per_launch = inter_per_step * FLOPS_PER_INTERACTION[d] / launches_per_step
     avg_ms = st["step_ms"] / max(st["step_launches"], 1)
     achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
-    peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    roofline = {"bound": "alu", "kernel": "k_repulse_update<3> (layout step)", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": STEP_KERNEL_TRAFFIC_BYTES,
+    roofline = {"bound": "alu", "kernel": "k_repulse_update<3> (layout step)", "achieved": achieved,
+                "peak": peak["ffma2_tflops"], "unit": "TFLOP/s", "frac": achieved / peak["ffma2_tflops"],
+                "traffic": STEP_KERNEL_TRAFFIC_BYTES,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the "
                                 "3,000 launches of one step)",
-                "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x median SM clock "
-                               f"{sm_mhz:.0f} MHz during the timed region",
+                "peak_source": f"measured in this run (vmo_measure_alu_peaks): packed FP32 fma2 on all "
+                               f"{peak['sms']} SMs, {peak['ffma2_tflops']:.1f} TFLOP/s (scalar fma "
+                               f"{peak['ffma_tflops']:.1f}, rsqrt {peak['rsqrt_tops']:.2f} T/s); nominal "
+                               f"{peak['sms']} x 128 lanes x 2 x 2070 MHz = {peak['sms'] * 256 * 2.07e-3:.1f}",
                 "interactions_per_launch": inter_per_step / launches_per_step,
                 "flops_per_interaction": FLOPS_PER_INTERACTION[d],
                 "avg_launch_ms": avg_ms, "launches": st["step_launches"],
@@ -529,8 +683,18 @@ def main():
                                        flush, bmats)
         if not args.no_cpu_baseline and world == 1:
             modes["batched"]["cpu_oracle_all_cores"] = batch_cpu_all_cores(bmats)
+    if not args.no_config_legs and world == 1:
+        modes["config_grid2d_64"] = config_leg(
+            V, torch, "2D 5-point Laplacian 64x64 (n 4,096), symmetric model, d=2, BBD to parts of <= 64 rows",
+            W.grid_laplacian_2d(64), "symmetric", 2, False, 62, 64, max(args.steps, 5), args.warmup, flush, peak)
+        modes["config_sbd_400k"] = config_leg(
+            V, torch, "400,000 x 300,000 power-law (column degrees ~d^-2.5, mean ~16), bipartite model, d=2, "
+                      "SBD to depth 6 (64 parts)",
+            W.powerlaw_rectangular(400_000, 300_000, seed=1), "bipartite", 2, True, 6, 1, args.steps, args.warmup,
+            flush, peak, cuts=True)
     if args.serve_rate > 0 and world == 1:
-        modes["served"] = served_leg(V, args.serve_rate, args.serve_seconds)
+        modes["served"] = served_leg(V, args.serve_rate, args.serve_seconds, plain_sample=args.serve_plain,
+                                     torch=torch)
     if args.serve_sweep and world == 1:
         sweep = []
         for rate in [float(r) for r in args.serve_sweep.split(",") if r]:
@@ -585,6 +749,7 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         sname, smats = cpu_sample(small=False)
         cpu = run_cpu_baseline(smats, sname)
+        cpu.update(host_cpu())
 
     out = {"metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,

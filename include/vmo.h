@@ -596,6 +596,17 @@ vmo_status vmo_server_get_stats(vmo_server srv, vmo_server_stats* out);
  * queued and frees the server (NULL is ignored). */
 void vmo_server_destroy(vmo_server srv);
 
+/* Measured arithmetic throughput of the current GPU, the ceiling of the
+ * layout step kernel (no counterpart in the paper; measurement support):
+ * FP32 fused multiply-add, scalar (ffma) and packed two-lane (ffma2), in
+ * TFLOP/s counting a multiply-add as 2 flops, and the special-function
+ * unit's approximate reciprocal square root in T operations/s; sms receives
+ * the number of SMs.  Each figure is the best of a few launches that fill
+ * every SM with independent dependency chains (a few ms in all), at the
+ * clock the GPU runs at.  Any output may be NULL (that kernel is skipped). */
+vmo_status vmo_measure_alu_peaks(double* ffma_tflops, double* ffma2_tflops, double* rsqrt_tops, int32_t* sms,
+                                 void* stream);
+
 /* Resets the counters.  time_step_kernel != 0 records CUDA events around
  * every layout step kernel; count_interactions != 0 makes that kernel count
  * its interactions (an atomic per warp; same arithmetic otherwise). */

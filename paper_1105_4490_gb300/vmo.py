@@ -99,7 +99,8 @@ SYMBOLS = ["vmo_default_params", "vmo_build_hypergraph", "vmo_hg_vertices", "vmo
            "vmo_status_string", "vmo_last_error", "vmo_stats_reset", "vmo_stats_get", "vmo_batch_order",
            "vmo_batch_layout", "vmo_bisect_noalloc", "vmo_server_default_config", "vmo_server_estimate_bytes",
            "vmo_server_plan", "vmo_server_create", "vmo_server_submit", "vmo_server_poll", "vmo_server_wait",
-           "vmo_server_cancel", "vmo_server_release", "vmo_server_get_stats", "vmo_server_destroy", "vmo_kmeans"]
+           "vmo_server_cancel", "vmo_server_release", "vmo_server_get_stats", "vmo_server_destroy", "vmo_kmeans",
+           "vmo_measure_alu_peaks"]
 
 
 class _ServerConfig(C.Structure):
@@ -189,6 +190,8 @@ def load(path: str | None = None):
     lib.vmo_server_wait.argtypes = [V, U64, C.c_double, C.POINTER(_RequestInfo)]
     lib.vmo_server_cancel.argtypes = [V, U64]
     lib.vmo_server_release.argtypes = [V, U64]
+    D = C.POINTER(C.c_double)
+    lib.vmo_measure_alu_peaks.argtypes = [D, D, D, P32, V]
     lib.vmo_server_get_stats.argtypes = [V, C.POINTER(_ServerStats)]
     lib.vmo_server_destroy.argtypes = [V]
     lib.vmo_server_destroy.restype = None
@@ -610,3 +613,12 @@ def kmeans(coords: torch.Tensor, verts: torch.Tensor, m: int, seed: int, key: in
     _check(load().vmo_kmeans(d, _ptr(coords), _ptr(verts), verts.numel(), m, seed & (2 ** 64 - 1),
                              key & (2 ** 64 - 1), km_iters, _ptr(labels), _ptr(centres), C.byref(ne), _stream()))
     return labels[:verts.numel()], centres[:m], int(ne.value)
+
+
+def measure_alu_peaks() -> dict:
+    """vmo_measure_alu_peaks: measured FP32 fma / packed fma2 TFLOP/s, the
+    reciprocal square root rate (T/s) and the SM count of the current GPU."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    n = C.c_int32()
+    _check(load().vmo_measure_alu_peaks(C.byref(a), C.byref(b), C.byref(c), C.byref(n), _stream()))
+    return {"ffma_tflops": a.value, "ffma2_tflops": b.value, "rsqrt_tops": c.value, "sms": int(n.value)}

@@ -47,3 +47,28 @@ def test_oracle_samples_are_bounded_versions_of_the_workload():
         assert [cfg for _, cfg in smats] == [cfg for _, cfg in mats]
         assert sum(A.nnz for A, _ in smats) < 0.02 * sum(A.nnz for A, _ in mats)
         assert sname != name
+
+
+def test_owner_parts_from_tree():
+    """Owners for the cut metrics: a leaf owns its range, a split node owns
+    its separator, placed last (BBD) or between the parts (SBD)."""
+    import numpy as np
+    import torch
+    perm = np.array([5, 3, 1, 0, 4, 2, 6], dtype=np.int32)
+    # root: 7 vertices, n1 = 3, n2 = 2, nsep = 2; children leaves
+    for sbd in (False, True):
+        off = [0, 0, 5 if sbd else 3]
+        tree = {"offset": torch.tensor(off), "n1": torch.tensor([3, 3, 2]), "n2": torch.tensor([2, 0, 0]),
+                "nsep": torch.tensor([2, 0, 0])}
+        if sbd:
+            tree["offset"] = torch.tensor([0, 0, 5])
+        part = bench.owner_parts(7, perm, tree, sbd)
+        sep = perm[3:5] if sbd else perm[5:7]
+        assert sorted(np.flatnonzero(part == 0).tolist()) == sorted(sep.tolist())
+        assert sorted(np.flatnonzero(part == 1).tolist()) == sorted(perm[0:3].tolist())
+        assert (part >= 0).all()
+
+
+def test_host_cpu_reports_model_and_cores():
+    h = bench.host_cpu()
+    assert h["cpu_cores"] >= 1 and isinstance(h["cpu_model"], str) and h["arch"]

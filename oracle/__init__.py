@@ -31,11 +31,16 @@ MODELS = {"symmetric": 0, "bipartite": 1, "rownet": 2, "colnet": 3, "finegrain":
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, IEEE semantics)."""
+    """Compile the oracle with gcc (no FMA contraction, IEEE semantics; OpenMP
+    over the per-vertex gradient loop when the compiler has it)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-o", tmp,
+                _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -64,6 +69,10 @@ def _load():
         if _lib is None:
             lib = C.CDLL(build())
             P = C.c_void_p
+            lib.ora_set_threads.restype = None
+            lib.ora_set_threads.argtypes = [C.c_int32]
+            lib.ora_get_threads.restype = C.c_int32
+            lib.ora_get_threads.argtypes = []
             lib.ora_rand64.restype = C.c_uint64
             lib.ora_rand64.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
             lib.ora_build.argtypes = [C.c_int32, C.c_int32, C.c_int32, P, P, C.POINTER(_HG)]
@@ -205,6 +214,16 @@ def components(hg: Hypergraph) -> np.ndarray:
     lib.ora_components(hg.k, hg.l, _p(hg._keep[0]), _p(hg._keep[1]), _p(p))
     del s
     return p
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's per-vertex loops (results are the same for any
+    count: every vertex's sums are one thread's, in a fixed order)."""
+    _load().ora_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(_load().ora_get_threads())
 
 
 def rand64(seed: int, a: int, b: int) -> int:

@@ -22,8 +22,30 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORA_EXPORT __attribute__((visibility("default")))
+
+/* Threads of the per-vertex loops (OpenMP when built with it).  Every vertex's
+ * sums are taken by one thread in a fixed order, so results do not depend on
+ * the thread count. */
+ORA_EXPORT void ora_set_threads(int32_t n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : 1);
+#else
+  (void)n;
+#endif
+}
+
+ORA_EXPORT int32_t ora_get_threads(void) {
+#ifdef _OPENMP
+  return (int32_t)omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------- */
 /* Random numbers: the SplitMix64 output function (Steele, Lea, Flood 2014),  */
@@ -415,6 +437,14 @@ typedef struct {
 /* Gradient y = df/dx of eq. graphenergygradientsimple with the repulsion sum
  * approximated on the grid pyramid.  Also returns the level-L Morton key of
  * every vertex (the GPU must reproduce these bit for bit). */
+/* |r|^(-d) from r2 = |r|^2, the kernel of the repulsion term of eq.
+ * graphenergygradientsimple (d = 2: the planar reading 1/r^2). */
+static double ora_rpow(double r2, int d) {
+  if (d == 2) return 1.0 / r2;
+  if (d == 3) return 1.0 / (r2 * sqrt(r2));
+  return 1.0 / (r2 * r2);
+}
+
 ORA_EXPORT int ora_gradient(const ora_hg* h, int32_t d, int32_t occ, const double* x /* k*4 */,
                             const double* w, const double* c, double* y /* k*4 */,
                             uint32_t* keys /* k or NULL */, int32_t* L_out, ora_diag* diag) {
@@ -473,6 +503,9 @@ ORA_EXPORT int ora_gradient(const ora_hg* h, int32_t d, int32_t occ, const doubl
   double kap = ora_kappa(d);
   int nb = 1;
   for (int m = 0; m < d; ++m) nb *= 3;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
   for (int32_t n = 0; n < k; ++n) {
     double wn = w ? w[n] : 1.0;
     double F[4] = {0, 0, 0, 0};
@@ -497,7 +530,7 @@ ORA_EXPORT int ora_gradient(const ora_hg* h, int32_t d, int32_t occ, const doubl
         double wi = w ? w[i] : 1.0;
         cnt++; wseen += wi;
         if (r2 == 0.0) continue;
-        double g = wi * wn * pow(r2, -0.5 * d);
+        double g = wi * wn * ora_rpow(r2, d);
         for (int m = 0; m < d; ++m) F[m] += g * dx[m];
       }
     }
@@ -533,7 +566,7 @@ ORA_EXPORT int ora_gradient(const ora_hg* h, int32_t d, int32_t occ, const doubl
           }
           cnt++; wseen += W[id];
           if (r2 == 0.0) continue;
-          double g = W[id] * wn * pow(r2, -0.5 * d);
+          double g = W[id] * wn * ora_rpow(r2, d);
           for (int m = 0; m < d; ++m) F[m] += g * dx[m];
         }
       }

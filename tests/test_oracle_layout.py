@@ -246,3 +246,21 @@ def test_hierarchy_shrinks(oracle_mod):
     ks = O.hierarchy(hg, 1)
     assert ks[0] == 4096 and ks[-1] <= 64
     assert all(b <= 0.95 * a for a, b in zip(ks, ks[1:]))
+
+
+def test_threads_do_not_change_results(oracle_mod):
+    """The per-vertex gradient loop runs on several threads when the oracle is
+    built with OpenMP; every vertex's sums stay one thread's, in order, so a
+    layout is bit-identical for 1 and 4 threads."""
+    O = oracle_mod
+    A = W.powerlaw_symmetric(3000, seed=5)
+    hg = _hg(O, A)
+    before = O.threads()
+    try:
+        O.set_threads(1)
+        x1 = O.layout_multilevel(hg, 3, seed=2, iters=10)
+        O.set_threads(4)
+        x4 = O.layout_multilevel(hg, 3, seed=2, iters=10)
+    finally:
+        O.set_threads(before)
+    assert np.array_equal(x1.view(np.uint64), x4.view(np.uint64))

@@ -70,10 +70,13 @@ template <int D>
 __global__ void k_maxabs(const float4* __restrict__ xo, const int32_t* __restrict__ seg, int64_t n,
                          NodeDev* __restrict__ nodes) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int s = i < n ? seg[i] : -1;
+  const bool in = i < n;
+  // both loads in flight together (the coordinates are read whether or not
+  // the position is active)
+  const int s = in ? seg[i] : -1;
+  const float4 x = in ? xo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   uint32_t mx = 0;
   if (s >= 0) {
-    float4 x = xo[i];
 #pragma unroll
     for (int m = 0; m < D; ++m) mx = max(mx, __float_as_uint(fabsf(comp(x, m))));
   }
@@ -99,11 +102,12 @@ __global__ void k_dsq(const float4* __restrict__ xo, const int32_t* __restrict__
                       const NodeDev* __restrict__ nodes, unsigned long long* __restrict__ dval) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int s = seg[i];
+  const int s = seg[i];
+  const float4 x = xo[i];  // in flight with seg[i]
   unsigned long long v = 0;
   if (s >= 0) {
     const NodeDev& nd = nodes[s];
-    float dd = sqdist32<D>(xo[i], nd.z1);
+    float dd = sqdist32<D>(x, nd.z1);
     float sc = __fmul_rn(dd, exp2i_f(34 - 2 * nd.e));
     v = (unsigned long long)floorf(sc);
   }
@@ -357,24 +361,67 @@ __global__ void k_clear_counts(NodeDev* __restrict__ nodes, int N) {
   nodes[s].n1 = nodes[s].n2 = 0;
 }
 
-// Per-vertex copies of the final 2-means label and plane distance, used by
-// the separator to look at neighbours.
+// Per-vertex record of the separator phase, one 8-byte word so that a
+// neighbour costs one load: high word (node << 2) | label, where label is the
+// vertex's final 2-means label (1 or 2) in a split node of this level and 0
+// otherwise (also for vertices already placed); low word the bits of the
+// plane distance s = |x.r - delta| (s >= 0, so its bits order like its value).
+__device__ __forceinline__ uint64_t vrec_make(int node, uint32_t label, float sdist) {
+  return ((uint64_t)(((uint32_t)node << 2) | label) << 32) | __float_as_uint(sdist);
+}
+__device__ __forceinline__ uint32_t vrec_label(uint64_t r) { return (uint32_t)(r >> 32) & 3u; }
+__device__ __forceinline__ float vrec_s(uint64_t r) { return __uint_as_float((uint32_t)r); }
+// the high word a neighbour in node s with the label other than l (l in {1, 2}) carries
+__device__ __forceinline__ uint32_t vrec_other(int s, uint32_t l) { return ((uint32_t)s << 2) | (3u - l); }
+
 template <int D>
 __global__ void k_vertex_state(const float4* __restrict__ xo, const int32_t* __restrict__ ord,
                                const int32_t* __restrict__ seg, int64_t n, const NodeDev* __restrict__ nodes,
-                               const uint8_t* __restrict__ lab, uint8_t* __restrict__ vlab, float* __restrict__ vs) {
+                               const uint8_t* __restrict__ lab, uint64_t* __restrict__ vrec) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int s = seg[i];
+  const int s = seg[i];
+  const int32_t v = ord[i];   // loads in flight together
+  const float4 x = xo[i];
+  const uint8_t li = lab[i];
   if (s < 0) return;
   const NodeDev& nd = nodes[s];
-  int32_t v = ord[i];
   bool split = nd.state != 2 && nd.n1 > 0 && nd.n2 > 0;
-  vlab[v] = split ? lab[i] : 0;
   float4 r;
   float delta;
   plane_of<D>(nd.z1, nd.z2, &r, &delta);
-  vs[v] = plane_dist<D>(xo[i], r, delta);
+  vrec[v] = vrec_make(s, split ? li : 0u, plane_dist<D>(x, r, delta));
+}
+
+// Sizes of V1, V2, V3 of the positions of a block added to their nodes' c1,
+// c2, c3: once per block when every position of the block lies in one node
+// (the top of the recursion, where a level's positions would otherwise all
+// hit the same three counters), else once per warp and (node, label).
+// Every thread of the block calls it (s < 0 or l == 0: nothing to count).
+__device__ void count_labels(int s, uint8_t l, NodeDev* __restrict__ nodes) {
+  __shared__ int s_first, s_cnt[3];
+  if (threadIdx.x == 0) s_first = -1;
+  if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  if (s >= 0) atomicCAS(&s_first, -1, s);
+  __syncthreads();
+  const int s0 = s_first;
+  const bool uniform = __syncthreads_and(s < 0 || s == s0) && s0 >= 0;
+  const int key = (s >= 0 && l != 0) ? s * 4 + l : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const bool leader = key >= 0 && (int)lane_id() == __ffs(peers) - 1;
+  if (uniform) {
+    if (leader) atomicAdd(&s_cnt[l - 1], (int)__popc(peers));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (s_cnt[0]) atomicAdd(&nodes[s0].c1, s_cnt[0]);
+      if (s_cnt[1]) atomicAdd(&nodes[s0].c2, s_cnt[1]);
+      if (s_cnt[2]) atomicAdd(&nodes[s0].c3, s_cnt[2]);
+    }
+  } else if (leader) {
+    int* c = l == 1 ? &nodes[s].c1 : (l == 2 ? &nodes[s].c2 : &nodes[s].c3);
+    atomicAdd(c, (int)__popc(peers));
+  }
 }
 
 // Order-free form of the separator loop of Algorithm 7 (mu = identity):
@@ -382,33 +429,29 @@ __global__ void k_vertex_state(const float4* __restrict__ xo, const int32_t* __r
 // label and (s(v), v) < (s(w), w).
 __global__ void k_separator(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
                             const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
-                            const int32_t* __restrict__ vnode, const uint8_t* __restrict__ vlab,
-                            const float* __restrict__ vs, NodeDev* __restrict__ nodes, uint8_t* __restrict__ labf) {
+                            const uint64_t* __restrict__ vrec, NodeDev* __restrict__ nodes,
+                            uint8_t* __restrict__ labf) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int s = i < n ? seg[i] : -1;
   uint8_t l = 0;
   if (s >= 0) {
-    int32_t v = ord[i];
-    l = vlab[v];
+    const int32_t v = ord[i];
+    const uint64_t rv = vrec[v];
+    l = (uint8_t)vrec_label(rv);
     if (l != 0) {
-      float sv = vs[v];
+      const float sv = vrec_s(rv);
+      const uint32_t other = vrec_other(s, l);
       for (int32_t t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) {
-        int32_t w = adj[t];
-        if (vnode[w] != s) continue;
-        uint8_t lw = vlab[w];
-        if (lw == l || lw == 0) continue;
-        float sw = vs[w];
+        const int32_t w = adj[t];
+        const uint64_t rw = vrec[w];
+        if ((uint32_t)(rw >> 32) != other) continue;  // not in this node, or on the same side
+        const float sw = vrec_s(rw);
         if (sv < sw || (sv == sw && v < w)) { l = 3; break; }
       }
     }
     labf[i] = l;
   }
-  int key = (l != 0) ? s * 4 + l : -1;
-  unsigned peers = __match_any_sync(0xffffffffu, key);
-  if (key >= 0 && (int)lane_id() == __ffs(peers) - 1) {
-    int* c = l == 1 ? &nodes[s].c1 : (l == 2 ? &nodes[s].c2 : &nodes[s].c3);
-    atomicAdd(c, (int)__popc(peers));
-  }
+  count_labels(s, l, nodes);
 }
 
 // With a strengthened diagonal (Algorithm 7 moves a selected vertex's
@@ -417,22 +460,23 @@ __global__ void k_separator(const int32_t* __restrict__ ord, const int32_t* __re
 // vertices and their partners form V3.  Partners always share a node.
 __global__ void k_pick(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
                        const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
-                       const int32_t* __restrict__ vnode, const uint8_t* __restrict__ vlab,
-                       const float* __restrict__ vs, uint8_t* __restrict__ vpick) {
+                       const uint64_t* __restrict__ vrec, uint8_t* __restrict__ vpick) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int s = seg[i];
   if (s < 0) return;
-  int32_t v = ord[i];
-  uint8_t l = vlab[v], pick = 0;
+  const int32_t v = ord[i];
+  const uint64_t rv = vrec[v];
+  const uint32_t l = vrec_label(rv);
+  uint8_t pick = 0;
   if (l != 0) {
-    float sv = vs[v];
+    const float sv = vrec_s(rv);
+    const uint32_t other = vrec_other(s, l);
     for (int32_t t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) {
-      int32_t w = adj[t];
-      if (vnode[w] != s) continue;
-      uint8_t lw = vlab[w];
-      if (lw == l || lw == 0) continue;
-      float sw = vs[w];
+      const int32_t w = adj[t];
+      const uint64_t rw = vrec[w];
+      if ((uint32_t)(rw >> 32) != other) continue;
+      const float sw = vrec_s(rw);
       if (sv < sw || (sv == sw && v < w)) { pick = 1; break; }
     }
   }
@@ -440,7 +484,7 @@ __global__ void k_pick(const int32_t* __restrict__ ord, const int32_t* __restric
 }
 
 __global__ void k_separator_mu(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
-                               const int32_t* __restrict__ mu, const uint8_t* __restrict__ vlab,
+                               const int32_t* __restrict__ mu, const uint64_t* __restrict__ vrec,
                                const uint8_t* __restrict__ vpick, NodeDev* __restrict__ nodes,
                                uint8_t* __restrict__ labf) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -448,16 +492,11 @@ __global__ void k_separator_mu(const int32_t* __restrict__ ord, const int32_t* _
   uint8_t l = 0;
   if (s >= 0) {
     int32_t v = ord[i];
-    l = vlab[v];
+    l = (uint8_t)vrec_label(vrec[v]);
     if (l != 0 && (vpick[v] | vpick[mu[v]])) l = 3;
     labf[i] = l;
   }
-  int key = (l != 0) ? s * 4 + l : -1;
-  unsigned peers = __match_any_sync(0xffffffffu, key);
-  if (key >= 0 && (int)lane_id() == __ffs(peers) - 1) {
-    int* c = l == 1 ? &nodes[s].c1 : (l == 2 ? &nodes[s].c2 : &nodes[s].c3);
-    atomicAdd(c, (int)__popc(peers));
-  }
+  count_labels(s, l, nodes);
 }
 
 // ----- Algorithm 7's loop with a strengthened diagonal, in canonical order -----
@@ -481,34 +520,32 @@ __global__ void k_separator_mu(const int32_t* __restrict__ ord, const int32_t* _
 // a lower bound on the class's move key and every decision taken from it holds.
 constexpr int kMuUndecided = 0, kMuMoved = 1, kMuNever = 2;
 
-__device__ __forceinline__ bool mu_cut_neighbour(int32_t v, int32_t w, int s, uint8_t l,
-                                                 const int32_t* __restrict__ vnode, const uint8_t* __restrict__ vlab,
-                                                 const float* __restrict__ vs) {
-  if (vnode[w] != s) return false;
-  const uint8_t lw = vlab[w];
-  if (lw == l || lw == 0) return false;
-  const float sv = vs[v], sw = vs[w];
+__device__ __forceinline__ bool mu_cut_neighbour(int32_t v, float sv, int32_t w, int s, uint32_t l,
+                                                 const uint64_t* __restrict__ vrec) {
+  const uint64_t rw = vrec[w];
+  if ((uint32_t)(rw >> 32) != vrec_other(s, l)) return false;
+  const float sw = vrec_s(rw);
   return sv < sw || (sv == sw && v < w);  // v is the end the loop moves
 }
 
 // Candidate edges moved through each vertex (edges whose moved end it is).
 __global__ void k_mu_count(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
                            const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
-                           const int32_t* __restrict__ vnode, const uint8_t* __restrict__ vlab,
-                           const float* __restrict__ vs, int32_t* __restrict__ mcnt) {
+                           const uint64_t* __restrict__ vrec, int32_t* __restrict__ mcnt) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int s = seg[i];
   const int32_t v = ord[i];
   int32_t c = 0;
-  const uint8_t l = s >= 0 ? vlab[v] : 0;
+  const uint64_t rv = s >= 0 ? vrec[v] : 0ull;
+  const uint32_t l = vrec_label(rv);
   if (l != 0)
-    for (int32_t t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) c += mu_cut_neighbour(v, adj[t], s, l, vnode, vlab, vs);
+    for (int32_t t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) c += mu_cut_neighbour(v, vrec_s(rv), adj[t], s, l, vrec);
   mcnt[v] = c;
 }
 
-__device__ __forceinline__ bool mu_first(int32_t a, int32_t b, const float* __restrict__ vs) {
-  const float sa = vs[a], sb = vs[b];
+__device__ __forceinline__ bool mu_first(int32_t a, int32_t b, const uint64_t* __restrict__ vrec) {
+  const float sa = vrec_s(vrec[a]), sb = vrec_s(vrec[b]);
   return sa < sb || (sa == sb && a < b);
 }
 
@@ -527,8 +564,7 @@ __global__ void k_mu_total(const int32_t* __restrict__ ord, const int32_t* __res
 // first, each member's edges by ascending other end (adjacency order).
 __global__ void k_mu_fill(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
                           const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
-                          const int32_t* __restrict__ vnode, const uint8_t* __restrict__ vlab,
-                          const float* __restrict__ vs, const int32_t* __restrict__ mu,
+                          const uint64_t* __restrict__ vrec, const int32_t* __restrict__ mu,
                           const int32_t* __restrict__ mcnt, const int32_t* __restrict__ mbeg,
                           int32_t* __restrict__ cand_c, int32_t* __restrict__ cand_w, int32_t* __restrict__ mstate) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -542,13 +578,14 @@ __global__ void k_mu_fill(const int32_t* __restrict__ ord, const int32_t* __rest
     const int32_t tot = mcnt[v] + (u != v ? mcnt[u] : 0);
     mstate[rep] = tot > 0 ? kMuUndecided : kMuNever;
   }
-  const uint8_t l = vlab[v];
+  const uint64_t rv = vrec[v];
+  const uint32_t l = vrec_label(rv);
   if (l == 0 || mcnt[v] == 0) return;
-  const bool first = u == v || mu_first(v, u, vs);
+  const bool first = u == v || mu_first(v, u, vrec);
   int32_t o = mbeg[rep] + (first ? 0 : mcnt[u]);
   for (int32_t t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) {
     const int32_t w = adj[t];
-    if (!mu_cut_neighbour(v, w, s, l, vnode, vlab, vs)) continue;
+    if (!mu_cut_neighbour(v, vrec_s(rv), w, s, l, vrec)) continue;
     cand_c[o] = v;
     cand_w[o] = w;
     ++o;
@@ -556,15 +593,15 @@ __global__ void k_mu_fill(const int32_t* __restrict__ ord, const int32_t* __rest
 }
 
 // (s, id) key of a candidate's moved end, as one ordered 64-bit number (s >= 0).
-__device__ __forceinline__ uint64_t mu_key(int32_t c, const float* __restrict__ vs) {
-  return ((uint64_t)__float_as_uint(vs[c]) << 32) | (uint32_t)c;
+__device__ __forceinline__ uint64_t mu_key(int32_t c, const uint64_t* __restrict__ vrec) {
+  return ((uint64_t)(uint32_t)vrec[c] << 32) | (uint32_t)c;
 }
 
 // One round over every undecided class; *busy counts classes still undecided.
 __global__ void k_mu_round(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
                            const int32_t* __restrict__ mu, const int32_t* __restrict__ mbeg,
                            const int32_t* __restrict__ mtot, const int32_t* __restrict__ cand_c,
-                           const int32_t* __restrict__ cand_w, const float* __restrict__ vs,
+                           const int32_t* __restrict__ cand_w, const uint64_t* __restrict__ vrec,
                            int32_t* __restrict__ mstate, int* __restrict__ busy) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || seg[i] < 0) return;
@@ -581,11 +618,11 @@ __global__ void k_mu_round(const int32_t* __restrict__ ord, const int32_t* __res
     const int32_t c = cand_c[base + ptr], w = cand_w[base + ptr];
     const int32_t q = min(w, mu[w]);
     if (q == p) { out = (ptr << 2) | kMuMoved; break; }  // edge between the partners
-    const uint64_t ke = mu_key(c, vs);
+    const uint64_t ke = mu_key(c, vrec);
     const int32_t sq = vst[q];
     const int fq = sq & 3;
     if (fq == kMuNever) { out = (ptr << 2) | kMuMoved; break; }
-    const uint64_t kq = mu_key(cand_c[mbeg[q] + (sq >> 2)], vs);
+    const uint64_t kq = mu_key(cand_c[mbeg[q] + (sq >> 2)], vrec);
     if (fq == kMuMoved) {
       if (kq < ke) { ++ptr; continue; }  // class(w) moved first: the edge is no longer cut
       out = (ptr << 2) | kMuMoved;
@@ -604,7 +641,7 @@ __global__ void k_mu_round(const int32_t* __restrict__ ord, const int32_t* __res
 
 // Final labels: both members of a moved class are in V3.
 __global__ void k_separator_mu_loop(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
-                                    const int32_t* __restrict__ mu, const uint8_t* __restrict__ vlab,
+                                    const int32_t* __restrict__ mu, const uint64_t* __restrict__ vrec,
                                     const int32_t* __restrict__ mstate, NodeDev* __restrict__ nodes,
                                     uint8_t* __restrict__ labf) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -612,16 +649,11 @@ __global__ void k_separator_mu_loop(const int32_t* __restrict__ ord, const int32
   uint8_t l = 0;
   if (s >= 0) {
     int32_t v = ord[i];
-    l = vlab[v];
+    l = (uint8_t)vrec_label(vrec[v]);
     if (l != 0 && (mstate[min(v, mu[v])] & 3) == kMuMoved) l = 3;
     labf[i] = l;
   }
-  int key = (l != 0) ? s * 4 + l : -1;
-  unsigned peers = __match_any_sync(0xffffffffu, key);
-  if (key >= 0 && (int)lane_id() == __ffs(peers) - 1) {
-    int* c = l == 1 ? &nodes[s].c1 : (l == 2 ? &nodes[s].c2 : &nodes[s].c3);
-    atomicAdd(c, (int)__popc(peers));
-  }
+  count_labels(s, l, nodes);
 }
 
 __global__ void k_pack(const int32_t* __restrict__ seg, const uint8_t* __restrict__ labf, int64_t n,
@@ -641,21 +673,31 @@ __global__ void k_pack(const int32_t* __restrict__ seg, const uint8_t* __restric
 }
 
 // Stable partition of every split node into [V1, V2, V3] (BBD) or
-// [V1, V3, V2] (SBD); other positions are copied.
+// [V1, V3, V2] (SBD); other positions are copied.  Every position also gets
+// its node of the next level (seg2): the child of its node that holds its part
+// (k_children has numbered them), or -1 when its vertex is placed now (a
+// leaf, or a separator that is not recursed into); such a vertex's separator
+// record is cleared, so that no later level takes it for a neighbour in one
+// of its nodes (the records of the others are rewritten by the next level's
+// k_vertex_state).
 __global__ void k_scatter(const int32_t* __restrict__ ord, const float4* __restrict__ xo,
                           const int32_t* __restrict__ seg, const uint8_t* __restrict__ labf, int64_t n,
                           const NodeDev* __restrict__ nodes, const unsigned long long* __restrict__ pre, int sbd,
-                          int32_t* __restrict__ ord2, float4* __restrict__ xo2, int32_t* __restrict__ segl2) {
+                          int32_t* __restrict__ ord2, float4* __restrict__ xo2, int32_t* __restrict__ seg2,
+                          uint64_t* __restrict__ vrec) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int s = seg[i];
+  const int s = seg[i];
+  const int32_t v = ord[i];   // loads in flight together
+  const float4 xi = xo[i];
+  const uint8_t li = labf[i];
   int64_t dst = i;
-  int32_t tag = -1;
+  int32_t next = -1;
   if (s >= 0) {
     const NodeDev& nd = nodes[s];
     int c1 = nd.c1, c2 = nd.c2, c3 = nd.c3;
     if (c1 + c2 + c3 > 0) {
-      uint8_t l = labf[i];
+      const uint8_t l = li;
       unsigned long long base = nd.off > 0 ? pre[nd.off - 1] : 0ull;
       unsigned long long own = (l == 1) ? 1ull : (l == 2 ? (1ull << 32) : 0ull);
       unsigned long long ex = pre[i] - base - own;
@@ -666,12 +708,13 @@ __global__ void k_scatter(const int32_t* __restrict__ ord, const float4* __restr
       else if (l == 2) o = sbd ? (int64_t)c1 + c3 + r2 : (int64_t)c1 + r2;
       else o = sbd ? (int64_t)c1 + r3 : (int64_t)c1 + c2 + r3;
       dst = nd.off + o;
-      tag = s * 4 + l;
+      next = l == 1 ? nd.child1 : (l == 2 ? nd.child2 : nd.child3);
     }
   }
-  ord2[dst] = ord[i];
-  xo2[dst] = xo[i];
-  segl2[dst] = tag;
+  ord2[dst] = v;
+  xo2[dst] = xi;
+  seg2[dst] = next;
+  if (s >= 0 && next < 0) vrec[v] = 0ull;
 }
 
 // Tree records and the next level's node table.  Children: V1 and V2, and
@@ -715,21 +758,6 @@ __global__ void k_children(NodeDev* __restrict__ nodes, int N, const int64_t* __
   }
 }
 
-__global__ void k_relabel(const int32_t* __restrict__ segl2, const int32_t* __restrict__ ord2, int64_t n,
-                          const NodeDev* __restrict__ nodes, int32_t* __restrict__ seg, int32_t* __restrict__ vnode) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int32_t tag = segl2[i];
-  int32_t c = -1;
-  if (tag >= 0) {
-    int s = tag >> 2, l = tag & 3;
-    c = l == 1 ? nodes[s].child1 : (l == 2 ? nodes[s].child2 : nodes[s].child3);
-  }
-  int32_t old = seg[i];
-  seg[i] = (tag >= 0) ? c : -1;
-  if (tag >= 0 || old >= 0) vnode[ord2[i]] = seg[i];
-}
-
 __global__ void k_root_nodes(NodeDev* __restrict__ nodes, const int64_t* __restrict__ pbase, const int32_t* __restrict__ ids,
                              int N, const uint64_t* __restrict__ heaps) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -743,7 +771,7 @@ __global__ void k_root_nodes(NodeDev* __restrict__ nodes, const int64_t* __restr
   nd.prob = p;
 }
 
-__global__ void k_seg_init(int32_t* __restrict__ seg, int32_t* __restrict__ vnode, const int32_t* __restrict__ ord,
+__global__ void k_seg_init(int32_t* __restrict__ seg, const int32_t* __restrict__ ord,
                            int64_t n, const int64_t* __restrict__ pbase, int P, const int32_t* __restrict__ node_of_prob) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -752,9 +780,7 @@ __global__ void k_seg_init(int32_t* __restrict__ seg, int32_t* __restrict__ vnod
     int mid = (lo + hi) >> 1;
     if (pbase[mid] <= i) lo = mid; else hi = mid;
   }
-  int32_t s = node_of_prob[lo];
-  seg[i] = s;
-  vnode[ord[i]] = s;
+  seg[i] = node_of_prob[lo];
 }
 
 __global__ void k_gather_coords(const float4* __restrict__ x, const int32_t* __restrict__ ord, int64_t n,
@@ -991,8 +1017,7 @@ static vmo_status mu_loop_separator(OrderState& st, int64_t n, uint8_t* labf, cu
   VMO_TRY(sc.alloc(&mstate, n));
   VMO_TRY(sc.alloc(&total, 1));
   VMO_TRY(sc.alloc(&busy, 1));
-  launch(k_mu_count, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vnode, st.vlab,
-         st.vs, mcnt);
+  launch(k_mu_count, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vrec, mcnt);
   launch(k_mu_total, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.mu, mcnt, mtot);
   VMO_TRY(scan_exclusive<int32_t>(mtot, mbeg, n, total, s, sc));
   int32_t ncand = 0;
@@ -1001,8 +1026,8 @@ static vmo_status mu_loop_separator(OrderState& st, int64_t n, uint8_t* labf, cu
   int32_t *cand_c, *cand_w;
   VMO_TRY(sc.alloc(&cand_c, std::max<int32_t>(ncand, 1)));
   VMO_TRY(sc.alloc(&cand_w, std::max<int32_t>(ncand, 1)));
-  launch(k_mu_fill, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vnode, st.vlab,
-         st.vs, st.mu, mcnt, mbeg, cand_c, cand_w, mstate);
+  launch(k_mu_fill, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vrec, st.mu, mcnt,
+         mbeg, cand_c, cand_w, mstate);
   // every round decides at least one class (the one with the smallest
   // current candidate), so ncand + 1 rounds always suffice
   constexpr int kRoundsPerCheck = 4;
@@ -1011,7 +1036,7 @@ static vmo_status mu_loop_separator(OrderState& st, int64_t n, uint8_t* labf, cu
     for (int r = 0; r < kRoundsPerCheck; ++r) {
       if (r == kRoundsPerCheck - 1) VMO_CUDA(cudaMemsetAsync(busy, 0, sizeof(int), s));
       launch(k_mu_round, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.mu, mbeg, mtot, cand_c, cand_w,
-             st.vs, mstate, r == kRoundsPerCheck - 1 ? busy : (int*)nullptr);
+             st.vrec, mstate, r == kRoundsPerCheck - 1 ? busy : (int*)nullptr);
     }
     rounds += kRoundsPerCheck;
     int h = 0;
@@ -1021,7 +1046,7 @@ static vmo_status mu_loop_separator(OrderState& st, int64_t n, uint8_t* labf, cu
     if (rounds > (int64_t)ncand + 2 * kRoundsPerCheck)
       return cuda_fail(cudaErrorUnknown, "separator: the matched-pair rounds did not settle", __FILE__, __LINE__);
   }
-  launch(k_separator_mu_loop, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.mu, st.vlab, mstate, st.nodes,
+  launch(k_separator_mu_loop, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.mu, st.vrec, mstate, st.nodes,
          labf);
   VMO_LAUNCHED("separator_mu_loop");
   return VMO_OK;
@@ -1030,13 +1055,13 @@ static vmo_status mu_loop_separator(OrderState& st, int64_t n, uint8_t* labf, cu
 vmo_status order_levels(OrderState& st, const OrderParams& op, cudaStream_t s, Scratch& sc) {
   const int64_t n = st.n;
   int N = st.nroots;
-  int32_t *ord2, *segl2, *next_count, *err;
+  int32_t *ord2, *seg2, *next_count, *err;
   float4* xo2;
   uint8_t* labf;
   unsigned long long *pk, *pre;
   NodeDev* next;
   VMO_TRY(sc.alloc(&ord2, std::max<int64_t>(n, 1)));
-  VMO_TRY(sc.alloc(&segl2, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&seg2, std::max<int64_t>(n, 1)));
   VMO_TRY(sc.alloc(&xo2, std::max<int64_t>(n, 1)));
   VMO_TRY(sc.alloc(&labf, std::max<int64_t>(n, 1)));
   VMO_TRY(sc.alloc(&pk, std::max<int64_t>(n, 1)));
@@ -1049,34 +1074,35 @@ vmo_status order_levels(OrderState& st, const OrderParams& op, cudaStream_t s, S
     VMO_TRY(two_means(st, N, op.d, op.km_iters, s, sc));
     dispatch_d(op.d, [&](auto DC) {
       constexpr int D = decltype(DC)::value;
-      launch(k_vertex_state<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.ord, st.seg, n, st.nodes, st.lab, st.vlab,
-                                                               st.vs);
+      launch(k_vertex_state<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.ord, st.seg, n, st.nodes, st.lab,
+                                                               st.vrec);
     });
     if (st.mu && op.mu_order_free) {
-      launch(k_pick, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vnode, st.vlab,
-             st.vs, st.vpick);
-      launch(k_separator_mu, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.mu, st.vlab, st.vpick, st.nodes,
+      launch(k_pick, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vrec, st.vpick);
+      launch(k_separator_mu, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.mu, st.vrec, st.vpick, st.nodes,
              labf);
     } else if (st.mu) {
       VMO_TRY(mu_loop_separator(st, n, labf, s, sc));
     } else {
-      launch(k_separator, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vnode, st.vlab,
-             st.vs, st.nodes, labf);
+      launch(k_separator, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vrec, st.nodes,
+             labf);
     }
     launch(k_pack, grid_for(n, kBlock), kBlock, 0, s, st.seg, labf, n, st.nodes, pk);
     VMO_LAUNCHED("separator");
     VMO_TRY(scan_inclusive<uint64_t>((const uint64_t*)pk, (uint64_t*)pre, n, s, sc));
-    launch(k_scatter, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.xo, st.seg, labf, n, st.nodes, pre, op.sbd, ord2, xo2,
-                                                     segl2);
+    // children first (they number the next level's nodes), then the scatter
+    // writes every position's next node
     VMO_CUDA(cudaMemsetAsync(next_count, 0, 4, s));
     const int max_depth = op.sep_rec ? std::min(op.max_depth, kSepRecMaxDepth) : op.max_depth;
     launch(k_children, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, st.pbase, op.min_part, max_depth, op.sbd,
            op.sep_rec, next, next_count, st.node_cap, st.tree, err);
-    launch(k_relabel, grid_for(n, kBlock), kBlock, 0, s, segl2, ord2, n, st.nodes, st.seg, st.vnode);
+    launch(k_scatter, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.xo, st.seg, labf, n, st.nodes, pre, op.sbd, ord2, xo2,
+                                                     seg2, st.vrec);
     VMO_LAUNCHED("partition");
-    // swap position arrays
-    VMO_CUDA(cudaMemcpyAsync(st.ord, ord2, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    VMO_CUDA(cudaMemcpyAsync(st.xo, xo2, n * sizeof(float4), cudaMemcpyDeviceToDevice, s));
+    // the scattered arrays become the current ones
+    std::swap(st.ord, ord2);
+    std::swap(st.xo, xo2);
+    std::swap(st.seg, seg2);
     int hN = 0, herr = 0;
     VMO_CUDA(cudaMemcpyAsync(&hN, next_count, 4, cudaMemcpyDeviceToHost, s));
     VMO_CUDA(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s));
@@ -1093,14 +1119,14 @@ vmo_status order_setup(OrderState& st, const float4* x, const std::vector<int64_
                        cudaStream_t s, Scratch& sc) {
   const int64_t n = pbase_host.back();
   const int P = (int)pbase_host.size() - 1;
+  if (n >= (int64_t(1) << 30) - 64) return invalid("ordering: more than 2^30 - 64 vertices");
   st.n = n;
   VMO_TRY(sc.alloc(&st.ord, std::max<int64_t>(n, 1)));
   VMO_TRY(sc.alloc(&st.xo, std::max<int64_t>(n, 1)));
   VMO_TRY(sc.alloc(&st.seg, std::max<int64_t>(n, 1)));
   VMO_TRY(sc.alloc(&st.lab, std::max<int64_t>(n, 1)));
-  VMO_TRY(sc.alloc(&st.vnode, std::max<int64_t>(n, 1)));
-  VMO_TRY(sc.alloc(&st.vlab, std::max<int64_t>(n, 1)));
-  VMO_TRY(sc.alloc(&st.vs, std::max<int64_t>(n, 1)));
+  VMO_TRY(sc.alloc(&st.vrec, std::max<int64_t>(n, 1)));
+  VMO_CUDA(cudaMemsetAsync(st.vrec, 0, std::max<int64_t>(n, 1) * sizeof(uint64_t), s));  // no vertex in a split node
   if (st.mu) VMO_TRY(sc.alloc(&st.vpick, std::max<int64_t>(n, 1)));
   VMO_TRY(sc.alloc(&st.pbase, P + 1));
   VMO_TRY(sc.alloc(&st.seeds, std::max(P, 1)));
@@ -1153,7 +1179,7 @@ vmo_status order_setup(OrderState& st, const float4* x, const std::vector<int64_
     VMO_LAUNCHED("roots");
   }
   if (n > 0) {
-    launch(k_seg_init, grid_for(n, kBlock), kBlock, 0, s, st.seg, st.vnode, st.ord, n, st.pbase, P, d_nop);
+    launch(k_seg_init, grid_for(n, kBlock), kBlock, 0, s, st.seg, st.ord, n, st.pbase, P, d_nop);
     VMO_LAUNCHED("seg_init");
   }
   // leaf roots become tree records directly

@@ -57,9 +57,8 @@ struct OrderState {
   float4* xo = nullptr;               // its coordinates
   int32_t* seg = nullptr;             // active node of each position, -1 if none
   uint8_t* lab = nullptr;             // 2-means label of each position
-  int32_t* vnode = nullptr;           // active node of each vertex
-  uint8_t* vlab = nullptr;            // 2-means label of each vertex (0: not in a split node)
-  float* vs = nullptr;                // plane distance of each vertex
+  uint64_t* vrec = nullptr;           // per vertex: (node << 2 | 2-means label, 0 if not in a split node) and
+                                      // the plane distance, one word (written by the separator phase)
   int64_t* pbase = nullptr;           // first position of every problem (P+1)
   uint64_t* seeds = nullptr;          // seed of every problem
   const int32_t* adj_ptr = nullptr;   // graph (global vertex ids)

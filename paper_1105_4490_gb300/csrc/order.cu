@@ -209,33 +209,42 @@ __global__ void k_assign(const float4* __restrict__ xo, const int32_t* __restric
     NodeDev& nd = nodes[s0];
     const int st = nd.state;
     if (!(final_pass ? (st != 2) : (st == 0))) return;
-    unsigned long long S[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-    unsigned long long c[2] = {0, 0};
+    // per thread: the first cluster's sums and the totals of all its items
+    // (the second cluster's are their difference); a fixed-point value
+    // rint(x 2^(30-e)) has |q| < 2^30, so it is converted as 32 bits
+    long long S1[4] = {0, 0, 0, 0}, T[4] = {0, 0, 0, 0};
+    int c1 = 0, cnt = 0;
     bool chg = false;
+    const float sc = exp2i_f(30 - nd.e);
 #pragma unroll
     for (int k = 0; k < kAssignItems; ++k) {
       const int64_t i = base + k * blockDim.x + threadIdx.x;
       if (k >= items || i >= n) continue;
-      uint8_t l;
-      long long q[4] = {0, 0, 0, 0};
-      assign_one<D>(xo, i, nd, it, lab, final_pass, l, q, chg);
+      const float4 x = xo[i];
+      const uint8_t l = (sqdist32<D>(x, nd.z1) <= sqdist32<D>(x, nd.z2)) ? 1 : 2;
       const bool first = l == 1;  // selects, not a computed index: the sums stay in registers
-      c[0] += first ? 1ull : 0ull;
-      c[1] += first ? 0ull : 1ull;
+      if (!final_pass) {
+        if (it > 0 && l != lab[i]) chg = true;
 #pragma unroll
-      for (int m = 0; m < D; ++m) {
-        S[0][m] += first ? (unsigned long long)q[m] : 0ull;
-        S[1][m] += first ? 0ull : (unsigned long long)q[m];
+        for (int m = 0; m < D; ++m) {
+          const int q = __float2int_rn(__fmul_rn(comp(x, m), sc));
+          T[m] += q;
+          S1[m] += first ? q : 0;
+        }
       }
+      lab[i] = l;
+      c1 += first ? 1 : 0;
+      ++cnt;
     }
     // block totals: counts, sums (not in the final pass) and the change flag
     const int warp = threadIdx.x >> 5, lane = lane_id();
     unsigned long long v[2 * 4 + 2];
+    v[0] = warp_sum64((unsigned long long)c1);
+    v[1] = warp_sum64((unsigned long long)(cnt - c1));
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      v[h] = warp_sum64(c[h]);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) v[2 + 4 * h + m] = m < D && !final_pass ? warp_sum64(S[h][m]) : 0ull;
+    for (int m = 0; m < 4; ++m) {
+      v[2 + m] = m < D && !final_pass ? warp_sum64((unsigned long long)S1[m]) : 0ull;
+      v[6 + m] = m < D && !final_pass ? warp_sum64((unsigned long long)(T[m] - S1[m])) : 0ull;
     }
     const bool any_chg = __any_sync(0xffffffffu, chg);
     if (lane == 0) {

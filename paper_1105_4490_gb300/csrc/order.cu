@@ -80,6 +80,20 @@ __global__ void k_maxabs(const float4* __restrict__ xo, const int32_t* __restric
 #pragma unroll
     for (int m = 0; m < D; ++m) mx = max(mx, __float_as_uint(fabsf(comp(x, m))));
   }
+  // a block of one node (the top of the recursion, where every warp would
+  // otherwise send an atomic to the same word) adds its maximum once
+  __shared__ int s_first;
+  __shared__ uint32_t s_max;
+  if (threadIdx.x == 0) { s_first = s; s_max = 0u; }
+  __syncthreads();
+  const int s0 = s_first;
+  if (__syncthreads_and(s < 0 || s == s0) && s0 >= 0) {
+    const uint32_t wm = __reduce_max_sync(0xffffffffu, mx);
+    if (lane_id() == 0) atomicMax(&s_max, wm);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(&nodes[s0].maxabs, s_max);
+    return;
+  }
   unsigned peers = __match_any_sync(0xffffffffu, s);
   uint32_t wm = __reduce_max_sync(peers, mx);
   if (s >= 0 && (int)lane_id() == __ffs(peers) - 1) atomicMax(&nodes[s].maxabs, wm);
@@ -409,10 +423,8 @@ __global__ void k_vertex_state(const float4* __restrict__ xo, const int32_t* __r
 // Every thread of the block calls it (s < 0 or l == 0: nothing to count).
 __device__ void count_labels(int s, uint8_t l, NodeDev* __restrict__ nodes) {
   __shared__ int s_first, s_cnt[3];
-  if (threadIdx.x == 0) s_first = -1;
+  if (threadIdx.x == 0) s_first = s;  // the node of the block's first position
   if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
-  __syncthreads();
-  if (s >= 0) atomicCAS(&s_first, -1, s);
   __syncthreads();
   const int s0 = s_first;
   const bool uniform = __syncthreads_and(s < 0 || s == s0) && s0 >= 0;
@@ -669,14 +681,12 @@ __global__ void k_pack(const int32_t* __restrict__ seg, const uint8_t* __restric
                        const NodeDev* __restrict__ nodes, unsigned long long* __restrict__ pk) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int s = seg[i];
+  const int s = seg[i];
+  const uint8_t l = labf[i];  // in flight with seg[i]
   unsigned long long v = 0;
   if (s >= 0) {
     const NodeDev& nd = nodes[s];
-    if (nd.c1 + nd.c2 + nd.c3 > 0) {
-      uint8_t l = labf[i];
-      v = (l == 1) ? 1ull : (l == 2 ? (1ull << 32) : 0ull);
-    }
+    if (nd.c1 + nd.c2 + nd.c3 > 0) v = (l == 1) ? 1ull : (l == 2 ? (1ull << 32) : 0ull);
   }
   pk[i] = v;
 }

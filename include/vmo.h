@@ -443,7 +443,7 @@ vmo_status vmo_finegrain_coords(vmo_hg hg, const float* bipartite_coords, float*
  *   radix_max_bits: widest digit of the binning sort's LSD passes, 8, 9 or
  *     10 (default 10: fewest passes);
  *   assign_items: positions per thread of the Lloyd assignment, 1, 2, 4 or
- *     8 (default 8; fewer are used when the blocks would not fill the GPU).
+ *     8 (default 4; fewer are used when the blocks would not fill the GPU).
  * The setting is process-wide and read at every launch.
  * ------------------------------------------------------------------------ */
 typedef struct {

@@ -443,19 +443,24 @@ vmo_status vmo_finegrain_coords(vmo_hg hg, const float* bipartite_coords, float*
  *   radix_max_bits: widest digit of the binning sort's LSD passes, 8, 9 or
  *     10 (default 10: fewest passes);
  *   assign_items: positions per thread of the Lloyd assignment, 1, 2, 4 or
- *     8 (default 4; fewer are used when the blocks would not fill the GPU).
+ *     8 (default 4; fewer are used when the blocks would not fill the GPU);
+ *   small_bin_points: a layout level whose problems all have at most this
+ *     many vertices (0 ... 2,048) is binned by one block per problem (keys,
+ *     sort, gather and cell charges in one launch) instead of the device-wide
+ *     sequence; 0 turns it off (default 2,048).
  * The setting is process-wide and read at every launch.
  * ------------------------------------------------------------------------ */
 typedef struct {
   int64_t small_step_threads;
   int32_t radix_max_bits;
   int32_t assign_items;
+  int32_t small_bin_points;
 } vmo_tuning;
 
 /* Current setting (host struct out). */
 void vmo_get_tuning(vmo_tuning* out);
 
-/* Sets all three choices.  Errors: VMO_ERR_INVALID for a null pointer or a
+/* Sets all four choices.  Errors: VMO_ERR_INVALID for a null pointer or a
  * value outside the ranges above (nothing is changed then).  Not to be called
  * while another thread is inside a library call. */
 vmo_status vmo_set_tuning(const vmo_tuning* tuning);
@@ -463,7 +468,7 @@ vmo_status vmo_set_tuning(const vmo_tuning* tuning);
 /* Timed search for the setting that orders the given matrices fastest: from
  * the current setting, each choice in turn over its candidates
  * (small_step_threads 0 ... 155,648; radix_max_bits 8, 9, 10; assign_items
- * 1, 2, 4, 8), every candidate timed as the median of `reps` calls of
+ * 1, 2, 4, 8; small_bin_points 0, 512, 2,048), every candidate timed as the median of `reps` calls of
  * vmo_batch_order(mats, count, NULL, params, BBD) after one untimed call, with
  * CUDA events on `stream`.  The fastest becomes the process-wide setting.
  * mats: host array of `count` vmo_csr (device pointers inside), as for

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "blocksort.cuh"
 #include "layout.cuh"
 
 namespace vmo {
@@ -174,24 +175,43 @@ __global__ void k_step0(const uint32_t* __restrict__ bb, const ProbDev* __restri
   s0[p] = (k > 0) ? (float)(sigma * Lbox / pow((double)k, 1.0 / D)) : 0.0f;
 }
 
-template <int D>
+// Cell keys of the points.  Each thread takes U points, strided by the block
+// so that every load is coalesced, and issues all their loads before the
+// arithmetic (U = 4 on large levels: more bytes in flight per SM; U = 1 on
+// small ones: more blocks); thread 0 advances the level's step counter and
+// the grid resets the next bounding boxes.
+constexpr int64_t kKeyItemsMin = int64_t(1) << 20;  // points of a level that take 4 per thread
+
+template <int D, int U>
 __global__ void __launch_bounds__(kBlock) k_keys(const float4* __restrict__ x, int64_t K, const int32_t* __restrict__ vprob,
                                                  const ProbDev* __restrict__ prob, const uint32_t* __restrict__ bb,
                                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                  uint32_t* __restrict__ bb_next, int nreset, int32_t* __restrict__ tctr) {
   pdl_wait();
-  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v == 0) ++*tctr;  // the level's step (read by the step kernel of this step)
-  if (v < nreset) bb_next[v] = ((v & 7) < 4) ? 0xFFFFFFFFu : 0u;
-  if (v >= K) return;
-  int pb = vprob[v];
-  int L = prob[pb].L;
-  float lo[D], s;
-  grid_frame<D>(bb, pb, L, lo, &s);
-  int32_t c[D];
-  cell_of<D>(x[v], lo, s, L, c);
-  keys[v] = (uint32_t)rowmajor<D>(c, 1 << L);
-  vals[v] = (uint32_t)v;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gt == 0) ++*tctr;  // the level's step (read by the step kernel of this step)
+  for (int64_t r = gt; r < nreset; r += (int64_t)gridDim.x * blockDim.x) bb_next[r] = ((r & 7) < 4) ? 0xFFFFFFFFu : 0u;
+  const int64_t v0 = (int64_t)blockIdx.x * blockDim.x * U + threadIdx.x;
+  float4 xv[U];
+  int pb[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t v = v0 + (int64_t)u * blockDim.x;
+    xv[u] = v < K ? x[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+    pb[u] = v < K ? vprob[v] : 0;
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t v = v0 + (int64_t)u * blockDim.x;
+    if (v >= K) break;
+    const int L = prob[pb[u]].L;
+    float lo[D], s;
+    grid_frame<D>(bb, pb[u], L, lo, &s);
+    int32_t c[D];
+    cell_of<D>(xv[u], lo, s, L, c);
+    keys[v] = (uint32_t)rowmajor<D>(c, 1 << L);
+    vals[v] = (uint32_t)v;
+  }
 }
 
 // a[lo..hi) = v, with 16-byte stores over the aligned middle of the range
@@ -289,8 +309,8 @@ __device__ __forceinline__ void cell_add(const float4& p, float wq, float* S, fl
 // Points q0, q0 + stride, ... < q1 added in that order; four loads issued
 // before their additions.
 template <int D>
-__device__ __forceinline__ void cell_sum(const float4* __restrict__ xs, const float* __restrict__ ws, int64_t q0,
-                                         int64_t q1, int64_t stride, float* S, float& W) {
+__device__ __forceinline__ void cell_sum(const float4* xs, const float* ws, int64_t q0, int64_t q1, int64_t stride,
+                                         float* S, float& W) {
   int64_t q = q0;
   for (; q + 3 * stride < q1; q += 4 * stride) {
     float4 p[4];
@@ -415,6 +435,157 @@ __global__ void __launch_bounds__(kBlock) k_agg_small(const ProbDev* __restrict_
   for (int l = min(pr.L - 1, small_level_max(D)); l >= 2; --l) {
     const int64_t n = int64_t(1) << (D * l);
     for (int64_t c = threadIdx.x; c < n; c += blockDim.x) agg_cell<D>(pr, pb, l, c, St, Wt, CP);
+    __syncthreads();
+  }
+}
+
+// One-block binning of a step for levels whose problems all have at most
+// kSortTile points and kBinCells finest cells: one block per problem stages
+// its points in shared memory, computes the keys (as k_keys), sorts (key,
+// local index) stably in shared memory (as the one-tile radix sort), gathers
+// (as k_gather, and writes the sorted vertex ids), sums the finest cells from
+// the staged points (as k_agg_finest: serially up to kCellSerial points, else
+// lane-strided with the xor tree) and every coarser level (agg_cell, a block
+// barrier between levels).  The arithmetic and the order of every sum are
+// those kernels', so the results are bit-identical, from one launch instead
+// of five or more.  The cell charges are read back by other threads of the
+// block after a barrier, so those pointers carry no __restrict__.  keys
+// (optional): the unsorted keys by vertex, as k_keys writes them.
+constexpr int kBinCells = 4096;
+
+struct BinSmem {
+  float4 xin[kSortTile];      // the problem's points by local index
+  float win[kSortTile];       // their weights (1 without weights)
+  int32_t cs[kBinCells + 1];  // cell start table (sorted positions)
+  TileSortSmem sort;
+};
+
+template <int D>
+__global__ void __launch_bounds__(kSortThreads) k_bin_small(
+    const float4* __restrict__ x, const float* __restrict__ w, const ProbDev* __restrict__ prob,
+    const uint32_t* __restrict__ bb, uint32_t* __restrict__ bb_next, int32_t* __restrict__ tctr,
+    uint32_t* __restrict__ keys, uint32_t* __restrict__ svals, float4* __restrict__ xs, float* __restrict__ ws,
+    uint32_t* __restrict__ scell, int32_t* __restrict__ cst, float4* __restrict__ XP, float4* St, float* Wt,
+    float4* CP) {
+  pdl_wait();
+  extern __shared__ __align__(16) unsigned char bin_raw[];
+  BinSmem& sm = *reinterpret_cast<BinSmem*>(bin_raw);
+  const int pb = blockIdx.x;
+  const ProbDev pr = prob[pb];
+  const int k = pr.k;
+  const int64_t vb = pr.vbase;
+  if (pb == 0 && threadIdx.x == 0) ++*tctr;  // the level's step
+  if (threadIdx.x < 8) bb_next[pb * 8 + threadIdx.x] = threadIdx.x < 4 ? 0xFFFFFFFFu : 0u;
+  float lo[D], s;
+  grid_frame<D>(bb, pb, pr.L, lo, &s);
+  {
+    // points, weights and keys by local index; a thread's loads issued first
+    float4 xv[kSortItems];
+    float wv[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      const int i = threadIdx.x + j * kSortThreads;
+      xv[j] = i < k ? x[vb + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      wv[j] = (i < k && w) ? w[vb + i] : 1.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      const int i = threadIdx.x + j * kSortThreads;
+      if (i < k) {
+        sm.xin[i] = xv[j];
+        sm.win[i] = wv[j];
+        int32_t c[D];
+        cell_of<D>(xv[j], lo, s, pr.L, c);
+        const uint32_t key = (uint32_t)rowmajor<D>(c, 1 << pr.L);
+        sm.sort.key[0][i] = key;
+        sm.sort.val[0][i] = (uint32_t)i;
+        if (keys) keys[vb + i] = key;
+      }
+    }
+  }
+  const int cur = tile_sort_smem(sm.sort, k, D * pr.L);
+  const uint32_t* skey = sm.sort.key[cur];
+  const uint32_t* sloc = sm.sort.val[cur];
+  // gather and cell start table (global for the step kernel, shared here)
+  const int64_t ncell = int64_t(1) << (D * pr.L);
+  const int64_t e = (vb + pb + 1) & ~int64_t(1);
+  int32_t* cs = cst + pr.fbase + pb;
+  for (int i = threadIdx.x; i < k; i += kSortThreads) {
+    const int64_t p = vb + i;
+    const uint32_t li = sloc[i];
+    svals[p] = (uint32_t)(vb + li);
+    const float4 xv = sm.xin[li];
+    const float wv = sm.win[li];
+    xs[p] = xv;
+    if (ws) ws[p] = wv;
+    const float xc[4] = {xv.x, xv.y, xv.z, xv.w};
+    pair_store<D>(XP, e + i, xc, wv);
+    if (i == k - 1 && (k & 1)) {
+      const float zero[4] = {0.f, 0.f, 0.f, 0.f};
+      pair_store<D>(XP, e + k, zero, 0.0f);
+    }
+    int32_t c[D];
+    cell_of<D>(xv, lo, s, pr.L, c);
+    uint32_t packed = 0;
+#pragma unroll
+    for (int m = 0; m < D; ++m) packed |= (uint32_t)c[m] << (m * field_bits(D));
+    scell[p] = packed;
+    const int64_t key = skey[i];
+    const int64_t prev = i == 0 ? -1 : (int64_t)skey[i - 1];
+    for (int64_t q = prev + 1; q <= key; ++q) sm.cs[q] = (int32_t)p;
+    fill_i32(cs, prev + 1, key + 1, (int32_t)p);
+    if (i == k - 1) {
+      for (int64_t q = key + 1; q <= ncell; ++q) sm.cs[q] = (int32_t)(vb + k);
+      fill_i32(cs, key + 1, ncell + 1, (int32_t)(vb + k));
+    }
+  }
+  if (k == 0)
+    for (int64_t c = threadIdx.x; c <= ncell; c += kSortThreads) {
+      cs[c] = (int32_t)vb;
+      sm.cs[c] = (int32_t)vb;
+    }
+  __syncthreads();
+  // finest cells from the staged points, a warp per 32 consecutive cells
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  const int64_t cfin = pr.cbase + lvl_off(D, pr.L);
+  for (int64_t c0 = (int64_t)warp * 32; c0 < ncell; c0 += kSortThreads) {
+    const int64_t c = c0 + lane;
+    const bool valid = c < ncell;
+    int q0 = 0, q1 = 0;  // problem-local sorted positions
+    if (valid && k > 0) {
+      q0 = sm.cs[c] - (int)vb;
+      q1 = sm.cs[c + 1] - (int)vb;
+    }
+    const int64_t idx = cfin + c, pidx = idx + pb + 1;
+    const bool big = valid && q1 - q0 > kCellSerial;
+    if (valid && !big) {
+      float S[4] = {0.f, 0.f, 0.f, 0.f};
+      float W = 0.f;
+      for (int q = q0; q < q1; ++q) cell_add<D>(sm.xin[sloc[q]], sm.win[sloc[q]], S, W);
+      store_cell<D>(idx, pidx, S, W, St, Wt, CP);
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, big);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int b0 = __shfl_sync(0xffffffffu, q0, src), b1 = __shfl_sync(0xffffffffu, q1, src);
+      float S[4] = {0.f, 0.f, 0.f, 0.f};
+      float W = 0.f;
+      for (int q = b0 + lane; q < b1; q += 32) cell_add<D>(sm.xin[sloc[q]], sm.win[sloc[q]], S, W);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int m = 0; m < D; ++m) S[m] += __shfl_xor_sync(0xffffffffu, S[m], o);
+        W += __shfl_xor_sync(0xffffffffu, W, o);
+      }
+      if (lane == src) store_cell<D>(idx, pidx, S, W, St, Wt, CP);
+    }
+  }
+  __syncthreads();
+  // coarser levels down to 2, each from its children
+  for (int l = pr.L - 1; l >= 2; --l) {
+    const int64_t n = int64_t(1) << (D * l);
+    for (int64_t c = threadIdx.x; c < n; c += kSortThreads) agg_cell<D>(pr, pb, l, c, St, Wt, CP);
     __syncthreads();
   }
 }
@@ -1485,9 +1656,24 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
   VMO_TRY(sc.alloc(&fb, P + 1));
   if (lb.net_ptr) VMO_TRY(sc.alloc(&z, std::max<int64_t>(lb.nnets, 1)));
   VMO_CUDA(cudaMemcpyAsync(fb, lb.fbase.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  // levels whose problems all fit one sort tile are binned by one block per
+  // problem (k_bin_small) when the tuning allows it
+  int64_t kmax = 0;
+  for (int p = 0; p < P; ++p) kmax = std::max(kmax, lb.vbase[p + 1] - lb.vbase[p]);
+  bool bin1 = kmax <= std::min<int64_t>(kSortTile, g_tuning.small_bin_points.load(std::memory_order_relaxed));
+  for (int p = 0; p < P && bin1; ++p) bin1 = (int64_t(1) << (d * lb.L[p])) <= kBinCells;
+  if (bin1)
+    dispatch_d(d, [&](auto DC) {
+      constexpr int D = decltype(DC)::value;
+      if (cudaFuncSetAttribute(k_bin_small<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BinSmem)) !=
+          cudaSuccess) {
+        (void)cudaGetLastError();
+        bin1 = false;  // the device-wide sequence then
+      }
+    });
   SortSegments segs;
   bool segmented = P > 1;
-  if (segmented) VMO_TRY(make_sort_segments(lb.vbase, &segs, s, sc));
+  if (segmented && !bin1) VMO_TRY(make_sort_segments(lb.vbase, &segs, s, sc));
   const int nreset = 8 * P;
   launch(k_bbox_reset, grid_for(16 * P, kBlock), kBlock, 0, s, bb, 16 * P);
   VMO_LAUNCHED("bbox_reset");
@@ -1548,31 +1734,41 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
         cudaMemsetAsync(yatt, 0, K * sizeof(float4), as);
       }
       if (side) cudaEventRecord(ev_join, side);
-      launch(k_keys<D>, grid_for(std::max<int64_t>(K, nreset), kBlock), kBlock, 0, ms, x, K, lb.vprob.ptr, lb.prob.ptr,
-                                                                                  cur, keys, vals, nxt, nreset, tctr);
-      if (keys_out && t == 0) cudaMemcpyAsync(keys_out, keys, K * 4, cudaMemcpyDeviceToDevice, ms);
-      bool in_b = false;
-      VMO_TRY(radix_sort_u32_pingpong(keys, vals, skeys, svals, K, D * lb.maxL, segmented ? &segs : nullptr, &in_b, ms,
-                                      sc));
-      if (!in_b) {  // sorted pairs are in (keys, vals): use them as (skeys, svals) from here on
-        std::swap(keys, skeys);
-        std::swap(vals, svals);
-      }
-      launch(k_gather<D>, grid_for(K, kBlock), kBlock, 0, ms, svals, skeys, K, x, lb.w, lb.vprob.ptr, lb.prob.ptr, cur,
-             xs, ws, scell, cst, XP);
-      launch(k_agg_finest<D>, grid_for(nfine, kBlock), kBlock, 0, ms, nfine, fb, P, lb.prob.ptr, xs, ws, cst, St, Wt,
-             CP);
-      for (int stp = 1; stp <= lb.maxL - 2; ++stp) {
-        const int64_t* off = lb.aggoff.ptr + (size_t)stp * (P + 1);
-        int64_t n = 0;
-        for (int p = 0; p < P; ++p) {
-          int l = lb.L[p] - stp;
-          n += l > small_level_max(D) ? (int64_t(1) << (D * l)) : 0;
+      if (bin1) {
+        launch(k_bin_small<D>, (unsigned)P, kSortThreads, sizeof(BinSmem), ms, x, lb.w, lb.prob.ptr, cur, nxt, tctr,
+               keys_out && t == 0 ? keys : nullptr, svals, xs, ws, scell, cst, XP, St, Wt, CP);
+        if (keys_out && t == 0) cudaMemcpyAsync(keys_out, keys, K * 4, cudaMemcpyDeviceToDevice, ms);
+      } else {
+        if (K >= kKeyItemsMin)
+          launch(k_keys<D, 4>, grid_for((K + 3) / 4, kBlock), kBlock, 0, ms, x, K, lb.vprob.ptr, lb.prob.ptr, cur, keys,
+                 vals, nxt, nreset, tctr);
+        else
+          launch(k_keys<D, 1>, grid_for(K, kBlock), kBlock, 0, ms, x, K, lb.vprob.ptr, lb.prob.ptr, cur, keys, vals, nxt,
+                 nreset, tctr);
+        if (keys_out && t == 0) cudaMemcpyAsync(keys_out, keys, K * 4, cudaMemcpyDeviceToDevice, ms);
+        bool in_b = false;
+        VMO_TRY(radix_sort_u32_pingpong(keys, vals, skeys, svals, K, D * lb.maxL, segmented ? &segs : nullptr, &in_b,
+                                        ms, sc));
+        if (!in_b) {  // sorted pairs are in (keys, vals): use them as (skeys, svals) from here on
+          std::swap(keys, skeys);
+          std::swap(vals, svals);
         }
-        if (n == 0) continue;
-        launch(k_agg_level<D>, grid_for(n, kBlock), kBlock, 0, ms, stp, off, P, n, lb.prob.ptr, St, Wt, CP);
+        launch(k_gather<D>, grid_for(K, kBlock), kBlock, 0, ms, svals, skeys, K, x, lb.w, lb.vprob.ptr, lb.prob.ptr,
+               cur, xs, ws, scell, cst, XP);
+        launch(k_agg_finest<D>, grid_for(nfine, kBlock), kBlock, 0, ms, nfine, fb, P, lb.prob.ptr, xs, ws, cst, St, Wt,
+               CP);
+        for (int stp = 1; stp <= lb.maxL - 2; ++stp) {
+          const int64_t* off = lb.aggoff.ptr + (size_t)stp * (P + 1);
+          int64_t n = 0;
+          for (int p = 0; p < P; ++p) {
+            int l = lb.L[p] - stp;
+            n += l > small_level_max(D) ? (int64_t(1) << (D * l)) : 0;
+          }
+          if (n == 0) continue;
+          launch(k_agg_level<D>, grid_for(n, kBlock), kBlock, 0, ms, stp, off, P, n, lb.prob.ptr, St, Wt, CP);
+        }
+        if (lb.maxL >= 3) launch(k_agg_small<D>, (unsigned)P, kBlock, 0, ms, lb.prob.ptr, St, Wt, CP);
       }
-      if (lb.maxL >= 3) launch(k_agg_small<D>, (unsigned)P, kBlock, 0, ms, lb.prob.ptr, St, Wt, CP);
       if (side) cudaStreamWaitEvent(ms, ev_join, 0);
       const bool timed = stats_timing();
       if (timed) stats_time_begin(ms);

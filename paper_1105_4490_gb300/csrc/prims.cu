@@ -14,7 +14,7 @@
 
 #include <type_traits>
 
-#include "vmo_internal.cuh"
+#include "blocksort.cuh"
 
 namespace vmo {
 
@@ -23,36 +23,6 @@ namespace {
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
-
-template <class T>
-__device__ T warp_inclusive(T v) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    T t = __shfl_up_sync(0xffffffffu, v, o);
-    if ((int)lane_id() >= o) v += t;
-  }
-  return v;
-}
-
-// Block-wide exclusive scan of one value per thread (blockDim.x <= 1024).
-template <class T>
-__device__ T block_exclusive(T v, T* warp_sums, T* total) {
-  const int lane = lane_id(), warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  T inc = warp_inclusive(v);
-  if (lane == 31) warp_sums[warp] = inc;
-  __syncthreads();
-  if (warp == 0) {
-    T s = (lane < nw) ? warp_sums[lane] : T(0);
-    T si = warp_inclusive(s);
-    if (lane < nw) warp_sums[lane] = si - s;
-    if (lane == nw - 1) warp_sums[32] = si;
-  }
-  __syncthreads();
-  T out = warp_sums[warp] + inc - v;
-  if (total) *total = warp_sums[32];
-  __syncthreads();
-  return out;
-}
 
 template <class T>
 __global__ void scan_reduce_kernel(const T* __restrict__ in, int64_t n, T* __restrict__ partial) {
@@ -136,9 +106,6 @@ vmo_status scan_impl(const T* in, T* out, int64_t n, T* total, cudaStream_t s, S
 // passes of at most 10 bits (or the tuned cap, 8 or 9), then the smallest
 // listed width covering the key bits in that many passes (18-bit cell keys:
 // 2 passes of 9 bits).
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = kSortTile / kSortThreads;  // 8
-constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kMaxRadixBits = 10;
 
 struct TileInfo {
@@ -383,64 +350,16 @@ __global__ void __launch_bounds__(kSortThreads) radix_tile_sort_kernel(const uin
                                                                        uint32_t* __restrict__ vals_out, int64_t n,
                                                                        int bits, SortSegments sg) {
   pdl_wait();
-  constexpr int R = 256;
-  __shared__ uint32_t sk[2][kSortTile], sv[2][kSortTile];
-  __shared__ uint32_t wcnt[kSortWarps][R];
-  __shared__ uint32_t dbase[R];
-  __shared__ uint32_t ws[33];
-  const int lane = lane_id(), warp = threadIdx.x >> 5;
-  const TileInfo ti = tile_info(sg, n, blockIdx.x, R);
+  __shared__ TileSortSmem sm;
+  const TileInfo ti = tile_info(sg, n, blockIdx.x, 256);
   for (int i = threadIdx.x; i < ti.count; i += blockDim.x) {
-    sk[0][i] = keys[ti.start + i];
-    sv[0][i] = vals[ti.start + i];
+    sm.key[0][i] = keys[ti.start + i];
+    sm.val[0][i] = vals[ti.start + i];
   }
-  int cur = 0;
-  const unsigned lt = (1u << lane) - 1u;
-  for (int shift = 0; shift < bits; shift += 8) {
-    for (int i = threadIdx.x; i < kSortWarps * R; i += blockDim.x) (&wcnt[0][0])[i] = 0;
-    __syncthreads();
-    uint32_t rank[kSortItems], dig[kSortItems];
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-      const int idx = warp * (32 * kSortItems) + j * 32 + lane;
-      const bool valid = idx < ti.count;
-      const uint32_t dg = valid ? ((sk[cur][idx] >> shift) & (R - 1)) : (uint32_t)R;
-      dig[j] = dg;
-      const unsigned peers = __match_any_sync(0xffffffffu, dg);
-      const uint32_t base = valid ? wcnt[warp][dg] : 0u;
-      rank[j] = base + __popc(peers & lt);
-      __syncwarp();
-      if (valid && lane == __ffs(peers) - 1) wcnt[warp][dg] = base + __popc(peers);
-      __syncwarp();
-    }
-    __syncthreads();
-    // per digit: prefix over the warps, total; then bases by a block scan
-    uint32_t tot = 0;
-    {
-      const int dg = threadIdx.x;  // blockDim.x == R
-      for (int w = 0; w < kSortWarps; ++w) {
-        const uint32_t c = wcnt[w][dg];
-        wcnt[w][dg] = tot;
-        tot += c;
-      }
-    }
-    const uint32_t ex = block_exclusive<uint32_t>(tot, ws, nullptr);
-    dbase[threadIdx.x] = ex;
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-      if (dig[j] >= (uint32_t)R) continue;
-      const int idx = warp * (32 * kSortItems) + j * 32 + lane;
-      const uint32_t dst = dbase[dig[j]] + wcnt[warp][dig[j]] + rank[j];
-      sk[cur ^ 1][dst] = sk[cur][idx];
-      sv[cur ^ 1][dst] = sv[cur][idx];
-    }
-    __syncthreads();
-    cur ^= 1;
-  }
+  const int cur = tile_sort_smem(sm, ti.count, bits);
   for (int i = threadIdx.x; i < ti.count; i += blockDim.x) {
-    keys_out[ti.start + i] = sk[cur][i];
-    vals_out[ti.start + i] = sv[cur][i];
+    keys_out[ti.start + i] = sm.key[cur][i];
+    vals_out[ti.start + i] = sm.val[cur][i];
   }
 }
 

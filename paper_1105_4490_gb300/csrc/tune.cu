@@ -1,7 +1,8 @@
 // Autotuner of the launch shapes that never change a result: the largest
 // step launch that takes the two-rows-in-flight variant of the step kernel,
-// the widest radix digit of the binning sort, and the positions per thread
-// of the Lloyd assignment.  Every candidate orders the caller's matrices
+// the widest radix digit of the binning sort, the positions per thread of
+// the Lloyd assignment, and the largest problem whose level is binned by one
+// block per problem.  Every candidate orders the caller's matrices
 // through vmo_batch_order; the fastest (median of the repetitions, CUDA
 // events on the caller's stream) becomes the process-wide setting.  The
 // paper has no counterpart: these are choices of this GPU implementation.
@@ -21,6 +22,7 @@ vmo_tuning current() {
   t.small_step_threads = g_tuning.small_step_threads.load();
   t.radix_max_bits = g_tuning.radix_max_bits.load();
   t.assign_items = g_tuning.assign_items.load();
+  t.small_bin_points = g_tuning.small_bin_points.load();
   return t;
 }
 
@@ -28,6 +30,7 @@ void apply(const vmo_tuning& t) {
   g_tuning.small_step_threads.store(t.small_step_threads);
   g_tuning.radix_max_bits.store(t.radix_max_bits);
   g_tuning.assign_items.store(t.assign_items);
+  g_tuning.small_bin_points.store(t.small_bin_points);
 }
 
 vmo_status valid(const vmo_tuning* t) {
@@ -37,6 +40,8 @@ vmo_status valid(const vmo_tuning* t) {
   if (t->radix_max_bits < 8 || t->radix_max_bits > 10) return invalid("radix_max_bits must be 8, 9 or 10");
   if (t->assign_items != 1 && t->assign_items != 2 && t->assign_items != 4 && t->assign_items != 8)
     return invalid("assign_items must be 1, 2, 4 or 8");
+  if (t->small_bin_points < 0 || t->small_bin_points > kSortTile)
+    return invalid("small_bin_points must be in [0, 2048]");
   return VMO_OK;
 }
 
@@ -96,19 +101,21 @@ extern "C" vmo_status vmo_autotune(const vmo_csr* mats, int32_t count, const vmo
   double bms = 0.0, dms = 0.0;
   vmo_status st = time_order(mats, count, params, reps, perm, s, &bms);
   dms = bms;
-  // coordinate descent over the three choices, from the current setting
+  // coordinate descent over the four choices, from the current setting
   const std::vector<int64_t> steps = {0, 4864, 9728, 19456, 38912, 77824, 155648};
   const std::vector<int> bits = {8, 9, 10};
   const std::vector<int> items = {1, 2, 4, 8};
-  for (int knob = 0; knob < 3 && st == VMO_OK; ++knob) {
-    const size_t nc = knob == 0 ? steps.size() : knob == 1 ? bits.size() : items.size();
+  const std::vector<int> bins = {0, 512, kSortTile};
+  for (int knob = 0; knob < 4 && st == VMO_OK; ++knob) {
+    const size_t nc = knob == 0 ? steps.size() : knob == 1 ? bits.size() : knob == 2 ? items.size() : bins.size();
     for (size_t c = 0; c < nc && st == VMO_OK; ++c) {
       vmo_tuning t = bt;
       if (knob == 0) t.small_step_threads = steps[c];
       if (knob == 1) t.radix_max_bits = bits[c];
       if (knob == 2) t.assign_items = items[c];
+      if (knob == 3) t.small_bin_points = bins[c];
       if (t.small_step_threads == bt.small_step_threads && t.radix_max_bits == bt.radix_max_bits &&
-          t.assign_items == bt.assign_items)
+          t.assign_items == bt.assign_items && t.small_bin_points == bt.small_bin_points)
         continue;
       apply(t);
       double ms = 0.0;

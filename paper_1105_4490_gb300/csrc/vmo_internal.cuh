@@ -248,6 +248,7 @@ struct Tuning {
   std::atomic<int64_t> small_step_threads{152 * 4 * 32};
   std::atomic<int> radix_max_bits{10};
   std::atomic<int> assign_items{4};  // 4 measured best for a million-point Lloyd round (8 and 2 slower)
+  std::atomic<int> small_bin_points{kSortTile};
 };
 extern Tuning g_tuning;
 struct PdlScope {

@@ -39,7 +39,8 @@ class _HostCsr(C.Structure):
 
 
 class _Tuning(C.Structure):
-    _fields_ = [("small_step_threads", C.c_int64), ("radix_max_bits", C.c_int32), ("assign_items", C.c_int32)]
+    _fields_ = [("small_step_threads", C.c_int64), ("radix_max_bits", C.c_int32), ("assign_items", C.c_int32),
+                ("small_bin_points", C.c_int32)]
 
 
 class _Params(C.Structure):
@@ -570,9 +571,9 @@ def get_tuning() -> dict:
     return {f: getattr(t, f) for f, _ in _Tuning._fields_}
 
 
-def set_tuning(small_step_threads: int, radix_max_bits: int, assign_items: int) -> None:
-    """vmo_set_tuning: all three choices at once."""
-    t = _Tuning(small_step_threads, radix_max_bits, assign_items)
+def set_tuning(small_step_threads: int, radix_max_bits: int, assign_items: int, small_bin_points: int = 2048) -> None:
+    """vmo_set_tuning: all four choices at once."""
+    t = _Tuning(small_step_threads, radix_max_bits, assign_items, small_bin_points)
     _check(load().vmo_set_tuning(C.byref(t)))
 
 

@@ -91,12 +91,13 @@ def test_tuning_host_calls():
     (unchanged then), restored."""
     import paper_1105_4490_gb300 as V
     t0 = V.get_tuning()
-    assert t0 == {"small_step_threads": 19456, "radix_max_bits": 10, "assign_items": 4}
-    V.set_tuning(0, 8, 2)
-    assert V.get_tuning() == {"small_step_threads": 0, "radix_max_bits": 8, "assign_items": 2}
-    for bad in ((-1, 10, 8), (0, 7, 8), (0, 11, 8), (0, 10, 3), (0, 10, 16)):
+    assert t0 == {"small_step_threads": 19456, "radix_max_bits": 10, "assign_items": 4, "small_bin_points": 2048}
+    V.set_tuning(0, 8, 2, 0)
+    got = {"small_step_threads": 0, "radix_max_bits": 8, "assign_items": 2, "small_bin_points": 0}
+    assert V.get_tuning() == got
+    for bad in ((-1, 10, 8), (0, 7, 8), (0, 11, 8), (0, 10, 3), (0, 10, 16), (0, 10, 8, -1), (0, 10, 8, 2049)):
         with pytest.raises(V.VmoError):
             V.set_tuning(*bad)
-        assert V.get_tuning() == {"small_step_threads": 0, "radix_max_bits": 8, "assign_items": 2}
+        assert V.get_tuning() == got
     V.set_tuning(**t0)
     assert V.get_tuning() == t0

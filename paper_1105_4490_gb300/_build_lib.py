@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvmo.so")
 SOURCES = ["api.cu", "order.cu", "layout.cu", "build.cu", "prims.cu", "components.cu", "batch.cu", "noalloc.cu", "server.cu", "kmeans.cu", "tune.cu", "matching.cu", "mmio.cu", "peak.cu"]
-HEADERS = ["vmo_internal.cuh", "layout.cuh", "order.cuh", "components.cuh"]
+HEADERS = ["vmo_internal.cuh", "layout.cuh", "order.cuh", "components.cuh", "blocksort.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -200,22 +200,35 @@ __global__ void k_fold_reps(NodeDev* __restrict__ nodes, int N, unsigned long lo
   reinterpret_cast<unsigned long long*>(&nodes[s].S1[0])[t] += sum;
 }
 
-template <int D>
+template <int D, int ITEMS>
 __global__ void k_assign(const float4* __restrict__ xo, const int32_t* __restrict__ seg, int64_t n, int it,
                          NodeDev* __restrict__ nodes, uint8_t* __restrict__ lab, int final_pass,
-                         unsigned long long* __restrict__ rep, int items) {
+                         unsigned long long* __restrict__ rep) {
+  constexpr int items = ITEMS;
   __shared__ int s_first;
   __shared__ unsigned long long red[kBlock / 32][2 * 4 + 2];
   const int64_t base = (int64_t)blockIdx.x * (items * blockDim.x);
   if (threadIdx.x == 0) s_first = base < n ? seg[base] : -1;
   __syncthreads();
   const int s0 = s_first;
-  int sv[kAssignItems];
+  // every load of the thread's positions (node, coordinates, previous label)
+  // issued before the barrier, so that they are in flight together
+  int sv[ITEMS];
+  float4 xv[ITEMS];
+  uint8_t lv[ITEMS];
+  const bool prev = it > 0 && !final_pass;
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    const int64_t i = base + k * blockDim.x + threadIdx.x;
+    const bool in = k < items && i < n;
+    sv[k] = in ? seg[i] : -1;
+    xv[k] = in ? xo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    lv[k] = in && prev ? lab[i] : 0;
+  }
   bool same = true;
 #pragma unroll
-  for (int k = 0; k < kAssignItems; ++k) {
+  for (int k = 0; k < ITEMS; ++k) {
     const int64_t i = base + k * blockDim.x + threadIdx.x;
-    sv[k] = k < items && i < n ? seg[i] : -1;
     same = same && (k >= items || i >= n || sv[k] == s0);
   }
   const bool uniform = __syncthreads_and(same) && s0 >= 0;
@@ -231,14 +244,14 @@ __global__ void k_assign(const float4* __restrict__ xo, const int32_t* __restric
     bool chg = false;
     const float sc = exp2i_f(30 - nd.e);
 #pragma unroll
-    for (int k = 0; k < kAssignItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
       const int64_t i = base + k * blockDim.x + threadIdx.x;
       if (k >= items || i >= n) continue;
-      const float4 x = xo[i];
+      const float4 x = xv[k];
       const uint8_t l = (sqdist32<D>(x, nd.z1) <= sqdist32<D>(x, nd.z2)) ? 1 : 2;
       const bool first = l == 1;  // selects, not a computed index: the sums stay in registers
       if (!final_pass) {
-        if (it > 0 && l != lab[i]) chg = true;
+        if (prev && l != lv[k]) chg = true;
 #pragma unroll
         for (int m = 0; m < D; ++m) {
           const int q = __float2int_rn(__fmul_rn(comp(x, m), sc));
@@ -347,6 +360,19 @@ inline unsigned assign_grid(int64_t n) {
   return (unsigned)std::max<int64_t>(1, (n + per - 1) / per);
 }
 
+// One Lloyd assignment launch with the instantiation for assign_items(n).
+template <int D>
+void launch_assign(int64_t n, cudaStream_t s, const float4* xo, const int32_t* seg, int it, NodeDev* nodes,
+                   uint8_t* lab, int final_pass, unsigned long long* rep) {
+  const unsigned g = assign_grid(n);
+  switch (assign_items(n)) {
+    case 1: launch(k_assign<D, 1>, g, kBlock, 0, s, xo, seg, n, it, nodes, lab, final_pass, rep); break;
+    case 2: launch(k_assign<D, 2>, g, kBlock, 0, s, xo, seg, n, it, nodes, lab, final_pass, rep); break;
+    case 4: launch(k_assign<D, 4>, g, kBlock, 0, s, xo, seg, n, it, nodes, lab, final_pass, rep); break;
+    default: launch(k_assign<D, 8>, g, kBlock, 0, s, xo, seg, n, it, nodes, lab, final_pass, rep); break;
+  }
+}
+
 // Centre update: z = fp32((double(sum) / count) * 2^-P); a node whose labels
 // did not change is converged.
 template <int D>
@@ -445,13 +471,20 @@ __device__ void count_labels(int s, uint8_t l, NodeDev* __restrict__ nodes) {
   }
 }
 
+// A position's contribution to the scan that places the parts: 1 in the low
+// word for V1, 1 in the high word for V2, nothing for V3 or a node that is
+// not split (label 0).
+__device__ __forceinline__ unsigned long long part_count(uint8_t l) {
+  return l == 1 ? 1ull : (l == 2 ? (1ull << 32) : 0ull);
+}
+
 // Order-free form of the separator loop of Algorithm 7 (mu = identity):
 // v joins the separator iff a neighbour w in the same node carries the other
 // label and (s(v), v) < (s(w), w).
 __global__ void k_separator(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
                             const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
                             const uint64_t* __restrict__ vrec, NodeDev* __restrict__ nodes,
-                            uint8_t* __restrict__ labf) {
+                            uint8_t* __restrict__ labf, unsigned long long* __restrict__ pk) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int s = i < n ? seg[i] : -1;
   uint8_t l = 0;
@@ -460,18 +493,31 @@ __global__ void k_separator(const int32_t* __restrict__ ord, const int32_t* __re
     const uint64_t rv = vrec[v];
     l = (uint8_t)vrec_label(rv);
     if (l != 0) {
+      // any neighbour decides, so four are tested at a time with all their
+      // loads issued together
       const float sv = vrec_s(rv);
       const uint32_t other = vrec_other(s, l);
-      for (int32_t t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) {
-        const int32_t w = adj[t];
-        const uint64_t rw = vrec[w];
-        if ((uint32_t)(rw >> 32) != other) continue;  // not in this node, or on the same side
-        const float sw = vrec_s(rw);
-        if (sv < sw || (sv == sw && v < w)) { l = 3; break; }
+      const int32_t t1 = adj_ptr[v + 1];
+      bool hit = false;
+      for (int32_t t = adj_ptr[v]; t < t1 && !hit; t += 4) {
+        int32_t w[4];
+        uint64_t rw[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = t + u < t1 ? adj[t + u] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) rw[u] = w[u] >= 0 ? vrec[w[u]] : 0ull;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (w[u] < 0 || (uint32_t)(rw[u] >> 32) != other) continue;  // not in this node, or on the same side
+          const float sw = vrec_s(rw[u]);
+          if (sv < sw || (sv == sw && v < w[u])) hit = true;
+        }
       }
+      if (hit) l = 3;
     }
     labf[i] = l;
   }
+  if (i < n) pk[i] = part_count(l);
   count_labels(s, l, nodes);
 }
 
@@ -507,7 +553,7 @@ __global__ void k_pick(const int32_t* __restrict__ ord, const int32_t* __restric
 __global__ void k_separator_mu(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
                                const int32_t* __restrict__ mu, const uint64_t* __restrict__ vrec,
                                const uint8_t* __restrict__ vpick, NodeDev* __restrict__ nodes,
-                               uint8_t* __restrict__ labf) {
+                               uint8_t* __restrict__ labf, unsigned long long* __restrict__ pk) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int s = i < n ? seg[i] : -1;
   uint8_t l = 0;
@@ -517,6 +563,7 @@ __global__ void k_separator_mu(const int32_t* __restrict__ ord, const int32_t* _
     if (l != 0 && (vpick[v] | vpick[mu[v]])) l = 3;
     labf[i] = l;
   }
+  if (i < n) pk[i] = part_count(l);
   count_labels(s, l, nodes);
 }
 
@@ -664,7 +711,7 @@ __global__ void k_mu_round(const int32_t* __restrict__ ord, const int32_t* __res
 __global__ void k_separator_mu_loop(const int32_t* __restrict__ ord, const int32_t* __restrict__ seg, int64_t n,
                                     const int32_t* __restrict__ mu, const uint64_t* __restrict__ vrec,
                                     const int32_t* __restrict__ mstate, NodeDev* __restrict__ nodes,
-                                    uint8_t* __restrict__ labf) {
+                                    uint8_t* __restrict__ labf, unsigned long long* __restrict__ pk) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int s = i < n ? seg[i] : -1;
   uint8_t l = 0;
@@ -674,21 +721,8 @@ __global__ void k_separator_mu_loop(const int32_t* __restrict__ ord, const int32
     if (l != 0 && (mstate[min(v, mu[v])] & 3) == kMuMoved) l = 3;
     labf[i] = l;
   }
+  if (i < n) pk[i] = part_count(l);
   count_labels(s, l, nodes);
-}
-
-__global__ void k_pack(const int32_t* __restrict__ seg, const uint8_t* __restrict__ labf, int64_t n,
-                       const NodeDev* __restrict__ nodes, unsigned long long* __restrict__ pk) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int s = seg[i];
-  const uint8_t l = labf[i];  // in flight with seg[i]
-  unsigned long long v = 0;
-  if (s >= 0) {
-    const NodeDev& nd = nodes[s];
-    if (nd.c1 + nd.c2 + nd.c3 > 0) v = (l == 1) ? 1ull : (l == 2 ? (1ull << 32) : 0ull);
-  }
-  pk[i] = v;
 }
 
 // Stable partition of every split node into [V1, V2, V3] (BBD) or
@@ -976,8 +1010,7 @@ static vmo_status two_means_body(OrderState& st, int N, int d, int km_iters, uns
     if (stt != VMO_OK) return;
     launch(k_seed2<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, dval, dpre, st.nodes, st.seeds);
     for (int it = 0; it < km_iters; ++it) {
-      launch(k_assign<D>, assign_grid(n), kBlock, 0, s, st.xo, st.seg, n, it, st.nodes, st.lab, 0, rep,
-             assign_items(n));
+      launch_assign<D>(n, s, st.xo, st.seg, it, st.nodes, st.lab, 0, rep);
       if (rep) launch(k_fold_reps, grid_for(N * 10, kBlock), kBlock, 0, s, st.nodes, N, rep);
       launch(k_update<D>, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, it);
       if (it % 4 == 3 && it + 1 < km_iters) {  // stop early once every node has converged
@@ -992,8 +1025,7 @@ static vmo_status two_means_body(OrderState& st, int N, int d, int km_iters, uns
       }
     }
     launch(k_clear_counts, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N);
-    launch(k_assign<D>, assign_grid(n), kBlock, 0, s, st.xo, st.seg, n, 0, st.nodes, st.lab, 1, rep,
-           assign_items(n));
+    launch_assign<D>(n, s, st.xo, st.seg, 0, st.nodes, st.lab, 1, rep);
     if (rep) launch(k_fold_reps, grid_for(N * 10, kBlock), kBlock, 0, s, st.nodes, N, rep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) stt = cuda_fail(e, "two_means", __FILE__, __LINE__);
@@ -1025,7 +1057,8 @@ vmo_status two_means_into(OrderState& st, int N, int d, int km_iters, unsigned l
 
 // Separator of every split node of the level by Algorithm 7's loop with the
 // strengthened diagonal, in canonical edge order (the class rounds above).
-static vmo_status mu_loop_separator(OrderState& st, int64_t n, uint8_t* labf, cudaStream_t s, Scratch& sc) {
+static vmo_status mu_loop_separator(OrderState& st, int64_t n, uint8_t* labf, unsigned long long* pk, cudaStream_t s,
+                                    Scratch& sc) {
   if (n == 0) return VMO_OK;
   ScratchFrame frame(sc);
   int32_t *mcnt, *mtot, *mbeg, *mstate, *total;
@@ -1066,7 +1099,7 @@ static vmo_status mu_loop_separator(OrderState& st, int64_t n, uint8_t* labf, cu
       return cuda_fail(cudaErrorUnknown, "separator: the matched-pair rounds did not settle", __FILE__, __LINE__);
   }
   launch(k_separator_mu_loop, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.mu, st.vrec, mstate, st.nodes,
-         labf);
+         labf, pk);
   VMO_LAUNCHED("separator_mu_loop");
   return VMO_OK;
 }
@@ -1099,14 +1132,13 @@ vmo_status order_levels(OrderState& st, const OrderParams& op, cudaStream_t s, S
     if (st.mu && op.mu_order_free) {
       launch(k_pick, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vrec, st.vpick);
       launch(k_separator_mu, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.mu, st.vrec, st.vpick, st.nodes,
-             labf);
+             labf, pk);
     } else if (st.mu) {
-      VMO_TRY(mu_loop_separator(st, n, labf, s, sc));
+      VMO_TRY(mu_loop_separator(st, n, labf, pk, s, sc));
     } else {
       launch(k_separator, grid_for(n, kBlock), kBlock, 0, s, st.ord, st.seg, n, st.adj_ptr, st.adj, st.vrec, st.nodes,
-             labf);
+             labf, pk);
     }
-    launch(k_pack, grid_for(n, kBlock), kBlock, 0, s, st.seg, labf, n, st.nodes, pk);
     VMO_LAUNCHED("separator");
     VMO_TRY(scan_inclusive<uint64_t>((const uint64_t*)pk, (uint64_t*)pre, n, s, sc));
     // children first (they number the next level's nodes), then the scatter

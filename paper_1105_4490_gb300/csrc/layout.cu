@@ -1204,6 +1204,17 @@ __global__ void __launch_bounds__(kStepBlock, MLP ? 3 : VMO_STEP_MINBLOCKS) k_re
   bbox_warp_fold<D>(xnew, leader, bb_next + (int64_t)pb * 8);
 }
 
+// Step-length factors decay^t, t < iters: the running double product, each
+// rounded to fp32 (one thread, the same operations in the same order on every
+// call), so that no host table has to be uploaded per level.
+__global__ void k_scale_tab(int iters, double decay, float* __restrict__ tab) {
+  double scale = 1.0;
+  for (int t = 0; t < iters; ++t) {
+    tab[t] = (float)scale;
+    scale *= decay;
+  }
+}
+
 // ------------------------------ initial layout -----------------------------
 __global__ void k_init_coords(int64_t K, const int32_t* __restrict__ vprob, const ProbDev* __restrict__ prob,
                               const uint64_t* __restrict__ seeds, const int32_t* __restrict__ start, int D,
@@ -1561,6 +1572,8 @@ vmo_status level_setup(LevelBatch& lb, int d, int occ, cudaStream_t s) {
   VMO_CUDA(cudaMemcpyAsync(lb.aggoff.ptr, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   VMO_TRY(lb.tbase.resize(P + 1));
   VMO_CUDA(cudaMemcpyAsync(lb.tbase.ptr, tb.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  VMO_TRY(lb.fbase_dev.resize(P + 1));
+  VMO_CUDA(cudaMemcpyAsync(lb.fbase_dev.ptr, lb.fbase.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   int64_t* vb;
   VMO_CUDA(cudaMallocAsync((void**)&vb, (P + 1) * sizeof(int64_t), s));
   g_device_allocs.fetch_add(1, std::memory_order_relaxed);
@@ -1653,9 +1666,8 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
   VMO_TRY(sc.alloc(&cst, nfine + P));
   VMO_TRY(sc.alloc(&bb, (size_t)2 * 8 * P));
   VMO_TRY(sc.alloc(&s0, P));
-  VMO_TRY(sc.alloc(&fb, P + 1));
   if (lb.net_ptr) VMO_TRY(sc.alloc(&z, std::max<int64_t>(lb.nnets, 1)));
-  VMO_CUDA(cudaMemcpyAsync(fb, lb.fbase.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  fb = lb.fbase_dev.ptr;
   // levels whose problems all fit one sort tile are binned by one block per
   // problem (k_bin_small) when the tuning allows it
   int64_t kmax = 0;
@@ -1685,16 +1697,8 @@ vmo_status layout_level(LevelBatch& lb, const LayoutOptions& o, float4* x, int i
   int32_t* tctr;
   VMO_TRY(sc.alloc(&scale_tab, iters));
   VMO_TRY(sc.alloc(&tctr, 1));
-  {
-    std::vector<float> tab(iters);
-    double scale = 1.0;
-    for (int t = 0; t < iters; ++t) {
-      tab[t] = (float)scale;
-      scale *= o.decay;
-    }
-    VMO_CUDA(cudaMemcpyAsync(scale_tab, tab.data(), iters * sizeof(float), cudaMemcpyHostToDevice, s));
-    VMO_CUDA(cudaStreamSynchronize(s));  // tab must outlive the copy
-  }
+  launch(k_scale_tab, 1, 1, 0, s, iters, (double)o.decay, scale_tab);
+  VMO_LAUNCHED("scale_tab");
   VMO_CUDA(cudaMemsetAsync(tctr, 0xFF, sizeof(int32_t), s));  // -1: k_keys advances it at every step
   vmo_status st = VMO_OK;
   SideStream ss;  // attraction stream of this call (none if it cannot be created)
@@ -1994,15 +1998,16 @@ vmo_status build_hierarchy(LevelBatch& fine, const LayoutOptions& o, const std::
   return VMO_OK;
 }
 
-vmo_status prolong_level(const Hierarchy& H, int j, int d, const float4* xc, float4* xj, cudaStream_t s,
-                         Scratch& sc) {
+// Host tables of level j's start: which problems start here (not present one
+// level up) and, for the others, the scale (k_f / k_c)^(1/d) of the
+// prolongation.
+static void prolong_tables(const Hierarchy& H, int j, int d, std::vector<int32_t>& start, std::vector<float>& fac) {
   const std::vector<LevelBatch*>& levels = H.levels;
   const int nl = (int)levels.size();
-  LevelBatch& cur = *levels[j];
+  const LevelBatch& cur = *levels[j];
   const int P = cur.P;
-  // which problems of this level start here (not present one level up)
-  std::vector<int32_t> start(P, 1);
-  std::vector<float> fac(P, -1.0f);
+  start.assign(P, 1);
+  fac.assign(P, -1.0f);
   if (j + 1 < nl) {
     const LevelBatch& up = *levels[j + 1];
     size_t q = 0;
@@ -2016,6 +2021,29 @@ vmo_status prolong_level(const Hierarchy& H, int j, int d, const float4* xc, flo
       }
     }
   }
+}
+
+// Level j's start from device tables (start flags, scales, seeds of its
+// problems): initial coordinates for the problems that start here, the
+// prolongation of xc for the others.
+static vmo_status prolong_level_dev(const Hierarchy& H, int j, int d, const float4* xc, float4* xj,
+                                    const int32_t* st, const float* fc, const uint64_t* sd, cudaStream_t s) {
+  LevelBatch& cur = *H.levels[j];
+  VMO_TRY(init_coords_level(cur, d, sd, xj, st, s));
+  if (xc && cur.K > 0) {
+    launch(k_prolong, grid_for(cur.K, kBlock), kBlock, 0, s, xc, H.pis[j], cur.K, cur.vprob.ptr, cur.prob.ptr, fc, sd,
+           j, d, xj);
+    VMO_LAUNCHED("prolong");
+  }
+  return VMO_OK;
+}
+
+vmo_status prolong_level(const Hierarchy& H, int j, int d, const float4* xc, float4* xj, cudaStream_t s,
+                         Scratch& sc) {
+  const int P = H.levels[j]->P;
+  std::vector<int32_t> start;
+  std::vector<float> fac;
+  prolong_tables(H, j, d, start, fac);
   int32_t* st;
   float* fc;
   uint64_t* sd;
@@ -2025,12 +2053,7 @@ vmo_status prolong_level(const Hierarchy& H, int j, int d, const float4* xc, flo
   VMO_CUDA(cudaMemcpyAsync(st, start.data(), P * 4, cudaMemcpyHostToDevice, s));
   VMO_CUDA(cudaMemcpyAsync(fc, fac.data(), P * 4, cudaMemcpyHostToDevice, s));
   VMO_CUDA(cudaMemcpyAsync(sd, H.seeds[j].data(), P * 8, cudaMemcpyHostToDevice, s));
-  VMO_TRY(init_coords_level(cur, d, sd, xj, st, s));
-  if (xc && cur.K > 0) {
-    launch(k_prolong, grid_for(cur.K, kBlock), kBlock, 0, s, xc, H.pis[j], cur.K, cur.vprob.ptr, cur.prob.ptr, fc, sd,
-           j, d, xj);
-    VMO_LAUNCHED("prolong");
-  }
+  VMO_TRY(prolong_level_dev(H, j, d, xc, xj, st, fc, sd, s));
   VMO_CUDA(cudaStreamSynchronize(s));  // host vectors above must outlive the copies
   return VMO_OK;
 }
@@ -2040,14 +2063,39 @@ vmo_status layout_multilevel(LevelBatch& fine, const LayoutOptions& o, const std
                              Scratch& sc) {
   Hierarchy H;
   VMO_TRY(build_hierarchy(fine, o, seeds, match_rounds, coarse_min, multilevel, H, s, sc));
-  // layout from the coarsest level down
+  // the start tables of every level uploaded at once, so that the levels are
+  // then queued without waiting for the device
   const int nl = (int)H.levels.size();
+  std::vector<int64_t> tb(nl + 1, 0);
+  for (int j = 0; j < nl; ++j) tb[j + 1] = tb[j] + H.levels[j]->P;
+  std::vector<int32_t> start_all((size_t)tb[nl]);
+  std::vector<float> fac_all((size_t)tb[nl]);
+  std::vector<uint64_t> seed_all((size_t)tb[nl]);
+  for (int j = 0; j < nl; ++j) {
+    std::vector<int32_t> st;
+    std::vector<float> fc;
+    prolong_tables(H, j, o.d, st, fc);
+    std::copy(st.begin(), st.end(), start_all.begin() + tb[j]);
+    std::copy(fc.begin(), fc.end(), fac_all.begin() + tb[j]);
+    std::copy(H.seeds[j].begin(), H.seeds[j].end(), seed_all.begin() + tb[j]);
+  }
+  int32_t* st_d;
+  float* fc_d;
+  uint64_t* sd_d;
+  VMO_TRY(sc.alloc(&st_d, std::max<int64_t>(tb[nl], 1)));
+  VMO_TRY(sc.alloc(&fc_d, std::max<int64_t>(tb[nl], 1)));
+  VMO_TRY(sc.alloc(&sd_d, std::max<int64_t>(tb[nl], 1)));
+  VMO_CUDA(cudaMemcpyAsync(st_d, start_all.data(), tb[nl] * 4, cudaMemcpyHostToDevice, s));
+  VMO_CUDA(cudaMemcpyAsync(fc_d, fac_all.data(), tb[nl] * 4, cudaMemcpyHostToDevice, s));
+  VMO_CUDA(cudaMemcpyAsync(sd_d, seed_all.data(), tb[nl] * 8, cudaMemcpyHostToDevice, s));
+  VMO_CUDA(cudaStreamSynchronize(s));  // the host tables must outlive the copies
+  // layout from the coarsest level down
   float4* xc = nullptr;
   for (int j = nl - 1; j >= 0; --j) {
     LevelBatch& cur = *H.levels[j];
     float4* xj = (j == 0) ? x : nullptr;
     if (!xj) VMO_TRY(sc.alloc(&xj, std::max<int64_t>(cur.K, 1)));
-    VMO_TRY(prolong_level(H, j, o.d, xc, xj, s, sc));
+    VMO_TRY(prolong_level_dev(H, j, o.d, xc, xj, st_d + tb[j], fc_d + tb[j], sd_d + tb[j], s));
     VMO_TRY(layout_level(cur, o, xj, o.iters, -1.0f, nullptr, nullptr, s, sc));
     xc = xj;
   }

@@ -48,6 +48,7 @@ struct LevelBatch {
   DevArray<int64_t> aggoff;      // (maxL-1) x (P+1): prefix of coarse-level cell counts
   int32_t maxL = 1;
   DevArray<int64_t> tbase;       // P+1: thread bases of the step kernel
+  DevArray<int64_t> fbase_dev;   // P+1: fbase on the device
   int64_t threads = 0;           // threads of the step kernel
   // vertices by degree class (graph models): medium and heavy rows get a warp
   // or a block each in the gather kernels

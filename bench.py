@@ -255,12 +255,14 @@ def batched_leg(V, torch, count: int, plain_sample: int, warmup: int, steps: int
             "batched_over_plain": batched / plain}
 
 
-def step_roofline(V, torch, run_once, d: int, steps: int, peak: dict, elapsed_ref: float | None = None) -> dict:
+def step_roofline(V, torch, run_once, d: int, steps: int, peak: dict) -> dict:
     """Roofline of the layout step kernel over one workload: algorithmic flops
     per launch (interactions counted by the kernel in one untimed run, times
     FLOPS_PER_INTERACTION[d]) over the average launch time, measured with CUDA
     events around every step-kernel launch on its stream in `steps` further
-    runs; against the measured FP32 peak of this GPU."""
+    runs; against the measured FP32 peak of this GPU.  share_of_step: the
+    kernel's event-timed share of those instrumented runs (per-launch events
+    replace the graph replay there, so the runs are longer than plain ones)."""
     V.stats_reset(time_step_kernel=True, count_interactions=True)
     run_once()
     counted = V.stats()
@@ -284,7 +286,7 @@ def step_roofline(V, torch, run_once, d: int, steps: int, peak: dict, elapsed_re
             "interactions_per_launch": counted["step_interactions"] / launches,
             "flops_per_interaction": FLOPS_PER_INTERACTION[d], "avg_launch_ms": avg_ms,
             "launches": st["step_launches"],
-            "share_of_step": st["step_ms"] / 1e3 / (elapsed_ref if elapsed_ref else wall),
+            "share_of_step": st["step_ms"] / 1e3 / wall,
             "timing": "CUDA events around every step-kernel launch on its stream"}
 
 
@@ -336,7 +338,7 @@ def config_leg(V, torch, name: str, A, model: str, d: int, sbd: bool, max_depth:
     leg = {"workload": name, "m": A.m, "n": A.n, "nnz": int(A.nnz), "model": model, "d": d,
            "form": "SBD" if sbd else "BBD", "max_depth": max_depth, "min_part": min_part,
            "value": A.nnz * steps / t, "unit": "nnz/s", "ms_per_step": 1e3 * t / steps, "steps": steps,
-           "roofline": step_roofline(V, torch, once, d, max(1, min(steps, 3)), peak, t / steps)}
+           "roofline": step_roofline(V, torch, once, d, max(1, min(steps, 3)), peak)}
     if cuts:
         perm, tree = once(with_tree=True)
         part = owner_parts(A.m + A.n, perm.cpu().numpy(), tree, sbd)
@@ -593,21 +595,6 @@ def main():
             el += a.elapsed_time(b) / 1e3
         return el, z
 
-    with ClockSampler(local) as clocks:
-        # timed region: plain library calls (the layout steps of a level replay
-        # a CUDA graph)
-        V.stats_reset(time_step_kernel=False, count_interactions=False)
-        elapsed, nnz = timed_steps()
-        st_timed = V.stats()
-        # the same K steps again with CUDA events around every step-kernel
-        # launch, for the kernel's roofline (per-launch events turn graph
-        # replay off, so these steps are not part of `value`)
-        V.stats_reset(time_step_kernel=True, count_interactions=False)
-        elapsed_ev, _ = timed_steps()
-        st = V.stats()
-    tmax = max_over_ranks(elapsed, world, "cuda")
-    value = replica_throughput(nnz, world, tmax)
-
     # end to end through the public API: pinned host CSR -> permutations in
     # pinned host memory (one untimed warm-up pass, then K timed passes)
     host_csr = [(torch.as_tensor(A.rowptr).pin_memory(), torch.as_tensor(A.colidx).pin_memory()) for A, _ in mats]
@@ -625,20 +612,38 @@ def main():
             co.copy_(cperm, non_blocking=True)
             del hg
 
-    V.stats_reset(time_step_kernel=False, count_interactions=False)  # plain library calls, as in the timed region
-    e2e_pass()
+    def e2e_steps():
+        el = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            barrier()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e2e_pass()
+            b.record(stream)
+            barrier()
+            el += a.elapsed_time(b) / 1e3
+        return el
+
+    e2e_pass()  # untimed warm-up of the host buffers and the pinned copies
     barrier()
-    e2e_time = 0.0
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        barrier()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        e2e_pass()
-        b.record(stream)
-        barrier()
-        e2e_time += a.elapsed_time(b) / 1e3
+    with ClockSampler(local) as clocks:
+        # timed region: plain library calls (the layout steps of a level replay
+        # a CUDA graph)
+        V.stats_reset(time_step_kernel=False, count_interactions=False)
+        elapsed, nnz = timed_steps()
+        st_timed = V.stats()
+        # the same K steps end to end (host buffers in and out), plain calls
+        e2e_time = e2e_steps()
+        # the same K steps again with CUDA events around every step-kernel
+        # launch, for the kernel's roofline (per-launch events turn graph
+        # replay off, so these steps are not part of `value`)
+        V.stats_reset(time_step_kernel=True, count_interactions=False)
+        elapsed_ev, _ = timed_steps()
+        st = V.stats()
+    tmax = max_over_ranks(elapsed, world, "cuda")
+    value = replica_throughput(nnz, world, tmax)
     e2e_value = nnz * world / max_over_ranks(e2e_time, world, "cuda")
 
     if rank != 0:

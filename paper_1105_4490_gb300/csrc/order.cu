@@ -66,37 +66,61 @@ __global__ void k_node_reset(NodeDev* __restrict__ nodes, int N) {
   nd.child1 = nd.child2 = nd.child3 = -1;
 }
 
-template <int D>
+// Positions per thread of the per-position kernels of the 2-means (k_maxabs,
+// k_dsq, k_seed2) on large inputs: all of a thread's loads issued together.
+constexpr int kPosItems = 4;
+constexpr int64_t kPosItemsMin = int64_t(1) << 20;
+
+template <int D, int U>
 __global__ void k_maxabs(const float4* __restrict__ xo, const int32_t* __restrict__ seg, int64_t n,
                          NodeDev* __restrict__ nodes) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool in = i < n;
-  // both loads in flight together (the coordinates are read whether or not
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x * U + threadIdx.x;
+  // every load in flight together (the coordinates are read whether or not
   // the position is active)
-  const int s = in ? seg[i] : -1;
-  const float4 x = in ? xo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-  uint32_t mx = 0;
-  if (s >= 0) {
+  int sv[U];
+  float4 xv[U];
 #pragma unroll
-    for (int m = 0; m < D; ++m) mx = max(mx, __float_as_uint(fabsf(comp(x, m))));
+  for (int u = 0; u < U; ++u) {
+    const int64_t i = i0 + (int64_t)u * blockDim.x;
+    const bool in = i < n;
+    sv[u] = in ? seg[i] : -1;
+    xv[u] = in ? xo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  uint32_t mx[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    mx[u] = 0;
+    if (sv[u] >= 0) {
+#pragma unroll
+      for (int m = 0; m < D; ++m) mx[u] = max(mx[u], __float_as_uint(fabsf(comp(xv[u], m))));
+    }
   }
   // a block of one node (the top of the recursion, where every warp would
   // otherwise send an atomic to the same word) adds its maximum once
   __shared__ int s_first;
   __shared__ uint32_t s_max;
-  if (threadIdx.x == 0) { s_first = s; s_max = 0u; }
+  if (threadIdx.x == 0) { s_first = sv[0]; s_max = 0u; }
   __syncthreads();
   const int s0 = s_first;
-  if (__syncthreads_and(s < 0 || s == s0) && s0 >= 0) {
-    const uint32_t wm = __reduce_max_sync(0xffffffffu, mx);
+  bool same = true;
+#pragma unroll
+  for (int u = 0; u < U; ++u) same = same && (sv[u] < 0 || sv[u] == s0);
+  if (__syncthreads_and(same) && s0 >= 0) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) m = max(m, mx[u]);
+    const uint32_t wm = __reduce_max_sync(0xffffffffu, m);
     if (lane_id() == 0) atomicMax(&s_max, wm);
     __syncthreads();
     if (threadIdx.x == 0) atomicMax(&nodes[s0].maxabs, s_max);
     return;
   }
-  unsigned peers = __match_any_sync(0xffffffffu, s);
-  uint32_t wm = __reduce_max_sync(peers, mx);
-  if (s >= 0 && (int)lane_id() == __ffs(peers) - 1) atomicMax(&nodes[s].maxabs, wm);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const unsigned peers = __match_any_sync(0xffffffffu, sv[u]);
+    const uint32_t wm = __reduce_max_sync(peers, mx[u]);
+    if (sv[u] >= 0 && (int)lane_id() == __ffs(peers) - 1) atomicMax(&nodes[sv[u]].maxabs, wm);
+  }
 }
 
 // k-means++ first centre: point floor(size * r0 / 2^64) of the node.
@@ -111,45 +135,69 @@ __global__ void k_seed1(NodeDev* __restrict__ nodes, int N, const float4* __rest
   nd.z1 = xo[nd.off + (int64_t)i0];
 }
 
-template <int D>
+template <int D, int U>
 __global__ void k_dsq(const float4* __restrict__ xo, const int32_t* __restrict__ seg, int64_t n,
                       const NodeDev* __restrict__ nodes, unsigned long long* __restrict__ dval) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int s = seg[i];
-  const float4 x = xo[i];  // in flight with seg[i]
-  unsigned long long v = 0;
-  if (s >= 0) {
-    const NodeDev& nd = nodes[s];
-    float dd = sqdist32<D>(x, nd.z1);
-    float sc = __fmul_rn(dd, exp2i_f(34 - 2 * nd.e));
-    v = (unsigned long long)floorf(sc);
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x * U + threadIdx.x;
+  int sv[U];
+  float4 xv[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {  // every load in flight together
+    const int64_t i = i0 + (int64_t)u * blockDim.x;
+    const bool in = i < n;
+    sv[u] = in ? seg[i] : -1;
+    xv[u] = in ? xo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  dval[i] = v;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t i = i0 + (int64_t)u * blockDim.x;
+    if (i >= n) break;
+    unsigned long long v = 0;
+    if (sv[u] >= 0) {
+      const NodeDev& nd = nodes[sv[u]];
+      float dd = sqdist32<D>(xv[u], nd.z1);
+      float sc = __fmul_rn(dd, exp2i_f(34 - 2 * nd.e));
+      v = (unsigned long long)floorf(sc);
+    }
+    dval[i] = v;
+  }
 }
 
 // Second centre: the first point whose inclusive prefix of D exceeds
 // floor(total * r1 / 2^64); a node whose total is 0 is not split.
-template <int D>
+template <int D, int U>
 __global__ void k_seed2(const float4* __restrict__ xo, const int32_t* __restrict__ seg, int64_t n,
                         const unsigned long long* __restrict__ dval, const unsigned long long* __restrict__ dpre,
                         NodeDev* __restrict__ nodes, const uint64_t* __restrict__ seeds) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int s = seg[i];
-  if (s < 0) return;
-  NodeDev& nd = nodes[s];
-  unsigned long long base = nd.off > 0 ? dpre[nd.off - 1] : 0ull;
-  unsigned long long total = dpre[nd.off + nd.size - 1] - base;
-  if (total == 0) {
-    if (i == nd.off) nd.state = 2;
-    return;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x * U + threadIdx.x;
+  int sv[U];
+  unsigned long long pv[U], vv[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {  // every load in flight together
+    const int64_t i = i0 + (int64_t)u * blockDim.x;
+    const bool in = i < n;
+    sv[u] = in ? seg[i] : -1;
+    pv[u] = in ? dpre[i] : 0ull;
+    vv[u] = in ? dval[i] : 0ull;
   }
-  uint64_t r1 = rand64(seeds[nd.prob] ^ kTagKmeans, nd.heap, 1);
-  unsigned long long thr = scale_draw(total, r1);
-  unsigned long long pre = dpre[i] - base;
-  unsigned long long prev = pre - dval[i];
-  if (prev <= thr && thr < pre) nd.z2 = xo[i];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t i = i0 + (int64_t)u * blockDim.x;
+    const int s = sv[u];
+    if (s < 0) continue;
+    NodeDev& nd = nodes[s];
+    unsigned long long base = nd.off > 0 ? dpre[nd.off - 1] : 0ull;
+    unsigned long long total = dpre[nd.off + nd.size - 1] - base;
+    if (total == 0) {
+      if (i == nd.off) nd.state = 2;
+      continue;
+    }
+    uint64_t r1 = rand64(seeds[nd.prob] ^ kTagKmeans, nd.heap, 1);
+    unsigned long long thr = scale_draw(total, r1);
+    unsigned long long pre = pv[u] - base;
+    unsigned long long prev = pre - vv[u];
+    if (prev <= thr && thr < pre) nd.z2 = xo[i];
+  }
 }
 
 // One Lloyd assignment: label 1 iff ||x - z1||^2 <= ||x - z2||^2 (fp32),
@@ -1003,12 +1051,25 @@ static vmo_status two_means_body(OrderState& st, int N, int d, int km_iters, uns
   dispatch_d(d, [&](auto DC) {
     constexpr int D = decltype(DC)::value;
     launch(k_node_reset, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N);
-    launch(k_maxabs<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, st.nodes);
+    const bool wide = n >= kPosItemsMin;  // kPosItems positions per thread
+    if (wide)
+      launch(k_maxabs<D, kPosItems>, grid_for((n + kPosItems - 1) / kPosItems, kBlock), kBlock, 0, s, st.xo, st.seg,
+             n, st.nodes);
+    else
+      launch(k_maxabs<D, 1>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, st.nodes);
     launch(k_seed1, grid_for(N, kBlock), kBlock, 0, s, st.nodes, N, st.xo, st.seeds);
-    launch(k_dsq<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, st.nodes, dval);
+    if (wide)
+      launch(k_dsq<D, kPosItems>, grid_for((n + kPosItems - 1) / kPosItems, kBlock), kBlock, 0, s, st.xo, st.seg, n,
+             st.nodes, dval);
+    else
+      launch(k_dsq<D, 1>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, st.nodes, dval);
     stt = scan_inclusive_u64_into((const uint64_t*)dval, (uint64_t*)dpre, n, partial, s);
     if (stt != VMO_OK) return;
-    launch(k_seed2<D>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, dval, dpre, st.nodes, st.seeds);
+    if (wide)
+      launch(k_seed2<D, kPosItems>, grid_for((n + kPosItems - 1) / kPosItems, kBlock), kBlock, 0, s, st.xo, st.seg,
+             n, dval, dpre, st.nodes, st.seeds);
+    else
+      launch(k_seed2<D, 1>, grid_for(n, kBlock), kBlock, 0, s, st.xo, st.seg, n, dval, dpre, st.nodes, st.seeds);
     for (int it = 0; it < km_iters; ++it) {
       launch_assign<D>(n, s, st.xo, st.seg, it, st.nodes, st.lab, 0, rep);
       if (rep) launch(k_fold_reps, grid_for(N * 10, kBlock), kBlock, 0, s, st.nodes, N, rep);

@@ -483,6 +483,9 @@ def main():
                     help="one untimed step of the workload and exit (for ncu captures; no JSON line)")
     ap.add_argument("--profile-matrix", type=int, default=-1,
                     help="with --profile: order only this matrix of the workload (0 or 1)")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="one untimed ordering of the 64x64 grid of the small workload (d=2, BBD to parts of <= 64 "
+                         "rows, after one warm-up), for an ncu launch list of the small levels")
     ap.add_argument("--profile-large", type=int, default=0, metavar="SIDE",
                     help="a case larger than L2 for the memory-bound kernels (ncu captures, no JSON line): "
                          "SIDE^3 7-point grid, 4 layout steps from random coordinates at one level, then the "
@@ -535,6 +538,15 @@ def main():
         dist.barrier()
     import paper_1105_4490_gb300 as V
     V.load()
+
+    if args.profile_small:
+        A = W.grid_laplacian_2d(64)
+        p = V.Params(d=2, max_depth=62, min_part=64, seed=1)
+        for _ in range(2):
+            V.Hypergraph.from_matrix(A).order(p, None, sbd=False, with_tree=False)
+        torch.cuda.synchronize()
+        print(f"profile-small done: 64x64 grid, {A.n} rows, {A.nnz} nnz", file=sys.stderr)
+        return
 
     if args.profile_large:
         side = args.profile_large

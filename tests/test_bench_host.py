@@ -40,12 +40,12 @@ def test_clock_summary_without_sampler():
 
 def test_oracle_samples_are_bounded_versions_of_the_workload():
     """The CPU samples keep the two families and parameters of the medium
-    workload at sizes the oracle finishes in seconds."""
+    workload at bounded sizes (a few to some tens of seconds of oracle work)."""
     name, mats = bench.medium_workload()
     for small in (True, False):
         sname, smats = bench.cpu_sample(small)
         assert [cfg for _, cfg in smats] == [cfg for _, cfg in mats]
-        assert sum(A.nnz for A, _ in smats) < 0.02 * sum(A.nnz for A, _ in mats)
+        assert sum(A.nnz for A, _ in smats) < 0.1 * sum(A.nnz for A, _ in mats)
         assert sname != name
 
 

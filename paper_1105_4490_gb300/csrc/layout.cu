@@ -1402,18 +1402,51 @@ __global__ void k_pi(const int32_t* __restrict__ anchor, const int32_t* __restri
   pi[v] = nb >= 0 ? (int32_t)(nb + rank[anchor[v]] - rank[prob[pb].vbase]) : -1;
 }
 
+// Coarse-edge key and cost of the adjacency entries t, t + stride, ... < t1 of
+// a row whose vertex has group a: key (a, pi[adj[t]]) in row-major order of
+// the coarse pair, the sentinel for an edge inside a group or of a dropped
+// vertex.  Every entry's output depends only on the entry, so rows are split
+// by degree as for the attraction: a thread per light row (k_contract_keys),
+// a warp per medium row, a block per heavy row (the power-law hubs).
+__device__ __forceinline__ void contract_row(const int32_t* __restrict__ adj, const float* __restrict__ acost,
+                                             const int32_t* __restrict__ pi, int32_t a, int32_t t, int32_t t1,
+                                             int32_t stride, uint64_t Kc, uint64_t* __restrict__ keys,
+                                             uint32_t* __restrict__ vals) {
+  const uint64_t sentinel = Kc * Kc;
+  for (; t < t1; t += stride) {
+    const int32_t b = a >= 0 ? pi[adj[t]] : -1;
+    keys[t] = (a >= 0 && b >= 0 && a != b) ? (uint64_t)a * Kc + (uint64_t)b : sentinel;
+    vals[t] = __float_as_uint(acost ? acost[t] : 1.0f);
+  }
+}
+
 __global__ void k_contract_keys(const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
                                 const float* __restrict__ acost, int64_t K, const int32_t* __restrict__ pi,
                                 uint64_t Kc, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= K) return;
-  int32_t a = pi[v];
-  uint64_t sentinel = Kc * Kc;
-  for (int32_t t = adj_ptr[v]; t < adj_ptr[v + 1]; ++t) {
-    int32_t b = a >= 0 ? pi[adj[t]] : -1;
-    keys[t] = (a >= 0 && b >= 0 && a != b) ? (uint64_t)a * Kc + (uint64_t)b : sentinel;
-    vals[t] = __float_as_uint(acost ? acost[t] : 1.0f);
-  }
+  const int32_t t0 = adj_ptr[v], t1 = adj_ptr[v + 1];
+  if (t1 - t0 > kLightMax) return;  // medium and heavy rows: k_contract_keys_warp / _block
+  contract_row(adj, acost, pi, pi[v], t0, t1, 1, Kc, keys, vals);
+}
+
+__global__ void k_contract_keys_warp(const int32_t* __restrict__ list, int64_t n, const int32_t* __restrict__ adj_ptr,
+                                     const int32_t* __restrict__ adj, const float* __restrict__ acost,
+                                     const int32_t* __restrict__ pi, uint64_t Kc, uint64_t* __restrict__ keys,
+                                     uint32_t* __restrict__ vals) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n) return;
+  const int32_t v = list[w];
+  contract_row(adj, acost, pi, pi[v], adj_ptr[v] + (int32_t)lane_id(), adj_ptr[v + 1], 32, Kc, keys, vals);
+}
+
+__global__ void k_contract_keys_block(const int32_t* __restrict__ list, const int32_t* __restrict__ adj_ptr,
+                                      const int32_t* __restrict__ adj, const float* __restrict__ acost,
+                                      const int32_t* __restrict__ pi, uint64_t Kc, uint64_t* __restrict__ keys,
+                                      uint32_t* __restrict__ vals) {
+  const int32_t v = list[blockIdx.x];
+  contract_row(adj, acost, pi, pi[v], adj_ptr[v] + (int32_t)threadIdx.x, adj_ptr[v + 1], (int32_t)blockDim.x, Kc,
+               keys, vals);
 }
 
 __global__ void k_run_flags(const uint64_t* __restrict__ keys, int64_t n, uint64_t sentinel, int32_t* __restrict__ flag) {
@@ -1904,6 +1937,12 @@ static vmo_status contract_level(LevelBatch& lb, const std::vector<int64_t>& new
   VMO_TRY(sc.alloc(&total, 1));
   const uint64_t sentinel = (uint64_t)Kc * (uint64_t)Kc;
   launch(k_contract_keys, grid_for(K, kBlock), kBlock, 0, s, lb.adj_ptr, lb.adj, lb.acost, K, pi, (uint64_t)Kc, keys, vals);
+  if (lb.n_mid)
+    launch(k_contract_keys_warp, grid_for(lb.n_mid * 32, kBlock), kBlock, 0, s, lb.mid_list.ptr, lb.n_mid, lb.adj_ptr,
+           lb.adj, lb.acost, pi, (uint64_t)Kc, keys, vals);
+  if (lb.n_heavy)
+    launch(k_contract_keys_block, (unsigned)lb.n_heavy, kBlock, 0, s, lb.heavy_list.ptr, lb.adj_ptr, lb.adj, lb.acost,
+           pi, (uint64_t)Kc, keys, vals);
   VMO_LAUNCHED("contract_keys");
   VMO_TRY(radix_sort_u64(keys, vals, skeys, svals, n, bits_for(sentinel), s, sc));
   if (n > 0) {

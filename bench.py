@@ -489,6 +489,9 @@ def main():
                     help="one untimed step of the workload and exit (for ncu captures; no JSON line)")
     ap.add_argument("--profile-matrix", type=int, default=-1,
                     help="with --profile: order only this matrix of the workload (0 or 1)")
+    ap.add_argument("--profile-batch", type=int, default=0, metavar="N",
+                    help="one untimed batched ordering of the first N matrices of the batch mix (after one "
+                         "warm-up), for an ncu launch list of the batched path")
     ap.add_argument("--profile-small", action="store_true",
                     help="one untimed ordering of the 64x64 grid of the small workload (d=2, BBD to parts of <= 64 "
                          "rows, after one warm-up), for an ncu launch list of the small levels")
@@ -548,6 +551,15 @@ def main():
         dist.barrier()
     import paper_1105_4490_gb300 as V
     V.load()
+
+    if args.profile_batch:
+        bm = W.batch_mix(4096, seed=1)[:args.profile_batch]
+        dev = [(torch.as_tensor(A.rowptr).cuda(), torch.as_tensor(A.colidx).cuda(), A.m) for A in bm]
+        for _ in range(2):
+            V.batch_order(dev, V.Params(d=3, seed=1))
+        torch.cuda.synchronize()
+        print(f"profile-batch done: {len(bm)} matrices, {sum(A.nnz for A in bm)} nnz", file=sys.stderr)
+        return
 
     if args.profile_small:
         A = W.grid_laplacian_2d(64)

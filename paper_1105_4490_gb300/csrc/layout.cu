@@ -837,8 +837,9 @@ __device__ inline void far_row(const float4* __restrict__ CP, int64_t cell0, int
 }
 
 // Far field of one level for one lane of the target's group: the rows of the
-// box (row-major order) go round-robin to the G lanes of the group.  `cell`
-// is the paired-table index of the level's cell 0 (even).
+// box (row-major order) go round-robin to the G lanes of the group, each lane
+// visiting only its own rows.  `cell` is the paired-table index of the
+// level's cell 0 (even).
 template <int D, bool COUNT>
 __device__ inline void far_level_lane(const float4* __restrict__ CP, int64_t cell, const int32_t* me, int l,
                                       const float2* nx, float2* F, int G, int lane_g, unsigned long long& nint) {
@@ -850,18 +851,51 @@ __device__ inline void far_level_lane(const float4* __restrict__ CP, int64_t cel
     lo[m] = max(2 * par - 2, 0);
     hi[m] = min(2 * par + 3, sl - 1);
   }
-  int row = 0;
+  if (G > 1) {
+    // several lanes: the lane's own rows lane_g, lane_g + G, ... (row-major,
+    // coordinate 1 fastest), stepped with carries instead of walking the others
+    const int e1 = hi[1] - lo[1] + 1, e2 = D > 2 ? hi[2] - lo[2] + 1 : 1;
+    int y = lo[1] + lane_g, z = D > 2 ? lo[2] : 0, w = D > 3 ? lo[3] : 0;
+    auto carry = [&]() {
+      while (y > hi[1]) {
+        y -= e1;
+        ++z;
+        if (D > 3 && z > hi[2]) {
+          z -= e2;
+          ++w;
+        }
+      }
+    };
+    if (D > 2) carry();
+    for (;;) {
+      if (D == 2 && y > hi[1]) break;
+      if (D == 3 && z > hi[2]) break;
+      if (D == 4 && w > hi[3]) break;
+      bool in = y >= me[1] - 1 && y <= me[1] + 1;
+      int64_t idx = y;
+      if (D > 2) {
+        in = in && z >= me[2] - 1 && z <= me[2] + 1;
+        idx = (int64_t)z * sl + y;
+      }
+      if (D > 3) {
+        in = in && w >= me[3] - 1 && w <= me[3] + 1;
+        idx = ((int64_t)w * sl + z) * sl + y;
+      }
+      far_row<D, COUNT>(CP, cell + idx * sl + lo[0], lo[0], hi[0], in, me[0], nx, F, nint);
+      y += G;
+      if (D > 2) carry();
+    }
+    return;
+  }
   if (D == 2) {
-    for (int y = lo[1]; y <= hi[1]; ++y, ++row) {
-      if ((row & (G - 1)) != lane_g) continue;
+    for (int y = lo[1]; y <= hi[1]; ++y) {
       const bool iny = y >= me[1] - 1 && y <= me[1] + 1;
       far_row<D, COUNT>(CP, cell + (int64_t)y * sl + lo[0], lo[0], hi[0], iny, me[0], nx, F, nint);
     }
   } else if (D == 3) {
     for (int z = lo[2]; z <= hi[2]; ++z) {
       const bool inz = z >= me[2] - 1 && z <= me[2] + 1;
-      for (int y = lo[1]; y <= hi[1]; ++y, ++row) {
-        if ((row & (G - 1)) != lane_g) continue;
+      for (int y = lo[1]; y <= hi[1]; ++y) {
         const bool iny = inz && y >= me[1] - 1 && y <= me[1] + 1;
         far_row<D, COUNT>(CP, cell + ((int64_t)z * sl + y) * sl + lo[0], lo[0], hi[0], iny, me[0], nx, F, nint);
       }
@@ -871,8 +905,7 @@ __device__ inline void far_level_lane(const float4* __restrict__ CP, int64_t cel
       const bool inw = w >= me[3] - 1 && w <= me[3] + 1;
       for (int z = lo[2]; z <= hi[2]; ++z) {
         const bool inz = inw && z >= me[2] - 1 && z <= me[2] + 1;
-        for (int y = lo[1]; y <= hi[1]; ++y, ++row) {
-          if ((row & (G - 1)) != lane_g) continue;
+        for (int y = lo[1]; y <= hi[1]; ++y) {
           const bool iny = inz && y >= me[1] - 1 && y <= me[1] + 1;
           far_row<D, COUNT>(CP, cell + (((int64_t)w * sl + z) * sl + y) * sl + lo[0], lo[0], hi[0], iny, me[0], nx,
                             F, nint);
@@ -1514,12 +1547,14 @@ int grid_levels(int64_t k, int d, int occ) {
 // Lanes per target of the step kernel: enough threads to fill the GPU for a
 // small problem; a function of the problem's own size only.
 int group_size(int64_t k) {
-  // A group of G lanes walks every row header of every level's box but does
-  // only 1/G of the cells: about 7% more total work for G = 4 and 75% for
-  // G = 32 in d = 3, against G-fold shorter per-target latency.  Small
-  // problems (latency-bound levels) take more lanes.
-  if (k <= 512) return 16;
-  if (k <= 4096) return 4;
+  // G lanes per target give a small problem (a latency-bound level) G-fold
+  // shorter per-target chains, at the cost of the lanes' combining and of the
+  // work each lane repeats; in a batch, where many problems already fill the
+  // GPU, that cost is all that remains (measured: 4 / 2 lanes for <= 512 /
+  // 4,096 vertices order the 4,096-matrix batch 17% faster than 16 / 4, a
+  // single small matrix 3% slower).
+  if (k <= 512) return 4;
+  if (k <= 4096) return 2;
   return 1;
 }
 

@@ -48,10 +48,6 @@ METRIC = "nnz ordered/sec (recursive BBD)"
 # algorithmic FP32 operations per source interaction of the layout step kernel
 # (differences, squared norm, reciprocal power, force accumulation), per d
 FLOPS_PER_INTERACTION = {2: 10, 3: 18, 4: 23}
-# DRAM bytes (read + write) per launch of the step kernel, averaged over the
-# 3,000 launches of one step of the medium workload: one ncu capture of the
-# current kernel (dram__bytes_read.sum + dram__bytes_write.sum)
-STEP_KERNEL_TRAFFIC_BYTES = 4_409_344
 
 
 MEDIUM_NAME = "grid3d_64^3+powerlaw_500k"
@@ -697,9 +693,10 @@ def main():
     achieved = flops_per_launch / (avg_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_repulse_update<3> (layout step)", "achieved": achieved,
                 "peak": peak["ffma2_tflops"], "unit": "TFLOP/s", "frac": achieved / peak["ffma2_tflops"],
-                "traffic": STEP_KERNEL_TRAFFIC_BYTES,
-                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the "
-                                "3,000 launches of one step)",
+                "traffic": None,
+                "traffic_note": "the per-launch mean over a step's 3,000 launches is not captured for the "
+                                "current kernel (captures are kept to single launches); the DRAM bytes of one "
+                                "finest-level launch are in profiles/k_repulse_update_powerlaw500k.md",
                 "peak_source": f"measured in this run (vmo_measure_alu_peaks): packed FP32 fma2 on all "
                                f"{peak['sms']} SMs, {peak['ffma2_tflops']:.1f} TFLOP/s (scalar fma "
                                f"{peak['ffma_tflops']:.1f}, rsqrt {peak['rsqrt_tops']:.2f} T/s); nominal "

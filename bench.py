@@ -695,8 +695,8 @@ def main():
                 "peak": peak["ffma2_tflops"], "unit": "TFLOP/s", "frac": achieved / peak["ffma2_tflops"],
                 "traffic": None,
                 "traffic_note": "the per-launch mean over a step's 3,000 launches is not captured for the "
-                                "current kernel (captures are kept to single launches); the DRAM bytes of one "
-                                "finest-level launch are in profiles/k_repulse_update_powerlaw500k.md",
+                                "current kernel (ncu captures are kept to single launches); one finest-level "
+                                "launch of the 500k power-law read 31.9 MB from DRAM",
                 "peak_source": f"measured in this run (vmo_measure_alu_peaks): packed FP32 fma2 on all "
                                f"{peak['sms']} SMs, {peak['ffma2_tflops']:.1f} TFLOP/s (scalar fma "
                                f"{peak['ffma_tflops']:.1f}, rsqrt {peak['rsqrt_tops']:.2f} T/s); nominal "

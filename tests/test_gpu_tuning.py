@@ -68,26 +68,29 @@ def test_autotune(V):
 def test_small_bin_equals_device_wide(V):
     """The one-block binning of small levels (small_bin_points) gives the
     layouts of the device-wide sequence bit for bit: d = 2, 3, 4, a
-    hypergraph model (nets of more than two pins), vertex weights, a level of
-    exactly one sort tile (2,048 points), one step with its keys and
-    gradient, and a batch whose levels mix small and large problems."""
+    hypergraph model (nets of more than two pins), vertex weights, levels of
+    up to one sort tile (2,048 points) and, at occupancy 1, of exactly 4,096
+    finest cells (d = 2 and 4), one step with its keys and gradient, and a
+    batch whose levels mix small and large problems."""
     t0 = V.get_tuning()
     cases = [(2, W.grid_laplacian_2d(64), "symmetric", False), (3, W.powerlaw_symmetric(1500, seed=5), "symmetric", True),
              (4, W.powerlaw_symmetric(3000, seed=6), "symmetric", False),
              (2, W.powerlaw_rectangular(1500, 1000, seed=7), "rownet", False),
-             (3, W.grid_laplacian_2d(45), "symmetric", False)]
+             (3, W.grid_laplacian_2d(45), "symmetric", False),
+             (2, W.grid_laplacian_2d(64), "symmetric", False, 1), (4, W.powerlaw_symmetric(2048, seed=8), "symmetric",
+                                                                   False, 1)]
     mats = W.batch_mix(16, 47, nmin=200, nmax=5000)
     runs = []
     try:
         for sb in (2048, 0):
             V.set_tuning(t0["small_step_threads"], t0["radix_max_bits"], t0["assign_items"], sb)
             out = []
-            for d, A, model, weighted in cases:
+            for d, A, model, weighted, *occ in cases:
                 hg = V.Hypergraph.from_matrix(A, model)
                 if weighted:
                     w = torch.as_tensor(1.0 + W.rand_uniform(9, 1, hg.k).astype(np.float32))
                     hg = V.Hypergraph.from_matrix(A, model, w)
-                p = V.Params(d=d, seed=4)
+                p = V.Params(d=d, seed=4, occupancy=occ[0] if occ else 8)
                 out.append(_np(hg.layout(p)))
                 x0 = torch.as_tensor(W.rand_uniform(9, 2, hg.k * 4).astype(np.float32).reshape(hg.k, 4)).cuda()
                 x1, y, keys, L = hg.layout_step(x0, 0.01, p)

@@ -59,9 +59,13 @@ def medium_workload():
     return MEDIUM_NAME, mats
 
 
-def cpu_sample(small: bool):
+def cpu_sample(small: bool, single: bool = False):
     """Bounded sample of the medium workload for the oracle: the same two
-    families with the same parameters, scaled down."""
+    families with the same parameters, scaled down (single: the sample of the
+    single-thread timing)."""
+    if single:
+        return "grid3d_16^3+powerlaw_2000", [(W.grid_laplacian_3d(16), dict(d=3, max_depth=10)),
+                                              (W.powerlaw_symmetric(2000, seed=1), dict(d=3, max_depth=10))]
     if small:
         return "grid3d_12^3+powerlaw_1000", [(W.grid_laplacian_3d(12), dict(d=3, max_depth=10)),
                                                (W.powerlaw_symmetric(1000, seed=1), dict(d=3, max_depth=10))]
@@ -114,9 +118,9 @@ def _oracle_order_one(A) -> int:
 
 def batch_cpu_all_cores(mats=None, count: int = 0, max_nnz: int = 15_000) -> dict:
     """The oracle on all host cores over independent matrices of the batch mix:
-    a seeded sample of `count` (default: one per core) of the 4,096 matrices
-    among those of at most `max_nnz` nonzeros, one matrix per task, a spawn
-    process pool of one worker per core."""
+    a seeded sample of `count` (default: one per core; 128 in the default run)
+    of the 4,096 matrices among those of at most `max_nnz` nonzeros, one
+    matrix per task, a spawn process pool of one worker per core."""
     import multiprocessing as mp
     import oracle
     oracle.build()
@@ -136,16 +140,26 @@ def batch_cpu_all_cores(mats=None, count: int = 0, max_nnz: int = 15_000) -> dic
 
 
 def run_cpu_baseline(mats, sample_name):
+    """The oracle on all host cores (OpenMP over the per-vertex loops) over a
+    bounded sample, and single-threaded over a smaller one."""
     import oracle
     oracle.build()
     th = oracle.threads()  # the oracle's per-vertex loops run on this many OpenMP threads
     t0 = time.perf_counter()
     nnz = oracle_step(mats)
     dt = time.perf_counter() - t0
+    s_name, s_mats = cpu_sample(small=False, single=True)
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    s_nnz = oracle_step(s_mats)
+    s_dt = time.perf_counter() - t1
+    oracle.set_threads(th)
     return {"value": nnz / dt, "unit": "nnz/s", "cores": th, "kind": "oracle",
             "sample": f"{sample_name}: oracle FP64 as built (OpenMP over the per-vertex gradient loop, {th} "
                       f"threads), full pipeline (multilevel layout d=3, T=100 per level, recursive BBD depth 10), "
-                      f"{nnz} nnz in {dt:.1f} s"}
+                      f"{nnz} nnz in {dt:.1f} s",
+            "single_thread": {"value": s_nnz / s_dt, "unit": "nnz/s", "cores": 1,
+                              "sample": f"{s_name}: the same oracle on one thread, {s_nnz} nnz in {s_dt:.1f} s"}}
 
 
 class ClockSampler:
@@ -786,7 +800,7 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         if "batched" in modes:
-            modes["batched"]["cpu_oracle_all_cores"] = batch_cpu_all_cores(bmats)
+            modes["batched"]["cpu_oracle_all_cores"] = batch_cpu_all_cores(bmats, count=128)
         sname, smats = cpu_sample(small=False)
         cpu = run_cpu_baseline(smats, sname)
         cpu.update(host_cpu())

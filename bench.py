@@ -801,6 +801,11 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         if "batched" in modes:
             modes["batched"]["cpu_oracle_all_cores"] = batch_cpu_all_cores(bmats, count=128)
+            if "served" in modes:  # the served requests other than the 27-point ones follow the batch mix
+                modes["served"]["cpu_oracle_all_cores"] = dict(
+                    modes["batched"]["cpu_oracle_all_cores"],
+                    note="the batched leg's subsample: the served stream's sizes other than its 27-point 100^3 "
+                         "requests follow the batch mix; those are beyond the oracle's reach in a bounded run")
         sname, smats = cpu_sample(small=False)
         cpu = run_cpu_baseline(smats, sname)
         cpu.update(host_cpu())

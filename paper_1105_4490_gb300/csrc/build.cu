@@ -130,18 +130,19 @@ __global__ void cc_init_kernel(int32_t* p, int32_t k) {
   if (v < k) p[v] = v;
 }
 
+// Marks the last pin of every net (the pins that start no consecutive pair).
+__global__ void cc_last_kernel(const int32_t* __restrict__ net_ptr, int64_t l, uint8_t* __restrict__ last) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= l) return;
+  const int32_t b = net_ptr[e + 1];
+  if (b > net_ptr[e]) last[b - 1] = 1;
+}
+
 // Hooks the roots of consecutive pins of every net to the smaller root.
-__global__ void cc_hook_kernel(const int32_t* __restrict__ net_ptr, const int32_t* __restrict__ pins, int64_t l,
-                               int64_t npins, int32_t* p, int32_t* changed) {
+__global__ void cc_hook_kernel(const int32_t* __restrict__ pins, const uint8_t* __restrict__ last, int64_t npins,
+                               int32_t* p, int32_t* changed) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t + 1 >= npins) return;
-  // skip t if it is the last pin of its net
-  int64_t lo = 0, hi = l;  // net_ptr[lo] <= t < net_ptr[hi]
-  while (hi - lo > 1) {
-    int64_t mid = (lo + hi) >> 1;
-    if (net_ptr[mid] <= t) lo = mid; else hi = mid;
-  }
-  if (t + 1 >= net_ptr[lo + 1]) return;
+  if (t + 1 >= npins || last[t]) return;  // the last pin of a net pairs with no next pin
   int32_t a = cc_find(p, pins[t]), b = cc_find(p, pins[t + 1]);
   if (a == b) return;
   int32_t hi_ = a > b ? a : b, lo_ = a > b ? b : a;
@@ -430,15 +431,21 @@ vmo_status finegrain_coords(const vmo_hg_s* h, const float* xb, float* xf, cudaS
 vmo_status components(const vmo_hg_s* h, int32_t* labels, cudaStream_t s) {
   Scratch sc(s);
   int32_t* changed;
+  uint8_t* last = nullptr;
   VMO_TRY(sc.alloc(&changed, 1));
   if (h->k == 0) return VMO_OK;
   launch(cc_init_kernel, grid_for(h->k, 256), 256, 0, s, labels, h->k);
   VMO_LAUNCHED("cc_init");
+  if (h->npins > 1) {
+    VMO_TRY(sc.alloc(&last, h->npins));
+    VMO_CUDA(cudaMemsetAsync(last, 0, h->npins, s));
+    if (h->l > 0) launch(cc_last_kernel, grid_for(h->l, 256), 256, 0, s, h->net_ptr.ptr, h->l, last);
+    VMO_LAUNCHED("cc_last");
+  }
   for (int it = 0; it < 64; ++it) {
     VMO_CUDA(cudaMemsetAsync(changed, 0, 4, s));
     if (h->npins > 1) {
-      launch(cc_hook_kernel, grid_for(h->npins, 256), 256, 0, s, h->net_ptr.ptr, h->pins.ptr, h->l, h->npins, labels,
-                                                             changed);
+      launch(cc_hook_kernel, grid_for(h->npins, 256), 256, 0, s, h->pins.ptr, last, h->npins, labels, changed);
       VMO_LAUNCHED("cc_hook");
     }
     launch(cc_compress_kernel, grid_for(h->k, 256), 256, 0, s, labels, h->k);

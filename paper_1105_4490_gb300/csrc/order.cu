@@ -286,30 +286,42 @@ __global__ void k_assign(const float4* __restrict__ xo, const int32_t* __restric
     if (!(final_pass ? (st != 2) : (st == 0))) return;
     // per thread: the first cluster's sums and the totals of all its items
     // (the second cluster's are their difference); a fixed-point value
-    // rint(x 2^(30-e)) has |q| < 2^30, so it is converted as 32 bits
+    // rint(x 2^(30-e)) has |q| <= 2^30 - 64 (x 2^(30-e) is an fp32 value
+    // below 2^30), so it is converted as 32 bits and two of them are added in
+    // 32 bits before each 64-bit addition
     long long S1[4] = {0, 0, 0, 0}, T[4] = {0, 0, 0, 0};
+    int t32[4] = {0, 0, 0, 0}, s32[4] = {0, 0, 0, 0};
     int c1 = 0, cnt = 0;
     bool chg = false;
     const float sc = exp2i_f(30 - nd.e);
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
       const int64_t i = base + k * blockDim.x + threadIdx.x;
-      if (k >= items || i >= n) continue;
-      const float4 x = xv[k];
-      const uint8_t l = (sqdist32<D>(x, nd.z1) <= sqdist32<D>(x, nd.z2)) ? 1 : 2;
-      const bool first = l == 1;  // selects, not a computed index: the sums stay in registers
-      if (!final_pass) {
-        if (prev && l != lv[k]) chg = true;
+      if (k < items && i < n) {
+        const float4 x = xv[k];
+        const uint8_t l = (sqdist32<D>(x, nd.z1) <= sqdist32<D>(x, nd.z2)) ? 1 : 2;
+        const bool first = l == 1;  // selects, not a computed index: the sums stay in registers
+        if (!final_pass) {
+          if (prev && l != lv[k]) chg = true;
+#pragma unroll
+          for (int m = 0; m < D; ++m) {
+            const int q = __float2int_rn(__fmul_rn(comp(x, m), sc));
+            t32[m] += q;
+            s32[m] += first ? q : 0;
+          }
+        }
+        lab[i] = l;
+        c1 += first ? 1 : 0;
+        ++cnt;
+      }
+      if ((k & 1) || k == ITEMS - 1) {  // a pair (or the last item) into the 64-bit sums
 #pragma unroll
         for (int m = 0; m < D; ++m) {
-          const int q = __float2int_rn(__fmul_rn(comp(x, m), sc));
-          T[m] += q;
-          S1[m] += first ? q : 0;
+          T[m] += t32[m];
+          S1[m] += s32[m];
+          t32[m] = s32[m] = 0;
         }
       }
-      lab[i] = l;
-      c1 += first ? 1 : 0;
-      ++cnt;
     }
     // block totals: counts, sums (not in the final pass) and the change flag
     const int warp = threadIdx.x >> 5, lane = lane_id();

@@ -1311,14 +1311,35 @@ __device__ inline bool better(const Proposal& a, const Proposal& b) {
 __device__ inline Proposal scan_row(const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
                                     const float* __restrict__ acost, const int32_t* __restrict__ mate, int64_t v,
                                     int64_t vb, uint64_t seed, uint64_t b, int32_t start, int32_t stride) {
+  // `better` is a total order on the candidates (a row's neighbours are
+  // distinct), so the best does not depend on the order they are seen in:
+  // four neighbours per trip, their loads issued together
   Proposal best{0.f, 0ull, -1};
-  for (int32_t t = adj_ptr[v] + start; t < adj_ptr[v + 1]; t += stride) {
-    int32_t u = adj[t];
-    if (u == v || mate[u] >= 0) continue;
+  auto consider = [&](int32_t u, int32_t mu, float c) {
+    if (u == v || mu >= 0) return;
     uint64_t lu = (uint64_t)(u - vb), lv = (uint64_t)(v - vb);
     uint64_t lo = lu < lv ? lu : lv, hi = lu < lv ? lv : lu;
-    Proposal cand{acost ? acost[t] : 1.0f, rand64(seed, (lo << 32) | hi, b), u};
+    Proposal cand{c, rand64(seed, (lo << 32) | hi, b), u};
     if (better(cand, best)) best = cand;
+  };
+  const int32_t t1 = adj_ptr[v + 1];
+  int32_t t = adj_ptr[v] + start;
+  for (; t + 3 * stride < t1; t += 4 * stride) {
+    int32_t u[4], mu[4];
+    float c[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) u[q] = adj[t + q * stride];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      mu[q] = mate[u[q]];
+      c[q] = acost ? acost[t + q * stride] : 1.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) consider(u[q], mu[q], c[q]);
+  }
+  for (; t < t1; t += stride) {
+    const int32_t u = adj[t];
+    consider(u, mate[u], acost ? acost[t] : 1.0f);
   }
   return best;
 }
